@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Throughput of the otVMC hot path: trajectory-steps per second on GB300.
+
+A step is one trajectory step (App. C: two evaluations -- Metropolis sampling, local
+estimators, observables, S and D, regularised solve -- and the predictor-corrector update)
+of every trajectory of the batch, on synthetic quenches of the long-range transverse-field
+Ising chain (64 spins, Jastrow P = 2080, 4096 samples, 256 trajectories per GPU, decay and
+dephasing, dt = 0.005, midpoint) from the coherent state along +x.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank drives one GPU with its own 256 trajectories (global ids
+rank*256 ...): weak scaling, no collective on the data path.  Rank 0 prints one JSON line.
+--impl reference times the CPU FP64 oracle (the only reference this method has) on a
+bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "trajectory-steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chain64_jastrow")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--ntraj", type=int, default=None, help="trajectories per GPU (default: the workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def workload(args):
+    import synth
+    w = synth.WORKLOADS[args.workload]
+    ntraj = args.ntraj or w.ntraj
+    return w, ntraj
+
+
+def build_model(w):
+    import numpy as np
+    import paper_2506_23928_gb300 as pkg
+    J = pkg.lattice_couplings(w.extent, w.J, w.alpha, w.kac, w.pbc)
+    model = pkg.Model(J, w.h, np.full(w.n, w.kappa), np.full(w.n, w.gamma))
+    return model, pkg.Ansatz(model)
+
+
+def run_desc(w, ntraj, traj0, step0, n_steps, precision, seed):
+    from paper_2506_23928_gb300 import abi
+    return abi.RunDesc(ntraj=ntraj, traj0=traj0, ns=w.ns, n_steps=n_steps, step0=step0, n_sweep=w.n_sweep, dt=w.dt,
+                       scheme=abi.OTVMC_HEUN if w.scheme == "heun" else abi.OTVMC_MIDPOINT, precision=precision,
+                       reg=abi.OTVMC_REG_SHIFT, eps=w.eps, snr_thresh=4.0, seed=seed, measure_every=1,
+                       measure_final=0, use_graph=0)
+
+
+def cpu_baseline(w, steps=1):
+    """The oracle as it stands: one trajectory, `steps` trajectory steps, on the host cores."""
+    import numpy as np
+    from oracle.model import Model, couplings
+    from oracle.ansatz import Jastrow
+    from oracle import trajectories as tr
+    m = Model(J=couplings(w.extent, w.J, w.alpha, kac=w.kac, pbc=w.pbc), h=w.h, kappa=w.kappa, gamma=w.gamma)
+    t0 = time.perf_counter()
+    tr.run_mc(m, Jastrow(w.n), 1, w.ns, steps, w.dt, 1, w.scheme, n_sweep=w.n_sweep, eps=w.eps)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max((i.get("num_threads", 1) for i in threadpool_info()), default=cores)
+    except Exception:
+        pass
+    return {"value": steps / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"1 trajectory x {steps} step(s) of {w.name} (N={w.n}, P={w.n * (w.n + 1) // 2}, "
+                      f"ns={w.ns}), numpy FP64", "seconds": dt}
+
+
+def run_reference(args):
+    w, ntraj = workload(args)
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(w, 1)
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        res = cpu_baseline(w, 1)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.n, "P": w.n * (w.n + 1) // 2, "ns": w.ns, "ntraj_per_step": 1,
+                       "note": "each step is 1 trajectory-step of 1 trajectory (bounded CPU sample)"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2506_23928_gb300 import abi, build
+    from paper_2506_23928_gb300.abi import check
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    prec = abi.OTVMC_PREC_MIXED if args.precision == "mixed" else abi.OTVMC_PREC_FP64
+    w, T = workload(args)
+    model, ans = build_model(w)
+    P = ans.P
+    seed = 20260603
+    traj0 = rank * T
+    W = (w.n + 63) // 64
+    stream = torch.cuda.current_stream()
+
+    theta = torch.zeros((T, P, 2), dtype=torch.float64, device="cuda")
+    spins = torch.zeros((T, w.ns, W), dtype=torch.int64, device="cuda")
+    check(abi.otvmc_init_chains(ans.handle, T, traj0, w.ns, seed, spins, stream))
+    d1 = run_desc(w, T, traj0, 0, 1, prec, seed)
+    nb = abi.otvmc_run_workspace_bytes(ans.handle, d1)
+    nbh = abi.otvmc_run_host_workspace_bytes(ans.handle, d1)
+    work = torch.zeros(max(nb, nbh), dtype=torch.uint8, device="cuda")
+    mom = torch.zeros((1, T, 9), dtype=torch.float64, device="cuda")
+
+    def step(i):
+        d = run_desc(w, T, traj0, i, 1, prec, seed)
+        check(abi.otvmc_run_trajectories(ans.handle, d, theta, spins, mom, work, nb, stream))
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    abi.otvmc_profile_enable(1)
+    l0 = abi.otvmc_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = abi.otvmc_launch_count() - l0
+    el_ms = ev0.elapsed_time(ev1)
+    prof = abi.profile_summary()
+    abi.otvmc_profile_enable(0)
+    clk = clocks.stop() if clocks else None
+    t = torch.tensor([el_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el_ms = float(t.item())
+    total_units = T * world * args.steps
+    value = total_units / (el_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        th_h = theta.cpu().pin_memory()
+        sp_h = spins.cpu().pin_memory()
+        mo_h = torch.zeros((1, T, 9), dtype=torch.float64).pin_memory()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            d = run_desc(w, T, traj0, args.warmup + args.steps + k, 1, prec, seed)
+            check(abi.otvmc_run_trajectories_host(ans.handle, d, th_h, sp_h, mo_h, work, nbh, stream))
+        torch.cuda.synchronize()
+        e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+        h2d = th_h.numel() * 8 + sp_h.numel() * 8
+        d2h = h2d + mo_h.numel() * 8
+        e2e = {"value": total_units / float(e2e_s.item()), "unit": METRIC, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    pk, pk_kind = peaks()
+    stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
+    dominant = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
+    ns = w.ns
+    roof = {}
+    # algorithmic work per launch (one evaluation of the batch)
+    gram_flops = 2.0 * ns * P * (P + 1) / 2 * T                       # symmetric half of G = O^T O
+    solve_flops = (P ** 3 / 3.0 + 2 * 2 * 2 * P ** 2 * 2) * T         # factor + 2 RHS x (fwd+bwd) x (1 + refine)
+    if "gram" in prof:
+        ms, cnt = prof["gram"]
+        ach = gram_flops / (ms / cnt / 1000.0) / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roof["gram"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                        "traffic": None, "peak_kind": f"bf16 sustained, {pk_kind}"}
+    if "solve" in prof:
+        ms, cnt = prof["solve"]
+        ach = solve_flops / (ms / cnt / 1000.0) / 1e12
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof["solve"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None, "peak_kind": "fp32 SIMT: 152 SMs x 128 lanes x 2 x max SM clock"}
+    rl = roof.get(dominant)
+    if rl is None and roof:
+        rl = next(iter(roof.values()))
+
+    fp64 = None
+    if not args.no_fp64_path and prec == abi.OTVMC_PREC_MIXED:
+        # the plain FP64 path (FP64 O, FP64 S, FP64 Cholesky) on a reduced slice of the batch
+        Tf = 2
+        thf = torch.zeros((Tf, P, 2), dtype=torch.float64, device="cuda")
+        spf = spins[:Tf].clone()
+        df = run_desc(w, Tf, 0, 0, 1, abi.OTVMC_PREC_FP64, seed)
+        nbf = abi.otvmc_run_workspace_bytes(ans.handle, df)
+        wf = torch.zeros(nbf, dtype=torch.uint8, device="cuda")
+        mf = torch.zeros((1, Tf, 9), dtype=torch.float64, device="cuda")
+        check(abi.otvmc_run_trajectories(ans.handle, df, thf, spf, mf, wf, nbf, stream))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        df = run_desc(w, Tf, 0, 1, 1, abi.OTVMC_PREC_FP64, seed)
+        check(abi.otvmc_run_trajectories(ans.handle, df, thf, spf, mf, wf, nbf, stream))
+        torch.cuda.synchronize()
+        fp64 = {"value": Tf / (time.perf_counter() - t0), "unit": METRIC,
+                "sample": f"{Tf} trajectories x 1 step, same workload, FP64 O / S / Cholesky"}
+        del wf
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w, 1)
+        cpu.pop("seconds", None)
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "mixed: bf16 Gram (exact), fp32 Cholesky + fp64 refinement, int64/fp64 fields"
+            if prec == abi.OTVMC_PREC_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "N": w.n, "P": P, "ns": ns, "ntraj_per_gpu": T, "dt": w.dt,
+                       "scheme": w.scheme, "n_sweep": w.n_sweep, "eps": w.eps, "precision": args.precision,
+                       "parallelism": f"trajectories sharded over {world} GPU(s)",
+                       "l2": "no flush: per-step working set (O, G, L of 256 trajectories, ~14 GB) exceeds L2"},
+            "roofline": rl, "roofline_by_kernel": roof, "dominant_kernel": dominant,
+            "stage_ms_per_step": stage_ms, "cpu_baseline": cpu, "fp64_path": fp64, "clocks": clk, "e2e": e2e,
+            "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,305 @@
+/*
+ * otvmc.h -- C ABI of a GB300 (sm_103a) implementation of the data-parallel hot path of
+ * open time-dependent variational Monte Carlo over quantum trajectories (otVMC):
+ * Apostoli, D'Alberto, Genoni, Bertaina, Galli, "Unraveling Open Quantum Dynamics with
+ * Time-Dependent Variational Monte Carlo", arXiv:2506.23928.
+ *
+ * Each trajectory carries complex variational parameters theta (P entries) of a
+ * wavefunction psi_theta over N spins-1/2.  One trajectory step (App. C) runs two
+ * *evaluations*; each evaluation samples configurations from |psi_theta|^2 (Metropolis),
+ * builds the local operators O_k, the local effective energy E_eff and local noises B^n
+ * (definitions after Eq. 8, effective Hamiltonian Eq. 5), the quantum geometric tensor S
+ * and the vector D = -i F dt + sum_n N^n dW_n (otVMC procedure paragraph), and solves
+ * (S + eps I) delta = D; the predictor-corrector scheme then moves theta.  Observables are
+ * the magnetisation and spin covariance (LITF paragraph), averaged over trajectories (Eq. 3).
+ *
+ * Conventions common to every entry point
+ * ---------------------------------------
+ * - Pointers named *_d are device pointers (any allocator; 16-byte aligned); pointers
+ *   named *_h are host pointers.  The caller owns every buffer it passes.  Handles
+ *   (otvmc_model, otvmc_ansatz) own only small device copies of model constants.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Stage
+ *   entry points enqueue work on it and return without synchronising; errors found on
+ *   the device are written to the status word at the start of the workspace and are
+ *   read (and cleared) by otvmc_check.  Entry points that synchronise say so.
+ * - `work_d` / `work_bytes`: caller-provided device scratch, at least the size returned
+ *   by otvmc_workspace_bytes for the same (ansatz, ntraj, ns, precision).  Its first 256
+ *   bytes hold the status word and per-call diagnostics; the rest is carved per call.
+ *   Contents do not carry over between calls unless stated.  Calls sharing a workspace
+ *   must be ordered on one stream.
+ * - Batches: every stage call processes `ntraj` trajectories with `ns` samples each;
+ *   trajectory t of the call has global id traj0 + t (the id keys the counter-based
+ *   random streams, so results do not depend on how trajectories are batched).
+ * - Complex numbers are interleaved (re, im) doubles (double2); theta is [ntraj][P].
+ * - Spin configurations: [ntraj][ns][W] uint64 with W = ceil(N/64); bit j % 64 of word
+ *   j / 64 is set iff sigma_j = +1 (spin up, eigenvalue +1 of sigma^z_j).  Unused high
+ *   bits are zero.  Sample s of a trajectory is the state of Markov chain s.
+ * - Errors are returned as otvmc_status and never abort; otvmc_last_error() gives a
+ *   thread-local message for the last failing call.  Device code never traps.
+ *
+ * Random draws (Philox4x32-10, Salmon et al. SC'11; key = (seed mod 2^32, seed >> 32)):
+ *   Wiener increments : counter (n/4, step, traj, 2<<28); 4 normals per counter by two
+ *                       Box-Muller pairs over words (0,1) and (2,3); dW = sqrt(dt) z.
+ *   Metropolis        : counter (p/2, chain, traj, (1<<28) | (eval & 0x0FFFFFFF)); proposal
+ *                       p uses words (2(p%2), 2(p%2)+1): site = (w * N) >> 32,
+ *                       u = (w' + 0.5) 2^-32, accept iff u < |psi(x')/psi(x)|^2 (FP64).
+ *   Initial chains    : counter (q, chain, traj, 3<<28); words 2q, 2q+1 = (w0 | w1<<32),
+ *                       (w2 | w3<<32).
+ *   eval = 2*step + stage (stage 0 predictor, 1 corrector; 2*n_steps for a final pass).
+ */
+#ifndef OTVMC_H
+#define OTVMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OTVMC_API __attribute__((visibility("default")))
+#else
+#define OTVMC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum otvmc_status {
+    OTVMC_OK = 0,
+    OTVMC_ERR_INVALID = 1,     /* bad argument, size or handle */
+    OTVMC_ERR_OOM = 2,         /* a handle's small device allocation failed */
+    OTVMC_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in otvmc_last_error) */
+    OTVMC_ERR_NOT_PD = 4,      /* S + eps I not positive definite after the shift retries */
+    OTVMC_ERR_TIMEOUT = 5,     /* a bounded device wait ran out (kernel returned early) */
+    OTVMC_ERR_NONFINITE = 6,   /* NaN / Inf in a parameter update */
+    OTVMC_ERR_RANGE = 7,       /* a fixed-point field or sample count exceeded its range */
+    OTVMC_ERR_UNSUPPORTED = 8, /* combination not built (e.g. RBM with this precision) */
+    OTVMC_ERR_WORKSPACE = 9    /* work_bytes smaller than otvmc_workspace_bytes */
+} otvmc_status;
+
+enum { OTVMC_JASTROW = 0, OTVMC_RBM = 1 };
+enum { OTVMC_PREC_FP64 = 0, OTVMC_PREC_MIXED = 1 };
+enum { OTVMC_REG_SHIFT = 0, OTVMC_REG_SNR = 1 };
+enum { OTVMC_HEUN = 0, OTVMC_MIDPOINT = 1 };
+
+#define OTVMC_MAX_SITES 256
+#define OTVMC_MOMENTS 9 /* m_x m_y m_z q_xx q_yy q_zz q_xy q_xz q_yz per trajectory */
+
+typedef struct otvmc_model otvmc_model;
+typedef struct otvmc_ansatz otvmc_ansatz;
+
+/* ------------------------------------------------------------------- model (Eq. 10, LITF)
+ * H = sum_{i<j} J_ij sz_i sz_j + h sum_i sx_i with explicit signed couplings (the
+ * paper's -(J/K) sum sz sz / r^alpha - h sum sx is J_ij = -J/(K r^alpha), h -> -h).
+ * Jump operators: decay L = sqrt(kappa_i) s^-_i and dephasing L = sqrt(gamma_i) sz_i,
+ * operators with zero rate omitted; order: decays in site order, then dephasings. */
+typedef struct otvmc_model_desc {
+    int n;               /* number of spins, 1 <= n <= OTVMC_MAX_SITES */
+    const double* J_h;   /* n*n row-major, symmetric, zero diagonal */
+    double h;            /* transverse field */
+    const double* kappa_h; /* n decay rates >= 0, or NULL for none */
+    const double* gamma_h; /* n dephasing rates >= 0, or NULL for none */
+} otvmc_model_desc;
+
+/* Couplings J_ij = J / r_ij^alpha of an open (pbc = 0) or periodic (pbc = 1, nearest
+ * image) chain (dim = 1, extent[0] = N) or square lattice (dim = 2, extent = {Lx, Ly},
+ * row-major sites); kac = 1 divides by K(alpha) = sum_{i<j} r_ij^-alpha / (N - 1)
+ * (LITF paragraph).  Host only; J_out_h has N*N entries. */
+OTVMC_API otvmc_status otvmc_lattice_couplings(int dim, const int* extent, double J, double alpha,
+                                     int kac, int pbc, double* J_out_h);
+
+/* Copies the description; allocates ~N*N*8 bytes of device memory for J. */
+OTVMC_API otvmc_status otvmc_model_create(const otvmc_model_desc* desc, otvmc_model** out);
+OTVMC_API void otvmc_model_destroy(otvmc_model* model);
+/* Number of jump operators N_L (length of each trajectory's dW and <L+L^+> rows). */
+OTVMC_API int otvmc_model_nops(const otvmc_model* model);
+
+/* ---------------------------------------------------------- ansatz (Eq. 11 RBM, Eq. 12 LJ)
+ * OTVMC_JASTROW: log psi = sum a_i s_i + sum_{j<k} eta_jk s_j s_k, P = N(N+1)/2,
+ *   theta = [a_0..a_{N-1}, eta_jk for j<k row-major].  n_hidden ignored.
+ * OTVMC_RBM: log psi = sum a_i s_i + sum_m log 2cosh(b_m + sum_i W_im s_i),
+ *   P = N + M + N M, theta = [a (N), b (M), W (N x M row-major)].
+ * The ansatz keeps a pointer to the model, which must outlive it. */
+OTVMC_API otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, int n_hidden,
+                                 otvmc_ansatz** out);
+OTVMC_API void otvmc_ansatz_destroy(otvmc_ansatz* ansatz);
+OTVMC_API int64_t otvmc_ansatz_nparams(const otvmc_ansatz* ansatz);
+
+/* Bytes of work_d needed by any stage entry point below for this batch shape. */
+OTVMC_API size_t otvmc_workspace_bytes(const otvmc_ansatz* ansatz, int ntraj, int ns, int precision);
+
+/* Synchronises `stream`, returns the first device-side error recorded in work_d since
+ * the last check (OTVMC_OK if none) and clears it. */
+OTVMC_API otvmc_status otvmc_check(void* work_d, void* stream);
+
+/* ------------------------------------------------------------------ A1: Wiener increments
+ * dW_d[t][n] = sqrt(dt) z, z ~ N(0,1) from the counter (n/4, step, traj0+t, 2<<28)
+ * (Eq. 2: independent increments of variance dt, one per jump operator; App. C uses the
+ * same draw in predictor and corrector).  dW_d: [ntraj][N_L] double. */
+OTVMC_API otvmc_status otvmc_draw_noise(const otvmc_model* model, int ntraj, int traj0, uint64_t seed,
+                              int64_t step, double dt, double* dW_d, void* stream);
+
+/* I.i.d. uniform chain states (exact samples of |psi|^2 at theta = 0, the coherent state
+ * along +x).  spins_d: [ntraj][ns][W] uint64. */
+OTVMC_API otvmc_status otvmc_init_chains(const otvmc_ansatz* ansatz, int ntraj, int traj0, int ns,
+                               uint64_t seed, uint64_t* spins_d, void* stream);
+
+/* ------------------------------------------------------------------- A2: Metropolis
+ * Continues every chain for n_sweep * N single-spin-flip proposals targeting
+ * |psi_theta(x)|^2 (otVMC procedure paragraph), in place on spins_d.  The acceptance
+ * test u < exp(2 Re log r) is decided as in FP64 (FP32 fast path with a guard band, FP64
+ * near the threshold).  accepted_d (optional, may be NULL): [ntraj] uint64 counts, added to. */
+OTVMC_API otvmc_status otvmc_sample(const otvmc_ansatz* ansatz, const double* theta_d, int ntraj,
+                          int traj0, int ns, int n_sweep, uint64_t seed, int64_t eval_index,
+                          uint64_t* spins_d, uint64_t* accepted_d, void* work_d,
+                          size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------ A3 + A5: local estimators
+ * For every sample x: flip ratios r_j(x), E_H(x) = sum_{i<j} J_ij s_i s_j + h sum_j r_j,
+ * <L_n + L_n^+> (real part of the sample mean of its local estimator; per trajectory),
+ * E_eff(x) = E_H - i/2 sum_n [(L^+L)_loc - 2 <L+L^+> B^n(x) + (L^2)_loc]  (Eq. 5, the
+ * c-number terms dropped: they cancel in F and N^n), and
+ * v(x) = -i dt E_eff(x) + sum_n dW_n B^n(x), so that D = Cov(O^*, v).
+ * Outputs (any may be NULL except v_d): Eeff_d [ntraj][ns] double2, v_d [ntraj][ns]
+ * double2, lpl_d [ntraj][N_L] double.  precision selects FP64 or FP32 transcendentals
+ * (fields are exact fixed-point sums in both). */
+OTVMC_API otvmc_status otvmc_local_estimators(const otvmc_ansatz* ansatz, const double* theta_d,
+                                    const uint64_t* spins_d, int ntraj, int ns,
+                                    const double* dW_d, double dt, int precision,
+                                    double* Eeff_d, double* v_d, double* lpl_d,
+                                    void* work_d, size_t work_bytes, void* stream);
+
+/* --------------------------------------------------------------- A4 + A6: S and D
+ * S = <O^* O> - <O^*><O>, D = <O^* v> - <O^*><v> over the ns samples (definitions after
+ * Eq. 8; D = -i F dt + sum_n N^n dW_n by linearity).  Jastrow: O is real (+-1), S real
+ * symmetric.
+ *   FP64:  S_d [ntraj][P][P] double (full symmetric) from FP64 centred O.
+ *   MIXED: G_d [ntraj][P][P] float, the uncentred Gram counts sum_x O_xi O_xj for j >= i
+ *          (row-major upper triangle; lower part unspecified), from a BF16 tcgen05 GEMM
+ *          (exact: O = +-1, FP32 accumulation exact below 2^24 samples); obar_d [ntraj][P]
+ *          double column means; S = G / ns - obar obar^T exactly.  S_d, if not NULL, is
+ *          also filled (full FP64).
+ * D_d: [ntraj][P] double2.  Inputs v_d from otvmc_local_estimators. */
+OTVMC_API otvmc_status otvmc_build_S_F(const otvmc_ansatz* ansatz, const double* theta_d,
+                             const uint64_t* spins_d, const double* v_d, int ntraj, int ns,
+                             int precision, double* S_d, float* G_d, double* obar_d,
+                             double* D_d, void* work_d, size_t work_bytes, void* stream);
+
+/* ----------------------------------------------------------------- A7: regularised solve
+ * delta = (S + eps I)^{-1} D by Cholesky (diagonal shift; otVMC procedure paragraph uses
+ * an SNR filter, OTVMC_REG_SNR, which is not built in this version).  If S + eps I is
+ * not positive definite the shift is raised (x100, up to 3 times) and OTVMC_ERR_NOT_PD is
+ * recorded only if all attempts fail (delta = 0 then).
+ *   FP64:  S_d (full FP64), FP64 Cholesky.
+ *   MIXED: G_d + obar_d; FP32 Cholesky of S + eps I, then two steps of iterative
+ *          refinement with the residual D - (S + eps I) x in FP64 from the exact G.
+ * shift_used_d (optional): [ntraj] double, the shift that succeeded.
+ * delta_d: [ntraj][P] double2. */
+OTVMC_API otvmc_status otvmc_solve_step(const otvmc_ansatz* ansatz, int ntraj, int ns, int precision,
+                              int reg, double eps, double snr_thresh, const double* S_d,
+                              const float* G_d, const double* obar_d, const double* D_d,
+                              double* delta_d, double* shift_used_d, void* work_d,
+                              size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ A8: SDE combination
+ * App. C on theta (all [ntraj][P] double2):
+ *   stage 0: out = theta + c delta0 with c = 1 (Heun: X-bar) or 1/2 (midpoint:
+ *            (X + X-bar)/2), the point of the corrector evaluation;
+ *   stage 1: out = theta + (delta0 + delta1)/2 (Heun) or theta + delta1 (midpoint).
+ * Non-finite results leave theta unchanged for that trajectory and record
+ * OTVMC_ERR_NONFINITE; failed_d (optional) [ntraj] int is set to 1 for it. */
+OTVMC_API otvmc_status otvmc_sde_combine(int ntraj, int64_t P, int scheme, int stage,
+                               const double* theta_d, const double* delta0_d,
+                               const double* delta1_d, double* out_d, int* failed_d,
+                               void* work_d, size_t work_bytes, void* stream);
+
+/* --------------------------------------------------------------------- A9: observables
+ * Per-trajectory moments from the current samples (local estimators, LITF paragraph):
+ * m_a = (1/N) sum_j <s^a_j>, q_ab = (1/N^2) sum_{jk} <(s^a_j s^b_k + s^b_k s^a_j)/2>.
+ * moments_d: [ntraj][OTVMC_MOMENTS] double in the order m_x m_y m_z q_xx q_yy q_zz q_xy
+ * q_xz q_yz. */
+OTVMC_API otvmc_status otvmc_observables(const otvmc_ansatz* ansatz, const double* theta_d,
+                               const uint64_t* spins_d, int ntraj, int ns, int precision,
+                               double* moments_d, void* work_d, size_t work_bytes,
+                               void* stream);
+
+/* Host: trajectory average (Eq. 3) of per-trajectory moments [ntraj][9] -> M[3],
+ * C[3][3] = <q> - M M^T, xi2 = N lambda_min(C on the plane perpendicular to M) / |M|^2,
+ * dM[3] = standard error of M.  Any output may be NULL. */
+OTVMC_API otvmc_status otvmc_ensemble(const double* moments_h, int ntraj, int n_sites, double* M_h,
+                            double* C_h, double* xi2_h, double* dM_h);
+
+/* ------------------------------------------------------------- whole trajectories (A1-A9)
+ * Runs n_steps trajectory steps for ntraj trajectories, all on the device, launching
+ * every stage above batched over the trajectories.  theta_d [ntraj][P] and spins_d
+ * [ntraj][ns][W] are the state (in/out; start chains with otvmc_init_chains).
+ * moments_d (may be NULL when measure_every = 0): [n_meas][ntraj][9] with one row per
+ * measured step (steps i with i % measure_every == 0, from the predictor samples at
+ * theta_i) plus, if measure_final, one row at the final time.  Synchronises and returns
+ * the device status at the end.  work_bytes >= otvmc_run_workspace_bytes(...). */
+typedef struct otvmc_run_desc {
+    int ntraj;
+    int traj0;
+    int ns;
+    int n_steps;
+    int64_t step0;       /* index of the first step (resume) */
+    int n_sweep;         /* Metropolis sweeps per evaluation */
+    double dt;
+    int scheme;          /* OTVMC_HEUN or OTVMC_MIDPOINT */
+    int precision;       /* OTVMC_PREC_FP64 or OTVMC_PREC_MIXED */
+    int reg;             /* OTVMC_REG_SHIFT */
+    double eps;          /* diagonal shift */
+    double snr_thresh;
+    uint64_t seed;
+    int measure_every;   /* 0: never */
+    int measure_final;   /* 1: add a row at the final time */
+    int use_graph;       /* 1: capture one step as a CUDA graph and replay it */
+} otvmc_run_desc;
+
+OTVMC_API size_t otvmc_run_workspace_bytes(const otvmc_ansatz* ansatz, const otvmc_run_desc* desc);
+OTVMC_API int otvmc_run_n_meas(const otvmc_run_desc* desc);
+OTVMC_API otvmc_status otvmc_run_trajectories(const otvmc_ansatz* ansatz, const otvmc_run_desc* desc,
+                                    double* theta_d, uint64_t* spins_d, double* moments_d,
+                                    void* work_d, size_t work_bytes, void* stream);
+
+/* Same with host buffers (pinned or pageable): copies theta_h / spins_h in, runs, copies
+ * theta_h / spins_h / moments_h back; device copies live in work_d, which must hold
+ * otvmc_run_host_workspace_bytes(...).  Synchronises. */
+OTVMC_API size_t otvmc_run_host_workspace_bytes(const otvmc_ansatz* ansatz, const otvmc_run_desc* desc);
+OTVMC_API otvmc_status otvmc_run_trajectories_host(const otvmc_ansatz* ansatz, const otvmc_run_desc* desc,
+                                         double* theta_h, uint64_t* spins_h, double* moments_h,
+                                         void* work_d, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ kernel timing
+ * When enabled, every kernel launch of the library is bracketed by two CUDA events on
+ * its own stream; otvmc_profile_read sums the elapsed times per kernel class.  Enabling
+ * clears earlier records.  Not for use inside CUDA graph capture. */
+enum {
+    OTVMC_K_SAMPLE = 0,  /* Metropolis sweeps */
+    OTVMC_K_PREP = 1,    /* fixed-point parameter tables */
+    OTVMC_K_EST1 = 2,    /* fields, flip ratios, E_H */
+    OTVMC_K_EST2 = 3,    /* E_eff, v */
+    OTVMC_K_REDUCE = 4,  /* site means, v reductions and quantisation */
+    OTVMC_K_OBS = 5,     /* observables */
+    OTVMC_K_D = 6,       /* D = Cov(O^*, v) and column means */
+    OTVMC_K_OBUILD = 7,  /* O in BF16 / FP64 */
+    OTVMC_K_GRAM = 8,    /* tensor-core Gram G = O^T O */
+    OTVMC_K_SYRK = 9,    /* FP64 S (plain path) */
+    OTVMC_K_SOLVE = 10,  /* Cholesky solve */
+    OTVMC_K_SDE = 11,    /* predictor-corrector combination */
+    OTVMC_K_NOISE = 12,  /* Wiener increments, chain initialisation */
+    OTVMC_K_CLASSES = 13
+};
+OTVMC_API void otvmc_profile_enable(int on);
+/* Synchronises the recorded events; total milliseconds and launch count of one class. */
+OTVMC_API otvmc_status otvmc_profile_read(int kernel_class, double* total_ms, uint64_t* launches);
+
+/* Thread-local message describing the last error returned on this thread. */
+OTVMC_API const char* otvmc_last_error(void);
+
+/* Number of kernel launches this library has enqueued in this process (all threads). */
+OTVMC_API uint64_t otvmc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OTVMC_H */

@@ -97,11 +97,13 @@ def wiener_increments(seed, traj_ids, step, n_ops, dt):
     return np.sqrt(dt) * z[:, :n_ops]
 
 
-def proposal_draws(seed, traj_id, n_chains, eval_index, p, n_sites):
-    """Site index and acceptance uniform of proposal p for every chain of one trajectory."""
-    ctr = np.zeros((n_chains, 4), dtype=np.uint64)
+def proposal_draws(seed, traj_id, n_chains, eval_index, p, n_sites, chain_ids=None):
+    """Site index and acceptance uniform of proposal p for every chain of one trajectory
+    (chains 0..n_chains-1, or the given chain ids)."""
+    ids = np.arange(n_chains, dtype=np.uint64) if chain_ids is None else np.asarray(chain_ids, dtype=np.uint64)
+    ctr = np.zeros((len(ids), 4), dtype=np.uint64)
     ctr[:, 0] = np.uint64(p // 2)
-    ctr[:, 1] = np.arange(n_chains, dtype=np.uint64)
+    ctr[:, 1] = ids
     ctr[:, 2] = np.uint64(traj_id)
     ctr[:, 3] = np.uint64((TAG_SAMPLE << 28) | (int(eval_index) & 0x0FFFFFFF))
     w = philox4x32_10(ctr, seed_key(seed)).astype(np.uint64)

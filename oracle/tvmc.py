@@ -160,19 +160,20 @@ def local_v(ev, dW, dt):
 
 # -------------------------------------------------------------------------------- sampler
 
-def metropolis(ans, theta, sig, seed, traj_id, eval_index, n_sweep):
+def metropolis(ans, theta, sig, seed, traj_id, eval_index, n_sweep, chain_ids=None):
     """Single-spin-flip Metropolis on |psi_theta|^2, one chain per row of sig.
 
     n_sweep * N proposals per chain; proposal p flips the site drawn for it and is
     accepted iff u < |psi(x')/psi(x)|^2 = exp(2 Re log r_site).  Plain FP64: the log
-    ratio is recomputed from scratch for every proposal.
+    ratio is recomputed from scratch for every proposal.  Row r of sig is chain r, or chain
+    chain_ids[r] when given (its random stream is keyed by the chain id).
     """
     sig = np.array(sig, dtype=np.int8, copy=True)
     nc, n = sig.shape
     rows = np.arange(nc)
     accepted = np.zeros(nc, dtype=np.int64)
     for p in range(n_sweep * n):
-        site, u = proposal_draws(seed, traj_id, nc, eval_index, p, n)
+        site, u = proposal_draws(seed, traj_id, nc, eval_index, p, n, chain_ids)
         lr = log_flip_ratio_at(ans, theta, sig, site)
         acc = u < np.exp(2.0 * lr.real)
         sig[rows[acc], site[acc]] *= -1

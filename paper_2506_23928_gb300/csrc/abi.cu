@@ -1,0 +1,754 @@
+// C ABI of libotvmc: handles, argument checks, workspace carving, stage entry points and
+// the batched trajectory driver (otVMC procedure paragraph, App. C).
+#include <atomic>
+#include <mutex>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace otvmc {
+
+static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static std::atomic<bool> g_prof_on{false};
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_prof_pool;
+
+bool profiling() { return g_prof_on.load(std::memory_order_relaxed); }
+
+void prof_record(int cls, cudaStream_t s, bool start) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t e;
+    if (!g_prof_pool.empty()) {
+        e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return;
+    }
+    cudaEventRecord(e, s);
+    if (start) {
+        g_prof.push_back({cls, e, nullptr});
+    } else {
+        for (auto it = g_prof.rbegin(); it != g_prof.rend(); ++it)
+            if (it->cls == cls && it->b == nullptr) {
+                it->b = e;
+                return;
+            }
+        g_prof_pool.push_back(e);
+    }
+}
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+otvmc_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return OTVMC_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return OTVMC_ERR_CUDA;
+}
+
+static otvmc_status fail(otvmc_status st, const std::string& msg) {
+    set_error(msg);
+    return st;
+}
+
+#define CK(expr, what)                                              \
+    do {                                                            \
+        cudaError_t e_ = (expr);                                    \
+        if (e_ != cudaSuccess) return cuda_status(e_, what);        \
+    } while (0)
+
+size_t eval_bufs_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
+    Carver c(nullptr, (size_t)-1);
+    carve_eval_bufs(c, a, ntraj, ns);
+    return c.off;
+}
+
+EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
+    const int n = a->n;
+    const size_t nblk = est_blocks(n, ns), vblk = v_blocks(ns);
+    EvalBufs b;
+    b.Qre = c.take<long long>((size_t)T * n * n);
+    b.Qim = c.take<long long>((size_t)T * n * n);
+    b.base_re = c.take<long long>((size_t)T * n);
+    b.base_im = c.take<long long>((size_t)T * n);
+    b.r = c.take<double2>((size_t)T * ns * n);
+    b.EH = c.take<double2>((size_t)T * ns);
+    b.part_r = c.take<double2>((size_t)T * nblk * n);
+    b.part_sr = c.take<double2>((size_t)T * nblk * n);
+    b.part_s = c.take<double>((size_t)T * nblk * n);
+    b.mean_r = c.take<double2>((size_t)T * n);
+    b.mean_sr = c.take<double2>((size_t)T * n);
+    b.mean_s = c.take<double>((size_t)T * n);
+    b.part_v = c.take<double2>((size_t)T * vblk);
+    b.part_vmax = c.take<double>((size_t)T * vblk);
+    b.qv = c.take<long long>((size_t)T * ns * 2);
+    b.vinfo = c.take<double>((size_t)T * 4);
+    b.qsum = c.take<long long>((size_t)T * 2);
+    b.Epm = c.take<double2>((size_t)T * 2 * n * n);
+    b.part_obs = c.take<double>((size_t)T * nblk * 9);
+    return b;
+}
+
+static size_t obuf_bytes(const otvmc_ansatz* a, int T, int ns, int precision) {
+    const size_t el = precision == OTVMC_PREC_FP64 ? 8 : 2;
+    return (size_t)T * a->P * ns * el + 256;
+}
+
+static bool valid_ansatz(const otvmc_ansatz* a) { return a != nullptr && a->model != nullptr && a->P > 0; }
+
+static otvmc_status check_batch(const otvmc_ansatz* a, int ntraj, int ns) {
+    if (!valid_ansatz(a)) return fail(OTVMC_ERR_INVALID, "null or invalid ansatz");
+    if (ntraj < 1 || ns < 1) return fail(OTVMC_ERR_INVALID, "ntraj and ns must be >= 1");
+    if (a->kind != OTVMC_JASTROW) return fail(OTVMC_ERR_UNSUPPORTED, "only the Jastrow ansatz is built");
+    return OTVMC_OK;
+}
+
+}  // namespace otvmc
+
+using namespace otvmc;
+
+extern "C" {
+
+const char* otvmc_last_error(void) { return g_err.c_str(); }
+
+void otvmc_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_prof) {
+        if (r.a) g_prof_pool.push_back(r.a);
+        if (r.b) g_prof_pool.push_back(r.b);
+    }
+    g_prof.clear();
+    g_prof_on.store(on != 0);
+}
+
+otvmc_status otvmc_profile_read(int cls, double* total_ms, uint64_t* launches) {
+    if (cls < 0 || cls >= OTVMC_K_CLASSES) return fail(OTVMC_ERR_INVALID, "unknown kernel class");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double ms = 0.0;
+    uint64_t cnt = 0;
+    for (auto& r : g_prof) {
+        if (r.cls != cls || !r.b) continue;
+        CK(cudaEventSynchronize(r.b), "event synchronize");
+        float f = 0.f;
+        CK(cudaEventElapsedTime(&f, r.a, r.b), "event elapsed");
+        ms += f;
+        ++cnt;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = cnt;
+    return OTVMC_OK;
+}
+uint64_t otvmc_launch_count(void) { return g_launches.load(); }
+
+otvmc_status otvmc_lattice_couplings(int dim, const int* extent, double J, double alpha, int kac, int pbc,
+                                     double* J_out_h) {
+    if ((dim != 1 && dim != 2) || !extent || !J_out_h) return fail(OTVMC_ERR_INVALID, "dim must be 1 or 2");
+    const int lx = extent[0], ly = dim == 2 ? extent[1] : 1;
+    if (lx < 1 || ly < 1) return fail(OTVMC_ERR_INVALID, "bad extent");
+    const int n = lx * ly;
+    double ksum = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            if (i == j) {
+                J_out_h[i * n + j] = 0.0;
+                continue;
+            }
+            double dx = std::fabs((double)(i / ly - j / ly)), dy = std::fabs((double)(i % ly - j % ly));
+            if (dim == 1) {
+                dx = std::fabs((double)(i - j));
+                dy = 0.0;
+            }
+            if (pbc) {
+                dx = std::fmin(dx, (double)lx - dx);
+                if (dim == 2) dy = std::fmin(dy, (double)ly - dy);
+            }
+            const double r = std::sqrt(dx * dx + dy * dy);
+            J_out_h[i * n + j] = J * std::pow(r, -alpha);
+            if (i < j) ksum += std::pow(r, -alpha);
+        }
+    if (kac && n > 1) {
+        const double K = ksum / (n - 1);
+        for (int i = 0; i < n * n; ++i) J_out_h[i] /= K;
+    }
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_model_create(const otvmc_model_desc* d, otvmc_model** out) {
+    if (!d || !out || !d->J_h) return fail(OTVMC_ERR_INVALID, "null model description");
+    const int n = d->n;
+    if (n < 1 || n > OTVMC_MAX_SITES) return fail(OTVMC_ERR_INVALID, "n out of range");
+    auto* m = new otvmc_model();
+    m->n = n;
+    m->h = d->h;
+    m->J.assign(d->J_h, d->J_h + (size_t)n * n);
+    m->kappa.assign(n, 0.0);
+    m->gamma.assign(n, 0.0);
+    if (d->kappa_h) m->kappa.assign(d->kappa_h, d->kappa_h + n);
+    if (d->gamma_h) m->gamma.assign(d->gamma_h, d->gamma_h + n);
+    for (int i = 0; i < n; ++i) {
+        if (!(m->kappa[i] >= 0.0) || !(m->gamma[i] >= 0.0) || !std::isfinite(m->kappa[i]) ||
+            !std::isfinite(m->gamma[i])) {
+            delete m;
+            return fail(OTVMC_ERR_INVALID, "rates must be finite and >= 0");
+        }
+        double rowsum = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double v = m->J[(size_t)i * n + j];
+            if (!std::isfinite(v) || v != m->J[(size_t)j * n + i] || (i == j && v != 0.0)) {
+                delete m;
+                return fail(OTVMC_ERR_INVALID, "J must be finite, symmetric, zero diagonal");
+            }
+            rowsum += std::fabs(v);
+        }
+        if (!(rowsum < 8192.0)) {
+            delete m;
+            return fail(OTVMC_ERR_RANGE, "row sums of |J| must be < 8192 (fixed-point range)");
+        }
+    }
+    std::vector<int> opidx(2 * n, -1);
+    for (int i = 0; i < n; ++i)
+        if (m->kappa[i] > 0) {
+            opidx[i] = (int)m->op_kind.size();
+            m->op_kind.push_back(0);
+            m->op_site.push_back(i);
+        }
+    for (int i = 0; i < n; ++i)
+        if (m->gamma[i] > 0) {
+            opidx[n + i] = (int)m->op_kind.size();
+            m->op_kind.push_back(1);
+            m->op_site.push_back(i);
+        }
+    m->nops = (int)m->op_kind.size();
+    std::vector<long long> QJ((size_t)n * n), baseJ(n);
+    for (int i = 0; i < n; ++i) {
+        long long s = 0;
+        for (int j = 0; j < n; ++j) {
+            QJ[(size_t)i * n + j] = std::llrint(m->J[(size_t)i * n + j] * 281474976710656.0);
+            s += QJ[(size_t)i * n + j];
+        }
+        baseJ[i] = -s;
+    }
+    std::vector<double> site(4 * n);
+    for (int i = 0; i < n; ++i) {
+        site[i] = m->kappa[i];
+        site[n + i] = m->gamma[i];
+        site[2 * n + i] = std::sqrt(m->kappa[i]);
+        site[3 * n + i] = std::sqrt(m->gamma[i]);
+    }
+    bool ok = cudaMalloc(&m->J_d, sizeof(double) * n * n) == cudaSuccess &&
+              cudaMalloc(&m->QJ_d, sizeof(long long) * n * n) == cudaSuccess &&
+              cudaMalloc(&m->baseJ_d, sizeof(long long) * n) == cudaSuccess &&
+              cudaMalloc(&m->site_d, sizeof(double) * 4 * n) == cudaSuccess &&
+              cudaMalloc(&m->opidx_d, sizeof(int) * 2 * n) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->J_d, m->J.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->QJ_d, QJ.data(), sizeof(long long) * n * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->baseJ_d, baseJ.data(), sizeof(long long) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->site_d, site.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->opidx_d, opidx.data(), sizeof(int) * 2 * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        otvmc_model_destroy(m);
+        return fail(OTVMC_ERR_OOM, "device allocation for the model failed");
+    }
+    *out = m;
+    return OTVMC_OK;
+}
+
+void otvmc_model_destroy(otvmc_model* m) {
+    if (!m) return;
+    cudaFree(m->J_d);
+    cudaFree(m->QJ_d);
+    cudaFree(m->baseJ_d);
+    cudaFree(m->site_d);
+    cudaFree(m->opidx_d);
+    delete m;
+}
+
+int otvmc_model_nops(const otvmc_model* m) { return m ? m->nops : 0; }
+
+otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, int n_hidden, otvmc_ansatz** out) {
+    if (!model || !out) return fail(OTVMC_ERR_INVALID, "null model");
+    if (kind != OTVMC_JASTROW && kind != OTVMC_RBM) return fail(OTVMC_ERR_INVALID, "unknown ansatz kind");
+    if (kind == OTVMC_RBM) return fail(OTVMC_ERR_UNSUPPORTED, "the RBM ansatz is not built in this version");
+    const int n = model->n;
+    if (n > 200) return fail(OTVMC_ERR_UNSUPPORTED, "Jastrow kernels are built for n <= 200");
+    (void)n_hidden;
+    auto* a = new otvmc_ansatz();
+    a->model = model;
+    a->kind = kind;
+    a->n = n;
+    a->P = (int64_t)n * (n + 1) / 2;
+    std::vector<int> pairs;
+    for (int j = 0; j < n; ++j)
+        for (int k = j + 1; k < n; ++k) {
+            pairs.push_back(j);
+            pairs.push_back(k);
+        }
+    std::vector<int2> tiles = gram_tiles((int)a->P);
+    a->ntiles = (int)tiles.size();
+    bool ok = true;
+    if (!pairs.empty())
+        ok = cudaMalloc(&a->pairs_d, sizeof(int) * pairs.size()) == cudaSuccess &&
+             cudaMemcpy(a->pairs_d, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMalloc(&a->tiles_d, sizeof(int2) * tiles.size()) == cudaSuccess &&
+         cudaMemcpy(a->tiles_d, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        otvmc_ansatz_destroy(a);
+        return fail(OTVMC_ERR_OOM, "device allocation for the ansatz failed");
+    }
+    *out = a;
+    return OTVMC_OK;
+}
+
+void otvmc_ansatz_destroy(otvmc_ansatz* a) {
+    if (!a) return;
+    cudaFree(a->pairs_d);
+    cudaFree(a->tiles_d);
+    delete a;
+}
+
+int64_t otvmc_ansatz_nparams(const otvmc_ansatz* a) { return a ? a->P : 0; }
+
+size_t otvmc_workspace_bytes(const otvmc_ansatz* a, int ntraj, int ns, int precision) {
+    if (!valid_ansatz(a) || ntraj < 1 || ns < 1) return 0;
+    const size_t ev = eval_bufs_bytes(a, ntraj, ns);
+    const size_t build = ev + obuf_bytes(a, ntraj, ns, precision) + (size_t)ntraj * a->P * 8 + 1024;
+    const size_t solve = 256 + chol_ws_bytes(ntraj, (int)a->P, precision);
+    size_t m = ev;
+    if (build > m) m = build;
+    if (solve > m) m = solve;
+    return m + 256;
+}
+
+otvmc_status otvmc_check(void* work_d, void* stream) {
+    if (!work_d) return fail(OTVMC_ERR_INVALID, "null workspace");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(s), "stream synchronize");
+    int st[2] = {0, 0};
+    CK(cudaMemcpy(st, work_d, sizeof(st), cudaMemcpyDeviceToHost), "status read");
+    if (st[0] != 0) {
+        const int zero[2] = {0, 0};
+        CK(cudaMemcpy(work_d, zero, sizeof(zero), cudaMemcpyHostToDevice), "status clear");
+        char buf[128];
+        std::snprintf(buf, sizeof(buf), "device status %d (trajectory/detail %d)", st[0], st[1]);
+        set_error(buf);
+        return (otvmc_status)st[0];
+    }
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_draw_noise(const otvmc_model* m, int ntraj, int traj0, uint64_t seed, int64_t step, double dt,
+                              double* dW_d, void* stream) {
+    if (!m || ntraj < 1 || traj0 < 0 || !(dt > 0.0) || (m->nops > 0 && !dW_d))
+        return fail(OTVMC_ERR_INVALID, "draw_noise: bad arguments");
+    CK(launch_noise(m, ntraj, traj0, seed, step, dt, dW_d, (cudaStream_t)stream), "noise launch");
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_init_chains(const otvmc_ansatz* a, int ntraj, int traj0, int ns, uint64_t seed,
+                               uint64_t* spins_d, void* stream) {
+    if (!valid_ansatz(a) || ntraj < 1 || ns < 1 || traj0 < 0 || !spins_d)
+        return fail(OTVMC_ERR_INVALID, "init_chains: bad arguments");
+    CK(launch_init_chains(a->n, ntraj, traj0, ns, seed, spins_d, (cudaStream_t)stream), "init launch");
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_sample(const otvmc_ansatz* a, const double* theta_d, int ntraj, int traj0, int ns, int n_sweep,
+                          uint64_t seed, int64_t eval_index, uint64_t* spins_d, uint64_t* accepted_d, void* work_d,
+                          size_t work_bytes, void* stream) {
+    otvmc_status st = check_batch(a, ntraj, ns);
+    if (st) return st;
+    if (!theta_d || !spins_d || !work_d || n_sweep < 0 || traj0 < 0)
+        return fail(OTVMC_ERR_INVALID, "sample: bad arguments");
+    if (work_bytes < 256) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    CK(launch_sample_jastrow(a, (const double2*)theta_d, ntraj, traj0, ns, n_sweep, seed, eval_index, spins_d,
+                             (unsigned long long*)accepted_d, (int*)work_d, (cudaStream_t)stream),
+       "sample launch");
+    return OTVMC_OK;
+}
+
+// est1 + site means + est2 on carved buffers; lpl may be internal.
+static otvmc_status run_estimators(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int T, int ns,
+                                   const double* dW, double dt, bool fp32, const EvalBufs& b, double* lpl,
+                                   double2* Eeff, double2* v, int* status, cudaStream_t s) {
+    CK(launch_jastrow_prep(a, theta, T, b, status, s), "prep launch");
+    CK(launch_est1_jastrow(a, spins, T, ns, fp32, b, status, s), "est1 launch");
+    CK(launch_site_means(a, T, ns, b, lpl, s), "site means launch");
+    if (v) CK(launch_est2(a, spins, T, ns, dW, dt, lpl, b, Eeff, v, s), "est2 launch");
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_local_estimators(const otvmc_ansatz* a, const double* theta_d, const uint64_t* spins_d, int ntraj,
+                                    int ns, const double* dW_d, double dt, int precision, double* Eeff_d,
+                                    double* v_d, double* lpl_d, void* work_d, size_t work_bytes, void* stream) {
+    otvmc_status st = check_batch(a, ntraj, ns);
+    if (st) return st;
+    if (!theta_d || !spins_d || !v_d || !work_d || (a->model->nops > 0 && !dW_d))
+        return fail(OTVMC_ERR_INVALID, "local_estimators: bad arguments");
+    if (precision != OTVMC_PREC_FP64 && precision != OTVMC_PREC_MIXED)
+        return fail(OTVMC_ERR_INVALID, "unknown precision");
+    Carver c(work_d, work_bytes);
+    EvalBufs b = carve_eval_bufs(c, a, ntraj, ns);
+    double* lpl = lpl_d ? lpl_d : c.take<double>((size_t)ntraj * (a->model->nops + 1));
+    if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    return run_estimators(a, (const double2*)theta_d, spins_d, ntraj, ns, dW_d, dt, precision == OTVMC_PREC_MIXED, b,
+                          lpl, (double2*)Eeff_d, (double2*)v_d, (int*)work_d, (cudaStream_t)stream);
+}
+
+// D (and obar) from v; S or G by precision.
+static otvmc_status run_build(const otvmc_ansatz* a, const uint64_t* spins, const double2* v, int T, int ns,
+                              int precision, bool v_parts_ready, const EvalBufs& b, void* obuf, double* S, float* G,
+                              double* obar, double2* D, int* status, cudaStream_t s) {
+    const int P = (int)a->P;
+    if (!v_parts_ready) CK(launch_vpart(T, ns, v, b, s), "vpart launch");
+    CK(launch_vquant(T, ns, v, b, s), "vquant launch");
+    CK(launch_D_fixed_jastrow(a, spins, T, ns, b, obar, D, s), "D launch");
+    if (precision == OTVMC_PREC_FP64) {
+        double* Oc = (double*)obuf;
+        CK(launch_obuild_f64_jastrow(a, spins, T, ns, obar, Oc, s), "obuild f64 launch");
+        CK(launch_syrk_f64(T, P, ns, Oc, S, s), "syrk launch");
+        CK(launch_gemv_D_f64(T, P, ns, Oc, v, b, D, s), "gemv launch");
+    } else {
+        uint16_t* Ot = (uint16_t*)obuf;
+        CK(launch_obuild_bf16_jastrow(a, spins, T, ns, Ot, s), "obuild bf16 launch");
+        CK(launch_gram_tc(T, P, ns, Ot, a->tiles_d, a->ntiles, G, status, s), "gram launch");
+        if (S) CK(launch_expand_S(T, P, ns, G, obar, S, s), "expand launch");
+    }
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_build_S_F(const otvmc_ansatz* a, const double* theta_d, const uint64_t* spins_d,
+                             const double* v_d, int ntraj, int ns, int precision, double* S_d, float* G_d,
+                             double* obar_d, double* D_d, void* work_d, size_t work_bytes, void* stream) {
+    (void)theta_d;
+    otvmc_status st = check_batch(a, ntraj, ns);
+    if (st) return st;
+    if (!spins_d || !v_d || !D_d || !work_d) return fail(OTVMC_ERR_INVALID, "build_S_F: bad arguments");
+    if (precision == OTVMC_PREC_FP64 && !S_d) return fail(OTVMC_ERR_INVALID, "FP64 build needs S_d");
+    if (precision == OTVMC_PREC_MIXED) {
+        if (!G_d) return fail(OTVMC_ERR_INVALID, "mixed build needs G_d");
+        if (ns % 8 != 0 || ns >= (1 << 24))
+            return fail(OTVMC_ERR_INVALID, "mixed build needs ns % 8 == 0 and ns < 2^24");
+    } else if (precision != OTVMC_PREC_FP64) {
+        return fail(OTVMC_ERR_INVALID, "unknown precision");
+    }
+    Carver c(work_d, work_bytes);
+    EvalBufs b = carve_eval_bufs(c, a, ntraj, ns);
+    void* obuf = c.take<char>(obuf_bytes(a, ntraj, ns, precision));
+    double* obar = obar_d ? obar_d : c.take<double>((size_t)ntraj * a->P);
+    if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    return run_build(a, spins_d, (const double2*)v_d, ntraj, ns, precision, false, b, obuf, S_d, G_d, obar,
+                     (double2*)D_d, (int*)work_d, (cudaStream_t)stream);
+}
+
+otvmc_status otvmc_solve_step(const otvmc_ansatz* a, int ntraj, int ns, int precision, int reg, double eps,
+                              double snr_thresh, const double* S_d, const float* G_d, const double* obar_d,
+                              const double* D_d, double* delta_d, double* shift_used_d, void* work_d,
+                              size_t work_bytes, void* stream) {
+    (void)snr_thresh;
+    otvmc_status st = check_batch(a, ntraj, ns);
+    if (st) return st;
+    if (reg != OTVMC_REG_SHIFT) return fail(OTVMC_ERR_UNSUPPORTED, "only the diagonal-shift regulariser is built");
+    if (!D_d || !delta_d || !work_d || !(eps >= 0.0)) return fail(OTVMC_ERR_INVALID, "solve_step: bad arguments");
+    if (precision == OTVMC_PREC_FP64 && !S_d) return fail(OTVMC_ERR_INVALID, "FP64 solve needs S_d");
+    if (precision == OTVMC_PREC_MIXED && (!G_d || !obar_d))
+        return fail(OTVMC_ERR_INVALID, "mixed solve needs G_d and obar_d");
+    if (work_bytes < 256 + chol_ws_bytes(ntraj, (int)a->P, precision))
+        return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    CK(launch_chol_solve(ntraj, (int)a->P, ns, precision, eps, S_d, G_d, obar_d, (const double2*)D_d,
+                         (double2*)delta_d, shift_used_d, (char*)work_d + 256, 1, (int*)work_d, (cudaStream_t)stream),
+       "solve launch");
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_sde_combine(int ntraj, int64_t P, int scheme, int stage, const double* theta_d,
+                               const double* delta0_d, const double* delta1_d, double* out_d, int* failed_d,
+                               void* work_d, size_t work_bytes, void* stream) {
+    if (ntraj < 1 || P < 1 || !theta_d || !delta0_d || !out_d || !work_d || work_bytes < 256 ||
+        (scheme != OTVMC_HEUN && scheme != OTVMC_MIDPOINT) || (stage != 0 && stage != 1) ||
+        (stage == 1 && scheme == OTVMC_HEUN && !delta1_d) || (stage == 1 && scheme == OTVMC_MIDPOINT && !delta1_d))
+        return fail(OTVMC_ERR_INVALID, "sde_combine: bad arguments");
+    CK(launch_sde(ntraj, P, scheme, stage, (const double2*)theta_d, (const double2*)delta0_d,
+                  (const double2*)delta1_d, (double2*)out_d, failed_d, (int*)work_d, (cudaStream_t)stream),
+       "sde launch");
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_observables(const otvmc_ansatz* a, const double* theta_d, const uint64_t* spins_d, int ntraj,
+                               int ns, int precision, double* moments_d, void* work_d, size_t work_bytes,
+                               void* stream) {
+    otvmc_status st = check_batch(a, ntraj, ns);
+    if (st) return st;
+    if (!theta_d || !spins_d || !moments_d || !work_d) return fail(OTVMC_ERR_INVALID, "observables: bad arguments");
+    Carver c(work_d, work_bytes);
+    EvalBufs b = carve_eval_bufs(c, a, ntraj, ns);
+    double* lpl = c.take<double>((size_t)ntraj * (a->model->nops + 1));
+    if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool fp32 = precision == OTVMC_PREC_MIXED;
+    st = run_estimators(a, (const double2*)theta_d, spins_d, ntraj, ns, nullptr, 0.0, fp32, b, lpl, nullptr, nullptr,
+                        (int*)work_d, s);
+    if (st) return st;
+    CK(launch_obs_prep(a, (const double2*)theta_d, ntraj, fp32, b, s), "obs prep launch");
+    CK(launch_observables(a, spins_d, ntraj, ns, fp32, b, moments_d, s), "observables launch");
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_ensemble(const double* mom, int ntraj, int n_sites, double* M_h, double* C_h, double* xi2_h,
+                            double* dM_h) {
+    if (!mom || ntraj < 1 || n_sites < 1) return fail(OTVMC_ERR_INVALID, "ensemble: bad arguments");
+    double M[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < ntraj; ++t) {
+        for (int a = 0; a < 3; ++a) M[a] += mom[t * 9 + a];
+        for (int a = 0; a < 6; ++a) Q[a] += mom[t * 9 + 3 + a];
+    }
+    for (int a = 0; a < 3; ++a) M[a] /= ntraj;
+    for (int a = 0; a < 6; ++a) Q[a] /= ntraj;
+    // q order: xx yy zz xy xz yz
+    double C[3][3];
+    C[0][0] = Q[0] - M[0] * M[0];
+    C[1][1] = Q[1] - M[1] * M[1];
+    C[2][2] = Q[2] - M[2] * M[2];
+    C[0][1] = C[1][0] = Q[3] - M[0] * M[1];
+    C[0][2] = C[2][0] = Q[4] - M[0] * M[2];
+    C[1][2] = C[2][1] = Q[5] - M[1] * M[2];
+    if (M_h)
+        for (int a = 0; a < 3; ++a) M_h[a] = M[a];
+    if (C_h)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) C_h[a * 3 + b] = C[a][b];
+    if (dM_h) {
+        for (int a = 0; a < 3; ++a) {
+            double s2 = 0.0;
+            for (int t = 0; t < ntraj; ++t) {
+                const double d = mom[t * 9 + a] - M[a];
+                s2 += d * d;
+            }
+            dM_h[a] = ntraj > 1 ? std::sqrt(s2 / (ntraj - 1) / ntraj) : 0.0;
+        }
+    }
+    if (xi2_h) {
+        const double nrm = std::sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
+        if (!(nrm > 0.0)) {
+            *xi2_h = NAN;
+        } else {
+            const double u[3] = {M[0] / nrm, M[1] / nrm, M[2] / nrm};
+            int amin = 0;
+            for (int a = 1; a < 3; ++a)
+                if (std::fabs(u[a]) < std::fabs(u[amin])) amin = a;
+            double e1[3] = {0, 0, 0};
+            e1[amin] = 1.0;
+            const double dot = e1[0] * u[0] + e1[1] * u[1] + e1[2] * u[2];
+            for (int a = 0; a < 3; ++a) e1[a] -= dot * u[a];
+            const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+            for (int a = 0; a < 3; ++a) e1[a] /= n1;
+            const double e2[3] = {u[1] * e1[2] - u[2] * e1[1], u[2] * e1[0] - u[0] * e1[2], u[0] * e1[1] - u[1] * e1[0]};
+            auto quad = [&](const double* x, const double* y) {
+                double s = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) s += x[a] * C[a][b] * y[b];
+                return s;
+            };
+            const double a11 = quad(e1, e1), a22 = quad(e2, e2), a12 = quad(e1, e2);
+            const double lmin = 0.5 * (a11 + a22) - std::sqrt(0.25 * (a11 - a22) * (a11 - a22) + a12 * a12);
+            *xi2_h = n_sites * lmin / (nrm * nrm);
+        }
+    }
+    return OTVMC_OK;
+}
+
+// ------------------------------------------------------------------------ trajectories
+struct RunBufs {
+    double2* theta_c;
+    double2* d0;
+    double2* d1;
+    double* dW;
+    double* lpl;
+    double2* Eeff;
+    double2* v;
+    double* obar;
+    double2* D;
+    double* S;
+    float* G;
+    void* obuf;
+    void* chol;
+    EvalBufs eb;
+};
+
+static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    const int T = d->ntraj, ns = d->ns;
+    const size_t P = (size_t)a->P;
+    RunBufs r;
+    r.eb = carve_eval_bufs(c, a, T, ns);
+    r.theta_c = c.take<double2>(T * P);
+    r.d0 = c.take<double2>(T * P);
+    r.d1 = c.take<double2>(T * P);
+    r.dW = c.take<double>((size_t)T * (a->model->nops + 1));
+    r.lpl = c.take<double>((size_t)T * (a->model->nops + 1));
+    r.Eeff = c.take<double2>((size_t)T * ns);
+    r.v = c.take<double2>((size_t)T * ns);
+    r.obar = c.take<double>(T * P);
+    r.D = c.take<double2>(T * P);
+    if (d->precision == OTVMC_PREC_FP64) {
+        r.S = c.take<double>(T * P * P);
+        r.G = nullptr;
+    } else {
+        r.S = nullptr;
+        r.G = c.take<float>(T * P * P);
+    }
+    r.obuf = c.take<char>(obuf_bytes(a, T, ns, d->precision));
+    r.chol = c.take<char>(chol_ws_bytes(T, (int)P, d->precision));
+    return r;
+}
+
+static otvmc_status check_run(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    otvmc_status st = check_batch(a, d ? d->ntraj : 0, d ? d->ns : 0);
+    if (st) return st;
+    if (d->n_steps < 0 || d->n_sweep < 0 || !(d->dt > 0.0) || d->traj0 < 0 || d->step0 < 0 ||
+        (d->scheme != OTVMC_HEUN && d->scheme != OTVMC_MIDPOINT) || d->measure_every < 0 || !(d->eps >= 0.0))
+        return fail(OTVMC_ERR_INVALID, "run: bad descriptor");
+    if (d->precision != OTVMC_PREC_FP64 && d->precision != OTVMC_PREC_MIXED)
+        return fail(OTVMC_ERR_INVALID, "unknown precision");
+    if (d->precision == OTVMC_PREC_MIXED && (d->ns % 8 != 0 || d->ns >= (1 << 24)))
+        return fail(OTVMC_ERR_INVALID, "mixed precision needs ns % 8 == 0 and ns < 2^24");
+    if (d->reg != OTVMC_REG_SHIFT) return fail(OTVMC_ERR_UNSUPPORTED, "only the diagonal-shift regulariser is built");
+    return OTVMC_OK;
+}
+
+int otvmc_run_n_meas(const otvmc_run_desc* d) {
+    if (!d) return 0;
+    int n = 0;
+    if (d->measure_every > 0)
+        for (int i = 0; i < d->n_steps; ++i)
+            if (i % d->measure_every == 0) ++n;
+    if (d->measure_final) ++n;
+    return n;
+}
+
+size_t otvmc_run_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    if (check_run(a, d)) return 0;
+    Carver c(nullptr, (size_t)-1);
+    carve_run(c, a, d);
+    return c.off + 256;
+}
+
+// One evaluation at theta (eval index ev): sample, estimators, [observables], S/D, solve.
+static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, const RunBufs& r, const double2* theta,
+                             uint64_t* spins, int64_t ev, double* moments_row, double2* delta, int* status,
+                             cudaStream_t s) {
+    const int T = d->ntraj, ns = d->ns;
+    const bool fp32 = d->precision == OTVMC_PREC_MIXED;
+    CK(launch_sample_jastrow(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, nullptr, status, s),
+       "sample launch");
+    otvmc_status st = run_estimators(a, theta, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s);
+    if (st) return st;
+    if (moments_row) {
+        CK(launch_obs_prep(a, theta, T, fp32, r.eb, s), "obs prep launch");
+        CK(launch_observables(a, spins, T, ns, fp32, r.eb, moments_row, s), "observables launch");
+    }
+    st = run_build(a, spins, r.v, T, ns, d->precision, true, r.eb, r.obuf, r.S, r.G, r.obar, r.D, status, s);
+    if (st) return st;
+    CK(launch_chol_solve(T, (int)a->P, ns, d->precision, d->eps, r.S, r.G, r.obar, r.D, delta, nullptr, r.chol, 1,
+                         status, s),
+       "solve launch");
+    return OTVMC_OK;
+}
+
+static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d, uint64_t* spins_d,
+                              double* moments_d, void* work_d, size_t work_bytes, cudaStream_t s) {
+    Carver c(work_d, work_bytes);
+    RunBufs r = carve_run(c, a, d);
+    if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    int* status = (int*)work_d;
+    const int T = d->ntraj;
+    const int64_t P = a->P;
+    double2* theta = (double2*)theta_d;
+    int row = 0;
+    for (int i = 0; i < d->n_steps; ++i) {
+        const int64_t step = d->step0 + i;
+        CK(launch_noise(a->model, T, d->traj0, d->seed, step, d->dt, r.dW, s), "noise launch");
+        double* mrow = nullptr;
+        if (d->measure_every > 0 && i % d->measure_every == 0 && moments_d)
+            mrow = moments_d + (size_t)(row++) * T * OTVMC_MOMENTS;
+        otvmc_status st = run_eval(a, d, r, theta, spins_d, 2 * step, mrow, r.d0, status, s);
+        if (st) return st;
+        CK(launch_sde(T, P, d->scheme, 0, theta, r.d0, nullptr, r.theta_c, nullptr, status, s), "sde launch");
+        st = run_eval(a, d, r, r.theta_c, spins_d, 2 * step + 1, nullptr, r.d1, status, s);
+        if (st) return st;
+        CK(launch_sde(T, P, d->scheme, 1, theta, r.d0, r.d1, theta, nullptr, status, s), "sde launch");
+    }
+    if (d->measure_final && moments_d) {
+        const int64_t ev = 2 * (d->step0 + d->n_steps);
+        CK(launch_sample_jastrow(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, nullptr, status, s),
+           "sample launch");
+        const bool fp32 = d->precision == OTVMC_PREC_MIXED;
+        otvmc_status st = run_estimators(a, theta, spins_d, T, d->ns, nullptr, 0.0, fp32, r.eb, r.lpl, nullptr,
+                                         nullptr, status, s);
+        if (st) return st;
+        CK(launch_obs_prep(a, theta, T, fp32, r.eb, s), "obs prep launch");
+        CK(launch_observables(a, spins_d, T, d->ns, fp32, r.eb, moments_d + (size_t)row * T * OTVMC_MOMENTS, s),
+           "observables launch");
+    }
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_run_trajectories(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d,
+                                    uint64_t* spins_d, double* moments_d, void* work_d, size_t work_bytes,
+                                    void* stream) {
+    otvmc_status st = check_run(a, d);
+    if (st) return st;
+    if (!theta_d || !spins_d || !work_d) return fail(OTVMC_ERR_INVALID, "run: null buffer");
+    if (otvmc_run_n_meas(d) > 0 && !moments_d) return fail(OTVMC_ERR_INVALID, "run: moments_d needed");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_steps(a, d, theta_d, spins_d, moments_d, work_d, work_bytes, s);
+    if (st) return st;
+    return otvmc_check(work_d, stream);
+}
+
+size_t otvmc_run_host_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    const size_t base = otvmc_run_workspace_bytes(a, d);
+    if (!base) return 0;
+    const size_t T = d->ntraj;
+    const size_t io = T * a->P * 16 + T * d->ns * ((a->n + 63) / 64) * 8 +
+                      (size_t)otvmc_run_n_meas(d) * T * OTVMC_MOMENTS * 8 + 3 * 256;
+    return base + io;
+}
+
+otvmc_status otvmc_run_trajectories_host(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_h,
+                                         uint64_t* spins_h, double* moments_h, void* work_d, size_t work_bytes,
+                                         void* stream) {
+    otvmc_status st = check_run(a, d);
+    if (st) return st;
+    if (!theta_h || !spins_h || !work_d) return fail(OTVMC_ERR_INVALID, "run_host: null buffer");
+    const int nmeas = otvmc_run_n_meas(d);
+    if (nmeas > 0 && !moments_h) return fail(OTVMC_ERR_INVALID, "run_host: moments_h needed");
+    const size_t base = otvmc_run_workspace_bytes(a, d);
+    if (work_bytes < otvmc_run_host_workspace_bytes(a, d)) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    const size_t T = d->ntraj;
+    const size_t th_bytes = T * a->P * 16, sp_bytes = T * d->ns * ((a->n + 63) / 64) * 8,
+                 mo_bytes = (size_t)nmeas * T * OTVMC_MOMENTS * 8;
+    char* io = (char*)work_d + ((base + 255) & ~(size_t)255);
+    double* th_d = (double*)io;
+    uint64_t* sp_d = (uint64_t*)(io + ((th_bytes + 255) & ~(size_t)255));
+    double* mo_d = (double*)((char*)sp_d + ((sp_bytes + 255) & ~(size_t)255));
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(th_d, theta_h, th_bytes, cudaMemcpyHostToDevice, s), "theta upload");
+    CK(cudaMemcpyAsync(sp_d, spins_h, sp_bytes, cudaMemcpyHostToDevice, s), "spins upload");
+    st = run_steps(a, d, th_d, sp_d, nmeas ? mo_d : nullptr, work_d, base, s);
+    if (st) return st;
+    CK(cudaMemcpyAsync(theta_h, th_d, th_bytes, cudaMemcpyDeviceToHost, s), "theta download");
+    CK(cudaMemcpyAsync(spins_h, sp_d, sp_bytes, cudaMemcpyDeviceToHost, s), "spins download");
+    if (nmeas) CK(cudaMemcpyAsync(moments_h, mo_d, mo_bytes, cudaMemcpyDeviceToHost, s), "moments download");
+    return otvmc_check(work_d, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// Host-side internals of libotvmc: handle layouts and kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/otvmc.h"
+
+struct otvmc_model {
+    int n = 0;
+    int nops = 0;
+    double h = 0.0;
+    std::vector<double> J, kappa, gamma;
+    std::vector<int> op_kind, op_site;  // per jump operator: 0 decay, 1 dephasing
+    // device copies
+    double* J_d = nullptr;         // [n][n]
+    long long* QJ_d = nullptr;     // [n][n] J in fixed point (2^-48 units)
+    long long* baseJ_d = nullptr;  // [n] -sum_k QJ[j][k]
+    double* site_d = nullptr;      // [4][n]: kappa, gamma, sqrt(kappa), sqrt(gamma)
+    int* opidx_d = nullptr;        // [2][n]: decay / dephasing operator index, -1 if none
+};
+
+struct otvmc_ansatz {
+    const otvmc_model* model = nullptr;
+    int kind = 0;
+    int n = 0;
+    int m = 0;
+    int64_t P = 0;
+    int* pairs_d = nullptr;  // Jastrow: [P - n][2] sites (j, k), j < k
+    int2* tiles_d = nullptr; // upper-triangle tiles of the tensor-core Gram kernel
+    int ntiles = 0;
+};
+
+namespace otvmc {
+
+void set_error(const std::string& msg);
+otvmc_status cuda_status(cudaError_t e, const char* what);
+void count_launch(int n = 1);
+
+// Kernel timing (otvmc_profile_enable): records a CUDA event pair around a launch.
+bool profiling();
+void prof_record(int cls, cudaStream_t s, bool start);
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    bool on;
+    ProfScope(int c, cudaStream_t st) : cls(c), s(st), on(profiling()) {
+        if (on) prof_record(cls, s, true);
+    }
+    ~ProfScope() {
+        if (on) prof_record(cls, s, false);
+    }
+};
+
+// Workspace carving: 256-byte aligned regions after the 256-byte status area.
+struct Carver {
+    char* base;
+    size_t off;
+    size_t cap;
+    explicit Carver(void* b, size_t c) : base((char*)b), off(256), cap(c) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+    bool ok() const { return off <= cap; }
+};
+
+constexpr int EST_SAMPLES_PER_THREAD = 8;
+inline int est_threads_per_sample(int n) { return ((n + 31) / 32) * 32; }
+inline int est_samples_per_block(int n) { return (256 / est_threads_per_sample(n)) * EST_SAMPLES_PER_THREAD; }
+inline int est_blocks(int n, int ns) { int sb = est_samples_per_block(n); return (ns + sb - 1) / sb; }
+constexpr int VRED_BLOCK = 256;  // samples per block of the v reduction
+inline int v_blocks(int ns) { return (ns + VRED_BLOCK - 1) / VRED_BLOCK; }
+
+// Per-trajectory scratch of one evaluation (all device pointers).
+struct EvalBufs {
+    long long* Qre;      // [T][n][n]
+    long long* Qim;      // [T][n][n]
+    long long* base_re;  // [T][n]
+    long long* base_im;  // [T][n]
+    double2* r;          // [T][ns][n] flip ratios
+    double2* EH;         // [T][ns]
+    double2* part_r;     // [T][nblk][n]
+    double2* part_sr;    // [T][nblk][n]
+    double* part_s;      // [T][nblk][n]
+    double2* mean_r;     // [T][n]
+    double2* mean_sr;    // [T][n]
+    double* mean_s;      // [T][n]
+    double2* part_v;     // [T][vblk]
+    double* part_vmax;   // [T][vblk]
+    long long* qv;       // [T][ns][2] quantised centred v
+    double* vinfo;       // [T][4]: mean re, mean im, 2^-e, qsum re/im as doubles? (see k_estim)
+    long long* qsum;     // [T][2]
+    double2* Epm;        // [T][2][n][n] exp(+-4 eta) for observables
+    double* part_obs;    // [T][nblk][9]
+};
+
+size_t eval_bufs_bytes(const otvmc_ansatz* a, int ntraj, int ns);
+EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int ntraj, int ns);
+
+// ---- launchers (return cudaGetLastError of the launch)
+cudaError_t launch_noise(const otvmc_model* m, int ntraj, int traj0, uint64_t seed, int64_t step,
+                         double dt, double* dW, cudaStream_t s);
+cudaError_t launch_init_chains(int n, int ntraj, int traj0, int ns, uint64_t seed, uint64_t* spins,
+                               cudaStream_t s);
+cudaError_t launch_sample_jastrow(const otvmc_ansatz* a, const double2* theta, int ntraj, int traj0,
+                                  int ns, int n_sweep, uint64_t seed, int64_t eval, uint64_t* spins,
+                                  unsigned long long* accepted, int* status, cudaStream_t s);
+cudaError_t launch_jastrow_prep(const otvmc_ansatz* a, const double2* theta, int ntraj, const EvalBufs& b,
+                                int* status, cudaStream_t s);
+cudaError_t launch_est1_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
+                                const EvalBufs& b, int* status, cudaStream_t s);
+cudaError_t launch_site_means(const otvmc_ansatz* a, int ntraj, int ns, const EvalBufs& b, double* lpl,
+                              cudaStream_t s);
+cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const double* dW,
+                        double dt, const double* lpl, const EvalBufs& b, double2* Eeff, double2* v,
+                        cudaStream_t s);
+cudaError_t launch_vpart(int ntraj, int ns, const double2* v, const EvalBufs& b, cudaStream_t s);
+cudaError_t launch_vquant(int ntraj, int ns, const double2* v, const EvalBufs& b, cudaStream_t s);
+cudaError_t launch_D_fixed_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
+                                   const EvalBufs& b, double* obar, double2* D, cudaStream_t s);
+cudaError_t launch_obuild_bf16_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
+                                       uint16_t* Ot, cudaStream_t s);
+cudaError_t launch_obuild_f64_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
+                                      const double* obar, double* Oc, cudaStream_t s);
+cudaError_t launch_syrk_f64(int ntraj, int P, int ns, const double* Oc, double* S, cudaStream_t s);
+cudaError_t launch_gemv_D_f64(int ntraj, int P, int ns, const double* Oc, const double2* v, const EvalBufs& b,
+                              double2* D, cudaStream_t s);
+std::vector<int2> gram_tiles(int P);
+cudaError_t launch_gram_tc(int ntraj, int P, int ns, const uint16_t* Ot, const int2* tiles, int ntiles, float* G,
+                           int* status, cudaStream_t s);
+cudaError_t launch_expand_S(int ntraj, int P, int ns, const float* G, const double* obar, double* S,
+                            cudaStream_t s);
+cudaError_t launch_chol_solve(int ntraj, int P, int ns, int precision, double eps, const double* S,
+                              const float* G, const double* obar, const double2* D, double2* delta,
+                              double* shift_used, void* ws, int refine_iters, int* status, cudaStream_t s);
+size_t chol_ws_bytes(int ntraj, int P, int precision);
+cudaError_t launch_sde(int ntraj, int64_t P, int scheme, int stage, const double2* theta, const double2* d0,
+                       const double2* d1, double2* out, int* failed, int* status, cudaStream_t s);
+cudaError_t launch_obs_prep(const otvmc_ansatz* a, const double2* theta, int ntraj, bool fp32,
+                            const EvalBufs& b, cudaStream_t s);
+cudaError_t launch_observables(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
+                               const EvalBufs& b, double* moments, cudaStream_t s);
+
+}  // namespace otvmc

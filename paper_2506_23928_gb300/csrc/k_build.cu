@@ -1,0 +1,281 @@
+// O_k, its column means, D = Cov(O^*, v) and (plain FP64 path) S by SIMT FP64, for the
+// Jastrow ansatz (definitions after Eq. 8: S = <O^* O> - <O^*><O>, F and N^n likewise;
+// D = -i F dt + sum_n N^n dW_n = Cov(O^*, v) with v = -i dt E_eff + sum_n dW_n B^n).
+// Jastrow log-derivatives are real: O_{a_j} = sigma_j, O_{eta_jk} = sigma_j sigma_k (Eq. 12).
+#include "common.cuh"
+
+namespace otvmc {
+
+// ------------------------------------------------------------------ D by exact int64 sums
+// Thread = parameter k.  With q(x) the quantised centred v, sum_x O_xk q(x) =
+// 2 sum_{x: O_xk = +1} q(x) - sum_x q(x) is exact; so is the count c_k = sum_x O_xk, whence
+// obar_k = c_k / ns and D_k = (sum_x O_xk q(x) - c_k Q / ns) 2^-e / ns (Q = sum_x q(x)).
+constexpr int DT = 256;  // samples staged per tile
+
+__global__ void __launch_bounds__(256) D_fixed_jastrow_kernel(int n, int W, int P, int ns,
+                                                              const uint64_t* __restrict__ spins,
+                                                              const int* __restrict__ pairs,
+                                                              const long long* __restrict__ qv,
+                                                              const double* __restrict__ vinfo,
+                                                              const long long* __restrict__ qsum,
+                                                              double* __restrict__ obar, double2* __restrict__ D) {
+    __shared__ uint64_t sw[DT * 4];
+    __shared__ longlong2 sq[DT];
+    const int t = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < P;
+    int j = 0, l = 0;
+    bool single = true;
+    if (valid) {
+        if (k < n) {
+            j = k;
+        } else {
+            j = pairs[2 * (k - n)];
+            l = pairs[2 * (k - n) + 1];
+            single = false;
+        }
+    }
+    const int wj = j >> 6, bj = j & 63, wl = l >> 6, bl = l & 63;
+    long long ar = 0, ai = 0;
+    int cnt = 0;
+    for (int x0 = 0; x0 < ns; x0 += DT) {
+        const int nt = min(DT, ns - x0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nt * W; i += blockDim.x) sw[i] = spins[((size_t)t * ns + x0) * W + i];
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const size_t o = ((size_t)t * ns + x0 + i) * 2;
+            sq[i] = make_longlong2(qv[o], qv[o + 1]);
+        }
+        __syncthreads();
+        if (valid) {
+            for (int x = 0; x < nt; ++x) {
+                const uint64_t bitj = (sw[x * W + wj] >> bj) & 1ull;
+                const uint64_t bitl = (sw[x * W + wl] >> bl) & 1ull;
+                const bool up = single ? (bitj != 0ull) : (bitj == bitl);
+                if (up) {
+                    const longlong2 q = sq[x];
+                    ar += q.x;
+                    ai += q.y;
+                    ++cnt;
+                }
+            }
+        }
+    }
+    if (!valid) return;
+    const long long Qr = qsum[2 * t], Qi = qsum[2 * t + 1];
+    const long long c = 2 * (long long)cnt - ns;
+    const double inv = vinfo[4 * t + 2] / ns;
+    const double dr = ((double)(2 * ar - Qr) - (double)c * (double)Qr / ns) * inv;
+    const double di = ((double)(2 * ai - Qi) - (double)c * (double)Qi / ns) * inv;
+    obar[(size_t)t * P + k] = (double)c / ns;
+    D[(size_t)t * P + k] = make_double2(dr, di);
+}
+
+cudaError_t launch_D_fixed_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
+                                   const EvalBufs& b, double* obar, double2* D, cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_D, s);
+    const int n = a->n, W = (n + 63) / 64, P = (int)a->P;
+    dim3 grid((P + 255) / 256, ntraj);
+    D_fixed_jastrow_kernel<<<grid, 256, 0, s>>>(n, W, P, ns, spins, a->pairs_d, b.qv, b.vinfo, b.qsum, obar, D);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ O in BF16 (K-major)
+// Ot[t][k][x] = O_xk as bf16 (+1 = 0x3F80, -1 = 0xBF80), rows k contiguous over samples x,
+// the operand layout of the tensor-core Gram kernel.  One thread = one sample, looping
+// over parameters: consecutive threads write consecutive samples of a row.
+__global__ void __launch_bounds__(256) obuild_bf16_jastrow_kernel(int n, int W, int P, int ns,
+                                                                  const uint64_t* __restrict__ spins,
+                                                                  const int* __restrict__ pairs,
+                                                                  uint16_t* __restrict__ Ot) {
+    const int t = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= ns) return;
+    uint64_t wd[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) wd[w] = (w < W) ? spins[((size_t)t * ns + x) * W + w] : 0ull;
+    auto bit = [&](int j) -> uint32_t {
+        const int w = j >> 6;
+        uint64_t v = wd[0];
+        if (w == 1) v = wd[1];
+        if (w == 2) v = wd[2];
+        if (w == 3) v = wd[3];
+        return (uint32_t)((v >> (j & 63)) & 1ull);
+    };
+    uint16_t* base = Ot + (size_t)t * P * ns + x;
+    for (int k = 0; k < P; ++k) {
+        uint32_t up;
+        if (k < n) {
+            up = bit(k);
+        } else {
+            const int j = __ldg(pairs + 2 * (k - n)), l = __ldg(pairs + 2 * (k - n) + 1);
+            up = (bit(j) == bit(l)) ? 1u : 0u;
+        }
+        base[(size_t)k * ns] = up ? (uint16_t)0x3F80 : (uint16_t)0xBF80;
+    }
+}
+
+cudaError_t launch_obuild_bf16_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
+                                       uint16_t* Ot, cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_OBUILD, s);
+    const int n = a->n, W = (n + 63) / 64, P = (int)a->P;
+    dim3 grid((ns + 255) / 256, ntraj);
+    obuild_bf16_jastrow_kernel<<<grid, 256, 0, s>>>(n, W, P, ns, spins, a->pairs_d, Ot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- plain FP64 path: O_c
+__global__ void __launch_bounds__(256) obuild_f64_jastrow_kernel(int n, int W, int P, int ns,
+                                                                 const uint64_t* __restrict__ spins,
+                                                                 const int* __restrict__ pairs,
+                                                                 const double* __restrict__ obar,
+                                                                 double* __restrict__ Oc) {
+    const int t = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= ns) return;
+    const uint64_t* w = spins + ((size_t)t * ns + x) * W;
+    double* base = Oc + (size_t)t * P * ns + x;
+    for (int k = 0; k < P; ++k) {
+        double o;
+        if (k < n) {
+            o = ((w[k >> 6] >> (k & 63)) & 1ull) ? 1.0 : -1.0;
+        } else {
+            const int j = __ldg(pairs + 2 * (k - n)), l = __ldg(pairs + 2 * (k - n) + 1);
+            const double sj = ((w[j >> 6] >> (j & 63)) & 1ull) ? 1.0 : -1.0;
+            const double sl = ((w[l >> 6] >> (l & 63)) & 1ull) ? 1.0 : -1.0;
+            o = sj * sl;
+        }
+        base[(size_t)k * ns] = o - obar[(size_t)t * P + k];
+    }
+}
+
+cudaError_t launch_obuild_f64_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
+                                      const double* obar, double* Oc, cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_OBUILD, s);
+    const int n = a->n, W = (n + 63) / 64, P = (int)a->P;
+    dim3 grid((ns + 255) / 256, ntraj);
+    obuild_f64_jastrow_kernel<<<grid, 256, 0, s>>>(n, W, P, ns, spins, a->pairs_d, obar, Oc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// S[i][j] = sum_x Oc[i][x] Oc[j][x] / ns, FP64 SIMT, 64x64 tiles of the upper triangle,
+// mirrored into the lower triangle.
+__global__ void __launch_bounds__(256) syrk_f64_kernel(int P, int ns, const double* __restrict__ Oc,
+                                                       double* __restrict__ S) {
+    constexpr int BT = 64, BK = 16;
+    __shared__ double As[BK][BT + 1];
+    __shared__ double Bs[BK][BT + 1];
+    const int t = blockIdx.z;
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bj < bi) return;
+    const double* O = Oc + (size_t)t * P * ns;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < ns; k0 += BK) {
+        for (int i = threadIdx.x; i < BT * BK; i += 256) {
+            const int r = i / BK, kk = i % BK;
+            const int gi = bi * BT + r, gj = bj * BT + r, gk = k0 + kk;
+            As[kk][r] = (gi < P && gk < ns) ? O[(size_t)gi * ns + gk] : 0.0;
+            Bs[kk][r] = (gj < P && gk < ns) ? O[(size_t)gj * ns + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[kk][ty * 4 + u];
+                b[u] = Bs[kk][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+    double* St = S + (size_t)t * P * P;
+    const double inv = 1.0 / ns;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int gi = bi * BT + ty * 4 + u, gj = bj * BT + tx * 4 + v;
+            if (gi < P && gj < P && gj >= gi) {
+                const double val = acc[u][v] * inv;
+                St[(size_t)gi * P + gj] = val;
+                St[(size_t)gj * P + gi] = val;
+            }
+        }
+}
+
+cudaError_t launch_syrk_f64(int ntraj, int P, int ns, const double* Oc, double* S, cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_SYRK, s);
+    const int nb = (P + 63) / 64;
+    dim3 grid(nb, nb, ntraj);
+    syrk_f64_kernel<<<grid, 256, 0, s>>>(P, ns, Oc, S);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// D_k = sum_x Oc[k][x] (v(x) - vbar) / ns, FP64: one warp per parameter.
+__global__ void __launch_bounds__(256) gemv_D_f64_kernel(int P, int ns, const double* __restrict__ Oc,
+                                                         const double2* __restrict__ v,
+                                                         const double* __restrict__ vinfo, double2* __restrict__ D) {
+    const int t = blockIdx.y;
+    const int k = blockIdx.x * 8 + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (k >= P) return;
+    const double mr = vinfo[4 * t], mi = vinfo[4 * t + 1];
+    const double* o = Oc + ((size_t)t * P + k) * ns;
+    const double2* vv = v + (size_t)t * ns;
+    double ar = 0.0, ai = 0.0;
+    for (int x = lane; x < ns; x += 32) {
+        const double c = o[x];
+        ar = fma(c, vv[x].x - mr, ar);
+        ai = fma(c, vv[x].y - mi, ai);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, off);
+        ai += __shfl_xor_sync(0xffffffffu, ai, off);
+    }
+    if (lane == 0) D[(size_t)t * P + k] = make_double2(ar / ns, ai / ns);
+}
+
+cudaError_t launch_gemv_D_f64(int ntraj, int P, int ns, const double* Oc, const double2* v, const EvalBufs& b,
+                              double2* D, cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_D, s);
+    dim3 grid((P + 7) / 8, ntraj);
+    gemv_D_f64_kernel<<<grid, 256, 0, s>>>(P, ns, Oc, v, b.vinfo, D);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// S = G / ns - obar obar^T (full, FP64) from the upper-triangle Gram counts.
+__global__ void expand_S_kernel(int P, int ns, const float* __restrict__ G, const double* __restrict__ obar,
+                                double* __restrict__ S) {
+    const int t = blockIdx.y;
+    const int i = blockIdx.x;
+    const float* Gt = G + (size_t)t * P * P;
+    const double* ob = obar + (size_t)t * P;
+    double* St = S + (size_t)t * P * P;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        const float g = (j >= i) ? Gt[(size_t)i * P + j] : Gt[(size_t)j * P + i];
+        St[(size_t)i * P + j] = (double)g / ns - ob[i] * ob[j];
+    }
+}
+
+cudaError_t launch_expand_S(int ntraj, int P, int ns, const float* G, const double* obar, double* S,
+                            cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_D, s);
+    dim3 grid(P, ntraj);
+    expand_S_kernel<<<grid, 256, 0, s>>>(P, ns, G, obar, S);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace otvmc

@@ -1,0 +1,284 @@
+// Uncentred Gram matrix G = O^T O of the local operators on the 5th-generation tensor cores
+// (tcgen05, sm_103a): the contraction behind the quantum geometric tensor
+// S = <O^* O> - <O^*><O> (definitions after Eq. 8), S = G / ns - obar obar^T.
+//
+// For the Jastrow ansatz O = +-1 is exact in BF16 and FP32 accumulation of up to 2^24
+// samples is exact, so G (and with the FP64 centring, S) is exact.
+//
+// One CTA computes one 128 x 256 tile of the upper triangle of G for one trajectory:
+//   warp 0      TMA producer: three 128-row boxes (A rows i, B rows j, j+128) of 64 samples
+//               per stage into a 4-stage ring, 128-byte swizzled, completing on mbarriers;
+//   warp 1      allocates 256 TMEM columns; one lane issues tcgen05.mma (M=128, N=256,
+//               K=16, BF16 in, FP32 accumulate in TMEM) and commits each stage back;
+//   warps 2..5  epilogue: tcgen05.ld of their 32 TMEM lanes, FP32 stores of the j >= i part.
+// Every mbarrier wait is bounded (2 s of %globaltimer); on timeout the CTA records
+// OTVMC_ERR_TIMEOUT, drains its own copies and MMAs (bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace otvmc {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int STAGES = 4;
+constexpr int BOX_BYTES = 128 * BK * 2;  // 16 KB: one 128-row box
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    const unsigned long long t0 = gtime();
+    while (true) {
+        if (mbar_try(b, parity)) return true;
+        if (abort_flag != nullptr && *abort_flag) return false;
+        if (gtime() - t0 > WAIT_NS) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            su32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor, kind::f16: D F32, A/B BF16, both K-major, N >> 3, M >> 4.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
+                                                          const int2* __restrict__ tiles, float* __restrict__ G,
+                                                          int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_BYTES;
+    uint64_t* full = (uint64_t*)(sB + STAGES * B_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int t = blockIdx.y;
+    const int2 tl = tiles[blockIdx.x];
+    const int i0 = tl.x * BM, j0 = tl.y * BN;
+    const int nk = (ns + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                tma_load_3d(sA + s * A_BYTES, &tmap, &full[s], kb * BK, i0, t);
+                tma_load_3d(sB + s * B_BYTES, &tmap, &full[s], kb * BK, j0, t);
+                tma_load_3d(sB + s * B_BYTES + BOX_BYTES, &tmap, &full[s], kb * BK, j0 + 128, t);
+                ++issued;
+            }
+            // drain: every issued stage must have landed before the CTA may exit
+            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+                mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, nullptr);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (!mbar_wait(&full[s], ph, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t a0 = su32(sA + s * A_BYTES), b0 = su32(sB + s * B_BYTES);
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)
+                    umma(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
+                umma_commit(&empty[s]);
+            }
+            umma_commit(done);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
+        int ok = 0;
+        if (lane == 0) ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        fence_after();
+        if (ok) {
+            const int row = q * 32 + lane;
+            const int gi = i0 + row;
+            float* Grow = G + ((size_t)t * P + (gi < P ? gi : 0)) * P;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                const int gj0 = j0 + c;
+                if (gi >= P || gj0 + 31 < gi || gj0 >= P) continue;
+                if (gj0 >= gi && gj0 + 31 < P) {
+                    float4* dst = (float4*)(Grow + gj0);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        dst[u] = make_float4(__uint_as_float(v[4 * u]), __uint_as_float(v[4 * u + 1]),
+                                             __uint_as_float(v[4 * u + 2]), __uint_as_float(v[4 * u + 3]));
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const int gj = gj0 + u;
+                        if (gj >= gi && gj < P) Grow[gj] = __uint_as_float(v[u]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) record_error(status, OTVMC_ERR_TIMEOUT, t);
+    if (warp == 1) {
+        // all MMAs of this CTA have completed once `done` fired; wait (bounded) before freeing
+        if (lane == 0) mbar_wait(done, 0, nullptr);
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+}  // namespace tc
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// Upper-triangle tiles (mb, nb) of 128 x 256 that contain some j >= i.
+std::vector<int2> gram_tiles(int P) {
+    std::vector<int2> v;
+    const int MT = (P + tc::BM - 1) / tc::BM, NT = (P + tc::BN - 1) / tc::BN;
+    for (int mb = 0; mb < MT; ++mb)
+        for (int nb = 0; nb < NT; ++nb)
+            if ((nb + 1) * tc::BN > mb * tc::BM) v.push_back(make_int2(mb, nb));
+    return v;
+}
+
+cudaError_t launch_gram_tc(int ntraj, int P, int ns, const uint16_t* Ot, const int2* tiles, int ntiles, float* G,
+                           int* status, cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_GRAM, s);
+    auto encode = get_encode();
+    if (!encode) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)ns, (cuuint64_t)P, (cuuint64_t)ntraj};
+    const cuuint64_t strides[2] = {(cuuint64_t)ns * 2, (cuuint64_t)P * ns * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)tc::BK, 128u, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Ot, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(tc::gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ntiles, ntraj);
+    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, P, ns, tiles, G, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace otvmc
