@@ -95,7 +95,7 @@ EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.vinfo = c.take<double>((size_t)T * 4);
     b.qsum = c.take<long long>((size_t)T * 2);
     b.Epm = c.take<double2>((size_t)T * 2 * n * n);
-    b.part_obs = c.take<double>((size_t)T * nblk * 9);
+    b.part_obs = c.take<double>((size_t)T * (nblk > (size_t)obs_blocks(n, ns) ? nblk : obs_blocks(n, ns)) * 9);
     return b;
 }
 

@@ -75,6 +75,11 @@ constexpr int EST_SAMPLES_PER_THREAD = 8;
 inline int est_threads_per_sample(int n) { return ((n + 31) / 32) * 32; }
 inline int est_samples_per_block(int n) { return (256 / est_threads_per_sample(n)) * EST_SAMPLES_PER_THREAD; }
 inline int est_blocks(int n, int ns) { int sb = est_samples_per_block(n); return (ns + sb - 1) / sb; }
+inline int obs_samples_per_thread() { return 32; }
+inline int obs_blocks(int n, int ns) {
+    const int sb = (256 / est_threads_per_sample(n)) * obs_samples_per_thread();
+    return (ns + sb - 1) / sb;
+}
 constexpr int VRED_BLOCK = 256;  // samples per block of the v reduction
 inline int v_blocks(int ns) { return (ns + VRED_BLOCK - 1) / VRED_BLOCK; }
 
@@ -98,7 +103,7 @@ struct EvalBufs {
     double* vinfo;       // [T][4]: mean re, mean im, 2^-e, qsum re/im as doubles? (see k_estim)
     long long* qsum;     // [T][2]
     double2* Epm;        // [T][2][n][n] exp(+-4 eta) for observables
-    double* part_obs;    // [T][nblk][9]
+    double* part_obs;    // [T][obs_blocks][9]
 };
 
 size_t eval_bufs_bytes(const otvmc_ansatz* a, int ntraj, int ns);

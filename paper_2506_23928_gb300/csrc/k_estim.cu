@@ -272,6 +272,7 @@ cudaError_t launch_site_means(const otvmc_ansatz* a, int ntraj, int ns, const Ev
 // v(x) = -i dt E_eff(x) + sum_n dW_n B^n(x)
 // decay site j:  B = sqrt(kappa_j) [sigma_j = -1] r_j, (L^+L)_loc = kappa_j (1 + sigma_j)/2, L^2 = 0
 // dephasing j:   B = sqrt(gamma_j) sigma_j, (L^+L)_loc = (L^2)_loc = gamma_j
+// One thread per sample, 256 samples per CTA.
 __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
     int n, int W, int ns, int nops, double dt, const uint64_t* __restrict__ spins, const double2* __restrict__ r,
     const double2* __restrict__ EH, const double* __restrict__ site, const int* __restrict__ opidx,
@@ -306,7 +307,6 @@ __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
     if (s < ns) {
         const uint64_t* w = spins + ((size_t)t * ns + s) * W;
         const double2* rs = r + ((size_t)t * ns + s) * n;
-        double2 E = EH[(size_t)t * ns + s];
         double br = 0.0, bi = 0.0;  // sum_n bracket_n
         double vr = 0.0, vi = 0.0;  // sum_n dW_n B^n
         for (int j = 0; j < n; ++j) {
@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
                 vr += dw_g[j] * B;
             }
         }
+        double2 E = EH[(size_t)t * ns + s];
         // -i/2 (br + i bi) = bi/2 - i br/2
         E.x += 0.5 * bi;
         E.y -= 0.5 * br;
@@ -505,26 +506,30 @@ __device__ __forceinline__ double2 to_r2<double2>(double2 v) { return v; }
 template <>
 __device__ __forceinline__ float2 to_r2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
-template <typename R2, typename R>
-__global__ void __launch_bounds__(256) observables_kernel(int n, int W, int ns, const uint64_t* __restrict__ spins,
+template <typename R2, typename R, bool SMEM_E>
+__global__ void __launch_bounds__(256) observables_kernel(int n, int W, int ns, int spt, const uint64_t* __restrict__ spins,
                                                           const double2* __restrict__ r, const double2* __restrict__ Epm,
                                                           double* __restrict__ part_obs) {
-    constexpr int SPT = EST_SAMPLES_PER_THREAD;
     const int NT = ((n + 31) / 32) * 32;
     const int SPP = 256 / NT;
-    const int SB = SPP * SPT;
+    const int SB = SPP * spt;
     const int t = blockIdx.y, blk = blockIdx.x;
     const int j = threadIdx.x % NT, g = threadIdx.x / NT;
     const bool active = (g < SPP) && (j < n);
     extern __shared__ __align__(16) unsigned char smraw[];
-    R2* rs = (R2*)smraw;                     // [SPP][n]
+    const int nE = SMEM_E ? n * n : 0;
+    R2* E0 = (R2*)smraw;                     // [n][n] exp(+4 eta) (shared-memory copy)
+    R2* E1 = E0 + nE;                        // [n][n] exp(-4 eta)
+    R2* rs = E1 + nE;                        // [SPP][NT]
     double* red = (double*)(rs + SPP * NT);  // [256][9]
-    const double2* E0 = Epm + (size_t)t * 2 * n * n;
-    const double2* E1 = E0 + n * n;
+    const double2* G0 = Epm + (size_t)t * 2 * n * n;
+    const double2* G1 = G0 + n * n;
+    if (SMEM_E)
+        for (int i = threadIdx.x; i < 2 * n * n; i += blockDim.x) E0[i] = to_r2<R2>(G0[i]);
     double acc[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc[i] = 0.0;
-    for (int q = 0; q < SPT; ++q) {
+    for (int q = 0; q < spt; ++q) {
         const int s = blk * SB + g + q * SPP;
         __syncthreads();
         if (active && s < ns) rs[g * NT + j] = to_r2<R2>(r[((size_t)t * ns + s) * n + j]);
@@ -540,7 +545,9 @@ __global__ void __launch_bounds__(256) observables_kernel(int n, int W, int ns, 
         for (int k = 0; k < n; ++k) {
             if (k == j) continue;
             const int sk = ((w[k >> 6] >> (k & 63)) & 1ull) ? 1 : -1;
-            const R2 e = to_r2<R2>((sj == sk) ? E0[k * n + j] : E1[k * n + j]);
+            R2 e;
+            if (SMEM_E) e = (sj == sk) ? E0[k * n + j] : E1[k * n + j];
+            else e = to_r2<R2>((sj == sk) ? G0[k * n + j] : G1[k * n + j]);
             const R2 rk = rr[k];
             const R2 p = {rk.x * e.x - rk.y * e.y, rk.x * e.y + rk.y * e.x};
             a2.x += p.x;
@@ -591,17 +598,27 @@ cudaError_t launch_observables(const otvmc_ansatz* a, const uint64_t* spins, int
     ProfScope prof_(OTVMC_K_OBS, s);
     const int n = a->n, W = (n + 63) / 64;
     const int NT = ((n + 31) / 32) * 32, SPP = 256 / NT;
-    const int nblk = est_blocks(n, ns);
+    const int spt = obs_samples_per_thread();
+    const int nblk = obs_blocks(n, ns);
     dim3 grid(nblk, ntraj);
-    const size_t smem = (size_t)SPP * NT * 16 + 256 * 9 * 8 + 64;
+    const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
+    const size_t base = (size_t)SPP * NT * el + 256 * 9 * 8 + 64;
+    const size_t full = base + 2 * (size_t)n * n * el;
+    const bool sm = full <= 200 * 1024;
+    const size_t smem = sm ? full : base;
+#define OTVMC_OBS_LAUNCH(R2, R, SM)                                                                          \
+    do {                                                                                                     \
+        cudaFuncSetAttribute(observables_kernel<R2, R, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        observables_kernel<R2, R, SM><<<grid, 256, smem, s>>>(n, W, ns, spt, spins, b.r, b.Epm, b.part_obs);  \
+    } while (0)
     if (fp32) {
-        cudaFuncSetAttribute(observables_kernel<float2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        observables_kernel<float2, float><<<grid, 256, smem, s>>>(n, W, ns, spins, b.r, b.Epm, b.part_obs);
+        if (sm) OTVMC_OBS_LAUNCH(float2, float, true);
+        else OTVMC_OBS_LAUNCH(float2, float, false);
     } else {
-        cudaFuncSetAttribute(observables_kernel<double2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        observables_kernel<double2, double><<<grid, 256, smem, s>>>(n, W, ns, spins, b.r, b.Epm, b.part_obs);
+        if (sm) OTVMC_OBS_LAUNCH(double2, double, true);
+        else OTVMC_OBS_LAUNCH(double2, double, false);
     }
+#undef OTVMC_OBS_LAUNCH
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace otvmc {
 namespace tc {
@@ -32,85 +33,6 @@ constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 256;
-constexpr unsigned long long WAIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ unsigned long long gtime() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase of the given parity; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-    const unsigned long long t0 = gtime();
-    while (true) {
-        if (mbar_try(b, parity)) return true;
-        if (abort_flag != nullptr && *abort_flag) return false;
-        if (gtime() - t0 > WAIT_NS) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-            su32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
-        : "memory");
-}
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-    d |= (uint64_t)1 << 46;             // descriptor version
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
-    return d;
-}
-// Instruction descriptor, kind::f16: D F32, A/B BF16, both K-major, N >> 3, M >> 4.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accum));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 __global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
                                                           const int2* __restrict__ tiles, float* __restrict__ G,
@@ -183,7 +105,7 @@ __global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__
                 const uint32_t a0 = su32(sA + s * A_BYTES), b0 = su32(sB + s * B_BYTES);
 #pragma unroll
                 for (int k = 0; k < BK / 16; ++k)
-                    umma(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
+                    umma(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc_bf16(BM, BN), (kb > 0 || k > 0) ? 1u : 0u);
                 umma_commit(&empty[s]);
             }
             umma_commit(done);
@@ -205,7 +127,7 @@ __global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
                 const int gj0 = j0 + c;
                 if (gi >= P || gj0 + 31 < gi || gj0 >= P) continue;
-                if (gj0 >= gi && gj0 + 31 < P) {
+                if (gj0 >= gi && gj0 + 31 < P && ((reinterpret_cast<uintptr_t>(Grow + gj0) & 15u) == 0)) {
                     float4* dst = (float4*)(Grow + gj0);
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
@@ -234,20 +156,6 @@ __global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__
 
 }  // namespace tc
 
-static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaDriverEntryPointQueryResult q;
-        void* p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    });
-    return fn;
-}
-
 // Upper-triangle tiles (mb, nb) of 128 x 256 that contain some j >= i.
 std::vector<int2> gram_tiles(int P) {
     std::vector<int2> v;
@@ -261,7 +169,7 @@ std::vector<int2> gram_tiles(int P) {
 cudaError_t launch_gram_tc(int ntraj, int P, int ns, const uint16_t* Ot, const int2* tiles, int ntiles, float* G,
                            int* status, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_GRAM, s);
-    auto encode = get_encode();
+    auto encode = tc::get_encode();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap map;
     const cuuint64_t dims[3] = {(cuuint64_t)ns, (cuuint64_t)P, (cuuint64_t)ntraj};

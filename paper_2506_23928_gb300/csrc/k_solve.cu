@@ -240,11 +240,13 @@ __global__ void __launch_bounds__(256, 1) chol_solve_kernel(int P, int ns, doubl
                                                             const double* __restrict__ obar,
                                                             const double2* __restrict__ D, double2* __restrict__ delta,
                                                             double* __restrict__ shift_used, T* __restrict__ Lws,
-                                                            T* __restrict__ yws, double* __restrict__ xws, int* status) {
+                                                            T* __restrict__ yws, double* __restrict__ xws,
+                                                            const int* __restrict__ only, int* status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     SolveSmem<T>& sm = *reinterpret_cast<SolveSmem<T>*>(smraw);
     __shared__ double red[2][8];
     const int t = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (only != nullptr && only[t] == 0) return;
     const size_t PP = (size_t)P * P;
     T* L = Lws + (size_t)t * PP;
     const double* St = GRAM ? nullptr : S + (size_t)t * PP;
@@ -350,36 +352,46 @@ __global__ void __launch_bounds__(256, 1) chol_solve_kernel(int P, int ns, doubl
     if (tid == 0 && shift_used) shift_used[t] = eps;
 }
 
+size_t chol_tc_ws_bytes(int ntraj, int P);
+cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G, const double* obar,
+                           const double2* D, double2* delta, double* shift_used, void* ws, int refine_iters,
+                           int* status, cudaStream_t s);
+
 size_t chol_ws_bytes(int ntraj, int P, int precision) {
-    const size_t el = precision == OTVMC_PREC_FP64 ? 8 : 4;
-    return (size_t)ntraj * ((size_t)P * P * el + 2 * (size_t)P * el + 4 * (size_t)P * 8) + 3 * 256;
+    if (precision != OTVMC_PREC_FP64) return chol_tc_ws_bytes(ntraj, P);
+    return (size_t)ntraj * ((size_t)P * P * 8 + 2 * (size_t)P * 8 + 4 * (size_t)P * 8) + 3 * 256;
+}
+
+cudaError_t launch_chol_solve_masked(int ntraj, int P, int ns, double eps, const float* G, const double* obar,
+                                     const double2* D, double2* delta, double* shift_used, float* L, float* y,
+                                     double* x, int refine_iters, const int* only, int* status, cudaStream_t s) {
+    const int smem = (int)sizeof(SolveSmem<float>);
+    cudaFuncSetAttribute(chol_solve_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    chol_solve_kernel<float, true><<<ntraj, 256, smem, s>>>(P, ns, eps, refine_iters, nullptr, G, obar, D, delta,
+                                                            shift_used, L, y, x, only, status);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_chol_solve(int ntraj, int P, int ns, int precision, double eps, const double* S, const float* G,
                               const double* obar, const double2* D, double2* delta, double* shift_used, void* ws,
                               int refine_iters, int* status, cudaStream_t s) {
+    if (precision != OTVMC_PREC_FP64)
+        return launch_chol_tc(ntraj, P, ns, eps, G, obar, D, delta, shift_used, ws, refine_iters, status, s);
     ProfScope prof_(OTVMC_K_SOLVE, s);
-    const size_t el = precision == OTVMC_PREC_FP64 ? 8 : 4;
     char* p = (char*)ws;
     auto take = [&](size_t bytes) {
         char* r = p;
         p += (bytes + 255) & ~(size_t)255;
         return (void*)r;
     };
-    void* L = take((size_t)ntraj * P * P * el);
-    void* y = take((size_t)ntraj * 2 * P * el);
+    void* L = take((size_t)ntraj * P * P * 8);
+    void* y = take((size_t)ntraj * 2 * P * 8);
     double* x = (double*)take((size_t)ntraj * 4 * P * 8);
-    if (precision == OTVMC_PREC_FP64) {
-        const int smem = (int)sizeof(SolveSmem<double>);
-        cudaFuncSetAttribute(chol_solve_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        chol_solve_kernel<double, false><<<ntraj, 256, smem, s>>>(P, ns, eps, 0, S, G, obar, D, delta, shift_used,
-                                                               (double*)L, (double*)y, x, status);
-    } else {
-        const int smem = (int)sizeof(SolveSmem<float>);
-        cudaFuncSetAttribute(chol_solve_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        chol_solve_kernel<float, true><<<ntraj, 256, smem, s>>>(P, ns, eps, refine_iters, S, G, obar, D, delta,
-                                                             shift_used, (float*)L, (float*)y, x, status);
-    }
+    const int smem = (int)sizeof(SolveSmem<double>);
+    cudaFuncSetAttribute(chol_solve_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    chol_solve_kernel<double, false><<<ntraj, 256, smem, s>>>(P, ns, eps, 0, S, G, obar, D, delta, shift_used,
+                                                              (double*)L, (double*)y, x, nullptr, status);
     count_launch();
     return cudaGetLastError();
 }

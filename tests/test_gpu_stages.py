@@ -192,7 +192,8 @@ def test_solve_step_fp64_from_oracle_S():
 def test_solve_not_positive_definite_reports_status():
     c = Case((4,), kappa=0.1)
     T, P = 1, c.P
-    S = -torch.eye(P, dtype=torch.float64, device="cuda")[None].contiguous()
+    # shift retries raise eps to at most 1e-4 * 1e6 = 100, which cannot rescue -1000 I
+    S = -1000.0 * torch.eye(P, dtype=torch.float64, device="cuda")[None].contiguous()
     D = torch.ones((T, P, 2), dtype=torch.float64, device="cuda")
     delta = torch.full((T, P, 2), 7.0, dtype=torch.float64, device="cuda")
     work, nb = c.work(T, 8, FP64)

@@ -61,15 +61,18 @@ def test_run_matches_oracle_chain8(precision, scheme):
 
 
 def test_run_matches_oracle_dephasing_and_two_words():
-    """65 spins (two spin words), decay and dephasing, midpoint, mixed precision."""
+    """65 spins (two spin words), decay and dephasing, midpoint, FP64 path.
+
+    Bit-identical chains need parameters that agree to ~1e-12: with ns = 64 < P the shifted
+    S has a condition number near 1e5, so this comparison runs on the FP64 path."""
     c = Case((65,), alpha=1.5, h=1.0, kappa=0.1, gamma=0.05)
     T, ns, steps, dt, seed = 2, 64, 2, 0.005, 5
-    th, sp, mom = run_gpu(c, T, ns, steps, dt, seed, abi.OTVMC_MIDPOINT, MIXED, traj0=3)
+    th, sp, mom = run_gpu(c, T, ns, steps, dt, seed, abi.OTVMC_MIDPOINT, FP64, traj0=3)
     oth, osig, om, oq = tr.run_mc(c.omodel, c.oans, T, ns, steps, dt, seed, "midpoint", n_sweep=2, eps=1e-4,
                                   traj0=3)
     assert np.array_equal(sp, osig)
-    assert rel_err(th, oth) < 1e-4
-    assert rel_err(mom, oracle_moments(om, oq)) < 1e-5
+    assert rel_err(th, oth) < 1e-8
+    assert rel_err(mom, oracle_moments(om, oq)) < 1e-9
 
 
 def test_run_host_buffers_equal_device_run():
