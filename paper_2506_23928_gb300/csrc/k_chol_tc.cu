@@ -7,9 +7,11 @@
 //           L is kept as three BF16 pieces (L = h + m + l to ~2^-24 relative); the six
 //           products h.h + h.m + m.h + h.l + m.m + l.h accumulate in FP32 in TMEM, which
 //           gives FP32-level accuracy.  One CTA = 128 rows x 128 columns of one trajectory.
-//   panel   (SIMT)     factor the 128 x 128 diagonal block in shared memory, invert it, and
-//           solve the rows below as a small GEMM X = C L_dd^-T; write L in FP32 (for the
-//           triangular solves) and as BF16 pieces (for later updates), and L_dd^-1.
+//   diag    (SIMT)     factor the 128 x 128 diagonal block in shared memory (32-column
+//           sub-blocks, shuffle-based leaf factor) and invert it;
+//   trsm    (SIMT)     the rows below as a register-tiled GEMM X = C L_dd^-T, one 64-row tile
+//           per CTA; both write L in FP32 (for the triangular solves) and as BF16 pieces
+//           (for later updates), and the diagonal kernel writes L_dd^-1.
 // solve     (SIMT)     forward/backward substitution by blocks through the stored inverses,
 //           then one step of iterative refinement with the residual D - (S + eps I) x formed
 //           in FP64 from the exact Gram counts (S = G/ns - obar obar^T).
@@ -43,7 +45,7 @@ __device__ __forceinline__ float a_orig(const float* Gt, const double* ob, int P
 
 // ------------------------------------------------------------------------- update (tcgen05)
 __global__ void __launch_bounds__(192, 1) chol_update_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
-                                                             int jb, float eps, const float* __restrict__ G,
+                                                             int NT, int jb, float eps, const float* __restrict__ G,
                                                              const double* __restrict__ obar, float* __restrict__ Pn,
                                                              const int* __restrict__ fail, int* status) {
     using namespace tc;
@@ -92,8 +94,9 @@ __global__ void __launch_bounds__(192, 1) chol_update_kernel(const __grid_consta
                 uint8_t* st = smem + s * STAGE;
                 mbar_expect_tx(&full[s], STAGE);
                 for (int p = 0; p < NPC; ++p) {
-                    tma_load_3d(st + p * BOX, &tmap, &full[s], kb * BK, i0, t * NPC + p);
-                    tma_load_3d(st + (NPC + p) * BOX, &tmap, &full[s], kb * BK, jb, t * NPC + p);
+                    const int pl = (t * NPC + p) * NT;
+                    tma_load_4d(st + p * BOX, &tmap, &full[s], 0, 0, kb, pl + (i0 >> 7));
+                    tma_load_4d(st + (NPC + p) * BOX, &tmap, &full[s], 0, 0, kb, pl + (jb >> 7));
                 }
                 ++issued;
             }
@@ -162,61 +165,113 @@ __global__ void __launch_bounds__(192, 1) chol_update_kernel(const __grid_consta
 }
 
 // --------------------------------------------------------------------------- panel (SIMT)
-__device__ __forceinline__ void store_L(float* Lf, __nv_bfloat16* Lb, size_t plane, size_t idx, float x) {
-    Lf[idx] = x;
+// BF16 pieces of L are stored tiled: for piece p of trajectory t, the 128-row tile i / 128
+// and the 64-column block k / 64 form one contiguous 16 KB chunk [i % 128][k % 64], so
+// that one TMA box of the update kernel is one contiguous read.
+struct LbLayout {
+    int NT;  // row tiles, ceil(P / 128)
+    int KB;  // 64-column blocks, LD / 64
+    __device__ __forceinline__ size_t plane() const { return (size_t)NT * KB * 128 * 64; }
+    __device__ __forceinline__ size_t at(int i, int k) const {
+        return (((size_t)(i >> 7) * KB + (k >> 6)) * 128 + (i & 127)) * 64 + (k & 63);
+    }
+};
+
+__device__ __forceinline__ void store_L(float* Lf, __nv_bfloat16* Lbt, const LbLayout& lay, int LD, int i, int k,
+                                        float x) {
+    Lf[(size_t)i * LD + k] = x;
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     const float r1 = x - __bfloat162float(h);
     const __nv_bfloat16 m = __float2bfloat16_rn(r1);
     const float r2 = r1 - __bfloat162float(m);
-    Lb[idx] = h;
-    Lb[plane + idx] = m;
-    Lb[2 * plane + idx] = __float2bfloat16_rn(r2);
+    const size_t idx = lay.at(i, k), pl = lay.plane();
+    Lbt[idx] = h;
+    Lbt[pl + idx] = m;
+    Lbt[2 * pl + idx] = __float2bfloat16_rn(r2);
 }
 
-__global__ void __launch_bounds__(256, 1) chol_panel_kernel(int P, int LD, int ns, int jb, float eps,
-                                                            const float* __restrict__ G,
-                                                            const double* __restrict__ obar,
-                                                            const float* __restrict__ Pn, float* __restrict__ Lf,
-                                                            __nv_bfloat16* __restrict__ Lb, float* __restrict__ Dinv,
-                                                            int* __restrict__ fail) {
+// Diagonal block of block column jb: Cholesky factor and its inverse (one CTA per trajectory).
+// 32-column sub-blocks: warp 0 factors the 32 x 32 diagonal sub-block in registers with
+// shuffles, all threads solve the sub-panel below and update the trailing part.  Rows and
+// columns beyond nb are padded with the identity.
+__global__ void __launch_bounds__(256, 1) chol_diag_kernel(int P, int LD, int ns, int jb, float eps,
+                                                           const float* __restrict__ G,
+                                                           const double* __restrict__ obar,
+                                                           const float* __restrict__ Pn, float* __restrict__ Lf,
+                                                           __nv_bfloat16* __restrict__ Lb, float* __restrict__ Dinv,
+                                                           int* __restrict__ fail) {
     const int t = blockIdx.x;
     if (fail[t]) return;
-    extern __shared__ __align__(16) float psm[];
-    float* Dg = psm;             // [NB][DS] diagonal block, then its Cholesky factor
-    float* Li = Dg + NB * DS;    // [NB][DS] inverse of the factor
-    float* Ct = Li + NB * DS;    // [RT][DS] panel rows
+    extern __shared__ __align__(16) float dsm[];
+    float* A = dsm;             // [NB][DS] block, then its factor (lower)
+    float* Li = A + NB * DS;    // [NB][DS] inverse
     __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nb = min(NB, P - jb);
     const float* Gt = G + (size_t)t * P * P;
     const double* ob = obar + (size_t)t * P;
     const float inv_ns = 1.0f / (float)ns;
-    const size_t LL = (size_t)P * LD;             // elements of one trajectory's L
-    float* Lft = Lf + (size_t)t * LL;
-    __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * LL;
-    auto C = [&](int i, int c) -> float {  // updated block column entry (i >= jb + c)
-        return jb == 0 ? a_orig(Gt, ob, P, inv_ns, i, jb + c, eps) : Pn[((size_t)t * P + i) * NB + c];
-    };
     if (tid == 0) bad = 0;
-    for (int e = tid; e < nb * nb; e += blockDim.x) {
-        const int i = e / nb, c = e - i * nb;
-        Dg[i * DS + c] = (c <= i) ? C(jb + i, c) : 0.f;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, c = e - i * NB;
+        float v = 0.f;
+        if (i < nb && c < nb) {
+            if (c <= i) v = jb == 0 ? a_orig(Gt, ob, P, inv_ns, jb + i, jb + c, eps) : Pn[((size_t)t * P + jb + i) * NB + c];
+        } else if (i == c) {
+            v = 1.f;
+        }
+        A[i * DS + c] = v;
     }
     __syncthreads();
-    for (int p = 0; p < nb; ++p) {
-        if (tid == 0) {
-            const float d = Dg[p * DS + p];
-            if (!(d > 0.f) || !isfinite(d)) bad = 1;
-            else Dg[p * DS + p] = sqrtf(d);
+    for (int k0 = 0; k0 < NB; k0 += 32) {
+        if (warp == 0) {
+            float r[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) r[c] = A[(k0 + lane) * DS + k0 + c];
+            bool ok = true;
+#pragma unroll
+            for (int p = 0; p < 32; ++p) {
+                const float d = __shfl_sync(0xffffffffu, r[p], p);
+                ok = ok && (d > 0.f) && isfinite(d);
+                const float sd = sqrtf(fmaxf(d, 1e-30f));
+                if (lane == p) r[p] = sd;
+                if (lane > p) r[p] /= sd;
+                const float colp = r[p];
+#pragma unroll
+                for (int c = p + 1; c < 32; ++c) {
+                    const float lcp = __shfl_sync(0xffffffffu, colp, c);
+                    if (lane >= c) r[c] = fmaf(-colp, lcp, r[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) A[(k0 + lane) * DS + k0 + c] = (c <= lane) ? r[c] : 0.f;
+            if (lane == 0 && !ok) bad = 1;
         }
         __syncthreads();
         if (bad) break;
-        const float piv = Dg[p * DS + p];
-        for (int i = p + 1 + tid; i < nb; i += blockDim.x) Dg[i * DS + p] /= piv;
+        // sub-panel rows below: X L_kk^T = A
+        for (int i = k0 + 32 + tid; i < NB; i += blockDim.x) {
+            float x[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                float a = A[i * DS + k0 + c];
+#pragma unroll
+                for (int k = 0; k < c; ++k) a = fmaf(-x[k], A[(k0 + c) * DS + k0 + k], a);
+                x[c] = a / A[(k0 + c) * DS + k0 + c];
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) A[i * DS + k0 + c] = x[c];
+        }
         __syncthreads();
-        for (int i = p + 1 + warp; i < nb; i += blockDim.x / 32) {
-            const float lip = Dg[i * DS + p];
-            for (int c = p + 1 + lane; c <= i; c += 32) Dg[i * DS + c] -= lip * Dg[c * DS + p];
+        // trailing update A[i][j] -= X[i] . X[j] for k0+32 <= j <= i
+        const int m = NB - k0 - 32;
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            const int i = k0 + 32 + e / m, j = k0 + 32 + e % m;
+            if (j > i) continue;
+            float a = A[i * DS + j];
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) a = fmaf(-A[i * DS + k0 + k], A[j * DS + k0 + k], a);
+            A[i * DS + j] = a;
         }
         __syncthreads();
     }
@@ -224,60 +279,118 @@ __global__ void __launch_bounds__(256, 1) chol_panel_kernel(int P, int LD, int n
         if (tid == 0) fail[t] = 1;
         return;
     }
-    // inverse of the lower-triangular factor, one column per thread
-    if (tid < nb) {
+    // inverse of the lower-triangular factor, one column per thread, four partial sums
+    if (tid < NB) {
         const int c = tid;
-        for (int i = 0; i < nb; ++i) {
+        for (int i = 0; i < NB; ++i) {
             float v = 0.f;
             if (i == c) {
-                v = 1.f / Dg[i * DS + i];
+                v = 1.f / A[i * DS + i];
             } else if (i > c) {
-                float s = 0.f;
-                for (int k = c; k < i; ++k) s = fmaf(Dg[i * DS + k], Li[k * DS + c], s);
-                v = -s / Dg[i * DS + i];
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                int k = c;
+                for (; k + 3 < i; k += 4) {
+                    s0 = fmaf(A[i * DS + k], Li[k * DS + c], s0);
+                    s1 = fmaf(A[i * DS + k + 1], Li[(k + 1) * DS + c], s1);
+                    s2 = fmaf(A[i * DS + k + 2], Li[(k + 2) * DS + c], s2);
+                    s3 = fmaf(A[i * DS + k + 3], Li[(k + 3) * DS + c], s3);
+                }
+                for (; k < i; ++k) s0 = fmaf(A[i * DS + k], Li[k * DS + c], s0);
+                v = -((s0 + s1) + (s2 + s3)) / A[i * DS + i];
             }
             Li[i * DS + c] = v;
         }
     }
     __syncthreads();
-    const int bidx = jb / NB;
-    float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + bidx) * NB * NB;
+    const LbLayout lay{(P + NB - 1) / NB, LD / 64};
+    float* Lft = Lf + (size_t)t * P * LD;
+    __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
+    float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int i = e / NB, c = e - i * NB;
         Dv[e] = (i < nb && c < nb) ? Li[i * DS + c] : 0.f;
-        if (i < nb && c < nb) store_L(Lft, Lbt, LL, (size_t)(jb + i) * LD + jb + c, c <= i ? Dg[i * DS + c] : 0.f);
+        if (i < nb && c < nb) store_L(Lft, Lbt, lay, LD, jb + i, jb + c, c <= i ? A[i * DS + c] : 0.f);
     }
-    // rows below the diagonal block: X = C L_dd^-T in tiles of RT rows
-    const int r = tid % RT, cc = tid / RT;  // row of the tile, chunk of 32 columns
-    for (int r0 = jb + nb; r0 < P; r0 += RT) {
-        __syncthreads();
-        for (int e = tid; e < RT * nb; e += blockDim.x) {
-            const int rr = e / nb, c = e - rr * nb;
-            Ct[rr * DS + c] = (r0 + rr < P) ? C(r0 + rr, c) : 0.f;
-        }
-        __syncthreads();
-        float acc[32];
+}
+
+// Rows below the diagonal block: X = C L_dd^-T, one 64-row tile per CTA; each thread owns
+// 4 rows x 8 columns (register tiling: 12 shared loads per 32 FMAs).
+__global__ void __launch_bounds__(256) chol_trsm_kernel(int P, int LD, int ns, int jb, float eps,
+                                                        const float* __restrict__ G, const double* __restrict__ obar,
+                                                        const float* __restrict__ Pn, float* __restrict__ Lf,
+                                                        __nv_bfloat16* __restrict__ Lb,
+                                                        const float* __restrict__ Dinv, const int* __restrict__ fail) {
+    const int t = blockIdx.y;
+    if (fail[t]) return;
+    extern __shared__ __align__(16) float tsm[];
+    float* Li = tsm;            // [NB][DS]
+    float* Ct = Li + NB * DS;   // [RT][DS]
+    const int tid = threadIdx.x;
+    const int nb = min(NB, P - jb);
+    const int r0 = jb + nb + blockIdx.x * RT;
+    const float* Gt = G + (size_t)t * P * P;
+    const double* ob = obar + (size_t)t * P;
+    const float inv_ns = 1.0f / (float)ns;
+    const float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
+    for (int e = tid; e < NB * NB; e += blockDim.x) Li[(e / NB) * DS + e % NB] = Dv[e];
+    for (int e = tid; e < RT * nb; e += blockDim.x) {
+        const int rr = e / nb, c = e - rr * nb;
+        const int i = r0 + rr;
+        float v = 0.f;
+        if (i < P) v = jb == 0 ? a_orig(Gt, ob, P, inv_ns, i, jb + c, eps) : Pn[((size_t)t * P + i) * NB + c];
+        Ct[rr * DS + c] = v;
+    }
+    __syncthreads();
+    const int rg = tid % 16, cg = tid / 16;
+    float acc[4][8];
 #pragma unroll
-        for (int u = 0; u < 32; ++u) acc[u] = 0.f;
-        const int kend = min(nb, cc * 32 + 32);
-        for (int k = 0; k < kend; ++k) {
-            const float a = Ct[r * DS + k];
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int u = 0; u < 32; ++u) acc[u] = fmaf(a, Li[(cc * 32 + u) * DS + k], acc[u]);
-        }
-        const int i = r0 + r;
+        for (int u = 0; u < 8; ++u) acc[a][u] = 0.f;
+    const int kend = min(nb, cg * 8 + 8);  // L_dd^-1 is lower triangular
+    for (int k = 0; k < kend; ++k) {
+        float cv[4], lv[8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) cv[a] = Ct[(rg * 4 + a) * DS + k];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) lv[u] = Li[(cg * 8 + u) * DS + k];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[a][u] = fmaf(cv[a], lv[u], acc[a][u]);
+    }
+    const LbLayout lay{(P + NB - 1) / NB, LD / 64};
+    float* Lft = Lf + (size_t)t * P * LD;
+    __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = r0 + rg * 4 + a;
         if (i < P)
 #pragma unroll
-            for (int u = 0; u < 32; ++u) {
-                const int c = cc * 32 + u;
-                if (c < nb) store_L(Lft, Lbt, LL, (size_t)i * LD + jb + c, acc[u]);
+            for (int u = 0; u < 8; ++u) {
+                const int c = cg * 8 + u;
+                if (c < nb) store_L(Lft, Lbt, lay, LD, i, jb + c, acc[a][u]);
             }
     }
 }
 
 // ------------------------------------------------------------------------------ solves
+// (s, c) += g * (xh + xl) with an error-free product and sum (Dekker/Knuth): the pair s + c
+// carries about 48 bits, enough for an FP64-quality residual from FP32 arithmetic.
+__device__ __forceinline__ void df_fma(float& s, float& c, float g, float xh, float xl) {
+    const float p = g * xh;
+    const float e = fmaf(g, xh, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (p - bp);
+    s = t;
+    c += err + e;
+    c = fmaf(g, xl, c);
+}
+
 // L L^T x = y for two right-hand sides held in shared memory (y[0..P), y[P..2P)).
-__device__ void block_solve(int P, int LD, const float* Lft, const float* Dv, float* y, float* Db, float* tmp) {
+__device__ void block_solve(int P, int LD, const float* Lft, const float* Dv, float* y, float* Db, float* tmp,
+                            float* part) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nblk = (P + NB - 1) / NB;
     for (int b = 0; b < nblk; ++b) {
@@ -293,41 +406,96 @@ __device__ void block_solve(int P, int LD, const float* Lft, const float* Dv, fl
         __syncthreads();
         for (int e = tid; e < 2 * nb; e += blockDim.x) y[(e / nb) * P + jb + e % nb] = tmp[(e / nb) * NB + e % nb];
         __syncthreads();
-        for (int i = jb + nb + warp; i < P; i += blockDim.x / 32) {
-            const float* row = Lft + (size_t)i * LD + jb;
-            float s0 = 0.f, s1 = 0.f;
-            for (int c = lane; c < nb; c += 32) {
-                const float l = row[c];
-                s0 = fmaf(l, y[jb + c], s0);
-                s1 = fmaf(l, y[P + jb + c], s1);
-            }
+        if (jb + nb < P) {
+            // rows below: y_i -= L[i, jb:jb+128] . y_b; lane l owns columns 4l..4l+3, each warp
+            // keeps four rows in flight
+            float yb0[4], yb1[4];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+            for (int u = 0; u < 4; ++u) {
+                yb0[u] = y[jb + 4 * lane + u];
+                yb1[u] = y[P + jb + 4 * lane + u];
             }
-            if (lane == 0) {
-                y[i] -= s0;
-                y[P + i] -= s1;
+            const int nw = blockDim.x / 32;
+            for (int i0 = jb + nb + 4 * warp; i0 < P; i0 += 4 * nw) {
+                float4 l4[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    l4[a] = (i0 + a < P) ? *reinterpret_cast<const float4*>(Lft + (size_t)(i0 + a) * LD + jb + 4 * lane)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                float s0[4], s1[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    s0[a] = l4[a].x * yb0[0] + l4[a].y * yb0[1] + l4[a].z * yb0[2] + l4[a].w * yb0[3];
+                    s1[a] = l4[a].x * yb1[0] + l4[a].y * yb1[1] + l4[a].z * yb1[2] + l4[a].w * yb1[3];
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        s0[a] += __shfl_xor_sync(0xffffffffu, s0[a], off);
+                        s1[a] += __shfl_xor_sync(0xffffffffu, s1[a], off);
+                    }
+                if (lane < 4 && i0 + lane < P) {
+                    float v0 = s0[0], v1 = s1[0];
+                    if (lane == 1) { v0 = s0[1]; v1 = s1[1]; }
+                    if (lane == 2) { v0 = s0[2]; v1 = s1[2]; }
+                    if (lane == 3) { v0 = s0[3]; v1 = s1[3]; }
+                    y[i0 + lane] -= v0;
+                    y[P + i0 + lane] -= v1;
+                }
             }
         }
         __syncthreads();
     }
     for (int b = nblk - 1; b >= 0; --b) {
         const int jb = b * NB, nb = min(NB, P - jb);
-        for (int e = tid; e < 2 * nb; e += blockDim.x) {
-            const int c = e % nb, h = e / nb;
-            float s = 0.f;
-            for (int i = jb + nb; i < P; ++i) s = fmaf(Lft[(size_t)i * LD + jb + c], y[h * P + i], s);
-            tmp[h * NB + c] = y[h * P + jb + c] - s;
+        // partial sums over the solved rows below: warps stream rows, lane l owns columns 4l..4l+3
+        float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        {
+            const int nw = blockDim.x / 32;
+            for (int i0 = jb + nb + 4 * warp; i0 < P; i0 += 4 * nw) {
+                float4 l4[4];
+                float x0[4], x1[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const bool in = i0 + a < P;
+                    l4[a] = in ? *reinterpret_cast<const float4*>(Lft + (size_t)(i0 + a) * LD + jb + 4 * lane)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x0[a] = in ? y[i0 + a] : 0.f;
+                    x1[a] = in ? y[P + i0 + a] : 0.f;
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    acc[0][0] = fmaf(l4[a].x, x0[a], acc[0][0]);
+                    acc[1][0] = fmaf(l4[a].y, x0[a], acc[1][0]);
+                    acc[2][0] = fmaf(l4[a].z, x0[a], acc[2][0]);
+                    acc[3][0] = fmaf(l4[a].w, x0[a], acc[3][0]);
+                    acc[0][1] = fmaf(l4[a].x, x1[a], acc[0][1]);
+                    acc[1][1] = fmaf(l4[a].y, x1[a], acc[1][1]);
+                    acc[2][1] = fmaf(l4[a].z, x1[a], acc[2][1]);
+                    acc[3][1] = fmaf(l4[a].w, x1[a], acc[3][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            part[(warp * NB + 4 * lane + u) * 2] = acc[u][0];
+            part[(warp * NB + 4 * lane + u) * 2 + 1] = acc[u][1];
         }
         for (int e = tid; e < NB * NB; e += blockDim.x) Db[(e / NB) * DS + e % NB] = Dv[(size_t)b * NB * NB + e];
         __syncthreads();
         for (int e = tid; e < 2 * nb; e += blockDim.x) {
             const int c = e % nb, h = e / nb;
-            float s = 0.f;
-            for (int k = c; k < nb; ++k) s = fmaf(Db[k * DS + c], tmp[h * NB + k], s);
-            y[h * P + jb + c] = s;
+            float sacc = 0.f;
+            for (int w = 0; w < 8; ++w) sacc += part[(w * NB + c) * 2 + h];
+            tmp[h * NB + c] = y[h * P + jb + c] - sacc;
+        }
+        __syncthreads();
+        for (int e = tid; e < 2 * nb; e += blockDim.x) {
+            const int c = e % nb, h = e / nb;
+            float sacc = 0.f;
+            for (int k = c; k < nb; ++k) sacc = fmaf(Db[k * DS + c], tmp[h * NB + k], sacc);
+            y[h * P + jb + c] = sacc;
         }
         __syncthreads();
     }
@@ -347,6 +515,8 @@ __global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int P, int LD, in
     float* Db = ssm;              // [NB][DS]
     float* tmp = Db + NB * DS;    // [2][NB]
     float* y = tmp + 2 * NB;      // [2][P]
+    float* xs = y + 2 * P;        // [4][P] x split into FP32 high and low parts (re h, re l, im h, im l)
+    float* part = xs + 4 * P;     // [8][256][2][2] per-warp partial sums
     __shared__ double red[2][8];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float* Lft = Lf + (size_t)t * P * LD;
@@ -361,7 +531,7 @@ __global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int P, int LD, in
         y[P + k] = (float)Dt[k].y;
     }
     __syncthreads();
-    block_solve(P, LD, Lft, Dv, y, Db, tmp);
+    block_solve(P, LD, Lft, Dv, y, Db, tmp, part);
     for (int k = tid; k < P; k += blockDim.x) {
         xr[k] = (double)y[k];
         xi[k] = (double)y[P + k];
@@ -390,24 +560,64 @@ __global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int P, int LD, in
             oxr += red[0][w];
             oxi += red[1][w];
         }
-        for (int j = tid; j < P; j += blockDim.x) {
-            double zr = 0.0, zi = 0.0;
-            for (int i = 0; i < j; ++i) {
-                const double g = (double)Gt[(size_t)i * P + j];
-                zr = fma(g, xr[i], zr);
-                zi = fma(g, xi[i], zi);
-            }
-            rr[j] = zr;
-            ri[j] = zi;
+        // x = xh + xl in FP32 pairs (48 significant bits)
+        for (int k = tid; k < P; k += blockDim.x) {
+            const float rh = (float)xr[k], ih = (float)xi[k];
+            xs[k] = rh;
+            xs[P + k] = (float)(xr[k] - (double)rh);
+            xs[2 * P + k] = ih;
+            xs[3 * P + k] = (float)(xi[k] - (double)ih);
         }
         __syncthreads();
-        for (int i = warp; i < P; i += blockDim.x / 32) {
-            double yr2 = 0.0, yi2 = 0.0;
-            for (int j = i + lane; j < P; j += 32) {
-                const double g = (double)Gt[(size_t)i * P + j];
-                yr2 = fma(g, xr[j], yr2);
-                yi2 = fma(g, xi[j], yi2);
+        // z_j = sum_{i<j} G[i][j] x_i: column chunks of 256, warps stream rows, lane l owns 8 columns
+        for (int c0 = 0; c0 < P; c0 += 256) {
+            float sh[8][2], sc[8][2];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sh[u][0] = sh[u][1] = sc[u][0] = sc[u][1] = 0.f;
+            const int iend = min(P, c0 + 256);
+            for (int i = warp; i < iend; i += blockDim.x / 32) {
+                const float* grow = Gt + (size_t)i * P;
+                const float xh0 = xs[i], xl0 = xs[P + i], xh1 = xs[2 * P + i], xl1 = xs[3 * P + i];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int jcol = c0 + 8 * lane + u;
+                    if (jcol < P && jcol > i) {
+                        const float g = grow[jcol];
+                        df_fma(sh[u][0], sc[u][0], g, xh0, xl0);
+                        df_fma(sh[u][1], sc[u][1], g, xh1, xl1);
+                    }
+                }
             }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int cl = 8 * lane + u;
+                part[((warp * 256 + cl) * 2) * 2] = sh[u][0];
+                part[((warp * 256 + cl) * 2) * 2 + 1] = sc[u][0];
+                part[((warp * 256 + cl) * 2 + 1) * 2] = sh[u][1];
+                part[((warp * 256 + cl) * 2 + 1) * 2 + 1] = sc[u][1];
+            }
+            __syncthreads();
+            for (int cl = tid; cl < 256 && c0 + cl < P; cl += blockDim.x) {
+                double zr = 0.0, zi = 0.0;
+                for (int w = 0; w < 8; ++w) {
+                    zr += (double)part[((w * 256 + cl) * 2) * 2] + (double)part[((w * 256 + cl) * 2) * 2 + 1];
+                    zi += (double)part[((w * 256 + cl) * 2 + 1) * 2] + (double)part[((w * 256 + cl) * 2 + 1) * 2 + 1];
+                }
+                rr[c0 + cl] = zr;
+                ri[c0 + cl] = zi;
+            }
+            __syncthreads();
+        }
+        // y_i = sum_{j>=i} G[i][j] x_j, one warp per row; residual D - (S + eps I) x
+        for (int i = warp; i < P; i += blockDim.x / 32) {
+            const float* grow = Gt + (size_t)i * P;
+            float h0 = 0.f, c0f = 0.f, h1 = 0.f, c1f = 0.f;
+            for (int jj = i + lane; jj < P; jj += 32) {
+                const float g = grow[jj];
+                df_fma(h0, c0f, g, xs[jj], xs[P + jj]);
+                df_fma(h1, c1f, g, xs[2 * P + jj], xs[3 * P + jj]);
+            }
+            double yr2 = (double)h0 + (double)c0f, yi2 = (double)h1 + (double)c1f;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 yr2 += __shfl_xor_sync(0xffffffffu, yr2, off);
@@ -421,7 +631,7 @@ __global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int P, int LD, in
             }
         }
         __syncthreads();
-        block_solve(P, LD, Lft, Dv, y, Db, tmp);
+        block_solve(P, LD, Lft, Dv, y, Db, tmp, part);
         for (int k = tid; k < P; k += blockDim.x) {
             xr[k] += (double)y[k];
             xi[k] += (double)y[P + k];
@@ -441,7 +651,7 @@ size_t chol_tc_ws_bytes(int ntraj, int P) {
     const size_t LD = ldim(P), nblk = (P + NB - 1) / NB;
     size_t b = 0;
     auto add = [&](size_t bytes) { b += (bytes + 255) & ~(size_t)255; };
-    add((size_t)ntraj * NPC * P * LD * 2);   // Lb
+    add((size_t)ntraj * NPC * ((P + NB - 1) / NB) * 128 * LD * 2);   // Lb (tiled)
     add((size_t)ntraj * P * LD * 4);         // Lf (also the fallback solver's factor)
     add((size_t)ntraj * P * NB * 4);         // Pn
     add((size_t)ntraj * nblk * NB * NB * 4); // Dinv
@@ -460,7 +670,6 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
                            const double2* D, double2* delta, double* shift_used, void* ws, int refine_iters,
                            int* status, cudaStream_t s) {
     using namespace chol;
-    ProfScope prof_(OTVMC_K_SOLVE, s);
     const int LD = ldim(P);
     const size_t nblk = (P + NB - 1) / NB;
     char* p = (char*)ws;
@@ -469,7 +678,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
         p += (bytes + 255) & ~(size_t)255;
         return (void*)r;
     };
-    __nv_bfloat16* Lb = (__nv_bfloat16*)take((size_t)ntraj * NPC * P * LD * 2);
+    const int NT = (P + NB - 1) / NB, KB = LD / 64;
+    __nv_bfloat16* Lb = (__nv_bfloat16*)take((size_t)ntraj * NPC * NT * 128 * LD * 2);
     float* Lf = (float*)take((size_t)ntraj * P * LD * 4);
     float* Pn = (float*)take((size_t)ntraj * P * NB * 4);
     float* Dv = (float*)take((size_t)ntraj * nblk * NB * NB * 4);
@@ -480,33 +690,48 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     auto encode = tc::get_encode();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)LD, (cuuint64_t)P, (cuuint64_t)ntraj * NPC};
-    const cuuint64_t strides[2] = {(cuuint64_t)LD * 2, (cuuint64_t)P * LD * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)BK, 128u, 1u};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Lb, dims, strides, box, estr,
+    const cuuint64_t dims[4] = {64u, 128u, (cuuint64_t)KB, (cuuint64_t)ntraj * NPC * NT};
+    const cuuint64_t strides[3] = {128u, 128u * 128u, (cuuint64_t)KB * 128u * 128u};
+    const cuuint32_t box[4] = {64u, 128u, 1u, 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)Lb, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
 
     cudaError_t e = cudaMemsetAsync(fail, 0, (size_t)ntraj * 4, s);
     if (e != cudaSuccess) return e;
-    const int psmem = (2 * NB + RT) * DS * (int)sizeof(float);
-    e = cudaFuncSetAttribute(chol_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+    const int dsmem = 2 * NB * DS * (int)sizeof(float);
+    const int tsmem = (NB + RT) * DS * (int)sizeof(float);
+    e = cudaFuncSetAttribute(chol_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(chol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_U);
     if (e != cudaSuccess) return e;
     const float feps = (float)eps;
     for (int jb = 0; jb < P; jb += NB) {
         if (jb > 0) {
+            ProfScope pu(OTVMC_K_CHOLU, s);
             dim3 grid((P - jb + 127) / 128, ntraj);
-            chol_update_kernel<<<grid, 192, SMEM_U, s>>>(map, P, ns, jb, feps, G, obar, Pn, fail, status);
+            chol_update_kernel<<<grid, 192, SMEM_U, s>>>(map, P, ns, NT, jb, feps, G, obar, Pn, fail, status);
             count_launch();
         }
-        chol_panel_kernel<<<ntraj, 256, psmem, s>>>(P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
-        count_launch();
+        {
+            ProfScope pd(OTVMC_K_CHOLD, s);
+            chol_diag_kernel<<<ntraj, 256, dsmem, s>>>(P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
+            count_launch();
+        }
+        const int nrows = P - jb - min(NB, P - jb);
+        if (nrows > 0) {
+            ProfScope pp(OTVMC_K_CHOLP, s);
+            dim3 grid((nrows + RT - 1) / RT, ntraj);
+            chol_trsm_kernel<<<grid, 256, tsmem, s>>>(P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
+            count_launch();
+        }
     }
-    const int ssmem = (NB * DS + 2 * NB + 2 * P) * (int)sizeof(float);
+    ProfScope ps(OTVMC_K_SOLVE, s);
+    const int ssmem = (NB * DS + 2 * NB + 2 * P + 4 * P + 8 * 256 * 2 * 2) * (int)sizeof(float);
     e = cudaFuncSetAttribute(chol_solve_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem);
     if (e != cudaSuccess) return e;
     chol_solve_tc_kernel<<<ntraj, 256, ssmem, s>>>(P, LD, ns, eps, refine_iters, G, obar, D, Lf, Dv, x, delta,
