@@ -52,7 +52,8 @@ void prof_record(int cls, cudaStream_t s, bool start) {
 void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 otvmc_status cuda_status(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return OTVMC_OK;
-    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    std::string detail = g_err.rfind("cholesky:", 0) == 0 ? " (" + g_err + ")" : std::string();
+    set_error(std::string(what) + ": " + cudaGetErrorString(e) + detail);
     return OTVMC_ERR_CUDA;
 }
 

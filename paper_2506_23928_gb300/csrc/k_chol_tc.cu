@@ -6,7 +6,8 @@
 //   update  (tcgen05)  C[i, jb:jb+128] = A[i, jb:jb+128] - sum_{k<jb} L[i,k] L[jb+c,k], i >= jb.
 //           L is kept as three BF16 pieces (L = h + m + l to ~2^-24 relative); the six
 //           products h.h + h.m + m.h + h.l + m.m + l.h accumulate in FP32 in TMEM, which
-//           gives FP32-level accuracy.  One CTA = 128 rows x 128 columns of one trajectory.
+//           gives FP32-level accuracy.  One CTA = 128 rows x 128 columns of one trajectory;
+//           32-column k slices (64-byte swizzle) in a 2-stage ring, two CTAs per SM.
 //   diag    (SIMT)     factor the 128 x 128 diagonal block in shared memory (32-column
 //           sub-blocks, shuffle-based leaf factor) and invert it;
 //   trsm    (SIMT)     the rows below as a register-tiled GEMM X = C L_dd^-T, one 64-row tile
@@ -19,6 +20,10 @@
 // solver, which raises the shift (x100, at most three times).
 #include <cuda_bf16.h>
 
+#include <cstdio>
+#include <mutex>
+#include <string>
+
 #include "common.cuh"
 #include "tc_common.cuh"
 
@@ -26,11 +31,11 @@ namespace otvmc {
 namespace chol {
 
 constexpr int NB = 128;                  // block column width
-constexpr int BK = 64;                   // k extent of one TMA box (bf16: 128 bytes)
+constexpr int BK = 32;                   // k extent of one TMA box (bf16: 64 bytes, 64-byte swizzle)
 constexpr int NPC = 3;                   // bf16 pieces of L
-constexpr int BOX = 128 * BK * 2;        // one 128-row box: 16 KB
-constexpr int STAGE = 2 * NPC * BOX;     // A pieces + B pieces: 96 KB
-constexpr int STAGES = 2;
+constexpr int BOX = 128 * BK * 2;        // one 128-row box: 8 KB
+constexpr int STAGE = 2 * NPC * BOX;     // A pieces + B pieces: 48 KB
+constexpr int STAGES = 2;                // about 97 KB of shared memory: two CTAs per SM
 constexpr int SMEM_U = STAGES * STAGE + 1024 + 256;
 constexpr uint32_t TCOLS = 128;
 constexpr int DS = NB + 1;               // shared-memory row stride of 128-wide blocks
@@ -44,12 +49,13 @@ __device__ __forceinline__ float a_orig(const float* Gt, const double* ob, int P
 }
 
 // ------------------------------------------------------------------------- update (tcgen05)
-__global__ void __launch_bounds__(192, 1) chol_update_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
-                                                             int NT, int jb, float eps, const float* __restrict__ G,
+__global__ void __launch_bounds__(192, 2) chol_update_kernel(const __grid_constant__ CUtensorMap tmap, int t0, int P,
+                                                             int ns, int NT, int jb, float eps,
+                                                             const float* __restrict__ G,
                                                              const double* __restrict__ obar, float* __restrict__ Pn,
                                                              const int* __restrict__ fail, int* status) {
     using namespace tc;
-    const int t = blockIdx.y;
+    const int t = t0 + blockIdx.y;
     if (fail[t]) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -93,10 +99,12 @@ __global__ void __launch_bounds__(192, 1) chol_update_kernel(const __grid_consta
                 }
                 uint8_t* st = smem + s * STAGE;
                 mbar_expect_tx(&full[s], STAGE);
+                // k slice kb covers columns [32 kb, 32 kb + 32) of the 64-column chunk kb / 2
+                const int kx = (kb & 1) * BK, kc = kb >> 1;
                 for (int p = 0; p < NPC; ++p) {
                     const int pl = (t * NPC + p) * NT;
-                    tma_load_4d(st + p * BOX, &tmap, &full[s], 0, 0, kb, pl + (i0 >> 7));
-                    tma_load_4d(st + (NPC + p) * BOX, &tmap, &full[s], 0, 0, kb, pl + (jb >> 7));
+                    tma_load_4d(st + p * BOX, &tmap, &full[s], kx, 0, kc, pl + (i0 >> 7));
+                    tma_load_4d(st + (NPC + p) * BOX, &tmap, &full[s], kx, 0, kc, pl + (jb >> 7));
                 }
                 ++issued;
             }
@@ -122,8 +130,8 @@ __global__ void __launch_bounds__(192, 1) chol_update_kernel(const __grid_consta
                 for (int k = 0; k < BK / 16; ++k)
 #pragma unroll
                     for (int q = 0; q < 6; ++q)
-                        umma(tmem, smem_desc(st + pa[q] * BOX + k * 32), smem_desc(st + (NPC + pb[q]) * BOX + k * 32),
-                             ID, (kb > 0 || k > 0 || q > 0) ? 1u : 0u);
+                        umma(tmem, smem_desc_sw64(st + pa[q] * BOX + k * 32),
+                             smem_desc_sw64(st + (NPC + pb[q]) * BOX + k * 32), ID, (kb > 0 || k > 0 || q > 0) ? 1u : 0u);
                 umma_commit(&empty[s]);
             }
             umma_commit(done);
@@ -194,17 +202,18 @@ __device__ __forceinline__ void store_L(float* Lf, __nv_bfloat16* Lbt, const LbL
 // 32-column sub-blocks: warp 0 factors the 32 x 32 diagonal sub-block in registers with
 // shuffles, all threads solve the sub-panel below and update the trailing part.  Rows and
 // columns beyond nb are padded with the identity.
-__global__ void __launch_bounds__(256, 1) chol_diag_kernel(int P, int LD, int ns, int jb, float eps,
+__global__ void __launch_bounds__(256) chol_diag_kernel(int t0, int P, int LD, int ns, int jb, float eps,
                                                            const float* __restrict__ G,
                                                            const double* __restrict__ obar,
                                                            const float* __restrict__ Pn, float* __restrict__ Lf,
                                                            __nv_bfloat16* __restrict__ Lb, float* __restrict__ Dinv,
                                                            int* __restrict__ fail) {
-    const int t = blockIdx.x;
+    const int t = t0 + blockIdx.x;
     if (fail[t]) return;
     extern __shared__ __align__(16) float dsm[];
-    float* A = dsm;             // [NB][DS] block, then its factor (lower)
-    float* Li = A + NB * DS;    // [NB][DS] inverse
+    float* A = dsm;             // [NB][DS] block, then its factor (lower) and its inverse
+                                // (strictly lower part of the inverse stored transposed above the diagonal)
+    float* lid = A + NB * DS;   // [NB] diagonal of the inverse
     __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nb = min(NB, P - jb);
@@ -279,26 +288,23 @@ __global__ void __launch_bounds__(256, 1) chol_diag_kernel(int P, int LD, int ns
         if (tid == 0) fail[t] = 1;
         return;
     }
-    // inverse of the lower-triangular factor, one column per thread, four partial sums
+    // inverse of the lower-triangular factor, one column per thread, four partial sums;
+    // column c of the inverse is kept in row c above the diagonal (Li[k][c] at A[c][k], k > c)
     if (tid < NB) {
         const int c = tid;
-        for (int i = 0; i < NB; ++i) {
-            float v = 0.f;
-            if (i == c) {
-                v = 1.f / A[i * DS + i];
-            } else if (i > c) {
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                int k = c;
-                for (; k + 3 < i; k += 4) {
-                    s0 = fmaf(A[i * DS + k], Li[k * DS + c], s0);
-                    s1 = fmaf(A[i * DS + k + 1], Li[(k + 1) * DS + c], s1);
-                    s2 = fmaf(A[i * DS + k + 2], Li[(k + 2) * DS + c], s2);
-                    s3 = fmaf(A[i * DS + k + 3], Li[(k + 3) * DS + c], s3);
-                }
-                for (; k < i; ++k) s0 = fmaf(A[i * DS + k], Li[k * DS + c], s0);
-                v = -((s0 + s1) + (s2 + s3)) / A[i * DS + i];
+        const float dc = 1.f / A[c * DS + c];
+        lid[c] = dc;
+        for (int i = c + 1; i < NB; ++i) {
+            float s0 = A[i * DS + c] * dc, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int k = c + 1;
+            for (; k + 3 < i; k += 4) {
+                s0 = fmaf(A[i * DS + k], A[c * DS + k], s0);
+                s1 = fmaf(A[i * DS + k + 1], A[c * DS + k + 1], s1);
+                s2 = fmaf(A[i * DS + k + 2], A[c * DS + k + 2], s2);
+                s3 = fmaf(A[i * DS + k + 3], A[c * DS + k + 3], s3);
             }
-            Li[i * DS + c] = v;
+            for (; k < i; ++k) s0 = fmaf(A[i * DS + k], A[c * DS + k], s0);
+            A[c * DS + i] = -((s0 + s1) + (s2 + s3)) / A[i * DS + i];
         }
     }
     __syncthreads();
@@ -308,19 +314,21 @@ __global__ void __launch_bounds__(256, 1) chol_diag_kernel(int P, int LD, int ns
     float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int i = e / NB, c = e - i * NB;
-        Dv[e] = (i < nb && c < nb) ? Li[i * DS + c] : 0.f;
+        float li = 0.f;
+        if (i < nb && c < nb) li = (i == c) ? lid[c] : (i > c ? A[c * DS + i] : 0.f);
+        Dv[e] = li;
         if (i < nb && c < nb) store_L(Lft, Lbt, lay, LD, jb + i, jb + c, c <= i ? A[i * DS + c] : 0.f);
     }
 }
 
 // Rows below the diagonal block: X = C L_dd^-T, one 64-row tile per CTA; each thread owns
 // 4 rows x 8 columns (register tiling: 12 shared loads per 32 FMAs).
-__global__ void __launch_bounds__(256) chol_trsm_kernel(int P, int LD, int ns, int jb, float eps,
+__global__ void __launch_bounds__(256) chol_trsm_kernel(int t0, int P, int LD, int ns, int jb, float eps,
                                                         const float* __restrict__ G, const double* __restrict__ obar,
                                                         const float* __restrict__ Pn, float* __restrict__ Lf,
                                                         __nv_bfloat16* __restrict__ Lb,
                                                         const float* __restrict__ Dinv, const int* __restrict__ fail) {
-    const int t = blockIdx.y;
+    const int t = t0 + blockIdx.y;
     if (fail[t]) return;
     extern __shared__ __align__(16) float tsm[];
     float* Li = tsm;            // [NB][DS]
@@ -501,7 +509,7 @@ __device__ void block_solve(int P, int LD, const float* Lft, const float* Dv, fl
     }
 }
 
-__global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int P, int LD, int ns, double eps, int refine,
+__global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int t0, int P, int LD, int ns, double eps, int refine,
                                                                const float* __restrict__ G,
                                                                const double* __restrict__ obar,
                                                                const double2* __restrict__ D, const float* __restrict__ Lf,
@@ -509,7 +517,7 @@ __global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int P, int LD, in
                                                                double* __restrict__ xws, double2* __restrict__ delta,
                                                                double* __restrict__ shift_used,
                                                                const int* __restrict__ fail) {
-    const int t = blockIdx.x;
+    const int t = t0 + blockIdx.x;
     if (fail[t]) return;
     extern __shared__ __align__(16) float ssm[];
     float* Db = ssm;              // [NB][DS]
@@ -644,6 +652,32 @@ __global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int P, int LD, in
 
 inline int ldim(int P) { return ((P + 63) / 64) * 64; }
 
+constexpr int CHOL_GROUPS = 4;
+struct GroupStreams {
+    cudaStream_t s[CHOL_GROUPS];
+    cudaEvent_t fork;
+    cudaEvent_t join[CHOL_GROUPS];
+};
+// Streams of the current device for the trajectory groups, created once per device.
+inline GroupStreams& group_streams() {
+    static std::mutex mu;
+    static GroupStreams per_dev[16];
+    static bool made[16] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    GroupStreams& g = per_dev[dev & 15];
+    if (!made[dev & 15]) {
+        for (int i = 0; i < CHOL_GROUPS; ++i) {
+            cudaStreamCreateWithFlags(&g.s[i], cudaStreamNonBlocking);
+            cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming);
+        }
+        cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
+        made[dev & 15] = true;
+    }
+    return g;
+}
+
 }  // namespace chol
 
 size_t chol_tc_ws_bytes(int ntraj, int P) {
@@ -666,10 +700,16 @@ cudaError_t launch_chol_solve_masked(int ntraj, int P, int ns, double eps, const
                                      const double2* D, double2* delta, double* shift_used, float* L, float* y,
                                      double* x, int refine_iters, const int* only, int* status, cudaStream_t s);
 
+static cudaError_t chol_fail(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) set_error(std::string("cholesky: ") + what + ": " + cudaGetErrorString(e));
+    return e;
+}
+
 cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G, const double* obar,
                            const double2* D, double2* delta, double* shift_used, void* ws, int refine_iters,
                            int* status, cudaStream_t s) {
     using namespace chol;
+    set_error("");
     const int LD = ldim(P);
     const size_t nblk = (P + NB - 1) / NB;
     char* p = (char*)ws;
@@ -692,53 +732,84 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     CUtensorMap map;
     const cuuint64_t dims[4] = {64u, 128u, (cuuint64_t)KB, (cuuint64_t)ntraj * NPC * NT};
     const cuuint64_t strides[3] = {128u, 128u * 128u, (cuuint64_t)KB * 128u * 128u};
-    const cuuint32_t box[4] = {64u, 128u, 1u, 1u};
+    const cuuint32_t box[4] = {(cuuint32_t)BK, 128u, 1u, 1u};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)Lb, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    const CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)Lb, dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+        char buf[256];
+        snprintf(buf, sizeof(buf),
+                 "cholesky: cuTensorMapEncodeTiled returned %d (addr %p dims %llu %llu %llu %llu strides %llu %llu "
+                 "%llu box %u %u)",
+                 (int)cr, (void*)Lb, (unsigned long long)dims[0], (unsigned long long)dims[1],
+                 (unsigned long long)dims[2], (unsigned long long)dims[3], (unsigned long long)strides[0],
+                 (unsigned long long)strides[1], (unsigned long long)strides[2], box[0], box[1]);
+        set_error(buf);
         return cudaErrorInvalidValue;
+    }
 
     cudaError_t e = cudaMemsetAsync(fail, 0, (size_t)ntraj * 4, s);
-    if (e != cudaSuccess) return e;
-    const int dsmem = 2 * NB * DS * (int)sizeof(float);
+    if (e != cudaSuccess) return chol_fail(e, "memset");
+    const int dsmem = (NB * DS + NB) * (int)sizeof(float);
     const int tsmem = (NB + RT) * DS * (int)sizeof(float);
     e = cudaFuncSetAttribute(chol_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return chol_fail(e, "diag attribute");
     e = cudaFuncSetAttribute(chol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return chol_fail(e, "trsm attribute");
     e = cudaFuncSetAttribute(chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_U);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return chol_fail(e, "update attribute");
     const float feps = (float)eps;
-    for (int jb = 0; jb < P; jb += NB) {
-        if (jb > 0) {
-            ProfScope pu(OTVMC_K_CHOLU, s);
-            dim3 grid((P - jb + 127) / 128, ntraj);
-            chol_update_kernel<<<grid, 192, SMEM_U, s>>>(map, P, ns, NT, jb, feps, G, obar, Pn, fail, status);
-            count_launch();
-        }
-        {
-            ProfScope pd(OTVMC_K_CHOLD, s);
-            chol_diag_kernel<<<ntraj, 256, dsmem, s>>>(P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
-            count_launch();
-        }
-        const int nrows = P - jb - min(NB, P - jb);
-        if (nrows > 0) {
-            ProfScope pp(OTVMC_K_CHOLP, s);
-            dim3 grid((nrows + RT - 1) / RT, ntraj);
-            chol_trsm_kernel<<<grid, 256, tsmem, s>>>(P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
-            count_launch();
-        }
-    }
-    ProfScope ps(OTVMC_K_SOLVE, s);
     const int ssmem = (NB * DS + 2 * NB + 2 * P + 4 * P + 8 * 256 * 2 * 2) * (int)sizeof(float);
     e = cudaFuncSetAttribute(chol_solve_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem);
-    if (e != cudaSuccess) return e;
-    chol_solve_tc_kernel<<<ntraj, 256, ssmem, s>>>(P, LD, ns, eps, refine_iters, G, obar, D, Lf, Dv, x, delta,
-                                                    shift_used, fail);
-    count_launch();
+    if (e != cudaSuccess) return chol_fail(e, "solve attribute");
+    // trajectory groups on forked streams: one group's latency-bound kernels overlap the
+    // others' (fork and join by events, so the call stays ordered on `s`)
+    const int ng = ntraj >= 16 ? CHOL_GROUPS : 1;
+    GroupStreams& gs = group_streams();
+    if (ng > 1) {
+        e = cudaEventRecord(gs.fork, s);
+        if (e != cudaSuccess) return chol_fail(e, "fork record");
+    }
+    for (int g = 0; g < ng; ++g) {
+        const int ta = (int)((long long)ntraj * g / ng), tb = (int)((long long)ntraj * (g + 1) / ng);
+        const int nt = tb - ta;
+        if (nt <= 0) continue;
+        cudaStream_t gsm = ng > 1 ? gs.s[g] : s;
+        if (ng > 1 && (e = cudaStreamWaitEvent(gsm, gs.fork, 0)) != cudaSuccess) return e;
+        for (int jb = 0; jb < P; jb += NB) {
+            if (jb > 0) {
+                ProfScope pu(OTVMC_K_CHOLU, gsm);
+                dim3 grid((P - jb + 127) / 128, nt);
+                chol_update_kernel<<<grid, 192, SMEM_U, gsm>>>(map, ta, P, ns, NT, jb, feps, G, obar, Pn, fail, status);
+                count_launch();
+            }
+            {
+                ProfScope pd(OTVMC_K_CHOLD, gsm);
+                chol_diag_kernel<<<nt, 256, dsmem, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
+                count_launch();
+            }
+            const int nrows = P - jb - min(NB, P - jb);
+            if (nrows > 0) {
+                ProfScope pp(OTVMC_K_CHOLP, gsm);
+                dim3 grid((nrows + RT - 1) / RT, nt);
+                chol_trsm_kernel<<<grid, 256, tsmem, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
+                count_launch();
+            }
+        }
+        {
+            ProfScope ps(OTVMC_K_SOLVE, gsm);
+            chol_solve_tc_kernel<<<nt, 256, ssmem, gsm>>>(ta, P, LD, ns, eps, refine_iters, G, obar, D, Lf, Dv, x,
+                                                           delta, shift_used, fail);
+            count_launch();
+        }
+        if (ng > 1) {
+            if ((e = cudaEventRecord(gs.join[g], gsm)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, gs.join[g], 0)) != cudaSuccess) return e;
+        }
+    }
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return chol_fail(e, "kernel launch");
     // trajectories whose pivot failed: robust solver with shift retries (exits at once for the others)
     return launch_chol_solve_masked(ntraj, P, ns, eps, G, obar, D, delta, shift_used, Lf, yf, x, refine_iters, fail,
                                     status, s);

@@ -69,6 +69,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;             // 128-byte swizzle
     return d;
 }
+// Same, 64-byte swizzle: rows of 64 bytes, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
 // Instruction descriptor, kind::f16: D F32, A/B BF16, both K-major, N >> 3, M >> 4.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -108,7 +118,7 @@ inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     std::call_once(once, [] {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, CUDART_VERSION, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
