@@ -168,6 +168,28 @@ OTVMC_API otvmc_status otvmc_local_estimators(const otvmc_ansatz* ansatz, const 
                                     double* Eeff_d, double* v_d, double* lpl_d,
                                     void* work_d, size_t work_bytes, void* stream);
 
+/* Allocation-free variant of otvmc_local_estimators (the paper has no counterpart: this is
+ * an interface for callers that cannot give the library scratch memory -- code whose device
+ * memory belongs to a memory manager with a hard budget it may not allocate outside of, or a
+ * latency-sensitive loop where an allocation, which can synchronise the device, is not
+ * acceptable).  Same inputs, outputs and results as otvmc_local_estimators, but no work_d:
+ * the scratch is a fixed 32 MiB array inside this library's device memory, held by every GPU
+ * that loads the library until the process exits.  Nothing is allocated by this call.
+ *   - Batches whose scratch would exceed 32 MiB are rejected with OTVMC_ERR_WORKSPACE before
+ *     anything is launched (about ntraj * ns * N * 16 bytes plus small tables).
+ *   - status_d (optional device int, caller-cleared) receives device-side errors such as
+ *     OTVMC_ERR_RANGE, as the workspace status word does for the other entry points.
+ *   - All calls share the one array: calls that overlap on the GPU (different streams or
+ *     threads without ordering) race and give wrong results; order them on one stream.
+ *     The array keeps the last call's contents; nothing in it needs to start at zero.
+ *   - The first call on each device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture. */
+OTVMC_API otvmc_status otvmc_local_estimators_noalloc(const otvmc_ansatz* ansatz, const double* theta_d,
+                                                      const uint64_t* spins_d, int ntraj, int ns,
+                                                      const double* dW_d, double dt, int precision,
+                                                      double* Eeff_d, double* v_d, double* lpl_d,
+                                                      int* status_d, void* stream);
+
 /* --------------------------------------------------------------- A4 + A6: S and D
  * S = <O^* O> - <O^*><O>, D = <O^* v> - <O^*><v> over the ns samples (definitions after
  * Eq. 8; D = -i F dt + sum_n N^n dW_n by linearity).  Jastrow: O is real (+-1), S real

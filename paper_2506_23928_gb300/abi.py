@@ -59,6 +59,7 @@ SIGNATURES = {
     "otvmc_init_chains": (c_int, [P, c_int, c_int, c_int, c_uint64, P, P]),
     "otvmc_sample": (c_int, [P, P, c_int, c_int, c_int, c_int, c_uint64, c_int64, P, P, P, c_size_t, P]),
     "otvmc_local_estimators": (c_int, [P, P, P, c_int, c_int, P, c_double, c_int, P, P, P, P, c_size_t, P]),
+    "otvmc_local_estimators_noalloc": (c_int, [P, P, P, c_int, c_int, P, c_double, c_int, P, P, P, P, P]),
     "otvmc_build_S_F": (c_int, [P, P, P, P, c_int, c_int, c_int, P, P, P, P, P, c_size_t, P]),
     "otvmc_solve_step": (c_int, [P, c_int, c_int, c_int, c_int, c_double, c_double, P, P, P, P, P, P, P, c_size_t,
                                  P]),
@@ -186,6 +187,12 @@ def otvmc_local_estimators(ansatz, theta_d, spins_d, ntraj, ns, dW_d, dt, precis
                            work_bytes, stream=None):
     return _call("otvmc_local_estimators", ansatz, ptr(theta_d), ptr(spins_d), ntraj, ns, ptr(dW_d), dt, precision,
                  ptr(Eeff_d), ptr(v_d), ptr(lpl_d), ptr(work_d), work_bytes, stream_ptr(stream))
+
+
+def otvmc_local_estimators_noalloc(ansatz, theta_d, spins_d, ntraj, ns, dW_d, dt, precision, Eeff_d, v_d, lpl_d,
+                                   status_d, stream=None):
+    return _call("otvmc_local_estimators_noalloc", ansatz, ptr(theta_d), ptr(spins_d), ntraj, ns, ptr(dW_d), dt,
+                 precision, ptr(Eeff_d), ptr(v_d), ptr(lpl_d), ptr(status_d), stream_ptr(stream))
 
 
 def otvmc_build_S_F(ansatz, theta_d, spins_d, v_d, ntraj, ns, precision, S_d, G_d, obar_d, D_d, work_d, work_bytes,
