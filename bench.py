@@ -30,6 +30,10 @@ METRIC = "trajectory-steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one gram_tc_kernel launch per trajectory at this workload, from
+# the ncu capture summarised in profiles/gram_tc_chain64_32traj.md (798.5 MB for 32 trajectories;
+# traffic grows in proportion to the trajectories of a launch).
+GRAM_DRAM_BYTES_PER_TRAJ = 798.5e6 / 32
 
 
 def parse():
@@ -276,24 +280,42 @@ def main():
     dominant = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     ns = w.ns
     roof = {}
-    # algorithmic work per launch (one evaluation of the batch)
-    gram_flops = 2.0 * ns * P * (P + 1) / 2 * T                       # symmetric half of G = O^T O
-    solve_flops = (P ** 3 / 3.0 + 2 * 2 * 2 * P ** 2 * 2) * T         # factor + 2 RHS x (fwd+bwd) x (1 + refine)
-    if "gram" in prof:
-        ms, cnt = prof["gram"]
-        ach = gram_flops / (ms / cnt / 1000.0) / 1e12
-        peak = pk["bf16_tflops_sustained"]
-        roof["gram"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                        "traffic": None, "peak_kind": f"bf16 sustained, {pk_kind}"}
-    if "solve" in prof:
-        ms, cnt = prof["solve"]
-        ach = solve_flops / (ms / cnt / 1000.0) / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof["solve"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": None, "peak_kind": "fp32 SIMT: 152 SMs x 128 lanes x 2 x max SM clock"}
+    evals = 2 * args.steps                                            # evaluations per trajectory in the timed region
+    NBK = 128
+    jbs = list(range(0, P, NBK))
+    # algorithmic work per trajectory-evaluation of each kernel class
+    work = {
+        # useful tensor flops of G = O^T O (upper triangle incl. diagonal)
+        "gram": ("tensor", 2.0 * ns * P * (P + 1) / 2),
+        # BF16 tensor flops of the Cholesky block-column updates: six BF16 products per FP32 product
+        "chol_update": ("tensor", 6 * 2.0 * sum((P - jb) * NBK * jb for jb in jbs if jb > 0)),
+        # FP32 flops of the panel solves X = C L_dd^-T (triangular: 128*129/2 multiply-adds per row)
+        "chol_trsm": ("alu", 2.0 * sum(max(0, P - jb - NBK) * NBK * (NBK + 1) / 2 for jb in jbs)),
+        # bytes the triangular solves and the refinement residual must read: the strictly lower
+        # factor (FP32) for four triangular passes and the upper Gram counts (FP32) twice
+        "solve": ("hbm", (4 + 2) * 4.0 * P * P / 2),
+    }
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    for cls, (bound, per_eval) in work.items():
+        if cls not in prof:
+            continue
+        ms, cnt = prof[cls]
+        total = per_eval * T * evals
+        if bound == "tensor":
+            ach, peak, unit = total / (ms / 1000.0) / 1e12, pk["bf16_tflops_sustained"], "TFLOP/s"
+            kind = f"bf16 sustained, {pk_kind}"
+        elif bound == "alu":
+            ach, peak, unit = total / (ms / 1000.0) / 1e12, fp32_peak, "TFLOP/s"
+            kind = "fp32 SIMT: 152 SMs x 128 lanes x 2 x max SM clock (derived)"
+        else:
+            ach, peak, unit = total / (ms / 1000.0) / 1e9, pk["hbm_gbs"], "GB/s"
+            kind = f"HBM copy, {pk_kind}"
+        traffic = GRAM_DRAM_BYTES_PER_TRAJ * T if (cls == "gram" and w.name == "chain64_jastrow") else None
+        roof[cls] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                     "traffic": traffic, "peak_kind": kind, "launches": cnt, "ms_total": ms}
+    # the dominant kernel class among those with a roofline (largest total event time)
+    dominant = max(roof, key=lambda k: roof[k]["ms_total"]) if roof else dominant
     rl = roof.get(dominant)
-    if rl is None and roof:
-        rl = next(iter(roof.values()))
 
     fp64 = None
     if not args.no_fp64_path and prec == abi.OTVMC_PREC_MIXED:
