@@ -291,9 +291,12 @@ def main():
         "chol_update": ("tensor", 6 * 2.0 * sum((P - jb) * NBK * jb for jb in jbs if jb > 0)),
         # FP32 flops of the panel solves X = C L_dd^-T (triangular: 128*129/2 multiply-adds per row)
         "chol_trsm": ("alu", 2.0 * sum(max(0, P - jb - NBK) * NBK * (NBK + 1) / 2 for jb in jbs)),
-        # bytes the triangular solves and the refinement residual must read: the strictly lower
-        # factor (FP32) for four triangular passes and the upper Gram counts (FP32) twice
-        "solve": ("hbm", (4 + 2) * 4.0 * P * P / 2),
+        # bytes the triangular substitutions must read: the lower factor (FP32) once for the
+        # backward pass after the factorization (its forward pass is fused into it) and twice
+        # for the correction of the refinement step
+        "solve": ("hbm", 3 * 4.0 * P * P / 2),
+        # bytes of the refinement residual: the upper triangle of the Gram counts (FP32) once
+        "chol_resid": ("hbm", 4.0 * P * (P + 1) / 2),
     }
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     for cls, (bound, per_eval) in work.items():

@@ -306,13 +306,14 @@ enum {
     OTVMC_K_OBUILD = 7,  /* O in BF16 / FP64 */
     OTVMC_K_GRAM = 8,    /* tensor-core Gram G = O^T O */
     OTVMC_K_SYRK = 9,    /* FP64 S (plain path) */
-    OTVMC_K_SOLVE = 10,  /* Cholesky solve (FP64 path) / triangular solves and refinement */
+    OTVMC_K_SOLVE = 10,  /* Cholesky solve (FP64 path) / triangular substitutions and refinement */
     OTVMC_K_SDE = 11,    /* predictor-corrector combination */
     OTVMC_K_NOISE = 12,  /* Wiener increments, chain initialisation */
     OTVMC_K_CHOLU = 13,  /* tensor-core block-column update of the Cholesky factorization */
     OTVMC_K_CHOLP = 14,  /* panel rows below the diagonal block (X = C L_dd^-T) */
     OTVMC_K_CHOLD = 15,  /* diagonal-block factor and inverse */
-    OTVMC_K_CLASSES = 16
+    OTVMC_K_RESID = 16,  /* refinement residual G x, tile-parallel */
+    OTVMC_K_CLASSES = 17
 };
 OTVMC_API void otvmc_profile_enable(int on);
 /* Synchronises the recorded events; total milliseconds and launch count of one class. */

@@ -26,7 +26,7 @@ OTVMC_REG_SHIFT, OTVMC_REG_SNR = 0, 1
 OTVMC_HEUN, OTVMC_MIDPOINT = 0, 1
 OTVMC_MOMENTS = 9
 KERNEL_CLASSES = ["sample", "prep", "est1", "est2", "reduce", "obs", "D", "obuild", "gram", "syrk", "solve", "sde",
-                  "noise", "chol_update", "chol_trsm", "chol_diag"]
+                  "noise", "chol_update", "chol_trsm", "chol_diag", "chol_resid"]
 
 c_int, c_int64, c_uint64, c_double, c_size_t, c_void_p = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
                                                          ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p)

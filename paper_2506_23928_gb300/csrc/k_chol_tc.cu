@@ -8,14 +8,17 @@
 //           products h.h + h.m + m.h + h.l + m.m + l.h accumulate in FP32 in TMEM, which
 //           gives FP32-level accuracy.  One CTA = 128 rows x 128 columns of one trajectory;
 //           32-column k slices (64-byte swizzle) in a 2-stage ring, two CTAs per SM.
-//   diag    (SIMT)     factor the 128 x 128 diagonal block in shared memory (32-column
-//           sub-blocks, shuffle-based leaf factor) and invert it;
+//   diag    (SIMT)     factor the 128 x 128 diagonal block and invert its factor in one pass of
+//           right-looking elimination over register-held 8 x 8 tiles;
 //   trsm    (SIMT)     the rows below as a register-tiled GEMM X = C L_dd^-T, one 64-row tile
 //           per CTA; both write L in FP32 (for the triangular solves) and as BF16 pieces
 //           (for later updates), and the diagonal kernel writes L_dd^-1.
-// solve     (SIMT)     forward/backward substitution by blocks through the stored inverses,
-//           then one step of iterative refinement with the residual D - (S + eps I) x formed
-//           in FP64 from the exact Gram counts (S = G/ns - obar obar^T).
+//   The forward substitution L y = D rides along: diag applies L_dd^-1 to its block of the
+//   right-hand side, trsm subtracts the block's contribution from the rows below.
+// solve     (SIMT)     backward substitution x = L^-T y by blocks through the stored inverses,
+//           then iterative refinement: the residual D - (S + eps I) x from the exact Gram
+//           counts (S = G/ns - obar obar^T) in double-float arithmetic, tile-parallel over
+//           many CTAs, and one more forward and backward substitution for the correction.
 // A trajectory whose pivot is not positive is marked and solved again by the single-CTA
 // solver, which raises the shift (x100, at most three times).
 #include <cuda_bf16.h>
@@ -38,7 +41,6 @@ constexpr int STAGE = 2 * NPC * BOX;     // A pieces + B pieces: 48 KB
 constexpr int STAGES = 2;                // about 97 KB of shared memory: two CTAs per SM
 constexpr int SMEM_U = STAGES * STAGE + 1024 + 256;
 constexpr uint32_t TCOLS = 128;
-constexpr int DS = NB + 1;               // shared-memory row stride of 128-wide blocks
 constexpr int RT = 64;                   // panel rows per tile
 
 __device__ __forceinline__ float a_orig(const float* Gt, const double* ob, int P, float inv_ns, int i, int j,
@@ -185,469 +187,812 @@ struct LbLayout {
     }
 };
 
-__device__ __forceinline__ void store_L(float* Lf, __nv_bfloat16* Lbt, const LbLayout& lay, int LD, int i, int k,
-                                        float x) {
-    Lf[(size_t)i * LD + k] = x;
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(m);
-    const size_t idx = lay.at(i, k), pl = lay.plane();
-    Lbt[idx] = h;
-    Lbt[pl + idx] = m;
-    Lbt[2 * pl + idx] = __float2bfloat16_rn(r2);
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// Diagonal block of block column jb: Cholesky factor and its inverse (one CTA per trajectory).
-// 32-column sub-blocks: warp 0 factors the 32 x 32 diagonal sub-block in registers with
-// shuffles, all threads solve the sub-panel below and update the trailing part.  Rows and
-// columns beyond nb are padded with the identity.
-__global__ void __launch_bounds__(256) chol_diag_kernel(int t0, int P, int LD, int ns, int jb, float eps,
-                                                           const float* __restrict__ G,
-                                                           const double* __restrict__ obar,
-                                                           const float* __restrict__ Pn, float* __restrict__ Lf,
-                                                           __nv_bfloat16* __restrict__ Lb, float* __restrict__ Dinv,
-                                                           int* __restrict__ fail) {
+// Eight consecutive entries L[i][k0 .. k0+8) (k0 a multiple of 8): FP32 copy for the
+// triangular solves and the three BF16 pieces h + m + l for the tensor-core updates.
+// Only the first nv entries are in the matrix.
+__device__ __forceinline__ void store_L8(float* Lft, __nv_bfloat16* Lbt, const LbLayout& lay, int LD, int i, int k0,
+                                         const float (&v)[8], int nv) {
+    __nv_bfloat16 hp[8], mp[8], lp[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        hp[u] = __float2bfloat16_rn(v[u]);
+        const float r1 = v[u] - __bfloat162float(hp[u]);
+        mp[u] = __float2bfloat16_rn(r1);
+        lp[u] = __float2bfloat16_rn(r1 - __bfloat162float(mp[u]));
+    }
+    const size_t idx = lay.at(i, k0), pl = lay.plane();
+    float* dst = Lft + (size_t)i * LD + k0;
+    if (nv >= 8) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+        *reinterpret_cast<uint4*>(Lbt + idx) = make_uint4(pack_bf16x2(hp[0], hp[1]), pack_bf16x2(hp[2], hp[3]),
+                                                          pack_bf16x2(hp[4], hp[5]), pack_bf16x2(hp[6], hp[7]));
+        *reinterpret_cast<uint4*>(Lbt + pl + idx) = make_uint4(pack_bf16x2(mp[0], mp[1]), pack_bf16x2(mp[2], mp[3]),
+                                                               pack_bf16x2(mp[4], mp[5]), pack_bf16x2(mp[6], mp[7]));
+        *reinterpret_cast<uint4*>(Lbt + 2 * pl + idx) = make_uint4(
+            pack_bf16x2(lp[0], lp[1]), pack_bf16x2(lp[2], lp[3]), pack_bf16x2(lp[4], lp[5]), pack_bf16x2(lp[6], lp[7]));
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (u < nv) {
+                dst[u] = v[u];
+                Lbt[idx + u] = hp[u];
+                Lbt[pl + idx + u] = mp[u];
+                Lbt[2 * pl + idx + u] = lp[u];
+            }
+    }
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float s) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
+}
+
+// Sum over the 32 lanes of eight values per lane in 9 shuffles (each step halves the values a
+// lane keeps).  Lane l ends with the total of value 4 b4 + 2 b3 + b2, where b4 b3 b2 are bits
+// 4, 3, 2 of l; the four lanes that differ in bits 0 and 1 hold the same total.
+__device__ __forceinline__ float reduce8(float (&v)[8], int lane) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const bool up = lane & 16;
+        const float send = up ? v[u] : v[u + 4];
+        const float keep = up ? v[u + 4] : v[u];
+        v[u] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const bool up = lane & 8;
+        const float send = up ? v[u] : v[u + 2];
+        const float keep = up ? v[u + 2] : v[u];
+        v[u] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const bool up = lane & 4;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+__device__ __forceinline__ int reduce8_index(int lane) {
+    return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+// ----------------------------------------------------------------------- diagonal block
+// Cholesky factor of the 128 x 128 diagonal block of block column jb and the inverse of that
+// factor, in one pass of right-looking elimination over its 128 columns; one CTA per
+// trajectory.  The block is held in registers as 8 x 8 tiles: threads 0..135 own the 136
+// lower tiles of A (becoming L), threads 136..271 the lower tiles of X (starting at I,
+// becoming L^-1).  Step m publishes column m of A and row m of X through shared memory,
+// then every tile applies its rank-one update:
+//     A[i][j] -= A[i][m] A[j][m] / A[m][m]      (i, j > m)
+//     X[i][j] -= A[i][m] X[m][j] / A[m][m]      (i > m)
+// with L[i][m] = A[i][m] / sqrt(A[m][m]) and (L^-1)[m][j] = X[m][j] / sqrt(A[m][m]).
+// The forward substitution of the solve is fused in: the block's right-hand sides (D for
+// the first block, else the running residual that the TRSM kernels of earlier block
+// columns left behind) are multiplied by L_dd^-1 here.  Rows and columns beyond nb are
+// padded with the identity.
+constexpr int T8 = NB / 8;                  // 16 tile rows
+constexpr int NTRI8 = T8 * (T8 + 1) / 2;    // 136 lower tiles
+constexpr int DIAG_THREADS = 288;
+
+__device__ __forceinline__ void tri8_index(int q, int& bi, int& bj) {
+    int b = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+    while ((b + 1) * (b + 2) / 2 <= q) ++b;
+    while (b * (b + 1) / 2 > q) --b;
+    bi = b;
+    bj = q - b * (b + 1) / 2;
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, int LD, int ns, int jb, float eps,
+                                                                    const float* __restrict__ G,
+                                                                    const double* __restrict__ obar,
+                                                                    const double2* __restrict__ D,
+                                                                    const float* __restrict__ Pn, float* __restrict__ Lf,
+                                                                    __nv_bfloat16* __restrict__ Lb,
+                                                                    float* __restrict__ Dinv, float* __restrict__ yv,
+                                                                    int* __restrict__ fail) {
     const int t = t0 + blockIdx.x;
     if (fail[t]) return;
-    extern __shared__ __align__(16) float dsm[];
-    float* A = dsm;             // [NB][DS] block, then its factor (lower) and its inverse
-                                // (strictly lower part of the inverse stored transposed above the diagonal)
-    float* lid = A + NB * DS;   // [NB] diagonal of the inverse
-    __shared__ int bad;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ float colbuf[2][NB], rowbuf[2][NB], rhs[2][NB];
+    __shared__ float fpart[NTRI8][8][2];
+    const int tid = threadIdx.x;
     const int nb = min(NB, P - jb);
-    const float* Gt = G + (size_t)t * P * P;
-    const double* ob = obar + (size_t)t * P;
-    const float inv_ns = 1.0f / (float)ns;
-    if (tid == 0) bad = 0;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int i = e / NB, c = e - i * NB;
+    const bool isA = tid < NTRI8, isX = tid >= NTRI8 && tid < 2 * NTRI8;
+    int bi = 0, bj = 0;
+    if (isA || isX) tri8_index(isA ? tid : tid - NTRI8, bi, bj);
+    float* yt = yv + (size_t)t * 2 * P;
+    const double2* Dt = D + (size_t)t * P;
+    if (tid < 2 * NB) {
+        const int h = tid >> 7, i = tid & (NB - 1);
         float v = 0.f;
-        if (i < nb && c < nb) {
-            if (c <= i) v = jb == 0 ? a_orig(Gt, ob, P, inv_ns, jb + i, jb + c, eps) : Pn[((size_t)t * P + jb + i) * NB + c];
-        } else if (i == c) {
-            v = 1.f;
-        }
-        A[i * DS + c] = v;
+        if (i < nb) v = jb == 0 ? (float)(h ? Dt[i].y : Dt[i].x) : yt[h * P + jb + i];
+        rhs[h][i] = v;
     }
-    __syncthreads();
-    for (int k0 = 0; k0 < NB; k0 += 32) {
-        if (warp == 0) {
-            float r[32];
+    if (jb == 0)
+        for (int k = NB + tid; k < P; k += blockDim.x) {
+            const double2 d = Dt[k];
+            yt[k] = (float)d.x;
+            yt[P + k] = (float)d.y;
+        }
+
+    float a[8][8];
+    if (isA) {
+        if (jb == 0) {
+            const float* Gt = G + (size_t)t * P * P;
+            const double* ob = obar + (size_t)t * P;
+            const float inv_ns = 1.0f / (float)ns;
+            float obi[8], obj[8];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) r[c] = A[(k0 + lane) * DS + k0 + c];
-            bool ok = true;
+            for (int r = 0; r < 8; ++r) {
+                const int i = bi * 8 + r, j = bj * 8 + r;
+                obi[r] = i < nb ? (float)ob[i] : 0.f;
+                obj[r] = j < nb ? (float)ob[j] : 0.f;
+            }
 #pragma unroll
-            for (int p = 0; p < 32; ++p) {
-                const float d = __shfl_sync(0xffffffffu, r[p], p);
-                ok = ok && (d > 0.f) && isfinite(d);
-                const float sd = sqrtf(fmaxf(d, 1e-30f));
-                if (lane == p) r[p] = sd;
-                if (lane > p) r[p] /= sd;
-                const float colp = r[p];
+            for (int r = 0; r < 8; ++r)
 #pragma unroll
-                for (int c = p + 1; c < 32; ++c) {
-                    const float lcp = __shfl_sync(0xffffffffu, colp, c);
-                    if (lane >= c) r[c] = fmaf(-colp, lcp, r[c]);
+                for (int c = 0; c < 8; ++c) {
+                    const int i = bi * 8 + r, j = bj * 8 + c;
+                    float v = i == j ? 1.f : 0.f;
+                    if (i < nb && j < nb && j <= i) {
+                        v = Gt[(size_t)j * P + i] * inv_ns - obi[r] * obj[c];
+                        if (i == j) v += eps;
+                    }
+                    a[r][c] = v;
+                }
+        } else {
+            const float* prow = Pn + ((size_t)t * P + jb + bi * 8) * NB + bj * 8;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+                if (bi * 8 + r < nb) {
+                    lo = ld4(prow + (size_t)r * NB);
+                    hi = ld4(prow + (size_t)r * NB + 4);
+                }
+                a[r][0] = lo.x; a[r][1] = lo.y; a[r][2] = lo.z; a[r][3] = lo.w;
+                a[r][4] = hi.x; a[r][5] = hi.y; a[r][6] = hi.z; a[r][7] = hi.w;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int i = bi * 8 + r, j = bj * 8 + c;
+                    if (i >= nb || j >= nb) a[r][c] = i == j ? 1.f : 0.f;
+                    else if (j > i) a[r][c] = 0.f;
+                }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) a[r][c] = (bi == bj && r == c) ? 1.f : 0.f;
+    }
+
+    bool ok = true;
+#pragma unroll 1
+    for (int bm = 0; bm < T8; ++bm) {
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+            const int m = bm * 8 + mm;
+            float* cb = colbuf[mm & 1];
+            float* rb = rowbuf[mm & 1];
+            if (isA && bj == bm) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) cb[bi * 8 + r] = a[r][mm];
+            }
+            if (isX && bi == bm) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) rb[bj * 8 + c] = a[mm][c];
+            }
+            __syncthreads();
+            const float d = cb[m];
+            ok = ok && d > 0.f && isfinite(d);
+            const float dd = ok ? d : 1.f;
+            const float isd = 1.0f / sqrtf(dd), id = 1.0f / dd;
+            if (isA && bj >= bm) {
+                float li[8], lj[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = bi * 8 + r;
+                    li[r] = i > m ? cb[i] * id : 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int j = bj * 8 + c;
+                    lj[c] = j > m ? cb[j] : 0.f;
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-li[r], lj[c], a[r][c]);
+                if (bj == bm) {
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+                        if (bi * 8 + r >= m) a[r][mm] = cb[bi * 8 + r] * isd;
                 }
             }
+            if (isX && bi >= bm && bj <= bm) {
+                float li[8], xm[8];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) A[(k0 + lane) * DS + k0 + c] = (c <= lane) ? r[c] : 0.f;
-            if (lane == 0 && !ok) bad = 1;
-        }
-        __syncthreads();
-        if (bad) break;
-        // sub-panel rows below: X L_kk^T = A
-        for (int i = k0 + 32 + tid; i < NB; i += blockDim.x) {
-            float x[32];
+                for (int r = 0; r < 8; ++r) {
+                    const int i = bi * 8 + r;
+                    li[r] = i > m ? cb[i] * id : 0.f;
+                }
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                float a = A[i * DS + k0 + c];
+                for (int c = 0; c < 8; ++c) xm[c] = rb[bj * 8 + c];
 #pragma unroll
-                for (int k = 0; k < c; ++k) a = fmaf(-x[k], A[(k0 + c) * DS + k0 + k], a);
-                x[c] = a / A[(k0 + c) * DS + k0 + c];
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-li[r], xm[c], a[r][c]);
+                if (bi == bm) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) a[mm][c] = xm[c] * isd;
+                }
             }
-#pragma unroll
-            for (int c = 0; c < 32; ++c) A[i * DS + k0 + c] = x[c];
         }
-        __syncthreads();
-        // trailing update A[i][j] -= X[i] . X[j] for k0+32 <= j <= i
-        const int m = NB - k0 - 32;
-        for (int e = tid; e < m * m; e += blockDim.x) {
-            const int i = k0 + 32 + e / m, j = k0 + 32 + e % m;
-            if (j > i) continue;
-            float a = A[i * DS + j];
-#pragma unroll 8
-            for (int k = 0; k < 32; ++k) a = fmaf(-A[i * DS + k0 + k], A[j * DS + k0 + k], a);
-            A[i * DS + j] = a;
-        }
-        __syncthreads();
     }
-    if (bad) {
+    // every thread saw the same pivots, so this exit is uniform
+    if (!ok) {
         if (tid == 0) fail[t] = 1;
         return;
     }
-    // inverse of the lower-triangular factor, one column per thread, four partial sums;
-    // column c of the inverse is kept in row c above the diagonal (Li[k][c] at A[c][k], k > c)
-    if (tid < NB) {
-        const int c = tid;
-        const float dc = 1.f / A[c * DS + c];
-        lid[c] = dc;
-        for (int i = c + 1; i < NB; ++i) {
-            float s0 = A[i * DS + c] * dc, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int k = c + 1;
-            for (; k + 3 < i; k += 4) {
-                s0 = fmaf(A[i * DS + k], A[c * DS + k], s0);
-                s1 = fmaf(A[i * DS + k + 1], A[c * DS + k + 1], s1);
-                s2 = fmaf(A[i * DS + k + 2], A[c * DS + k + 2], s2);
-                s3 = fmaf(A[i * DS + k + 3], A[c * DS + k + 3], s3);
+    const LbLayout lay{(P + NB - 1) / NB, LD / 64};
+    if (isA) {
+        float* Lft = Lf + (size_t)t * P * LD;
+        __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
+        const int nv = nb - bj * 8;
+        if (nv > 0) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int i = bi * 8 + r;
+                if (i >= nb) break;
+                float v[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c] = (bi == bj && c > r) ? 0.f : a[r][c];
+                store_L8(Lft, Lbt, lay, LD, jb + i, jb + bj * 8, v, nv);
             }
-            for (; k < i; ++k) s0 = fmaf(A[i * DS + k], A[c * DS + k], s0);
-            A[c * DS + i] = -((s0 + s1) + (s2 + s3)) / A[i * DS + i];
+        }
+    }
+    if (isX) {
+        float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
+        const int q = tid - NTRI8;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = bi * 8 + r;
+            float v[8];
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = bj * 8 + c;
+                v[c] = (i < nb && j < nb) ? a[r][c] : 0.f;
+                s0 = fmaf(v[c], rhs[0][j], s0);
+                s1 = fmaf(v[c], rhs[1][j], s1);
+            }
+            float4* dst = reinterpret_cast<float4*>(Dv + (size_t)i * NB + bj * 8);
+            dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+            dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+            if (bi != bj) {
+                float4* up = reinterpret_cast<float4*>(Dv + (size_t)(bj * 8 + r) * NB + bi * 8);
+                up[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                up[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            fpart[q][r][0] = s0;
+            fpart[q][r][1] = s1;
         }
     }
     __syncthreads();
-    const LbLayout lay{(P + NB - 1) / NB, LD / 64};
-    float* Lft = Lf + (size_t)t * P * LD;
-    __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
-    float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int i = e / NB, c = e - i * NB;
-        float li = 0.f;
-        if (i < nb && c < nb) li = (i == c) ? lid[c] : (i > c ? A[c * DS + i] : 0.f);
-        Dv[e] = li;
-        if (i < nb && c < nb) store_L(Lft, Lbt, lay, LD, jb + i, jb + c, c <= i ? A[i * DS + c] : 0.f);
+    if (tid < 2 * NB) {
+        const int h = tid >> 7, i = tid & (NB - 1), b = i >> 3, r = i & 7;
+        float s = 0.f;
+        for (int c = 0; c <= b; ++c) s += fpart[b * (b + 1) / 2 + c][r][h];
+        if (i < nb) yt[h * P + jb + i] = s;
     }
 }
 
-// Rows below the diagonal block: X = C L_dd^-T, one 64-row tile per CTA; each thread owns
-// 4 rows x 8 columns (register tiling: 12 shared loads per 32 FMAs).
-__global__ void __launch_bounds__(256) chol_trsm_kernel(int t0, int P, int LD, int ns, int jb, float eps,
-                                                        const float* __restrict__ G, const double* __restrict__ obar,
-                                                        const float* __restrict__ Pn, float* __restrict__ Lf,
-                                                        __nv_bfloat16* __restrict__ Lb,
-                                                        const float* __restrict__ Dinv, const int* __restrict__ fail) {
+// ---------------------------------------------------------------------------------- trsm
+// Rows below the diagonal block: X = C L_dd^-T, one 64-row tile per CTA.  Thread (rg, cg)
+// owns rows rg + 16 a (a < 4) and columns 8 cg .. 8 cg + 7; the k loop reads both operands
+// as float4 from shared memory (12 loads per 128 multiply-adds).  The forward substitution
+// is fused in: each row i below loses its component along this block column,
+//     y_i -= X[i, :] . y_b.
+constexpr int DSP = NB + 4;              // padded shared-memory row (16-byte aligned)
+constexpr int TRSM_SMEM = ((NB + RT) * DSP + 2 * NB) * (int)sizeof(float);
+
+__global__ void __launch_bounds__(256, 2) chol_trsm_kernel(int t0, int P, int LD, int ns, int jb, float eps,
+                                                           const float* __restrict__ G, const double* __restrict__ obar,
+                                                           const float* __restrict__ Pn, float* __restrict__ Lf,
+                                                           __nv_bfloat16* __restrict__ Lb,
+                                                           const float* __restrict__ Dinv, float* __restrict__ yv,
+                                                           const int* __restrict__ fail) {
     const int t = t0 + blockIdx.y;
     if (fail[t]) return;
     extern __shared__ __align__(16) float tsm[];
-    float* Li = tsm;            // [NB][DS]
-    float* Ct = Li + NB * DS;   // [RT][DS]
+    float* Li = tsm;               // [NB][DSP] L_dd^-1
+    float* Ct = Li + NB * DSP;     // [RT][DSP] C, later the fused-forward partial sums
+    float* yb = Ct + RT * DSP;     // [2][NB]
     const int tid = threadIdx.x;
     const int nb = min(NB, P - jb);
     const int r0 = jb + nb + blockIdx.x * RT;
-    const float* Gt = G + (size_t)t * P * P;
-    const double* ob = obar + (size_t)t * P;
-    const float inv_ns = 1.0f / (float)ns;
     const float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) Li[(e / NB) * DS + e % NB] = Dv[e];
-    for (int e = tid; e < RT * nb; e += blockDim.x) {
-        const int rr = e / nb, c = e - rr * nb;
-        const int i = r0 + rr;
-        float v = 0.f;
-        if (i < P) v = jb == 0 ? a_orig(Gt, ob, P, inv_ns, i, jb + c, eps) : Pn[((size_t)t * P + i) * NB + c];
-        Ct[rr * DS + c] = v;
+    float* yt = yv + (size_t)t * 2 * P;
+    {
+        float4 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = ld4(Dv + (size_t)(tid + 256 * q) * 4);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int e = tid + 256 * q;
+            *reinterpret_cast<float4*>(Li + (e >> 5) * DSP + 4 * (e & 31)) = v[q];
+        }
+    }
+    if (jb == 0) {
+        const float* Gt = G + (size_t)t * P * P;
+        const double* ob = obar + (size_t)t * P;
+        const float inv_ns = 1.0f / (float)ns;
+#pragma unroll 8
+        for (int q = 0; q < (NB * RT) / 256; ++q) {
+            const int e = tid + 256 * q, c = e / RT, rr = e % RT, i = r0 + rr;
+            float v = 0.f;
+            if (i < P && c < nb) v = a_orig(Gt, ob, P, inv_ns, i, c, eps);
+            Ct[rr * DSP + c] = v;
+        }
+    } else {
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = tid + 256 * q, rr = e >> 5, c4 = e & 31, i = r0 + rr;
+            v[q] = i < P ? ld4(Pn + ((size_t)t * P + i) * NB + 4 * c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = tid + 256 * q, rr = e >> 5, c4 = e & 31;
+            float4 w = v[q];
+            if (4 * c4 + 0 >= nb) w.x = 0.f;
+            if (4 * c4 + 1 >= nb) w.y = 0.f;
+            if (4 * c4 + 2 >= nb) w.z = 0.f;
+            if (4 * c4 + 3 >= nb) w.w = 0.f;
+            *reinterpret_cast<float4*>(Ct + rr * DSP + 4 * c4) = w;
+        }
+    }
+    if (tid < 2 * NB) {
+        const int h = tid >> 7, c = tid & (NB - 1);
+        yb[h * NB + c] = c < nb ? yt[h * P + jb + c] : 0.f;
     }
     __syncthreads();
-    const int rg = tid % 16, cg = tid / 16;
+    const int rg = tid & 15, cg = tid >> 4;
     float acc[4][8];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[a][u] = 0.f;
-    const int kend = min(nb, cg * 8 + 8);  // L_dd^-1 is lower triangular
-    for (int k = 0; k < kend; ++k) {
-        float cv[4], lv[8];
+    const int kq_end = (min(nb, cg * 8 + 8) + 3) >> 2;   // L_dd^-1 is lower triangular
+    for (int kq = 0; kq < kq_end; ++kq) {
+        float4 cv[4], lv[8];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) cv[a] = Ct[(rg * 4 + a) * DS + k];
+        for (int a = 0; a < 4; ++a) cv[a] = *reinterpret_cast<const float4*>(Ct + (rg + 16 * a) * DSP + 4 * kq);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) lv[u] = Li[(cg * 8 + u) * DS + k];
+        for (int u = 0; u < 8; ++u) lv[u] = *reinterpret_cast<const float4*>(Li + (cg * 8 + u) * DSP + 4 * kq);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc[a][u] = fmaf(cv[a], lv[u], acc[a][u]);
+            for (int u = 0; u < 8; ++u) acc[a][u] = dot4(cv[a], lv[u], acc[a][u]);
     }
     const LbLayout lay{(P + NB - 1) / NB, LD / 64};
     float* Lft = Lf + (size_t)t * P * LD;
     __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
+    const int nv = nb - cg * 8;
+    float pr[4][2];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int i = r0 + rg * 4 + a;
-        if (i < P)
+        const int i = r0 + rg + 16 * a;
+        if (i < P && nv > 0) store_L8(Lft, Lbt, lay, LD, i, jb + cg * 8, acc[a], nv);
+        float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = cg * 8 + u;
-                if (c < nb) store_L(Lft, Lbt, lay, LD, i, jb + c, acc[a][u]);
-            }
+        for (int u = 0; u < 8; ++u) {
+            s0 = fmaf(acc[a][u], yb[cg * 8 + u], s0);
+            s1 = fmaf(acc[a][u], yb[NB + cg * 8 + u], s1);
+        }
+        pr[a][0] = s0;
+        pr[a][1] = s1;
+    }
+    __syncthreads();   // C is no longer read
+    float* red = Ct;   // [16][RT][2]
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        red[(cg * RT + rg + 16 * a) * 2] = pr[a][0];
+        red[(cg * RT + rg + 16 * a) * 2 + 1] = pr[a][1];
+    }
+    __syncthreads();
+    if (tid < 2 * RT) {
+        const int rr = tid >> 1, h = tid & 1, i = r0 + rr;
+        if (i < P) {
+            float s = 0.f;
+#pragma unroll
+            for (int g = 0; g < 16; ++g) s += red[(g * RT + rr) * 2 + h];
+            yt[h * P + i] -= s;
+        }
     }
 }
 
 // ------------------------------------------------------------------------------ solves
-// (s, c) += g * (xh + xl) with an error-free product and sum (Dekker/Knuth): the pair s + c
-// carries about 48 bits, enough for an FP64-quality residual from FP32 arithmetic.
-__device__ __forceinline__ void df_fma(float& s, float& c, float g, float xh, float xl) {
+// Double-float pair (s + c carries about 48 bits) and its error-free accumulation.
+struct DF {
+    float s, c;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float t = a.s + b.s;
+    const float bp = t - a.s;
+    const float e = (a.s - (t - bp)) + (b.s - bp);
+    return DF{t, a.c + b.c + e};
+}
+// acc += g * (xh + xl), with the product g xh split exactly (FMA) and the sum by two-sum
+__device__ __forceinline__ void df_fma(DF& acc, float g, float xh, float xl) {
     const float p = g * xh;
     const float e = fmaf(g, xh, -p);
-    const float t = s + p;
-    const float bp = t - s;
-    const float err = (s - (t - bp)) + (p - bp);
-    s = t;
-    c += err + e;
-    c = fmaf(g, xl, c);
+    const float t = acc.s + p;
+    const float bp = t - acc.s;
+    const float err = (acc.s - (t - bp)) + (p - bp);
+    acc.s = t;
+    acc.c = fmaf(g, xl, acc.c + (err + e));
+}
+__device__ __forceinline__ DF shfl_df(DF v, int off) {
+    return DF{__shfl_xor_sync(0xffffffffu, v.s, off), __shfl_xor_sync(0xffffffffu, v.c, off)};
+}
+// reduce8 for double-float pairs (same lane-to-value map)
+__device__ __forceinline__ DF reduce8_df(DF (&v)[8], int lane) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const bool up = lane & 16;
+        const DF send = up ? v[u] : v[u + 4];
+        const DF keep = up ? v[u + 4] : v[u];
+        v[u] = df_add(keep, shfl_df(send, 16));
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const bool up = lane & 8;
+        const DF send = up ? v[u] : v[u + 2];
+        const DF keep = up ? v[u + 2] : v[u];
+        v[u] = df_add(keep, shfl_df(send, 8));
+    }
+    {
+        const bool up = lane & 4;
+        const DF send = up ? v[0] : v[1];
+        const DF keep = up ? v[1] : v[0];
+        v[0] = df_add(keep, shfl_df(send, 4));
+    }
+    v[0] = df_add(v[0], shfl_df(v[0], 2));
+    v[0] = df_add(v[0], shfl_df(v[0], 1));
+    return v[0];
 }
 
-// L L^T x = y for two right-hand sides held in shared memory (y[0..P), y[P..2P)).
-__device__ void block_solve(int P, int LD, const float* Lft, const float* Dv, float* y, float* Db, float* tmp,
-                            float* part) {
+// Refinement residual, tile-parallel: the products G x of the symmetric Gram counts with
+// the current solution, one 128 x 128 upper tile (I <= J) of one trajectory per CTA.  The
+// tile's row sums belong to row block I and its column sums (strictly below the diagonal
+// for I = J) to row block J; each is written to its own slot part[t][row block][other
+// block][128][2] (FP64), and the solve kernel adds the slots in a fixed order, so the
+// result does not depend on scheduling.  Products and sums in double-float arithmetic.
+__global__ void __launch_bounds__(256) chol_resid_kernel(int t0, int P, const float* __restrict__ G,
+                                                         const double* __restrict__ xw, double* __restrict__ part,
+                                                         const int* __restrict__ fail) {
+    const int t = t0 + blockIdx.y;
+    if (fail[t]) return;
+    const int nblk = (P + NB - 1) / NB;
+    int J = (int)((sqrtf(8.f * (float)blockIdx.x + 1.f) - 1.f) * 0.5f);
+    while ((J + 1) * (J + 2) / 2 <= (int)blockIdx.x) ++J;
+    while (J * (J + 1) / 2 > (int)blockIdx.x) --J;
+    const int I = blockIdx.x - J * (J + 1) / 2;
+    __shared__ float2 xI[2][NB], xJ[2][NB];
+    __shared__ DF cred[8][NB][2];
+    __shared__ double rowacc[2][NB];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const double* xt = xw + (size_t)t * 2 * P;
+    {
+        const int c = tid & (NB - 1), h = tid >> 7;
+        const int iI = I * NB + c, iJ = J * NB + c;
+        const double vI = iI < P ? xt[h * P + iI] : 0.0, vJ = iJ < P ? xt[h * P + iJ] : 0.0;
+        const float hI = (float)vI, hJ = (float)vJ;
+        xI[h][c] = make_float2(hI, (float)(vI - (double)hI));
+        xJ[h][c] = make_float2(hJ, (float)(vJ - (double)hJ));
+    }
+    __syncthreads();
+    const float* Gt = G + (size_t)t * P * P;
+    const int j0 = J * NB + 4 * lane;
+    const bool vec = (P & 3) == 0 && j0 + 3 < P;
+    float2 xj[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        xj[u][0] = xJ[0][4 * lane + u];
+        xj[u][1] = xJ[1][4 * lane + u];
+    }
+    DF cs[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cs[u][0] = cs[u][1] = DF{0.f, 0.f};
+#pragma unroll 1
+    for (int g = 0; g < 4; ++g) {
+        float gv[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = I * NB + warp * 16 + 4 * g + a;
+            const float* row = Gt + (size_t)i * P;
+            if (i < P && vec) {
+                const float4 q = ld4(row + j0);
+                gv[a][0] = q.x; gv[a][1] = q.y; gv[a][2] = q.z; gv[a][3] = q.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) gv[a][u] = (i < P && j0 + u < P) ? row[j0 + u] : 0.f;
+            }
+        }
+        DF rs[8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int r = warp * 16 + 4 * g + a;
+            rs[2 * a] = rs[2 * a + 1] = DF{0.f, 0.f};
+            const float2 xi0 = xI[0][r], xi1 = xI[1][r];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = 4 * lane + u;
+                const float g_row = (I < J || c >= r) ? gv[a][u] : 0.f;
+                const float g_col = (I < J || c > r) ? gv[a][u] : 0.f;
+                df_fma(rs[2 * a], g_row, xj[u][0].x, xj[u][0].y);
+                df_fma(rs[2 * a + 1], g_row, xj[u][1].x, xj[u][1].y);
+                df_fma(cs[u][0], g_col, xi0.x, xi0.y);
+                df_fma(cs[u][1], g_col, xi1.x, xi1.y);
+            }
+        }
+        const DF s = reduce8_df(rs, lane);
+        if ((lane & 3) == 0) {
+            const int idx = reduce8_index(lane);
+            rowacc[idx & 1][warp * 16 + 4 * g + (idx >> 1)] = (double)s.s + (double)s.c;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        cred[warp][4 * lane + u][0] = cs[u][0];
+        cred[warp][4 * lane + u][1] = cs[u][1];
+    }
+    __syncthreads();
+    {
+        const int c = tid >> 1, h = tid & 1;
+        DF s = cred[0][c][h];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) s = df_add(s, cred[w][c][h]);
+        const double col = (double)s.s + (double)s.c;
+        double* pt = part + (size_t)t * nblk * nblk * (2 * NB);
+        if (I < J) {
+            pt[((size_t)I * nblk + J) * (2 * NB) + 2 * c + h] = rowacc[h][c];
+            pt[((size_t)J * nblk + I) * (2 * NB) + 2 * c + h] = col;
+        } else {
+            pt[((size_t)I * nblk + I) * (2 * NB) + 2 * c + h] = rowacc[h][c] + col;
+        }
+    }
+}
+
+// Triangular solves L L^T x = y for the two right-hand sides (real and imaginary parts) of
+// one trajectory, held in shared memory as y[0..PY) and y[PY..2 PY); one CTA per trajectory.
+// Forward, block b (left-looking): the 128 rows of the block take their dot products with
+// y[0 : jb) (lanes along the row, four rows per warp in flight), then y_b = L_bb^-1 (.) from
+// the stored inverse.  Backward, block b from the last: column sums of the rows below
+// (lanes along the block's columns, warps along the rows), then x_b = L_bb^-T (.).
+__device__ void sweep_forward(int P, int PY, int LD, const float* Lt, const float* Dv, float* y, float* tb) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nblk = (P + NB - 1) / NB;
     for (int b = 0; b < nblk; ++b) {
         const int jb = b * NB, nb = min(NB, P - jb);
-        for (int e = tid; e < NB * NB; e += blockDim.x) Db[(e / NB) * DS + e % NB] = Dv[(size_t)b * NB * NB + e];
-        __syncthreads();
-        for (int e = tid; e < 2 * nb; e += blockDim.x) {
-            const int c = e % nb, h = e / nb;
-            float s = 0.f;
-            for (int k = 0; k <= c; ++k) s = fmaf(Db[c * DS + k], y[h * P + jb + k], s);
-            tmp[h * NB + c] = s;
-        }
-        __syncthreads();
-        for (int e = tid; e < 2 * nb; e += blockDim.x) y[(e / nb) * P + jb + e % nb] = tmp[(e / nb) * NB + e % nb];
-        __syncthreads();
-        if (jb + nb < P) {
-            // rows below: y_i -= L[i, jb:jb+128] . y_b; lane l owns columns 4l..4l+3, each warp
-            // keeps four rows in flight
-            float yb0[4], yb1[4];
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+            const int rl = warp * 16 + 4 * g;
+            float v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                yb0[u] = y[jb + 4 * lane + u];
-                yb1[u] = y[P + jb + 4 * lane + u];
-            }
-            const int nw = blockDim.x / 32;
-            for (int i0 = jb + nb + 4 * warp; i0 < P; i0 += 4 * nw) {
-                float4 l4[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-                    l4[a] = (i0 + a < P) ? *reinterpret_cast<const float4*>(Lft + (size_t)(i0 + a) * LD + jb + 4 * lane)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-                float s0[4], s1[4];
+            for (int u = 0; u < 8; ++u) v[u] = 0.f;
+#pragma unroll 2
+            for (int q = 0; q < b; ++q) {
+                const int c = q * NB + 4 * lane;
+                const float4 y0 = ld4(y + c), y1 = ld4(y + PY + c);
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    s0[a] = l4[a].x * yb0[0] + l4[a].y * yb0[1] + l4[a].z * yb0[2] + l4[a].w * yb0[3];
-                    s1[a] = l4[a].x * yb1[0] + l4[a].y * yb1[1] + l4[a].z * yb1[2] + l4[a].w * yb1[3];
+                    const int i = jb + rl + a;
+                    const float4 l = i < P ? ld4(Lt + (size_t)i * LD + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[2 * a] = dot4(l, y0, v[2 * a]);
+                    v[2 * a + 1] = dot4(l, y1, v[2 * a + 1]);
                 }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        s0[a] += __shfl_xor_sync(0xffffffffu, s0[a], off);
-                        s1[a] += __shfl_xor_sync(0xffffffffu, s1[a], off);
-                    }
-                if (lane < 4 && i0 + lane < P) {
-                    float v0 = s0[0], v1 = s1[0];
-                    if (lane == 1) { v0 = s0[1]; v1 = s1[1]; }
-                    if (lane == 2) { v0 = s0[2]; v1 = s1[2]; }
-                    if (lane == 3) { v0 = s0[3]; v1 = s1[3]; }
-                    y[i0 + lane] -= v0;
-                    y[P + i0 + lane] -= v1;
-                }
+            }
+            const float s = reduce8(v, lane);
+            if ((lane & 3) == 0) {
+                const int idx = reduce8_index(lane), h = idx & 1, r = rl + (idx >> 1);
+                tb[h * NB + r] = r < nb ? y[h * PY + jb + r] - s : 0.f;
             }
         }
         __syncthreads();
-    }
-    for (int b = nblk - 1; b >= 0; --b) {
-        const int jb = b * NB, nb = min(NB, P - jb);
-        // partial sums over the solved rows below: warps stream rows, lane l owns columns 4l..4l+3
-        float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        {
-            const int nw = blockDim.x / 32;
-            for (int i0 = jb + nb + 4 * warp; i0 < P; i0 += 4 * nw) {
-                float4 l4[4];
-                float x0[4], x1[4];
+        const float* Db = Dv + (size_t)b * NB * NB;
+        const float4 t0 = ld4(tb + 4 * lane), t1 = ld4(tb + NB + 4 * lane);
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+            const int rl = warp * 16 + 4 * g;
+            float v[8];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const bool in = i0 + a < P;
-                    l4[a] = in ? *reinterpret_cast<const float4*>(Lft + (size_t)(i0 + a) * LD + jb + 4 * lane)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-                    x0[a] = in ? y[i0 + a] : 0.f;
-                    x1[a] = in ? y[P + i0 + a] : 0.f;
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    acc[0][0] = fmaf(l4[a].x, x0[a], acc[0][0]);
-                    acc[1][0] = fmaf(l4[a].y, x0[a], acc[1][0]);
-                    acc[2][0] = fmaf(l4[a].z, x0[a], acc[2][0]);
-                    acc[3][0] = fmaf(l4[a].w, x0[a], acc[3][0]);
-                    acc[0][1] = fmaf(l4[a].x, x1[a], acc[0][1]);
-                    acc[1][1] = fmaf(l4[a].y, x1[a], acc[1][1]);
-                    acc[2][1] = fmaf(l4[a].z, x1[a], acc[2][1]);
-                    acc[3][1] = fmaf(l4[a].w, x1[a], acc[3][1]);
-                }
+            for (int a = 0; a < 4; ++a) {
+                const float4 l = ld4(Db + (size_t)(rl + a) * NB + 4 * lane);
+                v[2 * a] = dot4(l, t0, 0.f);
+                v[2 * a + 1] = dot4(l, t1, 0.f);
             }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            part[(warp * NB + 4 * lane + u) * 2] = acc[u][0];
-            part[(warp * NB + 4 * lane + u) * 2 + 1] = acc[u][1];
-        }
-        for (int e = tid; e < NB * NB; e += blockDim.x) Db[(e / NB) * DS + e % NB] = Dv[(size_t)b * NB * NB + e];
-        __syncthreads();
-        for (int e = tid; e < 2 * nb; e += blockDim.x) {
-            const int c = e % nb, h = e / nb;
-            float sacc = 0.f;
-            for (int w = 0; w < 8; ++w) sacc += part[(w * NB + c) * 2 + h];
-            tmp[h * NB + c] = y[h * P + jb + c] - sacc;
-        }
-        __syncthreads();
-        for (int e = tid; e < 2 * nb; e += blockDim.x) {
-            const int c = e % nb, h = e / nb;
-            float sacc = 0.f;
-            for (int k = c; k < nb; ++k) sacc = fmaf(Db[k * DS + c], tmp[h * NB + k], sacc);
-            y[h * P + jb + c] = sacc;
+            const float s = reduce8(v, lane);
+            if ((lane & 3) == 0) {
+                const int idx = reduce8_index(lane), h = idx & 1, r = rl + (idx >> 1);
+                if (r < nb) y[h * PY + jb + r] = s;
+            }
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(256, 1) chol_solve_tc_kernel(int t0, int P, int LD, int ns, double eps, int refine,
-                                                               const float* __restrict__ G,
-                                                               const double* __restrict__ obar,
-                                                               const double2* __restrict__ D, const float* __restrict__ Lf,
-                                                               const float* __restrict__ Dinv,
-                                                               double* __restrict__ xws, double2* __restrict__ delta,
-                                                               double* __restrict__ shift_used,
-                                                               const int* __restrict__ fail) {
+__device__ void sweep_backward(int P, int PY, int LD, const float* Lt, const float* Dv, float* y, float* tb,
+                               float* red) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nblk = (P + NB - 1) / NB;
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int jb = b * NB, nb = min(NB, P - jb);
+        float acc[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.f;
+#pragma unroll 4
+        for (int i = jb + NB + warp; i < P; i += 8) {
+            const float4 l = ld4(Lt + (size_t)i * LD + jb + 4 * lane);
+            const float x0 = y[i], x1 = y[PY + i];
+            acc[0][0] = fmaf(l.x, x0, acc[0][0]);
+            acc[1][0] = fmaf(l.y, x0, acc[1][0]);
+            acc[2][0] = fmaf(l.z, x0, acc[2][0]);
+            acc[3][0] = fmaf(l.w, x0, acc[3][0]);
+            acc[0][1] = fmaf(l.x, x1, acc[0][1]);
+            acc[1][1] = fmaf(l.y, x1, acc[1][1]);
+            acc[2][1] = fmaf(l.z, x1, acc[2][1]);
+            acc[3][1] = fmaf(l.w, x1, acc[3][1]);
+        }
+        reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[0] =
+            make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]);
+        reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[1] =
+            make_float4(acc[2][0], acc[2][1], acc[3][0], acc[3][1]);
+        __syncthreads();
+        {
+            const int c = tid >> 1, h = tid & 1;
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += red[(w * NB + c) * 2 + h];
+            tb[h * NB + c] = c < nb ? y[h * PY + jb + c] - s : 0.f;
+        }
+        __syncthreads();
+        const float* Db = Dv + (size_t)b * NB * NB;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.f;
+#pragma unroll 4
+        for (int k = warp; k < NB; k += 8) {
+            const float4 l = ld4(Db + (size_t)k * NB + 4 * lane);
+            const float t0 = tb[k], t1 = tb[NB + k];
+            acc[0][0] = fmaf(l.x, t0, acc[0][0]);
+            acc[1][0] = fmaf(l.y, t0, acc[1][0]);
+            acc[2][0] = fmaf(l.z, t0, acc[2][0]);
+            acc[3][0] = fmaf(l.w, t0, acc[3][0]);
+            acc[0][1] = fmaf(l.x, t1, acc[0][1]);
+            acc[1][1] = fmaf(l.y, t1, acc[1][1]);
+            acc[2][1] = fmaf(l.z, t1, acc[2][1]);
+            acc[3][1] = fmaf(l.w, t1, acc[3][1]);
+        }
+        reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[0] =
+            make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]);
+        reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[1] =
+            make_float4(acc[2][0], acc[2][1], acc[3][0], acc[3][1]);
+        __syncthreads();
+        {
+            const int c = tid >> 1, h = tid & 1;
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += red[(w * NB + c) * 2 + h];
+            if (c < nb) y[h * PY + jb + c] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Solve passes of one trajectory per CTA.
+//   mode 0: x = L^-T y from the forward result y that the factorization left in yv;
+//   mode 1: r = D - (S + eps I) x with S x = (G x) / ns - obar (obar . x), G x summed from the
+//           residual kernel's slots in FP64; then dx = L^-T L^-1 r and x += dx.
+// The last pass writes delta (and the shift used), the others keep x in xw (FP64).
+constexpr int SWEEP_THREADS = 256;
+__global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P, int LD, int ns, double eps, int mode,
+                                                                    int last, const double* __restrict__ obar,
+                                                                    const double2* __restrict__ D,
+                                                                    const float* __restrict__ Lf,
+                                                                    const float* __restrict__ Dinv,
+                                                                    const float* __restrict__ yv,
+                                                                    const double* __restrict__ part,
+                                                                    double* __restrict__ xw, double2* __restrict__ delta,
+                                                                    double* __restrict__ shift_used,
+                                                                    const int* __restrict__ fail) {
     const int t = t0 + blockIdx.x;
     if (fail[t]) return;
-    extern __shared__ __align__(16) float ssm[];
-    float* Db = ssm;              // [NB][DS]
-    float* tmp = Db + NB * DS;    // [2][NB]
-    float* y = tmp + 2 * NB;      // [2][P]
-    float* xs = y + 2 * P;        // [4][P] x split into FP32 high and low parts (re h, re l, im h, im l)
-    float* part = xs + 4 * P;     // [8][256][2][2] per-warp partial sums
-    __shared__ double red[2][8];
+    const int nblk = (P + NB - 1) / NB, PY = nblk * NB;
+    extern __shared__ __align__(16) float wsm[];
+    float* y = wsm;              // [2][PY]
+    float* red = y + 2 * PY;     // [8][NB][2]
+    float* tb = red + 8 * NB * 2;  // [2][NB]
+    __shared__ double dred[2][SWEEP_THREADS / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const float* Lft = Lf + (size_t)t * P * LD;
-    const float* Dv = Dinv + (size_t)t * ((P + NB - 1) / NB) * NB * NB;
+    const float* Lt = Lf + (size_t)t * P * LD;
+    const float* Dv = Dinv + (size_t)t * nblk * NB * NB;
+    double* xt = xw + (size_t)t * 2 * P;
     const double2* Dt = D + (size_t)t * P;
-    double* xr = xws + (size_t)t * 4 * P;
-    double* xi = xr + P;
-    double* rr = xi + P;
-    double* ri = rr + P;
-    for (int k = tid; k < P; k += blockDim.x) {
-        y[k] = (float)Dt[k].x;
-        y[P + k] = (float)Dt[k].y;
-    }
-    __syncthreads();
-    block_solve(P, LD, Lft, Dv, y, Db, tmp, part);
-    for (int k = tid; k < P; k += blockDim.x) {
-        xr[k] = (double)y[k];
-        xi[k] = (double)y[P + k];
-    }
-    __syncthreads();
-    const float* Gt = G + (size_t)t * P * P;
-    const double* ob = obar + (size_t)t * P;
-    for (int it = 0; it < refine; ++it) {
-        double a = 0.0, b = 0.0;
+    for (int k = P + tid; k < PY; k += blockDim.x) y[k] = y[PY + k] = 0.f;
+    if (mode == 0) {
+        const float* yt = yv + (size_t)t * 2 * P;
         for (int k = tid; k < P; k += blockDim.x) {
-            a += ob[k] * xr[k];
-            b += ob[k] * xi[k];
+            y[k] = yt[k];
+            y[PY + k] = yt[P + k];
+        }
+        __syncthreads();
+    } else {
+        const double* ob = obar + (size_t)t * P;
+        double a0 = 0.0, a1 = 0.0;
+        for (int k = tid; k < P; k += blockDim.x) {
+            a0 += ob[k] * xt[k];
+            a1 += ob[k] * xt[P + k];
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, off);
-            b += __shfl_xor_sync(0xffffffffu, b, off);
+            a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, off);
         }
         if (lane == 0) {
-            red[0][warp] = a;
-            red[1][warp] = b;
+            dred[0][warp] = a0;
+            dred[1][warp] = a1;
         }
         __syncthreads();
-        double oxr = 0.0, oxi = 0.0;
-        for (int w = 0; w < 8; ++w) {
-            oxr += red[0][w];
-            oxi += red[1][w];
+        double ox0 = 0.0, ox1 = 0.0;
+        for (int w = 0; w < SWEEP_THREADS / 32; ++w) {
+            ox0 += dred[0][w];
+            ox1 += dred[1][w];
         }
-        // x = xh + xl in FP32 pairs (48 significant bits)
+        const double* pt = part + (size_t)t * nblk * nblk * (2 * NB);
+        const double inv_ns = 1.0 / (double)ns;
         for (int k = tid; k < P; k += blockDim.x) {
-            const float rh = (float)xr[k], ih = (float)xi[k];
-            xs[k] = rh;
-            xs[P + k] = (float)(xr[k] - (double)rh);
-            xs[2 * P + k] = ih;
-            xs[3 * P + k] = (float)(xi[k] - (double)ih);
+            const double2* pp = reinterpret_cast<const double2*>(pt + (size_t)(k >> 7) * nblk * (2 * NB) + 2 * (k & 127));
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll 4
+            for (int J = 0; J < nblk; ++J) {
+                const double2 q = pp[(size_t)J * NB];
+                s0 += q.x;
+                s1 += q.y;
+            }
+            const double r0 = Dt[k].x - (s0 * inv_ns - ob[k] * ox0 + eps * xt[k]);
+            const double r1 = Dt[k].y - (s1 * inv_ns - ob[k] * ox1 + eps * xt[P + k]);
+            y[k] = (float)r0;
+            y[PY + k] = (float)r1;
         }
         __syncthreads();
-        // z_j = sum_{i<j} G[i][j] x_i: column chunks of 256, warps stream rows, lane l owns 8 columns
-        for (int c0 = 0; c0 < P; c0 += 256) {
-            float sh[8][2], sc[8][2];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) sh[u][0] = sh[u][1] = sc[u][0] = sc[u][1] = 0.f;
-            const int iend = min(P, c0 + 256);
-            for (int i = warp; i < iend; i += blockDim.x / 32) {
-                const float* grow = Gt + (size_t)i * P;
-                const float xh0 = xs[i], xl0 = xs[P + i], xh1 = xs[2 * P + i], xl1 = xs[3 * P + i];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int jcol = c0 + 8 * lane + u;
-                    if (jcol < P && jcol > i) {
-                        const float g = grow[jcol];
-                        df_fma(sh[u][0], sc[u][0], g, xh0, xl0);
-                        df_fma(sh[u][1], sc[u][1], g, xh1, xl1);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int cl = 8 * lane + u;
-                part[((warp * 256 + cl) * 2) * 2] = sh[u][0];
-                part[((warp * 256 + cl) * 2) * 2 + 1] = sc[u][0];
-                part[((warp * 256 + cl) * 2 + 1) * 2] = sh[u][1];
-                part[((warp * 256 + cl) * 2 + 1) * 2 + 1] = sc[u][1];
-            }
-            __syncthreads();
-            for (int cl = tid; cl < 256 && c0 + cl < P; cl += blockDim.x) {
-                double zr = 0.0, zi = 0.0;
-                for (int w = 0; w < 8; ++w) {
-                    zr += (double)part[((w * 256 + cl) * 2) * 2] + (double)part[((w * 256 + cl) * 2) * 2 + 1];
-                    zi += (double)part[((w * 256 + cl) * 2 + 1) * 2] + (double)part[((w * 256 + cl) * 2 + 1) * 2 + 1];
-                }
-                rr[c0 + cl] = zr;
-                ri[c0 + cl] = zi;
-            }
-            __syncthreads();
-        }
-        // y_i = sum_{j>=i} G[i][j] x_j, one warp per row; residual D - (S + eps I) x
-        for (int i = warp; i < P; i += blockDim.x / 32) {
-            const float* grow = Gt + (size_t)i * P;
-            float h0 = 0.f, c0f = 0.f, h1 = 0.f, c1f = 0.f;
-            for (int jj = i + lane; jj < P; jj += 32) {
-                const float g = grow[jj];
-                df_fma(h0, c0f, g, xs[jj], xs[P + jj]);
-                df_fma(h1, c1f, g, xs[2 * P + jj], xs[3 * P + jj]);
-            }
-            double yr2 = (double)h0 + (double)c0f, yi2 = (double)h1 + (double)c1f;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                yr2 += __shfl_xor_sync(0xffffffffu, yr2, off);
-                yi2 += __shfl_xor_sync(0xffffffffu, yi2, off);
-            }
-            if (lane == 0) {
-                const double sxr = (yr2 + rr[i]) / ns - ob[i] * oxr + eps * xr[i];
-                const double sxi = (yi2 + ri[i]) / ns - ob[i] * oxi + eps * xi[i];
-                y[i] = (float)(Dt[i].x - sxr);
-                y[P + i] = (float)(Dt[i].y - sxi);
-            }
-        }
-        __syncthreads();
-        block_solve(P, LD, Lft, Dv, y, Db, tmp, part);
-        for (int k = tid; k < P; k += blockDim.x) {
-            xr[k] += (double)y[k];
-            xi[k] += (double)y[P + k];
-        }
-        __syncthreads();
+        sweep_forward(P, PY, LD, Lt, Dv, y, tb);
     }
-    for (int k = tid; k < P; k += blockDim.x) delta[(size_t)t * P + k] = make_double2(xr[k], xi[k]);
-    if (tid == 0 && shift_used) shift_used[t] = eps;
+    sweep_backward(P, PY, LD, Lt, Dv, y, tb, red);
+    for (int k = tid; k < P; k += blockDim.x) {
+        double vr = (double)y[k], vi = (double)y[PY + k];
+        if (mode == 1) {
+            vr += xt[k];
+            vi += xt[P + k];
+        }
+        if (last) {
+            delta[(size_t)t * P + k] = make_double2(vr, vi);
+        } else {
+            xt[k] = vr;
+            xt[P + k] = vi;
+        }
+    }
+    if (last && tid == 0 && shift_used) shift_used[t] = eps;
 }
 
 inline int ldim(int P) { return ((P + 63) / 64) * 64; }
@@ -691,7 +1036,9 @@ size_t chol_tc_ws_bytes(int ntraj, int P) {
     add((size_t)ntraj * nblk * NB * NB * 4); // Dinv
     add((size_t)ntraj * 4);                  // fail
     add((size_t)ntraj * 2 * P * 4);          // fallback y
-    add((size_t)ntraj * 4 * P * 8);          // x, residual
+    add((size_t)ntraj * 4 * P * 8);          // x (and the fallback's residual)
+    add((size_t)ntraj * 2 * P * 4);          // forward-substitution vector
+    add((size_t)ntraj * nblk * nblk * 2 * NB * 8);  // residual slots
     return b + 256;
 }
 
@@ -726,6 +1073,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     int* fail = (int*)take((size_t)ntraj * 4);
     float* yf = (float*)take((size_t)ntraj * 2 * P * 4);
     double* x = (double*)take((size_t)ntraj * 4 * P * 8);
+    float* yv = (float*)take((size_t)ntraj * 2 * P * 4);
+    double* part = (double*)take((size_t)ntraj * nblk * nblk * 2 * NB * 8);
 
     auto encode = tc::get_encode();
     if (!encode) return cudaErrorNotSupported;
@@ -751,18 +1100,15 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
 
     cudaError_t e = cudaMemsetAsync(fail, 0, (size_t)ntraj * 4, s);
     if (e != cudaSuccess) return chol_fail(e, "memset");
-    const int dsmem = (NB * DS + NB) * (int)sizeof(float);
-    const int tsmem = (NB + RT) * DS * (int)sizeof(float);
-    e = cudaFuncSetAttribute(chol_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
-    if (e != cudaSuccess) return chol_fail(e, "diag attribute");
-    e = cudaFuncSetAttribute(chol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem);
+    e = cudaFuncSetAttribute(chol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TRSM_SMEM);
     if (e != cudaSuccess) return chol_fail(e, "trsm attribute");
     e = cudaFuncSetAttribute(chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_U);
     if (e != cudaSuccess) return chol_fail(e, "update attribute");
     const float feps = (float)eps;
-    const int ssmem = (NB * DS + 2 * NB + 2 * P + 4 * P + 8 * 256 * 2 * 2) * (int)sizeof(float);
-    e = cudaFuncSetAttribute(chol_solve_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem);
-    if (e != cudaSuccess) return chol_fail(e, "solve attribute");
+    const int PY = (int)nblk * NB;
+    const int wsmem = (2 * PY + 8 * NB * 2 + 2 * NB) * (int)sizeof(float);
+    e = cudaFuncSetAttribute(chol_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
+    if (e != cudaSuccess) return chol_fail(e, "sweep attribute");
     // trajectory groups on forked streams: one group's latency-bound kernels overlap the
     // others' (fork and join by events, so the call stays ordered on `s`)
     const int ng = ntraj >= 16 ? CHOL_GROUPS : 1;
@@ -786,21 +1132,35 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
             }
             {
                 ProfScope pd(OTVMC_K_CHOLD, gsm);
-                chol_diag_kernel<<<nt, 256, dsmem, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
+                chol_diag_kernel<<<nt, DIAG_THREADS, 0, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, D, Pn, Lf, Lb, Dv, yv,
+                                                               fail);
                 count_launch();
             }
             const int nrows = P - jb - min(NB, P - jb);
             if (nrows > 0) {
                 ProfScope pp(OTVMC_K_CHOLP, gsm);
                 dim3 grid((nrows + RT - 1) / RT, nt);
-                chol_trsm_kernel<<<grid, 256, tsmem, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, fail);
+                chol_trsm_kernel<<<grid, 256, TRSM_SMEM, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, yv,
+                                                                fail);
                 count_launch();
             }
         }
         {
             ProfScope ps(OTVMC_K_SOLVE, gsm);
-            chol_solve_tc_kernel<<<nt, 256, ssmem, gsm>>>(ta, P, LD, ns, eps, refine_iters, G, obar, D, Lf, Dv, x,
-                                                           delta, shift_used, fail);
+            chol_sweep_kernel<<<nt, SWEEP_THREADS, wsmem, gsm>>>(ta, P, LD, ns, eps, 0, refine_iters <= 0 ? 1 : 0, obar,
+                                                                  D, Lf, Dv, yv, part, x, delta, shift_used, fail);
+            count_launch();
+        }
+        for (int it = 0; it < refine_iters; ++it) {
+            {
+                ProfScope pr(OTVMC_K_RESID, gsm);
+                dim3 grid((unsigned)(nblk * (nblk + 1) / 2), nt);
+                chol_resid_kernel<<<grid, 256, 0, gsm>>>(ta, P, G, x, part, fail);
+                count_launch();
+            }
+            ProfScope ps(OTVMC_K_SOLVE, gsm);
+            chol_sweep_kernel<<<nt, SWEEP_THREADS, wsmem, gsm>>>(ta, P, LD, ns, eps, 1, it == refine_iters - 1 ? 1 : 0,
+                                                                  obar, D, Lf, Dv, yv, part, x, delta, shift_used, fail);
             count_launch();
         }
         if (ng > 1) {
