@@ -384,7 +384,7 @@ static otvmc_status run_estimators(const otvmc_ansatz* a, const double2* theta, 
     CK(launch_jastrow_prep(a, theta, T, b, status, s), "prep launch");
     CK(launch_est1_jastrow(a, spins, T, ns, fp32, b, status, s), "est1 launch");
     CK(launch_site_means(a, T, ns, b, lpl, s), "site means launch");
-    if (v) CK(launch_est2(a, spins, T, ns, dW, dt, lpl, b, Eeff, v, s), "est2 launch");
+    if (v) CK(launch_est2(a, spins, T, ns, fp32, dW, dt, lpl, b, Eeff, v, s), "est2 launch");
     return OTVMC_OK;
 }
 

@@ -45,6 +45,14 @@ constexpr double FX_SCALE = 281474976710656.0;      // 2^48
 constexpr double FX_INV = 1.0 / 281474976710656.0;  // 2^-48
 // |coefficient| * 2^48 must stay below this so that N of them cannot overflow int64.
 __device__ __forceinline__ long long fx_quant(double x) { return __double2ll_rn(x * FX_SCALE); }
+// 2 pi in units of 2^-48, rounded to the nearest integer
+constexpr long long FX_TWO_PI = 1768559438007110LL;
+// v 2^-48 in FP32 without FP64 arithmetic: high word (exact below 2^24) plus low word
+__device__ __forceinline__ float fx_to_float(long long v) {
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)(v & 0xffffffffll);
+    return fmaf((float)hi, 0x1.0p-16f, (float)lo * 0x1.0p-48f);
+}
 
 // ------------------------------------------------------------------------ misc
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {

@@ -123,8 +123,8 @@ cudaError_t launch_est1_jastrow(const otvmc_ansatz* a, const uint64_t* spins, in
                                 const EvalBufs& b, int* status, cudaStream_t s);
 cudaError_t launch_site_means(const otvmc_ansatz* a, int ntraj, int ns, const EvalBufs& b, double* lpl,
                               cudaStream_t s);
-cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const double* dW,
-                        double dt, const double* lpl, const EvalBufs& b, double2* Eeff, double2* v,
+cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
+                        const double* dW, double dt, const double* lpl, const EvalBufs& b, double2* Eeff, double2* v,
                         cudaStream_t s);
 cudaError_t launch_vpart(int ntraj, int ns, const double2* v, const EvalBufs& b, cudaStream_t s);
 cudaError_t launch_vquant(int ntraj, int ns, const double2* v, const EvalBufs& b, cudaStream_t s);

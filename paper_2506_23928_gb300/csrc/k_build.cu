@@ -83,36 +83,62 @@ cudaError_t launch_D_fixed_jastrow(const otvmc_ansatz* a, const uint64_t* spins,
 
 // ------------------------------------------------------------------ O in BF16 (K-major)
 // Ot[t][k][x] = O_xk as bf16 (+1 = 0x3F80, -1 = 0xBF80), rows k contiguous over samples x,
-// the operand layout of the tensor-core Gram kernel.  One thread = one sample, looping
-// over parameters: consecutive threads write consecutive samples of a row.
+// the operand layout of the tensor-core Gram kernel.  One thread = eight consecutive
+// samples: it first transposes their spins into one byte per site (bit s = sigma_j of
+// sample s is +1), then writes each parameter's eight values as one 16-byte store, so a
+// warp writes 512 contiguous bytes per parameter.
+constexpr int OB_SPT = 8;
+
+__device__ __forceinline__ uint4 bf16_pm1x8(uint32_t e) {
+    // bit s of e set -> +1 (0x3F80), clear -> -1 (0xBF80); sample 2q in the low half of word q
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        w[q] = 0xBF80BF80u ^ ((e << (15 - 2 * q)) & 0x8000u) ^ ((e << (30 - 2 * q)) & 0x80000000u);
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 __global__ void __launch_bounds__(256) obuild_bf16_jastrow_kernel(int n, int W, int P, int ns,
                                                                   const uint64_t* __restrict__ spins,
                                                                   const int* __restrict__ pairs,
                                                                   uint16_t* __restrict__ Ot) {
-    const int t = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= ns) return;
-    uint64_t wd[4];
+    extern __shared__ uint8_t msk[];  // [n][256]: site masks of each thread's samples
+    const int t = blockIdx.y, tid = threadIdx.x;
+    const int x0 = (blockIdx.x * blockDim.x + tid) * OB_SPT;
+    for (int w = 0; w < W; ++w) {
+        uint64_t wd[OB_SPT];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) wd[w] = (w < W) ? spins[((size_t)t * ns + x) * W + w] : 0ull;
-    auto bit = [&](int j) -> uint32_t {
-        const int w = j >> 6;
-        uint64_t v = wd[0];
-        if (w == 1) v = wd[1];
-        if (w == 2) v = wd[2];
-        if (w == 3) v = wd[3];
-        return (uint32_t)((v >> (j & 63)) & 1ull);
-    };
-    uint16_t* base = Ot + (size_t)t * P * ns + x;
+        for (int q = 0; q < OB_SPT; ++q) wd[q] = (x0 + q < ns) ? spins[((size_t)t * ns + x0 + q) * W + w] : 0ull;
+        const int bend = min(64, n - 64 * w);
+        for (int b = 0; b < bend; ++b) {
+            uint32_t m = 0;
+#pragma unroll
+            for (int q = 0; q < OB_SPT; ++q) m |= (uint32_t)((wd[q] >> b) & 1ull) << q;
+            msk[(64 * w + b) * blockDim.x + tid] = (uint8_t)m;
+        }
+    }
+    __syncthreads();
+    if (x0 >= ns) return;
+    uint16_t* base = Ot + (size_t)t * P * ns + x0;
+    const bool vec = (ns % OB_SPT) == 0;  // rows start on 16-byte boundaries and hold whole groups
     for (int k = 0; k < P; ++k) {
-        uint32_t up;
+        uint32_t e;
         if (k < n) {
-            up = bit(k);
+            e = msk[k * blockDim.x + tid];
         } else {
             const int j = __ldg(pairs + 2 * (k - n)), l = __ldg(pairs + 2 * (k - n) + 1);
-            up = (bit(j) == bit(l)) ? 1u : 0u;
+            e = ~(uint32_t)(msk[j * blockDim.x + tid] ^ msk[l * blockDim.x + tid]) & 0xFFu;
         }
-        base[(size_t)k * ns] = up ? (uint16_t)0x3F80 : (uint16_t)0xBF80;
+        const uint4 v = bf16_pm1x8(e);
+        uint16_t* dst = base + (size_t)k * ns;
+        if (vec) {
+            *reinterpret_cast<uint4*>(dst) = v;
+        } else {
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < OB_SPT; ++q)
+                if (x0 + q < ns) dst[q] = (uint16_t)(wv[q >> 1] >> (16 * (q & 1)));
+        }
     }
 }
 
@@ -120,8 +146,15 @@ cudaError_t launch_obuild_bf16_jastrow(const otvmc_ansatz* a, const uint64_t* sp
                                        uint16_t* Ot, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_OBUILD, s);
     const int n = a->n, W = (n + 63) / 64, P = (int)a->P;
-    dim3 grid((ns + 255) / 256, ntraj);
-    obuild_bf16_jastrow_kernel<<<grid, 256, 0, s>>>(n, W, P, ns, spins, a->pairs_d, Ot);
+    const int per_block = 256 * OB_SPT;
+    dim3 grid((ns + per_block - 1) / per_block, ntraj);
+    const size_t smem = (size_t)n * 256;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(obuild_bf16_jastrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    obuild_bf16_jastrow_kernel<<<grid, 256, smem, s>>>(n, W, P, ns, spins, a->pairs_d, Ot);
     count_launch();
     return cudaGetLastError();
 }

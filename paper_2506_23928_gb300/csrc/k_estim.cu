@@ -64,7 +64,7 @@ template <bool FP32T>
 __global__ void __launch_bounds__(256) est1_jastrow_kernel(
     int n, int W, int ns, double h, const uint64_t* __restrict__ spins, const long long* __restrict__ Qre,
     const long long* __restrict__ Qim, const long long* __restrict__ base_re, const long long* __restrict__ base_im,
-    const long long* __restrict__ QJ, const long long* __restrict__ baseJ, double2* __restrict__ r_out,
+    const long long* __restrict__ QJ, const long long* __restrict__ baseJ, void* __restrict__ r_out,
     double2* __restrict__ EH_out, double2* __restrict__ part_r, double2* __restrict__ part_sr,
     double* __restrict__ part_s) {
     constexpr int SPT = EST_SAMPLES_PER_THREAD;
@@ -123,35 +123,87 @@ __global__ void __launch_bounds__(256) est1_jastrow_kernel(
     }
     __syncthreads();
 
+    const int lane = threadIdx.x & 31, wis = j / 32;  // warp index within the sample's NT threads
     double2 pr = make_double2(0, 0), psr = make_double2(0, 0);
     double ps = 0.0;
-    const int lane = threadIdx.x & 31, wis = j / 32;  // warp index within the sample's NT threads
+    if constexpr (FP32T) {
+        // MIXED: fields converted from the exact fixed-point sums straight to FP32, the phase
+        // reduced modulo 2 pi in fixed point, ratios kept in FP32; per-thread sums in FP32.
+        float2* rf = reinterpret_cast<float2*>(r_out);
+        float2 prf = make_float2(0.f, 0.f), psrf = make_float2(0.f, 0.f);
+        int psi = 0;
 #pragma unroll
-    for (int q = 0; q < SPT; ++q) {
-        const int sl = g + q * SPP;
-        const int s = s0 + sl;
-        double2 contrib = make_double2(0.0, 0.0);
-        if (active && s < ns) {
-            const int sj = ((sw[sl * W + (j >> 6)] >> (j & 63)) & 1ull) ? 1 : -1;
-            const double fre = (double)(base_re[(size_t)t * n + j] + 2 * ar[q]) * FX_INV;
-            const double fim = (double)(base_im[(size_t)t * n + j] + 2 * ai[q]) * FX_INV;
-            const double fj = (double)(baseJ[j] + 2 * aj[q]) * FX_INV;
-            const double2 r = cexp_prec(-2.0 * sj * fre, -2.0 * sj * fim, FP32T);
-            r_out[((size_t)t * ns + s) * n + j] = r;
-            contrib = make_double2(0.5 * sj * fj + h * r.x, h * r.y);
-            pr.x += r.x;
-            pr.y += r.y;
-            psr.x += sj * r.x;
-            psr.y += sj * r.y;
-            ps += sj;
-        }
-        // sum over the sample's sites: butterfly within each warp, then warps in order
+        for (int q = 0; q < SPT; ++q) {
+            const int sl = g + q * SPP;
+            const int s = s0 + sl;
+            float hrx = 0.f, hry = 0.f;
+            long long isg = 0;
+            if (active && s < ns) {
+                const bool up = (sw[sl * W + (j >> 6)] >> (j & 63)) & 1ull;
+                const long long fre = base_re[(size_t)t * n + j] + 2 * ar[q];
+                const long long fim = base_im[(size_t)t * n + j] + 2 * ai[q];
+                const long long fj = baseJ[j] + 2 * aj[q];
+                // log r_j = -2 sigma_j f_j
+                const long long lre = up ? -2 * fre : 2 * fre;
+                const long long lim = up ? -2 * fim : 2 * fim;
+                const float e = expf(fx_to_float(lre));
+                const int kq = __float2int_rn(fx_to_float(lim) * 0.15915494309189535f);
+                const long long red = lim - (long long)kq * FX_TWO_PI;
+                float sn, cs;
+                sincosf(fx_to_float(red), &sn, &cs);
+                const float2 r = make_float2(e * cs, e * sn);
+                rf[((size_t)t * ns + s) * n + j] = r;
+                hrx = r.x;
+                hry = r.y;
+                isg = (up ? fj : -fj) >> 8;  // sigma_j f^J_j in units of 2^-40 (no overflow for n <= 256)
+                prf.x += r.x;
+                prf.y += r.y;
+                psrf.x += up ? r.x : -r.x;
+                psrf.y += up ? r.y : -r.y;
+                psi += up ? 1 : -1;
+            }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            contrib.x += __shfl_xor_sync(0xffffffffu, contrib.x, off);
-            contrib.y += __shfl_xor_sync(0xffffffffu, contrib.y, off);
+            for (int off = 16; off > 0; off >>= 1) {
+                hrx += __shfl_xor_sync(0xffffffffu, hrx, off);
+                hry += __shfl_xor_sync(0xffffffffu, hry, off);
+                isg += __shfl_xor_sync(0xffffffffu, isg, off);
+            }
+            if (lane == 0 && g < SPP)
+                ered[sl * (NT / 32) + wis] =
+                    make_double2(0.5 * (double)isg * 0x1.0p-40 + h * (double)hrx, h * (double)hry);
         }
-        if (lane == 0 && g < SPP) ered[sl * (NT / 32) + wis] = contrib;
+        pr = make_double2((double)prf.x, (double)prf.y);
+        psr = make_double2((double)psrf.x, (double)psrf.y);
+        ps = (double)psi;
+    } else {
+        double2* rd = reinterpret_cast<double2*>(r_out);
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+            const int sl = g + q * SPP;
+            const int s = s0 + sl;
+            double2 contrib = make_double2(0.0, 0.0);
+            if (active && s < ns) {
+                const int sj = ((sw[sl * W + (j >> 6)] >> (j & 63)) & 1ull) ? 1 : -1;
+                const double fre = (double)(base_re[(size_t)t * n + j] + 2 * ar[q]) * FX_INV;
+                const double fim = (double)(base_im[(size_t)t * n + j] + 2 * ai[q]) * FX_INV;
+                const double fj = (double)(baseJ[j] + 2 * aj[q]) * FX_INV;
+                const double2 r = cexp_prec(-2.0 * sj * fre, -2.0 * sj * fim, false);
+                rd[((size_t)t * ns + s) * n + j] = r;
+                contrib = make_double2(0.5 * sj * fj + h * r.x, h * r.y);
+                pr.x += r.x;
+                pr.y += r.y;
+                psr.x += sj * r.x;
+                psr.y += sj * r.y;
+                ps += sj;
+            }
+            // sum over the sample's sites: butterfly within each warp, then warps in order
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                contrib.x += __shfl_xor_sync(0xffffffffu, contrib.x, off);
+                contrib.y += __shfl_xor_sync(0xffffffffu, contrib.y, off);
+            }
+            if (lane == 0 && g < SPP) ered[sl * (NT / 32) + wis] = contrib;
+        }
     }
     __syncthreads();
     if (threadIdx.x < SB) {
@@ -273,8 +325,9 @@ cudaError_t launch_site_means(const otvmc_ansatz* a, int ntraj, int ns, const Ev
 // decay site j:  B = sqrt(kappa_j) [sigma_j = -1] r_j, (L^+L)_loc = kappa_j (1 + sigma_j)/2, L^2 = 0
 // dephasing j:   B = sqrt(gamma_j) sigma_j, (L^+L)_loc = (L^2)_loc = gamma_j
 // One thread per sample, 256 samples per CTA.
+template <typename R2>
 __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
-    int n, int W, int ns, int nops, double dt, const uint64_t* __restrict__ spins, const double2* __restrict__ r,
+    int n, int W, int ns, int nops, double dt, const uint64_t* __restrict__ spins, const R2* __restrict__ r,
     const double2* __restrict__ EH, const double* __restrict__ site, const int* __restrict__ opidx,
     const double* __restrict__ lpl, const double* __restrict__ dW, double2* __restrict__ Eeff_out,
     double2* __restrict__ v_out, double2* __restrict__ part_v, double* __restrict__ part_vmax) {
@@ -306,7 +359,7 @@ __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
     double2 v = make_double2(0, 0);
     if (s < ns) {
         const uint64_t* w = spins + ((size_t)t * ns + s) * W;
-        const double2* rs = r + ((size_t)t * ns + s) * n;
+        const R2* rs = r + ((size_t)t * ns + s) * n;
         double br = 0.0, bi = 0.0;  // sum_n bracket_n
         double vr = 0.0, vi = 0.0;  // sum_n dW_n B^n
         for (int j = 0; j < n; ++j) {
@@ -314,7 +367,7 @@ __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
             if (kap[j] > 0.0) {
                 double2 B = make_double2(0.0, 0.0);
                 if (sj < 0) {
-                    const double2 rj = rs[j];
+                    const double2 rj = make_double2((double)rs[j].x, (double)rs[j].y);
                     B = make_double2(skap[j] * rj.x, skap[j] * rj.y);
                 }
                 br += kap[j] * 0.5 * (1 + sj) - 2.0 * lpl_d[j] * B.x;
@@ -354,16 +407,21 @@ __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
     }
 }
 
-cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const double* dW,
-                        double dt, const double* lpl, const EvalBufs& b, double2* Eeff, double2* v,
+cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
+                        const double* dW, double dt, const double* lpl, const EvalBufs& b, double2* Eeff, double2* v,
                         cudaStream_t s) {
     ProfScope prof_(OTVMC_K_EST2, s);
     const otvmc_model* m = a->model;
     const int n = a->n, W = (n + 63) / 64;
     const size_t smem = (size_t)8 * n * 8 + VRED_BLOCK * 24 + 64;
     dim3 grid(v_blocks(ns), ntraj);
-    est2_kernel<<<grid, VRED_BLOCK, smem, s>>>(n, W, ns, m->nops, dt, spins, b.r, b.EH, m->site_d, m->opidx_d, lpl,
-                                               dW, Eeff, v, b.part_v, b.part_vmax);
+    if (fp32)
+        est2_kernel<float2><<<grid, VRED_BLOCK, smem, s>>>(n, W, ns, m->nops, dt, spins,
+                                                           reinterpret_cast<const float2*>(b.r), b.EH, m->site_d,
+                                                           m->opidx_d, lpl, dW, Eeff, v, b.part_v, b.part_vmax);
+    else
+        est2_kernel<double2><<<grid, VRED_BLOCK, smem, s>>>(n, W, ns, m->nops, dt, spins, b.r, b.EH, m->site_d,
+                                                            m->opidx_d, lpl, dW, Eeff, v, b.part_v, b.part_vmax);
     count_launch();
     return cudaGetLastError();
 }
@@ -508,7 +566,7 @@ __device__ __forceinline__ float2 to_r2<float2>(double2 v) { return make_float2(
 
 template <typename R2, typename R, bool SMEM_E>
 __global__ void __launch_bounds__(256) observables_kernel(int n, int W, int ns, int spt, const uint64_t* __restrict__ spins,
-                                                          const double2* __restrict__ r, const double2* __restrict__ Epm,
+                                                          const R2* __restrict__ r, const double2* __restrict__ Epm,
                                                           double* __restrict__ part_obs) {
     const int NT = ((n + 31) / 32) * 32;
     const int SPP = 256 / NT;
@@ -526,13 +584,13 @@ __global__ void __launch_bounds__(256) observables_kernel(int n, int W, int ns, 
     const double2* G1 = G0 + n * n;
     if (SMEM_E)
         for (int i = threadIdx.x; i < 2 * n * n; i += blockDim.x) E0[i] = to_r2<R2>(G0[i]);
-    double acc[9];
+    R acc[9];  // per-thread sums over its spt samples (FP32 on the MIXED path), then FP64
 #pragma unroll
-    for (int i = 0; i < 9; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 9; ++i) acc[i] = (R)0;
     for (int q = 0; q < spt; ++q) {
         const int s = blk * SB + g + q * SPP;
         __syncthreads();
-        if (active && s < ns) rs[g * NT + j] = to_r2<R2>(r[((size_t)t * ns + s) * n + j]);
+        if (active && s < ns) rs[g * NT + j] = r[((size_t)t * ns + s) * n + j];
         __syncthreads();
         if (!(active && s < ns)) continue;
         const uint64_t* w = spins + ((size_t)t * ns + s) * W;
@@ -555,22 +613,23 @@ __global__ void __launch_bounds__(256) observables_kernel(int n, int W, int ns, 
             b2.x += (R)sk * p.x;
             b2.y += (R)sk * p.y;
         }
-        const double2 rj = make_double2((double)rr[j].x, (double)rr[j].y);
-        const double2 ra = make_double2(rj.x * a2.x - rj.y * a2.y, rj.x * a2.y + rj.y * a2.x);
-        const double2 rb = make_double2(rj.x * b2.x - rj.y * b2.y, rj.x * b2.y + rj.y * b2.x);
+        const R2 rj = rr[j];
+        const R rax = rj.x * a2.x - rj.y * a2.y;
+        const R2 rb = {rj.x * b2.x - rj.y * b2.y, rj.x * b2.y + rj.y * b2.x};
+        const R fs = (R)sj, fS = (R)(S - sj);
         acc[0] += rj.x;
-        acc[1] += sj * rj.y;
-        acc[2] += sj;
-        acc[3] += ra.x;
-        acc[4] += -sj * rb.x;
-        if (j == 0) acc[5] += (double)S * S - n;
+        acc[1] += fs * rj.y;
+        acc[2] += fs;
+        acc[3] += rax;
+        acc[4] -= fs * rb.x;
+        if (j == 0) acc[5] += (R)(S * S - n);
         acc[6] += rb.y;
-        acc[7] += rj.x * (S - sj);
-        acc[8] += sj * rj.y * (S - sj);
+        acc[7] += rj.x * fS;
+        acc[8] += fs * rj.y * fS;
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 9; ++i) red[threadIdx.x * 9 + i] = acc[i];
+    for (int i = 0; i < 9; ++i) red[threadIdx.x * 9 + i] = (double)acc[i];
     __syncthreads();
     if (threadIdx.x < 9) {
         double sum = 0.0;
@@ -609,7 +668,8 @@ cudaError_t launch_observables(const otvmc_ansatz* a, const uint64_t* spins, int
 #define OTVMC_OBS_LAUNCH(R2, R, SM)                                                                          \
     do {                                                                                                     \
         cudaFuncSetAttribute(observables_kernel<R2, R, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        observables_kernel<R2, R, SM><<<grid, 256, smem, s>>>(n, W, ns, spt, spins, b.r, b.Epm, b.part_obs);  \
+        observables_kernel<R2, R, SM><<<grid, 256, smem, s>>>(n, W, ns, spt, spins,                           \
+                                                             reinterpret_cast<const R2*>(b.r), b.Epm, b.part_obs);  \
     } while (0)
     if (fp32) {
         if (sm) OTVMC_OBS_LAUNCH(float2, float, true);

@@ -86,7 +86,7 @@ extern "C" otvmc_status otvmc_local_estimators_noalloc(const otvmc_ansatz* a, co
     if (e != cudaSuccess) return cuda_status(e, "local_estimators_noalloc: est1 launch");
     e = launch_site_means(a, ntraj, ns, b, lpl, s);
     if (e != cudaSuccess) return cuda_status(e, "local_estimators_noalloc: site means launch");
-    e = launch_est2(a, spins_d, ntraj, ns, dW_d, dt, lpl, b, (double2*)Eeff_d, (double2*)v_d, s);
+    e = launch_est2(a, spins_d, ntraj, ns, fp32, dW_d, dt, lpl, b, (double2*)Eeff_d, (double2*)v_d, s);
     if (e != cudaSuccess) return cuda_status(e, "local_estimators_noalloc: est2 launch");
     return OTVMC_OK;
 }
