@@ -97,6 +97,7 @@ EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.qsum = c.take<long long>((size_t)T * 2);
     b.Epm = c.take<double2>((size_t)T * 2 * n * n);
     b.part_obs = c.take<double>((size_t)T * (nblk > (size_t)obs_blocks(n, ns) ? nblk : obs_blocks(n, ns)) * 9);
+    b.dsum = c.take<long long>((size_t)T * a->P * 3);
     return b;
 }
 

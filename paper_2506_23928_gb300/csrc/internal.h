@@ -104,6 +104,7 @@ struct EvalBufs {
     long long* qsum;     // [T][2]
     double2* Epm;        // [T][2][n][n] exp(+-4 eta) for observables
     double* part_obs;    // [T][obs_blocks][9]
+    long long* dsum;     // [T][P][3] exact sums behind D and obar
 };
 
 size_t eval_bufs_bytes(const otvmc_ansatz* a, int ntraj, int ns);

@@ -7,63 +7,97 @@
 namespace otvmc {
 
 // ------------------------------------------------------------------ D by exact int64 sums
-// Thread = parameter k.  With q(x) the quantised centred v, sum_x O_xk q(x) =
-// 2 sum_{x: O_xk = +1} q(x) - sum_x q(x) is exact; so is the count c_k = sum_x O_xk, whence
-// obar_k = c_k / ns and D_k = (sum_x O_xk q(x) - c_k Q / ns) 2^-e / ns (Q = sum_x q(x)).
-constexpr int DT = 256;  // samples staged per tile
+// With q(x) the quantised centred v, sum_x O_xk q(x) = 2 sum_{x: O_xk = +1} q(x) - sum_x q(x)
+// is exact; so is the count c_k = sum_x O_xk, whence obar_k = c_k / ns and
+// D_k = (sum_x O_xk q(x) - c_k Q / ns) 2^-e / ns (Q = sum_x q(x)).
+//
+// The sums over {x: O_xk = +1} run as an outer-product tile: a CTA takes the 64-site blocks
+// (JB, LB), JB <= LB, and a quarter of the samples; thread (tj, tl) owns sites
+// j = 64 JB + 4 tj + a, l = 64 LB + 4 tl + b (a, b < 4), i.e. the pairs (j, l), j < l, and on
+// the diagonal of a diagonal tile the singles O = sigma_j.  Partial sums are added into
+// dsum with 64-bit integer atomics (exact, so the order does not matter).
+constexpr int DT = 256;      // samples staged per pass
+constexpr int DSPLIT = 4;    // sample ranges per trajectory
 
-__global__ void __launch_bounds__(256) D_fixed_jastrow_kernel(int n, int W, int P, int ns,
-                                                              const uint64_t* __restrict__ spins,
-                                                              const int* __restrict__ pairs,
-                                                              const long long* __restrict__ qv,
-                                                              const double* __restrict__ vinfo,
-                                                              const long long* __restrict__ qsum,
-                                                              double* __restrict__ obar, double2* __restrict__ D) {
-    __shared__ uint64_t sw[DT * 4];
+__host__ __device__ __forceinline__ int d_pair_idx(int lo, int hi, int n) {
+    return lo * n - lo * (lo + 1) / 2 + (hi - lo - 1);
+}
+
+__global__ void __launch_bounds__(256) D_sums_jastrow_kernel(int n, int W, int P, int ns,
+                                                             const uint64_t* __restrict__ spins,
+                                                             const long long* __restrict__ qv,
+                                                             unsigned long long* __restrict__ dsum) {
+    __shared__ uint64_t swJ[DT], swL[DT];
     __shared__ longlong2 sq[DT];
-    const int t = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = k < P;
-    int j = 0, l = 0;
-    bool single = true;
-    if (valid) {
-        if (k < n) {
-            j = k;
-        } else {
-            j = pairs[2 * (k - n)];
-            l = pairs[2 * (k - n) + 1];
-            single = false;
-        }
-    }
-    const int wj = j >> 6, bj = j & 63, wl = l >> 6, bl = l & 63;
-    long long ar = 0, ai = 0;
-    int cnt = 0;
-    for (int x0 = 0; x0 < ns; x0 += DT) {
-        const int nt = min(DT, ns - x0);
+    const int t = blockIdx.z, tid = threadIdx.x;
+    int LB = 0;
+    while ((LB + 1) * (LB + 2) / 2 <= (int)blockIdx.y) ++LB;
+    const int JB = blockIdx.y - LB * (LB + 1) / 2;
+    const int tj = tid >> 4, tl = tid & 15;
+    const int j0 = 64 * JB + 4 * tj, l0 = 64 * LB + 4 * tl;
+    const bool diag = (JB == LB) && (tj == tl);
+    // this thread owns a useful entry iff some (j, l) with j <= l, both < n
+    const bool work = j0 < n && l0 < n && j0 <= l0 + 3;
+    const int xs = (int)(((long long)ns * blockIdx.x) / gridDim.x), xe = (int)(((long long)ns * (blockIdx.x + 1)) / gridDim.x);
+    long long ar[16], ai[16];
+    int cnt[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) ar[e] = ai[e] = 0, cnt[e] = 0;
+    for (int x0 = xs; x0 < xe; x0 += DT) {
+        const int nt = min(DT, xe - x0);
         __syncthreads();
-        for (int i = threadIdx.x; i < nt * W; i += blockDim.x) sw[i] = spins[((size_t)t * ns + x0) * W + i];
-        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-            const size_t o = ((size_t)t * ns + x0 + i) * 2;
-            sq[i] = make_longlong2(qv[o], qv[o + 1]);
+        for (int i = tid; i < nt; i += blockDim.x) {
+            const size_t xo = (size_t)t * ns + x0 + i;
+            swJ[i] = spins[xo * W + JB];
+            swL[i] = spins[xo * W + LB];
+            sq[i] = make_longlong2(qv[xo * 2], qv[xo * 2 + 1]);
         }
         __syncthreads();
-        if (valid) {
+        if (work) {
             for (int x = 0; x < nt; ++x) {
-                const uint64_t bitj = (sw[x * W + wj] >> bj) & 1ull;
-                const uint64_t bitl = (sw[x * W + wl] >> bl) & 1ull;
-                const bool up = single ? (bitj != 0ull) : (bitj == bitl);
-                if (up) {
-                    const longlong2 q = sq[x];
-                    ar += q.x;
-                    ai += q.y;
-                    ++cnt;
-                }
+                const uint32_t bj = (uint32_t)(swJ[x] >> (4 * tj)) & 0xFu;
+                const uint32_t bl = (uint32_t)(swL[x] >> (4 * tl)) & 0xFu;
+                const longlong2 q = sq[x];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const uint32_t up = (diag && a == b) ? (bj >> a) & 1u : ~((bj >> a) ^ (bl >> b)) & 1u;
+                        if (up) {
+                            ar[4 * a + b] += q.x;
+                            ai[4 * a + b] += q.y;
+                            ++cnt[4 * a + b];
+                        }
+                    }
             }
         }
     }
-    if (!valid) return;
+    if (!work) return;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int j = j0 + a, l = l0 + b;
+            if (j >= n || l >= n || j > l || (j == l && !diag)) continue;
+            const int k = j == l ? j : n + d_pair_idx(j, l, n);
+            unsigned long long* d = dsum + ((size_t)t * P + k) * 3;
+            atomicAdd(d, (unsigned long long)ar[4 * a + b]);
+            atomicAdd(d + 1, (unsigned long long)ai[4 * a + b]);
+            atomicAdd(d + 2, (unsigned long long)(long long)cnt[4 * a + b]);
+        }
+}
+
+__global__ void __launch_bounds__(256) D_final_kernel(int P, int ns, const long long* __restrict__ dsum,
+                                                      const double* __restrict__ vinfo,
+                                                      const long long* __restrict__ qsum, double* __restrict__ obar,
+                                                      double2* __restrict__ D) {
+    const int t = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const long long* d = dsum + ((size_t)t * P + k) * 3;
+    const long long ar = d[0], ai = d[1], cnt = d[2];
     const long long Qr = qsum[2 * t], Qi = qsum[2 * t + 1];
-    const long long c = 2 * (long long)cnt - ns;
+    const long long c = 2 * cnt - ns;
     const double inv = vinfo[4 * t + 2] / ns;
     const double dr = ((double)(2 * ar - Qr) - (double)c * (double)Qr / ns) * inv;
     const double di = ((double)(2 * ai - Qi) - (double)c * (double)Qi / ns) * inv;
@@ -75,8 +109,14 @@ cudaError_t launch_D_fixed_jastrow(const otvmc_ansatz* a, const uint64_t* spins,
                                    const EvalBufs& b, double* obar, double2* D, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_D, s);
     const int n = a->n, W = (n + 63) / 64, P = (int)a->P;
-    dim3 grid((P + 255) / 256, ntraj);
-    D_fixed_jastrow_kernel<<<grid, 256, 0, s>>>(n, W, P, ns, spins, a->pairs_d, b.qv, b.vinfo, b.qsum, obar, D);
+    cudaError_t e = cudaMemsetAsync(b.dsum, 0, (size_t)ntraj * P * 3 * sizeof(long long), s);
+    if (e != cudaSuccess) return e;
+    dim3 grid(DSPLIT, W * (W + 1) / 2, ntraj);
+    D_sums_jastrow_kernel<<<grid, 256, 0, s>>>(n, W, P, ns, spins, b.qv, (unsigned long long*)b.dsum);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    D_final_kernel<<<dim3((P + 255) / 256, ntraj), 256, 0, s>>>(P, ns, b.dsum, b.vinfo, b.qsum, obar, D);
     count_launch();
     return cudaGetLastError();
 }

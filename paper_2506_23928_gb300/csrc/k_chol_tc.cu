@@ -51,8 +51,8 @@ __device__ __forceinline__ float a_orig(const float* Gt, const double* ob, int P
 }
 
 // ------------------------------------------------------------------------- update (tcgen05)
-__global__ void __launch_bounds__(192, 2) chol_update_kernel(const __grid_constant__ CUtensorMap tmap, int t0, int P,
-                                                             int ns, int NT, int jb, float eps,
+__global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16* __restrict__ Lb, size_t plane,
+                                                             int KC, int t0, int P, int ns, int jb, float eps,
                                                              const float* __restrict__ G,
                                                              const double* __restrict__ obar, float* __restrict__ Pn,
                                                              const int* __restrict__ fail, int* status) {
@@ -101,12 +101,12 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __grid_consta
                 }
                 uint8_t* st = smem + s * STAGE;
                 mbar_expect_tx(&full[s], STAGE);
-                // k slice kb covers columns [32 kb, 32 kb + 32) of the 64-column chunk kb / 2
-                const int kx = (kb & 1) * BK, kc = kb >> 1;
+                // k slice kb = chunk kb of the row tiles i0 / 128 (A) and jb / 128 (B): each an
+                // 8 KB contiguous image of the swizzled shared-memory box
                 for (int p = 0; p < NPC; ++p) {
-                    const int pl = (t * NPC + p) * NT;
-                    tma_load_4d(st + p * BOX, &tmap, &full[s], kx, 0, kc, pl + (i0 >> 7));
-                    tma_load_4d(st + (NPC + p) * BOX, &tmap, &full[s], kx, 0, kc, pl + (jb >> 7));
+                    const __nv_bfloat16* pl = Lb + (size_t)(t * NPC + p) * plane;
+                    bulk_load(st + p * BOX, pl + ((size_t)(i0 >> 7) * KC + kb) * (BOX / 2), BOX, &full[s]);
+                    bulk_load(st + (NPC + p) * BOX, pl + ((size_t)(jb >> 7) * KC + kb) * (BOX / 2), BOX, &full[s]);
                 }
                 ++issued;
             }
@@ -176,14 +176,17 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __grid_consta
 
 // --------------------------------------------------------------------------- panel (SIMT)
 // BF16 pieces of L are stored tiled: for piece p of trajectory t, the 128-row tile i / 128
-// and the 64-column block k / 64 form one contiguous 16 KB chunk [i % 128][k % 64], so
-// that one TMA box of the update kernel is one contiguous read.
+// and the 32-column chunk k / 32 form one contiguous 8 KB block [i % 128][k % 32] laid out
+// exactly as the update kernel's shared-memory operand box: rows of 64 bytes with the
+// 64-byte swizzle (16-byte unit u of row r stored at unit u ^ ((r / 2) mod 4)), so that one
+// box is one contiguous bulk copy.
 struct LbLayout {
     int NT;  // row tiles, ceil(P / 128)
-    int KB;  // 64-column blocks, LD / 64
-    __device__ __forceinline__ size_t plane() const { return (size_t)NT * KB * 128 * 64; }
+    int KC;  // 32-column chunks, LD / 32
+    __host__ __device__ __forceinline__ size_t plane() const { return (size_t)NT * KC * 128 * 32; }
     __device__ __forceinline__ size_t at(int i, int k) const {
-        return (((size_t)(i >> 7) * KB + (k >> 6)) * 128 + (i & 127)) * 64 + (k & 63);
+        const int r = i & 127, u = (k & 31) >> 3;
+        return (((size_t)(i >> 7) * KC + (k >> 5)) * 128 + r) * 32 + ((u ^ ((r >> 1) & 3)) << 3) + (k & 7);
     }
 };
 
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         if (tid == 0) fail[t] = 1;
         return;
     }
-    const LbLayout lay{(P + NB - 1) / NB, LD / 64};
+    const LbLayout lay{(P + NB - 1) / NB, LD / 32};
     if (isA) {
         float* Lft = Lf + (size_t)t * P * LD;
         __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
@@ -585,7 +588,7 @@ __global__ void __launch_bounds__(256, 2) chol_trsm_kernel(int t0, int P, int LD
 #pragma unroll
             for (int u = 0; u < 8; ++u) acc[a][u] = dot4(cv[a], lv[u], acc[a][u]);
     }
-    const LbLayout lay{(P + NB - 1) / NB, LD / 64};
+    const LbLayout lay{(P + NB - 1) / NB, LD / 32};
     float* Lft = Lf + (size_t)t * P * LD;
     __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
     const int nv = nb - cg * 8;
@@ -776,23 +779,28 @@ __global__ void __launch_bounds__(256) chol_resid_kernel(int t0, int P, const fl
 }
 
 // Triangular solves L L^T x = y for the two right-hand sides (real and imaginary parts) of
-// one trajectory, held in shared memory as y[0..PY) and y[PY..2 PY); one CTA per trajectory.
-// Forward, block b (left-looking): the 128 rows of the block take their dot products with
-// y[0 : jb) (lanes along the row, four rows per warp in flight), then y_b = L_bb^-1 (.) from
-// the stored inverse.  Backward, block b from the last: column sums of the rows below
-// (lanes along the block's columns, warps along the rows), then x_b = L_bb^-T (.).
+// one trajectory, held in shared memory as y[0..PY) and y[PY..2 PY); one CTA of SW_WARPS
+// warps per trajectory.  Forward, block b (left-looking): the 128 rows of the block take
+// their dot products with y[0 : jb) (lanes along the row, four rows per warp and four
+// column steps in flight), then y_b = L_bb^-1 (.) from the stored inverse.  Backward,
+// block b from the last: column sums of the rows below (lanes along the block's columns,
+// warps along the rows, eight rows per warp in flight), then x_b = L_bb^-T (.).
+constexpr int SW_WARPS = 16;
+constexpr int SWEEP_THREADS = 32 * SW_WARPS;
+constexpr int SW_ROWS = NB / SW_WARPS;   // rows of a block per warp
+
 __device__ void sweep_forward(int P, int PY, int LD, const float* Lt, const float* Dv, float* y, float* tb) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nblk = (P + NB - 1) / NB;
     for (int b = 0; b < nblk; ++b) {
         const int jb = b * NB, nb = min(NB, P - jb);
 #pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
-            const int rl = warp * 16 + 4 * g;
+        for (int g = 0; g < SW_ROWS / 4; ++g) {
+            const int rl = warp * SW_ROWS + 4 * g;
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = 0.f;
-#pragma unroll 2
+#pragma unroll 4
             for (int q = 0; q < b; ++q) {
                 const int c = q * NB + 4 * lane;
                 const float4 y0 = ld4(y + c), y1 = ld4(y + PY + c);
@@ -813,9 +821,9 @@ __device__ void sweep_forward(int P, int PY, int LD, const float* Lt, const floa
         __syncthreads();
         const float* Db = Dv + (size_t)b * NB * NB;
         const float4 t0 = ld4(tb + 4 * lane), t1 = ld4(tb + NB + 4 * lane);
-#pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
-            const int rl = warp * 16 + 4 * g;
+#pragma unroll
+        for (int g = 0; g < SW_ROWS / 4; ++g) {
+            const int rl = warp * SW_ROWS + 4 * g;
             float v[8];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
@@ -833,6 +841,25 @@ __device__ void sweep_forward(int P, int PY, int LD, const float* Lt, const floa
     }
 }
 
+__device__ __forceinline__ void acc_col4(float (&acc)[4][2], float4 l, float x0, float x1) {
+    acc[0][0] = fmaf(l.x, x0, acc[0][0]);
+    acc[1][0] = fmaf(l.y, x0, acc[1][0]);
+    acc[2][0] = fmaf(l.z, x0, acc[2][0]);
+    acc[3][0] = fmaf(l.w, x0, acc[3][0]);
+    acc[0][1] = fmaf(l.x, x1, acc[0][1]);
+    acc[1][1] = fmaf(l.y, x1, acc[1][1]);
+    acc[2][1] = fmaf(l.z, x1, acc[2][1]);
+    acc[3][1] = fmaf(l.w, x1, acc[3][1]);
+}
+
+// Sum of the warps' partial column sums (fixed order); red is [SW_WARPS][NB][2].
+__device__ __forceinline__ void put_col4(float* red, int warp, int lane, const float (&acc)[4][2]) {
+    reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[0] =
+        make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]);
+    reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[1] =
+        make_float4(acc[2][0], acc[2][1], acc[3][0], acc[3][1]);
+}
+
 __device__ void sweep_backward(int P, int PY, int LD, const float* Lt, const float* Dv, float* y, float* tb,
                                float* red) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -842,58 +869,40 @@ __device__ void sweep_backward(int P, int PY, int LD, const float* Lt, const flo
         float acc[4][2];
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.f;
-#pragma unroll 4
-        for (int i = jb + NB + warp; i < P; i += 8) {
-            const float4 l = ld4(Lt + (size_t)i * LD + jb + 4 * lane);
-            const float x0 = y[i], x1 = y[PY + i];
-            acc[0][0] = fmaf(l.x, x0, acc[0][0]);
-            acc[1][0] = fmaf(l.y, x0, acc[1][0]);
-            acc[2][0] = fmaf(l.z, x0, acc[2][0]);
-            acc[3][0] = fmaf(l.w, x0, acc[3][0]);
-            acc[0][1] = fmaf(l.x, x1, acc[0][1]);
-            acc[1][1] = fmaf(l.y, x1, acc[1][1]);
-            acc[2][1] = fmaf(l.z, x1, acc[2][1]);
-            acc[3][1] = fmaf(l.w, x1, acc[3][1]);
+        int i = jb + NB + warp;
+        for (; i + 7 * SW_WARPS < P; i += 8 * SW_WARPS) {
+            float4 l[8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) l[a] = ld4(Lt + (size_t)(i + a * SW_WARPS) * LD + jb + 4 * lane);
+#pragma unroll
+            for (int a = 0; a < 8; ++a) acc_col4(acc, l[a], y[i + a * SW_WARPS], y[PY + i + a * SW_WARPS]);
         }
-        reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[0] =
-            make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]);
-        reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[1] =
-            make_float4(acc[2][0], acc[2][1], acc[3][0], acc[3][1]);
+        for (; i < P; i += SW_WARPS) acc_col4(acc, ld4(Lt + (size_t)i * LD + jb + 4 * lane), y[i], y[PY + i]);
+        put_col4(red, warp, lane, acc);
         __syncthreads();
-        {
+        if (tid < 2 * NB) {
             const int c = tid >> 1, h = tid & 1;
             float s = 0.f;
 #pragma unroll
-            for (int w = 0; w < 8; ++w) s += red[(w * NB + c) * 2 + h];
+            for (int w = 0; w < SW_WARPS; ++w) s += red[(w * NB + c) * 2 + h];
             tb[h * NB + c] = c < nb ? y[h * PY + jb + c] - s : 0.f;
         }
         __syncthreads();
         const float* Db = Dv + (size_t)b * NB * NB;
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.f;
-#pragma unroll 4
-        for (int k = warp; k < NB; k += 8) {
-            const float4 l = ld4(Db + (size_t)k * NB + 4 * lane);
-            const float t0 = tb[k], t1 = tb[NB + k];
-            acc[0][0] = fmaf(l.x, t0, acc[0][0]);
-            acc[1][0] = fmaf(l.y, t0, acc[1][0]);
-            acc[2][0] = fmaf(l.z, t0, acc[2][0]);
-            acc[3][0] = fmaf(l.w, t0, acc[3][0]);
-            acc[0][1] = fmaf(l.x, t1, acc[0][1]);
-            acc[1][1] = fmaf(l.y, t1, acc[1][1]);
-            acc[2][1] = fmaf(l.z, t1, acc[2][1]);
-            acc[3][1] = fmaf(l.w, t1, acc[3][1]);
+#pragma unroll
+        for (int kk = 0; kk < NB / SW_WARPS; ++kk) {
+            const int k = warp + kk * SW_WARPS;
+            acc_col4(acc, ld4(Db + (size_t)k * NB + 4 * lane), tb[k], tb[NB + k]);
         }
-        reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[0] =
-            make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]);
-        reinterpret_cast<float4*>(red + (warp * NB + 4 * lane) * 2)[1] =
-            make_float4(acc[2][0], acc[2][1], acc[3][0], acc[3][1]);
+        put_col4(red, warp, lane, acc);
         __syncthreads();
-        {
+        if (tid < 2 * NB) {
             const int c = tid >> 1, h = tid & 1;
             float s = 0.f;
 #pragma unroll
-            for (int w = 0; w < 8; ++w) s += red[(w * NB + c) * 2 + h];
+            for (int w = 0; w < SW_WARPS; ++w) s += red[(w * NB + c) * 2 + h];
             if (c < nb) y[h * PY + jb + c] = s;
         }
         __syncthreads();
@@ -905,7 +914,6 @@ __device__ void sweep_backward(int P, int PY, int LD, const float* Lt, const flo
 //   mode 1: r = D - (S + eps I) x with S x = (G x) / ns - obar (obar . x), G x summed from the
 //           residual kernel's slots in FP64; then dx = L^-T L^-1 r and x += dx.
 // The last pass writes delta (and the shift used), the others keep x in xw (FP64).
-constexpr int SWEEP_THREADS = 256;
 __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P, int LD, int ns, double eps, int mode,
                                                                     int last, const double* __restrict__ obar,
                                                                     const double2* __restrict__ D,
@@ -921,8 +929,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
     const int nblk = (P + NB - 1) / NB, PY = nblk * NB;
     extern __shared__ __align__(16) float wsm[];
     float* y = wsm;              // [2][PY]
-    float* red = y + 2 * PY;     // [8][NB][2]
-    float* tb = red + 8 * NB * 2;  // [2][NB]
+    float* red = y + 2 * PY;              // [SW_WARPS][NB][2]
+    float* tb = red + SW_WARPS * NB * 2;  // [2][NB]
     __shared__ double dred[2][SWEEP_THREADS / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float* Lt = Lf + (size_t)t * P * LD;
@@ -1065,7 +1073,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
         p += (bytes + 255) & ~(size_t)255;
         return (void*)r;
     };
-    const int NT = (P + NB - 1) / NB, KB = LD / 64;
+    const int NT = (P + NB - 1) / NB;
     __nv_bfloat16* Lb = (__nv_bfloat16*)take((size_t)ntraj * NPC * NT * 128 * LD * 2);
     float* Lf = (float*)take((size_t)ntraj * P * LD * 4);
     float* Pn = (float*)take((size_t)ntraj * P * NB * 4);
@@ -1076,27 +1084,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     float* yv = (float*)take((size_t)ntraj * 2 * P * 4);
     double* part = (double*)take((size_t)ntraj * nblk * nblk * 2 * NB * 8);
 
-    auto encode = tc::get_encode();
-    if (!encode) return cudaErrorNotSupported;
-    CUtensorMap map;
-    const cuuint64_t dims[4] = {64u, 128u, (cuuint64_t)KB, (cuuint64_t)ntraj * NPC * NT};
-    const cuuint64_t strides[3] = {128u, 128u * 128u, (cuuint64_t)KB * 128u * 128u};
-    const cuuint32_t box[4] = {(cuuint32_t)BK, 128u, 1u, 1u};
-    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
-    const CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)Lb, dims, strides, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) {
-        char buf[256];
-        snprintf(buf, sizeof(buf),
-                 "cholesky: cuTensorMapEncodeTiled returned %d (addr %p dims %llu %llu %llu %llu strides %llu %llu "
-                 "%llu box %u %u)",
-                 (int)cr, (void*)Lb, (unsigned long long)dims[0], (unsigned long long)dims[1],
-                 (unsigned long long)dims[2], (unsigned long long)dims[3], (unsigned long long)strides[0],
-                 (unsigned long long)strides[1], (unsigned long long)strides[2], box[0], box[1]);
-        set_error(buf);
-        return cudaErrorInvalidValue;
-    }
+    const LbLayout lay{NT, LD / 32};
+    const size_t plane = lay.plane();
 
     cudaError_t e = cudaMemsetAsync(fail, 0, (size_t)ntraj * 4, s);
     if (e != cudaSuccess) return chol_fail(e, "memset");
@@ -1106,7 +1095,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     if (e != cudaSuccess) return chol_fail(e, "update attribute");
     const float feps = (float)eps;
     const int PY = (int)nblk * NB;
-    const int wsmem = (2 * PY + 8 * NB * 2 + 2 * NB) * (int)sizeof(float);
+    const int wsmem = (2 * PY + SW_WARPS * NB * 2 + 2 * NB) * (int)sizeof(float);
     e = cudaFuncSetAttribute(chol_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
     if (e != cudaSuccess) return chol_fail(e, "sweep attribute");
     // trajectory groups on forked streams: one group's latency-bound kernels overlap the
@@ -1127,7 +1116,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
             if (jb > 0) {
                 ProfScope pu(OTVMC_K_CHOLU, gsm);
                 dim3 grid((P - jb + 127) / 128, nt);
-                chol_update_kernel<<<grid, 192, SMEM_U, gsm>>>(map, ta, P, ns, NT, jb, feps, G, obar, Pn, fail, status);
+                chol_update_kernel<<<grid, 192, SMEM_U, gsm>>>(Lb, plane, LD / 32, ta, P, ns, jb, feps, G, obar, Pn,
+                                                               fail, status);
                 count_launch();
             }
             {

@@ -407,6 +407,100 @@ __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
     }
 }
 
+// MIXED path of est2: the same sums regrouped per site,
+//   sum_n bracket_n = C0 + sum_j c_j sigma_j + sum_{j down} alpha_j r_j,
+//   sum_n dW_n B^n  =      sum_j d_j sigma_j + sum_{j down} beta_j r_j,
+// with C0 = sum_j (kappa_j / 2 + 2 gamma_j), c_j = kappa_j / 2 - 2 <L+L^+>_deph sqrt(gamma_j),
+// d_j = dW_deph sqrt(gamma_j), alpha_j = -2 <L+L^+>_decay sqrt(kappa_j), beta_j = dW_decay
+// sqrt(kappa_j).  Products and runs of eight sites in FP32, the runs added in FP64.
+__global__ void __launch_bounds__(VRED_BLOCK) est2_mixed_kernel(
+    int n, int W, int ns, int nops, double dt, const uint64_t* __restrict__ spins, const float2* __restrict__ r,
+    const double2* __restrict__ EH, const double* __restrict__ site, const int* __restrict__ opidx,
+    const double* __restrict__ lpl, const double* __restrict__ dW, double2* __restrict__ Eeff_out,
+    double2* __restrict__ v_out, double2* __restrict__ part_v, double* __restrict__ part_vmax) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* al = (float*)smraw;  // [n]
+    float* be = al + n;
+    float* cc = be + n;
+    float* dd = cc + n;
+    double2* red = (double2*)(((uintptr_t)(dd + n) + 15) & ~(uintptr_t)15);  // [VRED_BLOCK]
+    double* redm = (double*)(red + VRED_BLOCK);
+    __shared__ double c0s;
+    const int t = blockIdx.y;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int od = opidx[j], og = opidx[n + j];
+        const double lpd = od >= 0 ? lpl[(size_t)t * nops + od] : 0.0, lpg = og >= 0 ? lpl[(size_t)t * nops + og] : 0.0;
+        const double dwd = od >= 0 ? dW[(size_t)t * nops + od] : 0.0, dwg = og >= 0 ? dW[(size_t)t * nops + og] : 0.0;
+        const double kap = site[j], skap = site[2 * n + j], sgam = site[3 * n + j];
+        al[j] = (float)(-2.0 * lpd * skap);
+        be[j] = (float)(dwd * skap);
+        cc[j] = (float)(0.5 * kap - 2.0 * lpg * sgam);
+        dd[j] = (float)(dwg * sgam);
+    }
+    if (threadIdx.x == 0) {
+        double c0 = 0.0;
+        for (int j = 0; j < n; ++j) c0 += 0.5 * site[j] + 2.0 * site[n + j];
+        c0s = c0;
+    }
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double2 v = make_double2(0, 0);
+    if (s < ns) {
+        const uint64_t* w = spins + ((size_t)t * ns + s) * W;
+        const float2* rs = r + ((size_t)t * ns + s) * n;
+        double Ar = 0.0, Ai = 0.0, Vr = 0.0, Vi = 0.0, Cs = 0.0, Ds = 0.0;
+        for (int j0 = 0; j0 < n; j0 += 8) {
+            const uint64_t word = w[j0 >> 6] >> (j0 & 63);
+            float ar = 0.f, ai = 0.f, vr = 0.f, vi = 0.f, cs = 0.f, ds = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = j0 + jj;
+                if (j < n) {
+                    const bool up = (word >> jj) & 1ull;
+                    const float sg = up ? 1.f : -1.f;
+                    cs = fmaf(cc[j], sg, cs);
+                    ds = fmaf(dd[j], sg, ds);
+                    if (!up) {
+                        const float2 rj = rs[j];
+                        ar = fmaf(al[j], rj.x, ar);
+                        ai = fmaf(al[j], rj.y, ai);
+                        vr = fmaf(be[j], rj.x, vr);
+                        vi = fmaf(be[j], rj.y, vi);
+                    }
+                }
+            }
+            Ar += ar;
+            Ai += ai;
+            Vr += vr;
+            Vi += vi;
+            Cs += cs;
+            Ds += ds;
+        }
+        const double br = c0s + Cs + Ar, bi = Ai;
+        double2 E = EH[(size_t)t * ns + s];
+        E.x += 0.5 * bi;
+        E.y -= 0.5 * br;
+        v = make_double2(dt * E.y + Ds + Vr, -dt * E.x + Vi);
+        if (Eeff_out) Eeff_out[(size_t)t * ns + s] = E;
+        v_out[(size_t)t * ns + s] = v;
+    }
+    red[threadIdx.x] = v;
+    redm[threadIdx.x] = fmax(fabs(v.x), fabs(v.y));
+    __syncthreads();
+    for (int st = VRED_BLOCK / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            red[threadIdx.x].x += red[threadIdx.x + st].x;
+            red[threadIdx.x].y += red[threadIdx.x + st].y;
+            redm[threadIdx.x] = fmax(redm[threadIdx.x], redm[threadIdx.x + st]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_v[(size_t)t * gridDim.x + blockIdx.x] = red[0];
+        part_vmax[(size_t)t * gridDim.x + blockIdx.x] = redm[0];
+    }
+}
+
 cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
                         const double* dW, double dt, const double* lpl, const EvalBufs& b, double2* Eeff, double2* v,
                         cudaStream_t s) {
@@ -416,9 +510,9 @@ cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj,
     const size_t smem = (size_t)8 * n * 8 + VRED_BLOCK * 24 + 64;
     dim3 grid(v_blocks(ns), ntraj);
     if (fp32)
-        est2_kernel<float2><<<grid, VRED_BLOCK, smem, s>>>(n, W, ns, m->nops, dt, spins,
-                                                           reinterpret_cast<const float2*>(b.r), b.EH, m->site_d,
-                                                           m->opidx_d, lpl, dW, Eeff, v, b.part_v, b.part_vmax);
+        est2_mixed_kernel<<<grid, VRED_BLOCK, (size_t)4 * n * 4 + 16 + VRED_BLOCK * 24, s>>>(
+            n, W, ns, m->nops, dt, spins, reinterpret_cast<const float2*>(b.r), b.EH, m->site_d, m->opidx_d, lpl, dW,
+            Eeff, v, b.part_v, b.part_vmax);
     else
         est2_kernel<double2><<<grid, VRED_BLOCK, smem, s>>>(n, W, ns, m->nops, dt, spins, b.r, b.EH, m->site_d,
                                                             m->opidx_d, lpl, dW, Eeff, v, b.part_v, b.part_vmax);
@@ -597,21 +691,37 @@ __global__ void __launch_bounds__(256) observables_kernel(int n, int W, int ns, 
         int S = 0;
         for (int ww = 0; ww < W; ++ww) S += 2 * __popcll(w[ww]);
         S -= n;
-        const int sj = ((w[j >> 6] >> (j & 63)) & 1ull) ? 1 : -1;
+        const uint64_t sjb = (w[j >> 6] >> (j & 63)) & 1ull;
+        const int sj = sjb ? 1 : -1;
         R2 a2 = {0, 0}, b2 = {0, 0};
         const R2* rr = rs + g * NT;
-        for (int k = 0; k < n; ++k) {
-            if (k == j) continue;
-            const int sk = ((w[k >> 6] >> (k & 63)) & 1ull) ? 1 : -1;
-            R2 e;
-            if (SMEM_E) e = (sj == sk) ? E0[k * n + j] : E1[k * n + j];
-            else e = to_r2<R2>((sj == sk) ? G0[k * n + j] : G1[k * n + j]);
-            const R2 rk = rr[k];
-            const R2 p = {rk.x * e.x - rk.y * e.y, rk.x * e.y + rk.y * e.x};
-            a2.x += p.x;
-            a2.y += p.y;
-            b2.x += (R)sk * p.x;
-            b2.y += (R)sk * p.y;
+        // all k, the diagonal included (E^{+}_jj = 1), whose term r_j (and sigma_j r_j) is
+        // removed after the loop
+        for (int k0 = 0; k0 < n; k0 += 64) {
+            uint64_t word = w[k0 >> 6];
+            const int kend = min(64, n - k0);
+#pragma unroll 4
+            for (int kk = 0; kk < kend; ++kk, word >>= 1) {
+                const int k = k0 + kk;
+                const uint64_t skb = word & 1ull;
+                R2 e;
+                if (SMEM_E) e = (skb == sjb ? E0 : E1)[k * n + j];
+                else e = to_r2<R2>((skb == sjb ? G0 : G1)[k * n + j]);
+                const R2 rk = rr[k];
+                const R2 p = {rk.x * e.x - rk.y * e.y, rk.x * e.y + rk.y * e.x};
+                const R sk = skb ? (R)1 : (R)-1;
+                a2.x += p.x;
+                a2.y += p.y;
+                b2.x = fma(sk, p.x, b2.x);
+                b2.y = fma(sk, p.y, b2.y);
+            }
+        }
+        {
+            const R2 rjj = rr[j];
+            a2.x -= rjj.x;
+            a2.y -= rjj.y;
+            b2.x -= (R)sj * rjj.x;
+            b2.y -= (R)sj * rjj.y;
         }
         const R2 rj = rr[j];
         const R rax = rj.x * a2.x - rj.y * a2.y;
