@@ -207,8 +207,8 @@ OTVMC_API otvmc_status otvmc_build_S_F(const otvmc_ansatz* ansatz, const double*
                              double* D_d, void* work_d, size_t work_bytes, void* stream);
 
 /* ----------------------------------------------------------------- A7: regularised solve
- * delta = (S + eps I)^{-1} D by Cholesky (diagonal shift; otVMC procedure paragraph uses
- * an SNR filter, OTVMC_REG_SNR, which is not built in this version).  If S + eps I is
+ * delta = (S + eps I)^{-1} D by Cholesky (diagonal shift; the SNR filter of the otVMC
+ * procedure paragraph needs the samples and is otvmc_solve_snr).  If S + eps I is
  * not positive definite the shift is raised (x100, up to 3 times) and OTVMC_ERR_NOT_PD is
  * recorded only if all attempts fail (delta = 0 then).
  *   FP64:  S_d (full FP64), FP64 Cholesky.
@@ -221,6 +221,24 @@ OTVMC_API otvmc_status otvmc_solve_step(const otvmc_ansatz* ansatz, int ntraj, i
                               const float* G_d, const double* obar_d, const double* D_d,
                               double* delta_d, double* shift_used_d, void* work_d,
                               size_t work_bytes, void* stream);
+
+/* SNR-filtered pseudo-inverse in the eigenbasis of S (otVMC procedure paragraph; the filter of
+ * the signal-to-noise regularisation it cites, whose shape the paper does not print -- read
+ * here as below).  S = V diag(lambda) V^T, rho = V^T D, and per sample
+ * Q_k(x) = (V^T O_c(x))_k v_c(x) (O_c, v_c centred by their sample means), whose mean is rho_k:
+ *   SNR_k = |rho_k| / sqrt(Var_x Q_k / ns),
+ *   f_k = 1 / (1 + (snr_thresh / SNR_k)^6) * 1 / (1 + (eps_svd lambda_max / lambda_k)^6),
+ *   delta = V diag(f_k / lambda_k) rho, eigenvalues lambda_k <= 0 dropped.
+ * Jastrow ansatz, P <= 96: one CTA per trajectory does a cyclic Jacobi eigen-decomposition
+ * in FP64 in shared memory (else OTVMC_ERR_UNSUPPORTED).  Inputs: S_d [ntraj][P][P] full
+ * FP64 S (otvmc_build_S_F), obar_d [ntraj][P], spins_d [ntraj][ns][W], v_d [ntraj][ns]
+ * double2 (otvmc_local_estimators), D_d [ntraj][P] double2.  Outputs: delta_d [ntraj][P]
+ * double2; lambda_d (optional) [ntraj][P] eigenvalues, unordered.  A decomposition that has
+ * not converged after 40 sweeps records OTVMC_ERR_NONFINITE in the status word. */
+OTVMC_API otvmc_status otvmc_solve_snr(const otvmc_ansatz* ansatz, int ntraj, int ns, const double* S_d,
+                                       const double* obar_d, const uint64_t* spins_d, const double* v_d,
+                                       const double* D_d, double snr_thresh, double eps_svd, double* delta_d,
+                                       double* lambda_d, void* work_d, size_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------ A8: SDE combination
  * App. C on theta (all [ntraj][P] double2):
@@ -268,7 +286,7 @@ typedef struct otvmc_run_desc {
     double dt;
     int scheme;          /* OTVMC_HEUN or OTVMC_MIDPOINT */
     int precision;       /* OTVMC_PREC_FP64 or OTVMC_PREC_MIXED */
-    int reg;             /* OTVMC_REG_SHIFT */
+    int reg;             /* OTVMC_REG_SHIFT, or OTVMC_REG_SNR (P <= 96, eps_svd = 1e-12) */
     double eps;          /* diagonal shift */
     double snr_thresh;
     uint64_t seed;

@@ -63,6 +63,7 @@ SIGNATURES = {
     "otvmc_build_S_F": (c_int, [P, P, P, P, c_int, c_int, c_int, P, P, P, P, P, c_size_t, P]),
     "otvmc_solve_step": (c_int, [P, c_int, c_int, c_int, c_int, c_double, c_double, P, P, P, P, P, P, P, c_size_t,
                                  P]),
+    "otvmc_solve_snr": (c_int, [P, c_int, c_int, P, P, P, P, P, c_double, c_double, P, P, P, c_size_t, P]),
     "otvmc_sde_combine": (c_int, [c_int, c_int64, c_int, c_int, P, P, P, P, P, P, c_size_t, P]),
     "otvmc_observables": (c_int, [P, P, P, c_int, c_int, c_int, P, P, c_size_t, P]),
     "otvmc_ensemble": (c_int, [P, c_int, c_int, P, P, P, P]),
@@ -205,6 +206,12 @@ def otvmc_solve_step(ansatz, ntraj, ns, precision, reg, eps, snr_thresh, S_d, G_
                      shift_used_d, work_d, work_bytes, stream=None):
     return _call("otvmc_solve_step", ansatz, ntraj, ns, precision, reg, eps, snr_thresh, ptr(S_d), ptr(G_d),
                  ptr(obar_d), ptr(D_d), ptr(delta_d), ptr(shift_used_d), ptr(work_d), work_bytes, stream_ptr(stream))
+
+
+def otvmc_solve_snr(ansatz, ntraj, ns, S_d, obar_d, spins_d, v_d, D_d, snr_thresh, eps_svd, delta_d, lambda_d,
+                    work_d, work_bytes, stream=None):
+    return _call("otvmc_solve_snr", ansatz, ntraj, ns, ptr(S_d), ptr(obar_d), ptr(spins_d), ptr(v_d), ptr(D_d),
+                 snr_thresh, eps_svd, ptr(delta_d), ptr(lambda_d), ptr(work_d), work_bytes, stream_ptr(stream))
 
 
 def otvmc_sde_combine(ntraj, P_, scheme, stage, theta_d, delta0_d, delta1_d, out_d, failed_d, work_d, work_bytes,

@@ -459,7 +459,9 @@ otvmc_status otvmc_solve_step(const otvmc_ansatz* a, int ntraj, int ns, int prec
     (void)snr_thresh;
     otvmc_status st = check_batch(a, ntraj, ns);
     if (st) return st;
-    if (reg != OTVMC_REG_SHIFT) return fail(OTVMC_ERR_UNSUPPORTED, "only the diagonal-shift regulariser is built");
+    if (reg != OTVMC_REG_SHIFT)
+        return fail(OTVMC_ERR_UNSUPPORTED, "solve_step takes the diagonal shift; the SNR filter needs the samples: "
+                                           "use otvmc_solve_snr");
     if (!D_d || !delta_d || !work_d || !(eps >= 0.0)) return fail(OTVMC_ERR_INVALID, "solve_step: bad arguments");
     if (precision == OTVMC_PREC_FP64 && !S_d) return fail(OTVMC_ERR_INVALID, "FP64 solve needs S_d");
     if (precision == OTVMC_PREC_MIXED && (!G_d || !obar_d))
@@ -469,6 +471,25 @@ otvmc_status otvmc_solve_step(const otvmc_ansatz* a, int ntraj, int ns, int prec
     CK(launch_chol_solve(ntraj, (int)a->P, ns, precision, eps, S_d, G_d, obar_d, (const double2*)D_d,
                          (double2*)delta_d, shift_used_d, (char*)work_d + 256, 1, (int*)work_d, (cudaStream_t)stream),
        "solve launch");
+    return OTVMC_OK;
+}
+
+otvmc_status otvmc_solve_snr(const otvmc_ansatz* a, int ntraj, int ns, const double* S_d, const double* obar_d,
+                             const uint64_t* spins_d, const double* v_d, const double* D_d, double snr_thresh,
+                             double eps_svd, double* delta_d, double* lambda_d, void* work_d, size_t work_bytes,
+                             void* stream) {
+    otvmc_status st = check_batch(a, ntraj, ns);
+    if (st) return st;
+    if (a->kind != OTVMC_JASTROW) return fail(OTVMC_ERR_UNSUPPORTED, "solve_snr: only the Jastrow ansatz is built");
+    if (a->P > SNR_PMAX)
+        return fail(OTVMC_ERR_UNSUPPORTED, "solve_snr: built for P <= " + std::to_string(SNR_PMAX));
+    if (!S_d || !obar_d || !spins_d || !v_d || !D_d || !delta_d || !work_d || !(snr_thresh >= 0.0) ||
+        !(eps_svd >= 0.0))
+        return fail(OTVMC_ERR_INVALID, "solve_snr: bad arguments");
+    if (work_bytes < 256) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    CK(launch_snr_solve(a, ntraj, ns, spins_d, S_d, obar_d, (const double2*)v_d, (const double2*)D_d, snr_thresh,
+                        eps_svd, (double2*)delta_d, lambda_d, (int*)work_d, (cudaStream_t)stream),
+       "snr solve launch");
     return OTVMC_OK;
 }
 
@@ -604,7 +625,8 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
         r.S = c.take<double>(T * P * P);
         r.G = nullptr;
     } else {
-        r.S = nullptr;
+        // the SNR filter works on the full FP64 S, expanded from the exact counts
+        r.S = d->reg == OTVMC_REG_SNR ? c.take<double>(T * P * P) : nullptr;
         r.G = c.take<float>(T * P * P);
     }
     r.obuf = c.take<char>(obuf_bytes(a, T, ns, d->precision));
@@ -622,7 +644,10 @@ static otvmc_status check_run(const otvmc_ansatz* a, const otvmc_run_desc* d) {
         return fail(OTVMC_ERR_INVALID, "unknown precision");
     if (d->precision == OTVMC_PREC_MIXED && (d->ns % 8 != 0 || d->ns >= (1 << 24)))
         return fail(OTVMC_ERR_INVALID, "mixed precision needs ns % 8 == 0 and ns < 2^24");
-    if (d->reg != OTVMC_REG_SHIFT) return fail(OTVMC_ERR_UNSUPPORTED, "only the diagonal-shift regulariser is built");
+    if (d->reg != OTVMC_REG_SHIFT && d->reg != OTVMC_REG_SNR) return fail(OTVMC_ERR_INVALID, "unknown regulariser");
+    if (d->reg == OTVMC_REG_SNR && (a->P > SNR_PMAX || !(d->snr_thresh >= 0.0)))
+        return fail(OTVMC_ERR_UNSUPPORTED, "SNR regulariser: built for P <= " + std::to_string(SNR_PMAX) +
+                                               " (one CTA per trajectory) and snr_thresh >= 0");
     return OTVMC_OK;
 }
 
@@ -659,7 +684,13 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     }
     st = run_build(a, spins, r.v, T, ns, d->precision, true, r.eb, r.obuf, r.S, r.G, r.obar, r.D, status, s);
     if (st) return st;
-    CK(launch_chol_solve(T, (int)a->P, ns, d->precision, d->eps, r.S, r.G, r.obar, r.D, delta, nullptr, r.chol, 1,
+if (d->reg == OTVMC_REG_SNR) {
+        CK(launch_snr_solve(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr, status,
+                            s),
+           "snr solve launch");
+        return OTVMC_OK;
+    }
+        CK(launch_chol_solve(T, (int)a->P, ns, d->precision, d->eps, r.S, r.G, r.obar, r.D, delta, nullptr, r.chol, 1,
                          status, s),
        "solve launch");
     return OTVMC_OK;

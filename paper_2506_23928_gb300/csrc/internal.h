@@ -143,6 +143,13 @@ cudaError_t launch_gram_tc(int ntraj, int P, int ns, const uint16_t* Ot, const i
                            int* status, cudaStream_t s);
 cudaError_t launch_expand_S(int ntraj, int P, int ns, const float* G, const double* obar, double* S,
                             cudaStream_t s);
+// SNR-filtered eigen pseudo-inverse (one CTA per trajectory, P <= SNR_PMAX)
+constexpr int SNR_PMAX = 96;
+constexpr double SNR_EPS_SVD = 1e-12;
+size_t snr_smem_bytes(int P);
+cudaError_t launch_snr_solve(const otvmc_ansatz* a, int ntraj, int ns, const uint64_t* spins, const double* S,
+                             const double* obar, const double2* v, const double2* D, double thr, double eps_svd,
+                             double2* delta, double* lam, int* status, cudaStream_t s);
 cudaError_t launch_chol_solve(int ntraj, int P, int ns, int precision, double eps, const double* S,
                               const float* G, const double* obar, const double2* D, double2* delta,
                               double* shift_used, void* ws, int refine_iters, int* status, cudaStream_t s);
