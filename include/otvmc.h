@@ -117,7 +117,9 @@ OTVMC_API int otvmc_model_nops(const otvmc_model* model);
  * OTVMC_JASTROW: log psi = sum a_i s_i + sum_{j<k} eta_jk s_j s_k, P = N(N+1)/2,
  *   theta = [a_0..a_{N-1}, eta_jk for j<k row-major].  n_hidden ignored.
  * OTVMC_RBM: log psi = sum a_i s_i + sum_m log 2cosh(b_m + sum_i W_im s_i),
- *   P = N + M + N M, theta = [a (N), b (M), W (N x M row-major)].
+ *   P = N + M + N M, theta = [a (N), b (M), W (N x M row-major)], M = n_hidden in
+ *   [1, 4096].  Built on the FP64 path (sample, local_estimators, build_S_F, solve_step,
+ *   observables, run_trajectories); MIXED calls return OTVMC_ERR_UNSUPPORTED.
  * The ansatz keeps a pointer to the model, which must outlive it. */
 OTVMC_API otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, int n_hidden,
                                  otvmc_ansatz** out);
@@ -200,6 +202,10 @@ OTVMC_API otvmc_status otvmc_local_estimators_noalloc(const otvmc_ansatz* ansatz
  *          (exact: O = +-1, FP32 accumulation exact below 2^24 samples); obar_d [ntraj][P]
  *          double column means; S = G / ns - obar obar^T exactly.  S_d, if not NULL, is
  *          also filled (full FP64).
+ * RBM (FP64 only; theta_d required): O is complex (O_a = s, O_b = tanh gamma, O_W = s tanh
+ *          gamma), S_d is [ntraj][P][P] double2 (complex Hermitian, full), obar_d (optional)
+ *          [ntraj][P] double2; built as R^T R / ns with R = [[Re O_c, -Im O_c], [Im O_c, Re O_c]]
+ *          (the real embedding of S), G_d unused.
  * D_d: [ntraj][P] double2.  Inputs v_d from otvmc_local_estimators. */
 OTVMC_API otvmc_status otvmc_build_S_F(const otvmc_ansatz* ansatz, const double* theta_d,
                              const uint64_t* spins_d, const double* v_d, int ntraj, int ns,
@@ -214,6 +220,8 @@ OTVMC_API otvmc_status otvmc_build_S_F(const otvmc_ansatz* ansatz, const double*
  *   FP64:  S_d (full FP64), FP64 Cholesky.
  *   MIXED: G_d + obar_d; FP32 Cholesky of S + eps I, then two steps of iterative
  *          refinement with the residual D - (S + eps I) x in FP64 from the exact G.
+ *   RBM (FP64 only): S_d the complex [ntraj][P][P] double2 of otvmc_build_S_F; the real
+ *          embedding [[Re S, -Im S], [Im S, Re S]] + eps I (size 2P) is factored in FP64.
  * shift_used_d (optional): [ntraj] double, the shift that succeeded.
  * delta_d: [ntraj][P] double2. */
 OTVMC_API otvmc_status otvmc_solve_step(const otvmc_ansatz* ansatz, int ntraj, int ns, int precision,
@@ -270,7 +278,9 @@ OTVMC_API otvmc_status otvmc_ensemble(const double* moments_h, int ntraj, int n_
 
 /* ------------------------------------------------------------- whole trajectories (A1-A9)
  * Runs n_steps trajectory steps for ntraj trajectories, all on the device, launching
- * every stage above batched over the trajectories.  theta_d [ntraj][P] and spins_d
+ * every stage above batched over the trajectories.  RBM (FP64): when P > ns the solve takes
+ * the push-through form delta = O_c^+ (T + eps I)^-1 v_c / ns with T = O_c O_c^+ / ns (the
+ * same delta as (S + eps I)^-1 D), factoring a system of size 2 ns instead of 2 P.  theta_d [ntraj][P] and spins_d
  * [ntraj][ns][W] are the state (in/out; start chains with otvmc_init_chains).
  * moments_d (may be NULL when measure_every = 0): [n_meas][ntraj][9] with one row per
  * measured step (steps i with i % measure_every == 0, from the predictor samples at

@@ -41,7 +41,7 @@ class Model:
 
 
 class Ansatz:
-    """otvmc_ansatz handle (Jastrow of Eq. 12; the RBM of Eq. 11 is declared, not built)."""
+    """otvmc_ansatz handle: Jastrow (Eq. 12) or RBM with n_hidden hidden units (Eq. 11)."""
 
     def __init__(self, model, kind=abi.OTVMC_JASTROW, n_hidden=0):
         out = ctypes.c_void_p()

@@ -111,7 +111,11 @@ static bool valid_ansatz(const otvmc_ansatz* a) { return a != nullptr && a->mode
 static otvmc_status check_batch(const otvmc_ansatz* a, int ntraj, int ns) {
     if (!valid_ansatz(a)) return fail(OTVMC_ERR_INVALID, "null or invalid ansatz");
     if (ntraj < 1 || ns < 1) return fail(OTVMC_ERR_INVALID, "ntraj and ns must be >= 1");
-    if (a->kind != OTVMC_JASTROW) return fail(OTVMC_ERR_UNSUPPORTED, "only the Jastrow ansatz is built");
+    return OTVMC_OK;
+}
+static otvmc_status rbm_precision(const otvmc_ansatz* a, int precision) {
+    if (a->kind == OTVMC_RBM && precision != OTVMC_PREC_FP64)
+        return fail(OTVMC_ERR_UNSUPPORTED, "the RBM ansatz is built on the FP64 path only");
     return OTVMC_OK;
 }
 
@@ -280,10 +284,19 @@ int otvmc_model_nops(const otvmc_model* m) { return m ? m->nops : 0; }
 otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, int n_hidden, otvmc_ansatz** out) {
     if (!model || !out) return fail(OTVMC_ERR_INVALID, "null model");
     if (kind != OTVMC_JASTROW && kind != OTVMC_RBM) return fail(OTVMC_ERR_INVALID, "unknown ansatz kind");
-    if (kind == OTVMC_RBM) return fail(OTVMC_ERR_UNSUPPORTED, "the RBM ansatz is not built in this version");
     const int n = model->n;
+    if (kind == OTVMC_RBM) {
+        if (n_hidden < 1 || n_hidden > 4096) return fail(OTVMC_ERR_INVALID, "RBM needs 1 <= n_hidden <= 4096");
+        auto* a = new otvmc_ansatz();
+        a->model = model;
+        a->kind = kind;
+        a->n = n;
+        a->m = n_hidden;
+        a->P = (int64_t)n + n_hidden + (int64_t)n * n_hidden;
+        *out = a;
+        return OTVMC_OK;
+    }
     if (n > 200) return fail(OTVMC_ERR_UNSUPPORTED, "Jastrow kernels are built for n <= 200");
-    (void)n_hidden;
     auto* a = new otvmc_ansatz();
     a->model = model;
     a->kind = kind;
@@ -323,6 +336,17 @@ int64_t otvmc_ansatz_nparams(const otvmc_ansatz* a) { return a ? a->P : 0; }
 size_t otvmc_workspace_bytes(const otvmc_ansatz* a, int ntraj, int ns, int precision) {
     if (!valid_ansatz(a) || ntraj < 1 || ns < 1) return 0;
     const size_t ev = eval_bufs_bytes(a, ntraj, ns);
+    if (a->kind == OTVMC_RBM) {
+        // sample scratch, estimators + lpl, build (R, embedded S, obar), solve (embedded S + Cholesky)
+        size_t m = rbm_sample_bytes(a, ntraj, ns) + 256;
+        const size_t est = ev + (size_t)ntraj * (a->model->nops + 1) * 8 + 1024;
+        const size_t build = ev + rbm_build_bytes(a, ntraj, ns) + 1024;
+        const size_t solve = 256 + rbm_solve_bytes(ntraj, (int)a->P) + 1024;
+        if (est > m) m = est;
+        if (build > m) m = build;
+        if (solve > m) m = solve;
+        return m + 256;
+    }
     const size_t build = ev + obuf_bytes(a, ntraj, ns, precision) + (size_t)ntraj * a->P * 8 + 1024;
     const size_t solve = 256 + chol_ws_bytes(ntraj, (int)a->P, precision);
     size_t m = ev;
@@ -372,6 +396,16 @@ otvmc_status otvmc_sample(const otvmc_ansatz* a, const double* theta_d, int ntra
     if (!theta_d || !spins_d || !work_d || n_sweep < 0 || traj0 < 0)
         return fail(OTVMC_ERR_INVALID, "sample: bad arguments");
     if (work_bytes < 256) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    if (a->kind == OTVMC_RBM) {
+        Carver c(work_d, work_bytes);
+        double2* gam = c.take<double2>((size_t)ntraj * a->m * ns);
+        double* lcr = c.take<double>((size_t)ntraj * a->m * ns);
+        if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+        CK(launch_sample_rbm(a, (const double2*)theta_d, ntraj, traj0, ns, n_sweep, seed, eval_index, spins_d, gam, lcr,
+                             (unsigned long long*)accepted_d, (cudaStream_t)stream),
+           "sample launch");
+        return OTVMC_OK;
+    }
     CK(launch_sample_jastrow(a, (const double2*)theta_d, ntraj, traj0, ns, n_sweep, seed, eval_index, spins_d,
                              (unsigned long long*)accepted_d, (int*)work_d, (cudaStream_t)stream),
        "sample launch");
@@ -382,8 +416,12 @@ otvmc_status otvmc_sample(const otvmc_ansatz* a, const double* theta_d, int ntra
 static otvmc_status run_estimators(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int T, int ns,
                                    const double* dW, double dt, bool fp32, const EvalBufs& b, double* lpl,
                                    double2* Eeff, double2* v, int* status, cudaStream_t s) {
-    CK(launch_jastrow_prep(a, theta, T, b, status, s), "prep launch");
-    CK(launch_est1_jastrow(a, spins, T, ns, fp32, b, status, s), "est1 launch");
+    if (a->kind == OTVMC_RBM) {
+        CK(launch_est_rbm(a, theta, spins, T, ns, b, s), "est rbm launch");
+    } else {
+        CK(launch_jastrow_prep(a, theta, T, b, status, s), "prep launch");
+        CK(launch_est1_jastrow(a, spins, T, ns, fp32, b, status, s), "est1 launch");
+    }
     CK(launch_site_means(a, T, ns, b, lpl, s), "site means launch");
     if (v) CK(launch_est2(a, spins, T, ns, fp32, dW, dt, lpl, b, Eeff, v, s), "est2 launch");
     return OTVMC_OK;
@@ -398,6 +436,7 @@ otvmc_status otvmc_local_estimators(const otvmc_ansatz* a, const double* theta_d
         return fail(OTVMC_ERR_INVALID, "local_estimators: bad arguments");
     if (precision != OTVMC_PREC_FP64 && precision != OTVMC_PREC_MIXED)
         return fail(OTVMC_ERR_INVALID, "unknown precision");
+    if ((st = rbm_precision(a, precision))) return st;
     Carver c(work_d, work_bytes);
     EvalBufs b = carve_eval_bufs(c, a, ntraj, ns);
     double* lpl = lpl_d ? lpl_d : c.take<double>((size_t)ntraj * (a->model->nops + 1));
@@ -431,10 +470,24 @@ static otvmc_status run_build(const otvmc_ansatz* a, const uint64_t* spins, cons
 otvmc_status otvmc_build_S_F(const otvmc_ansatz* a, const double* theta_d, const uint64_t* spins_d,
                              const double* v_d, int ntraj, int ns, int precision, double* S_d, float* G_d,
                              double* obar_d, double* D_d, void* work_d, size_t work_bytes, void* stream) {
-    (void)theta_d;
     otvmc_status st = check_batch(a, ntraj, ns);
     if (st) return st;
     if (!spins_d || !v_d || !D_d || !work_d) return fail(OTVMC_ERR_INVALID, "build_S_F: bad arguments");
+    if (a->kind == OTVMC_RBM) {
+        if ((st = rbm_precision(a, precision))) return st;
+        if (!theta_d || !S_d) return fail(OTVMC_ERR_INVALID, "RBM build needs theta_d and S_d");
+        Carver c(work_d, work_bytes);
+        EvalBufs b = carve_eval_bufs(c, a, ntraj, ns);
+        char* ws = c.take<char>(rbm_build_bytes(a, ntraj, ns));
+        if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+        cudaStream_t s = (cudaStream_t)stream;
+        CK(launch_vpart(ntraj, ns, (const double2*)v_d, b, s), "vpart launch");
+        CK(launch_vquant(ntraj, ns, (const double2*)v_d, b, s), "vquant launch");
+        CK(launch_rbm_build(a, (const double2*)theta_d, spins_d, (const double2*)v_d, b.vinfo, ntraj, ns, ws,
+                            (double2*)S_d, (double2*)obar_d, (double2*)D_d, s),
+           "rbm build launch");
+        return OTVMC_OK;
+    }
     if (precision == OTVMC_PREC_FP64 && !S_d) return fail(OTVMC_ERR_INVALID, "FP64 build needs S_d");
     if (precision == OTVMC_PREC_MIXED) {
         if (!G_d) return fail(OTVMC_ERR_INVALID, "mixed build needs G_d");
@@ -463,6 +516,15 @@ otvmc_status otvmc_solve_step(const otvmc_ansatz* a, int ntraj, int ns, int prec
         return fail(OTVMC_ERR_UNSUPPORTED, "solve_step takes the diagonal shift; the SNR filter needs the samples: "
                                            "use otvmc_solve_snr");
     if (!D_d || !delta_d || !work_d || !(eps >= 0.0)) return fail(OTVMC_ERR_INVALID, "solve_step: bad arguments");
+    if (a->kind == OTVMC_RBM) {
+        if ((st = rbm_precision(a, precision))) return st;
+        if (!S_d) return fail(OTVMC_ERR_INVALID, "RBM solve needs the complex S_d");
+        if (work_bytes < 256 + rbm_solve_bytes(ntraj, (int)a->P)) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+        CK(launch_rbm_solve_S(a, ntraj, ns, eps, (const double2*)S_d, (const double2*)D_d, (double2*)delta_d,
+                              shift_used_d, (char*)work_d + 256, (int*)work_d, (cudaStream_t)stream),
+           "rbm solve launch");
+        return OTVMC_OK;
+    }
     if (precision == OTVMC_PREC_FP64 && !S_d) return fail(OTVMC_ERR_INVALID, "FP64 solve needs S_d");
     if (precision == OTVMC_PREC_MIXED && (!G_d || !obar_d))
         return fail(OTVMC_ERR_INVALID, "mixed solve needs G_d and obar_d");
@@ -518,9 +580,15 @@ otvmc_status otvmc_observables(const otvmc_ansatz* a, const double* theta_d, con
     if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     const bool fp32 = precision == OTVMC_PREC_MIXED;
+    if ((st = rbm_precision(a, precision))) return st;
     st = run_estimators(a, (const double2*)theta_d, spins_d, ntraj, ns, nullptr, 0.0, fp32, b, lpl, nullptr, nullptr,
                         (int*)work_d, s);
     if (st) return st;
+    if (a->kind == OTVMC_RBM) {
+        CK(launch_obs_rbm(a, (const double2*)theta_d, spins_d, ntraj, ns, b, s), "observables launch");
+        CK(launch_obs_final(a->n, ns, ntraj, b, moments_d, s), "observables launch");
+        return OTVMC_OK;
+    }
     CK(launch_obs_prep(a, (const double2*)theta_d, ntraj, fp32, b, s), "obs prep launch");
     CK(launch_observables(a, spins_d, ntraj, ns, fp32, b, moments_d, s), "observables launch");
     return OTVMC_OK;
@@ -604,6 +672,9 @@ struct RunBufs {
     float* G;
     void* obuf;
     void* chol;
+    double2* gam;  // RBM sampler scratch
+    double* lcr;
+    void* rbm;     // RBM build scratch
     EvalBufs eb;
 };
 
@@ -621,6 +692,19 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
     r.v = c.take<double2>((size_t)T * ns);
     r.obar = c.take<double>(T * P);
     r.D = c.take<double2>(T * P);
+    r.gam = nullptr;
+    r.lcr = nullptr;
+    r.rbm = nullptr;
+    if (a->kind == OTVMC_RBM) {
+        r.S = nullptr;
+        r.G = nullptr;
+        r.obuf = nullptr;
+        r.gam = c.take<double2>((size_t)T * a->m * ns);
+        r.lcr = c.take<double>((size_t)T * a->m * ns);
+        r.rbm = c.take<char>(rbm_build_bytes(a, T, ns));
+        r.chol = c.take<char>(chol_ws_bytes(T, 2 * (int)(P <= (size_t)ns ? P : (size_t)ns), OTVMC_PREC_FP64));
+        return r;
+    }
     if (d->precision == OTVMC_PREC_FP64) {
         r.S = c.take<double>(T * P * P);
         r.G = nullptr;
@@ -645,7 +729,10 @@ static otvmc_status check_run(const otvmc_ansatz* a, const otvmc_run_desc* d) {
     if (d->precision == OTVMC_PREC_MIXED && (d->ns % 8 != 0 || d->ns >= (1 << 24)))
         return fail(OTVMC_ERR_INVALID, "mixed precision needs ns % 8 == 0 and ns < 2^24");
     if (d->reg != OTVMC_REG_SHIFT && d->reg != OTVMC_REG_SNR) return fail(OTVMC_ERR_INVALID, "unknown regulariser");
-    if (d->reg == OTVMC_REG_SNR && (a->P > SNR_PMAX || !(d->snr_thresh >= 0.0)))
+    if ((st = rbm_precision(a, d->precision))) return st;
+    if (a->kind == OTVMC_RBM && d->reg != OTVMC_REG_SHIFT)
+        return fail(OTVMC_ERR_UNSUPPORTED, "the SNR regulariser is built for the Jastrow ansatz");
+    if (d->reg == OTVMC_REG_SNR && a->kind == OTVMC_JASTROW && (a->P > SNR_PMAX || !(d->snr_thresh >= 0.0)))
         return fail(OTVMC_ERR_UNSUPPORTED, "SNR regulariser: built for P <= " + std::to_string(SNR_PMAX) +
                                                " (one CTA per trajectory) and snr_thresh >= 0");
     return OTVMC_OK;
@@ -674,6 +761,21 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
                              cudaStream_t s) {
     const int T = d->ntraj, ns = d->ns;
     const bool fp32 = d->precision == OTVMC_PREC_MIXED;
+    if (a->kind == OTVMC_RBM) {
+        CK(launch_sample_rbm(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, r.gam, r.lcr, nullptr, s),
+           "sample launch");
+        otvmc_status st =
+            run_estimators(a, theta, spins, T, ns, r.dW, d->dt, false, r.eb, r.lpl, r.Eeff, r.v, status, s);
+        if (st) return st;
+        if (moments_row) {
+            CK(launch_obs_rbm(a, theta, spins, T, ns, r.eb, s), "observables launch");
+            CK(launch_obs_final(a->n, ns, T, r.eb, moments_row, s), "observables launch");
+        }
+        CK(launch_vquant(T, ns, r.v, r.eb, s), "vquant launch");
+        CK(launch_rbm_build_solve(a, theta, spins, r.v, r.eb.vinfo, T, ns, d->eps, r.rbm, r.chol, delta, status, s),
+           "rbm build/solve launch");
+        return OTVMC_OK;
+    }
     CK(launch_sample_jastrow(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, nullptr, status, s),
        "sample launch");
     otvmc_status st = run_estimators(a, theta, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s);
@@ -684,13 +786,13 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     }
     st = run_build(a, spins, r.v, T, ns, d->precision, true, r.eb, r.obuf, r.S, r.G, r.obar, r.D, status, s);
     if (st) return st;
-if (d->reg == OTVMC_REG_SNR) {
+    if (d->reg == OTVMC_REG_SNR) {
         CK(launch_snr_solve(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr, status,
                             s),
            "snr solve launch");
         return OTVMC_OK;
     }
-        CK(launch_chol_solve(T, (int)a->P, ns, d->precision, d->eps, r.S, r.G, r.obar, r.D, delta, nullptr, r.chol, 1,
+    CK(launch_chol_solve(T, (int)a->P, ns, d->precision, d->eps, r.S, r.G, r.obar, r.D, delta, nullptr, r.chol, 1,
                          status, s),
        "solve launch");
     return OTVMC_OK;

@@ -143,6 +143,29 @@ cudaError_t launch_gram_tc(int ntraj, int P, int ns, const uint16_t* Ot, const i
                            int* status, cudaStream_t s);
 cudaError_t launch_expand_S(int ntraj, int P, int ns, const float* G, const double* obar, double* S,
                             cudaStream_t s);
+// RBM ansatz, FP64 path (k_rbm.cu)
+cudaError_t launch_sample_rbm(const otvmc_ansatz* an, const double2* theta, int ntraj, int traj0, int ns, int n_sweep,
+                              uint64_t seed, int64_t eval, uint64_t* spins, double2* gam, double* lcr,
+                              unsigned long long* accepted, cudaStream_t s);
+cudaError_t launch_est_rbm(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int ntraj, int ns,
+                           const EvalBufs& b, cudaStream_t s);
+cudaError_t launch_obs_rbm(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int ntraj, int ns,
+                           const EvalBufs& b, cudaStream_t s);
+cudaError_t launch_obs_final(int n, int ns, int ntraj, const EvalBufs& b, double* moments, cudaStream_t s);
+size_t rbm_build_bytes(const otvmc_ansatz* a, int ntraj, int ns);
+size_t rbm_solve_bytes(int ntraj, int P);
+cudaError_t launch_rbm_build(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, const double2* v,
+                             const double* vinfo, int T, int ns, void* ws, double2* S_out, double2* obar_out,
+                             double2* D_out, cudaStream_t s);
+cudaError_t launch_rbm_solve_S(const otvmc_ansatz* a, int T, int ns, double eps, const double2* S, const double2* D,
+                               double2* delta, double* shift_used, void* ws, int* status, cudaStream_t s);
+cudaError_t launch_rbm_build_solve(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, const double2* v,
+                                   const double* vinfo, int T, int ns, double eps, void* ws, void* chol,
+                                   double2* delta, int* status, cudaStream_t s);
+inline size_t rbm_sample_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
+    return (size_t)ntraj * a->m * ns * (16 + 8) + 512;
+}
+
 // SNR-filtered eigen pseudo-inverse (one CTA per trajectory, P <= SNR_PMAX)
 constexpr int SNR_PMAX = 96;
 constexpr double SNR_EPS_SVD = 1e-12;

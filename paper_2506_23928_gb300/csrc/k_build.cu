@@ -234,9 +234,9 @@ cudaError_t launch_obuild_f64_jastrow(const otvmc_ansatz* a, const uint64_t* spi
     return cudaGetLastError();
 }
 
-// S[i][j] = sum_x Oc[i][x] Oc[j][x] / ns, FP64 SIMT, 64x64 tiles of the upper triangle,
-// mirrored into the lower triangle.
-__global__ void __launch_bounds__(256) syrk_f64_kernel(int P, int ns, const double* __restrict__ Oc,
+// S[i][j] = inv sum_x Oc[i][x] Oc[j][x] over the K columns x of the rows i, j < P, FP64
+// SIMT, 64x64 tiles of the upper triangle, mirrored into the lower triangle.
+__global__ void __launch_bounds__(256) syrk_f64_kernel(int P, int ns, double inv, const double* __restrict__ Oc,
                                                        double* __restrict__ S) {
     constexpr int BT = 64, BK = 16;
     __shared__ double As[BK][BT + 1];
@@ -271,7 +271,6 @@ __global__ void __launch_bounds__(256) syrk_f64_kernel(int P, int ns, const doub
         __syncthreads();
     }
     double* St = S + (size_t)t * P * P;
-    const double inv = 1.0 / ns;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -285,13 +284,18 @@ __global__ void __launch_bounds__(256) syrk_f64_kernel(int P, int ns, const doub
         }
 }
 
-cudaError_t launch_syrk_f64(int ntraj, int P, int ns, const double* Oc, double* S, cudaStream_t s) {
+cudaError_t launch_syrk_f64_scaled(int ntraj, int rows, int K, double inv, const double* O, double* S,
+                                   cudaStream_t s) {
     ProfScope prof_(OTVMC_K_SYRK, s);
-    const int nb = (P + 63) / 64;
+    const int nb = (rows + 63) / 64;
     dim3 grid(nb, nb, ntraj);
-    syrk_f64_kernel<<<grid, 256, 0, s>>>(P, ns, Oc, S);
+    syrk_f64_kernel<<<grid, 256, 0, s>>>(rows, K, inv, O, S);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_syrk_f64(int ntraj, int P, int ns, const double* Oc, double* S, cudaStream_t s) {
+    return launch_syrk_f64_scaled(ntraj, P, ns, 1.0 / ns, Oc, S, s);
 }
 
 // D_k = sum_x Oc[k][x] (v(x) - vbar) / ns, FP64: one warp per parameter.

@@ -762,6 +762,12 @@ __global__ void obs_final_kernel(int n, int ns, int nblk, const double* __restri
     moments[(size_t)t * 9 + i] = out;
 }
 
+cudaError_t launch_obs_final(int n, int ns, int ntraj, const EvalBufs& b, double* moments, cudaStream_t s) {
+    obs_final_kernel<<<ntraj, 32, 0, s>>>(n, ns, obs_blocks(n, ns), b.part_obs, moments);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_observables(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
                                const EvalBufs& b, double* moments, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_OBS, s);

@@ -1,0 +1,186 @@
+"""RBM ansatz (Eq. 11) on the FP64 path, stage by stage and whole trajectories, against the
+oracle's RBM (complex log-derivatives, complex Hermitian S) on the same inputs; both the S
+path (P <= ns) and the push-through T path (P > ns) of the solve."""
+import numpy as np
+import pytest
+
+from gpu_helpers import require_gpu, to_dev_complex, from_dev_complex, unpack, rel_err, torch
+import synth
+from oracle import tvmc, trajectories as tr
+from oracle.ansatz import RBM
+from oracle.model import Model as OModel, couplings
+from oracle.observables import moments_from_samples
+from paper_2506_23928_gb300 import abi
+from paper_2506_23928_gb300.abi import check
+
+pytestmark = pytest.mark.gpu
+FP64, MIXED = abi.OTVMC_PREC_FP64, abi.OTVMC_PREC_MIXED
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+class RbmCase:
+    def __init__(self, n, m, h=0.9, kappa=0.1, gamma=0.0, alpha=1.5):
+        import paper_2506_23928_gb300 as pkg
+        self.J = couplings((n,), 1.0, alpha)
+        self.n, self.m = n, m
+        self.kappa = np.full(n, kappa)
+        self.gamma = np.full(n, gamma)
+        self.omodel = OModel(J=self.J, h=h, kappa=self.kappa, gamma=self.gamma)
+        self.oans = RBM(n, m)
+        self.model = pkg.Model(self.J, h, self.kappa, self.gamma)
+        self.ans = pkg.Ansatz(self.model, kind=abi.OTVMC_RBM, n_hidden=m)
+        self.P = self.ans.P
+        self.nops = self.model.nops
+        self.W = (n + 63) // 64
+        assert self.P == self.oans.P == n + m + n * m
+
+    def theta(self, seed, ntraj, scale):
+        th = synth.random_theta(seed, ntraj, self.P, scale)
+        return th, to_dev_complex(th)
+
+    def spins(self, seed, ntraj, ns):
+        sig = synth.random_spins(seed, ntraj, ns, self.n)
+        return sig, torch.from_numpy(synth.pack_spins(sig).view(np.int64)).cuda()
+
+    def work(self, ntraj, ns, precision=FP64):
+        nb = abi.otvmc_workspace_bytes(self.ans.handle, ntraj, ns, precision)
+        assert nb > 0
+        return torch.zeros(nb, dtype=torch.uint8, device="cuda"), nb
+
+
+@pytest.mark.parametrize("n,m,ns", [(6, 4, 150), (9, 7, 64), (70, 3, 40)])
+def test_rbm_sample_bit_exact(n, m, ns):
+    c = RbmCase(n, m)
+    T, traj0, seed, ev, sweeps = 2, 3, 77, 5, 2
+    th, th_d = c.theta(1, T, 0.3)
+    sig, sp = c.spins(2, T, ns)
+    acc = torch.zeros(T, dtype=torch.int64, device="cuda")
+    work, nb = c.work(T, ns)
+    check(abi.otvmc_sample(c.ans.handle, th_d, T, traj0, ns, sweeps, seed, ev, sp, acc, work, nb))
+    check(abi.otvmc_check(work))
+    got = unpack(sp, n)
+    for t in range(T):
+        want, a = tvmc.metropolis(c.oans, th[t], sig[t], seed, traj0 + t, ev, sweeps)
+        assert np.array_equal(got[t], want)
+        assert int(acc[t]) == int(a.sum())
+
+
+def _evaluate(c, T, ns, seed, scale, dt):
+    th, th_d = c.theta(seed, T, scale)
+    sig, sp = c.spins(seed + 1, T, ns)
+    dW = synth.random_normals(seed + 2, (T, c.nops), np.sqrt(dt))
+    w = tvmc.mc_weights(ns)
+    evs = [tvmc.evaluate(c.omodel, c.oans, th[t], sig[t], w, dW[t], dt) for t in range(T)]
+    return th, th_d, sig, sp, dW, evs
+
+
+@pytest.mark.parametrize("n,m,ns,gamma", [(7, 5, 300, 0.0), (10, 12, 96, 0.05)])
+def test_rbm_local_estimators(n, m, ns, gamma):
+    c = RbmCase(n, m, gamma=gamma)
+    T, dt = 3, 0.01
+    th, th_d, sig, sp, dW, evs = _evaluate(c, T, ns, 11, 0.2, dt)
+    dW_d = torch.from_numpy(dW).cuda()
+    E = torch.zeros((T, ns, 2), dtype=torch.float64, device="cuda")
+    v = torch.zeros_like(E)
+    lpl = torch.zeros((T, max(c.nops, 1)), dtype=torch.float64, device="cuda")
+    work, nb = c.work(T, ns)
+    check(abi.otvmc_local_estimators(c.ans.handle, th_d, sp, T, ns, dW_d, dt, FP64, E, v, lpl, work, nb))
+    check(abi.otvmc_check(work))
+    E, v = from_dev_complex(E)[..., 0], from_dev_complex(v)[..., 0]
+    for t in range(T):
+        assert rel_err(E[t], evs[t]["E"]) < TOL
+        assert rel_err(v[t], tvmc.local_v(evs[t], dW[t], dt)) < TOL
+        assert rel_err(lpl.cpu().numpy()[t, :c.nops], evs[t]["lpl"]) < TOL
+    # the mixed path is not built for the RBM
+    st = abi.otvmc_local_estimators(c.ans.handle, th_d, sp, T, ns, dW_d, dt, MIXED, E, v, lpl, work, nb)
+    assert st == abi.OTVMC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("n,m,ns", [(6, 4, 200), (5, 9, 40)])
+def test_rbm_build_and_solve(n, m, ns):
+    """Complex Hermitian S, complex obar and D, then (S + eps I) delta = D through the real
+    embedding, including P > ns (S singular, only the shift makes it definite)."""
+    c = RbmCase(n, m, gamma=0.05)
+    T, dt, eps = 2, 0.01, 1e-3
+    th, th_d, sig, sp, dW, evs = _evaluate(c, T, ns, 21, 0.2, dt)
+    v = np.stack([tvmc.local_v(evs[t], dW[t], dt) for t in range(T)])
+    P = c.P
+    S = torch.zeros((T, P, P, 2), dtype=torch.float64, device="cuda")
+    ob = torch.zeros((T, P, 2), dtype=torch.float64, device="cuda")
+    D = torch.zeros((T, P, 2), dtype=torch.float64, device="cuda")
+    work, nb = c.work(T, ns)
+    check(abi.otvmc_build_S_F(c.ans.handle, th_d, sp, to_dev_complex(v), T, ns, FP64, S, None, ob, D, work, nb))
+    check(abi.otvmc_check(work))
+    Sg, obg, Dg = from_dev_complex(S)[..., 0], from_dev_complex(ob)[..., 0], from_dev_complex(D)[..., 0]
+    for t in range(T):
+        assert rel_err(Sg[t], evs[t]["S"]) < 1e-12
+        assert rel_err(obg[t], evs[t]["O"].mean(axis=0)) < 1e-13
+        assert rel_err(Dg[t], evs[t]["D"]) < 1e-11
+    delta = torch.zeros((T, P, 2), dtype=torch.float64, device="cuda")
+    shift = torch.zeros(T, dtype=torch.float64, device="cuda")
+    check(abi.otvmc_solve_step(c.ans.handle, T, ns, FP64, abi.OTVMC_REG_SHIFT, eps, 4.0, S, None, None, D, delta,
+                               shift, work, nb))
+    check(abi.otvmc_check(work))
+    got = from_dev_complex(delta)[..., 0]
+    for t in range(T):
+        assert rel_err(got[t], tvmc.solve_shift(evs[t]["S"], evs[t]["D"], eps)) < 1e-9
+        assert float(shift[t]) == eps
+
+
+@pytest.mark.parametrize("n,m,ns", [(6, 3, 100), (4, 5, 33)])
+def test_rbm_observables(n, m, ns):
+    c = RbmCase(n, m)
+    T = 2
+    th, th_d = c.theta(31, T, 0.3)
+    sig, sp = c.spins(32, T, ns)
+    mom = torch.zeros((T, 9), dtype=torch.float64, device="cuda")
+    work, nb = c.work(T, ns)
+    check(abi.otvmc_observables(c.ans.handle, th_d, sp, T, ns, FP64, mom, work, nb))
+    check(abi.otvmc_check(work))
+    got = mom.cpu().numpy()
+    for t in range(T):
+        mm, q = moments_from_samples(c.oans, th[t], sig[t], tvmc.mc_weights(ns))
+        want = np.concatenate([mm, q[[0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]]])
+        assert rel_err(got[t], want) < TOL
+
+
+@pytest.mark.parametrize("n,m,ns,scheme", [(6, 4, 128, abi.OTVMC_HEUN),     # S path, P = 34 <= ns
+                                          (6, 4, 24, abi.OTVMC_MIDPOINT),   # T path, P = 34 > ns
+                                          (5, 6, 16, abi.OTVMC_HEUN)])      # T path, P = 41
+def test_rbm_run_matches_oracle(n, m, ns, scheme):
+    """Whole trajectories from theta = 0 with decay and dephasing: bit-identical chains and
+    parameters within 1e-8 of the oracle, whose solve always goes through S; on the T path
+    the push-through identity gives the same delta."""
+    c = RbmCase(n, m, gamma=0.05)
+    T, steps, dt, seed, eps = 2, 3, 0.01, 4242, 1e-3
+    desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=scheme,
+                       precision=FP64, reg=abi.OTVMC_REG_SHIFT, eps=eps, snr_thresh=4.0, seed=seed,
+                       measure_every=1, measure_final=1, use_graph=0)
+    nmeas = abi.otvmc_run_n_meas(desc)
+    theta = torch.zeros((T, c.P, 2), dtype=torch.float64, device="cuda")
+    spins = torch.zeros((T, ns, c.W), dtype=torch.int64, device="cuda")
+    check(abi.otvmc_init_chains(c.ans.handle, T, 0, ns, seed, spins))
+    nb = abi.otvmc_run_workspace_bytes(c.ans.handle, desc)
+    assert nb > 0
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    mom = torch.zeros((nmeas, T, 9), dtype=torch.float64, device="cuda")
+    check(abi.otvmc_run_trajectories(c.ans.handle, desc, theta, spins, mom, work, nb))
+    sname = "heun" if scheme == abi.OTVMC_HEUN else "midpoint"
+    oth, osig, om, oq = tr.run_mc(c.omodel, c.oans, T, ns, steps, dt, seed, sname, n_sweep=2, eps=eps)
+    assert np.array_equal(unpack(spins, c.n), osig)
+    assert rel_err(from_dev_complex(theta)[..., 0], oth) < 1e-8
+    want = np.concatenate([om, oq[..., [0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]]], axis=-1)
+    assert rel_err(mom.cpu().numpy(), want) < 1e-8
+
+
+def test_rbm_mixed_run_rejected():
+    c = RbmCase(4, 2)
+    desc = abi.RunDesc(ntraj=1, traj0=0, ns=64, n_steps=1, step0=0, n_sweep=1, dt=0.01, scheme=abi.OTVMC_HEUN,
+                       precision=MIXED, reg=abi.OTVMC_REG_SHIFT, eps=1e-4, snr_thresh=4.0, seed=1,
+                       measure_every=0, measure_final=0, use_graph=0)
+    assert abi.otvmc_run_workspace_bytes(c.ans.handle, desc) == 0
