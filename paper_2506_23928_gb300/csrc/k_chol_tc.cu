@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
     const int t = t0 + blockIdx.y;
     if (fail[t]) return;
     extern __shared__ uint8_t smem_raw[];
+    __shared__ float obj_s[NB];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
     uint64_t* empty = full + STAGES;
@@ -140,26 +141,41 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
         }
         __syncwarp();
     } else {
+        // epilogue: C = A - acc, written transposed (PnT[t][c][i]) so that the lanes of a warp
+        // (consecutive rows i) store consecutive addresses
         const int q = warp & 3;
+        const float* Gt = G + (size_t)t * P * P;
+        const double* ob = obar + (size_t)t * P;
+        for (int c = threadIdx.x - 64; c < NB; c += 128) obj_s[c] = jb + c < P ? (float)ob[jb + c] : 0.f;
         int ok = 0;
         if (lane == 0) ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         fence_after();
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // obj_s written by the four epilogue warps
         if (ok) {
             const int i = i0 + q * 32 + lane;
-            const float* Gt = G + (size_t)t * P * P;
-            const double* ob = obar + (size_t)t * P;
+            const int ii = i < P ? i : P - 1;
             const float inv_ns = 1.0f / (float)ns;
-            float* prow = Pn + ((size_t)t * P + (i < P ? i : 0)) * NB;
+            const float obi = (float)ob[ii];
+            float* pcol = Pn + (size_t)t * NB * P + ii;
 #pragma unroll 1
             for (int c0 = 0; c0 < NB; c0 += 32) {
+                // the chunk's 32 Gram counts first, unconditionally (clamped index), so that the
+                // loads are all in flight before any store
+                float g[32];
+#pragma unroll
+                for (int u = 0; u < 32; ++u) g[u] = __ldg(Gt + (size_t)min(jb + c0 + u, P - 1) * P + ii);
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                 if (i >= P) continue;
 #pragma unroll
                 for (int u = 0; u < 32; ++u) {
                     const int j = jb + c0 + u;
-                    if (j < P && j <= i) prow[c0 + u] = a_orig(Gt, ob, P, inv_ns, i, j, eps) - __uint_as_float(v[u]);
+                    if (j < P && j <= i) {
+                        float a = g[u] * inv_ns - obi * obj_s[c0 + u];
+                        if (i == j) a += eps;
+                        pcol[(size_t)(c0 + u) * P] = a - __uint_as_float(v[u]);
+                    }
                 }
             }
         }
@@ -352,17 +368,12 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
                     a[r][c] = v;
                 }
         } else {
-            const float* prow = Pn + ((size_t)t * P + jb + bi * 8) * NB + bj * 8;
+            // C of the update kernel, stored transposed: PnT[t][c][i]
+            const float* pcol = Pn + ((size_t)t * NB + bj * 8) * P + jb + bi * 8;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-                if (bi * 8 + r < nb) {
-                    lo = ld4(prow + (size_t)r * NB);
-                    hi = ld4(prow + (size_t)r * NB + 4);
-                }
-                a[r][0] = lo.x; a[r][1] = lo.y; a[r][2] = lo.z; a[r][3] = lo.w;
-                a[r][4] = hi.x; a[r][5] = hi.y; a[r][6] = hi.z; a[r][7] = hi.w;
-            }
+            for (int c = 0; c < 8; ++c)
+#pragma unroll
+                for (int r = 0; r < 8; ++r) a[r][c] = bi * 8 + r < nb ? pcol[(size_t)c * P + r] : 0.f;
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -501,13 +512,14 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
 }
 
 // ---------------------------------------------------------------------------------- trsm
-// Rows below the diagonal block: X = C L_dd^-T, one 64-row tile per CTA.  Thread (rg, cg)
-// owns rows rg + 16 a (a < 4) and columns 8 cg .. 8 cg + 7; the k loop reads both operands
-// as float4 from shared memory (12 loads per 128 multiply-adds).  The forward substitution
-// is fused in: each row i below loses its component along this block column,
-//     y_i -= X[i, :] . y_b.
-constexpr int DSP = NB + 4;              // padded shared-memory row (16-byte aligned)
-constexpr int TRSM_SMEM = ((NB + RT) * DSP + 2 * NB) * (int)sizeof(float);
+// Rows below the diagonal block: X = C L_dd^-T, one 64-row tile per CTA, both operands held
+// transposed in shared memory (CT[k][row], LT[k][col]).  Thread (rg, cg) owns rows
+// 4 rg .. 4 rg + 3 and columns 8 cg .. 8 cg + 7; per k it reads one float4 of C^T and two of
+// L_dd^-T (3 loads per 32 multiply-adds).  The forward substitution is fused in: each row i
+// below loses its component along this block column, y_i -= X[i, :] . y_b.
+constexpr int DCT = RT + 4;              // CT row: 64 rows + pad (16-byte aligned)
+constexpr int DLT = NB + 4;              // LT row: 128 columns + pad
+constexpr int TRSM_SMEM = (NB * DCT + NB * DLT + 2 * NB) * (int)sizeof(float);
 
 __global__ void __launch_bounds__(256, 2) chol_trsm_kernel(int t0, int P, int LD, int ns, int jb, float eps,
                                                            const float* __restrict__ G, const double* __restrict__ obar,
@@ -518,51 +530,59 @@ __global__ void __launch_bounds__(256, 2) chol_trsm_kernel(int t0, int P, int LD
     const int t = t0 + blockIdx.y;
     if (fail[t]) return;
     extern __shared__ __align__(16) float tsm[];
-    float* Li = tsm;               // [NB][DSP] L_dd^-1
-    float* Ct = Li + NB * DSP;     // [RT][DSP] C, later the fused-forward partial sums
-    float* yb = Ct + RT * DSP;     // [2][NB]
+    float* CT = tsm;               // [NB][DCT]  C^T (k = column of C, then row)
+    float* LT = CT + NB * DCT;     // [NB][DLT]  (L_dd^-1)^T: LT[k][c] = Linv[c][k]
+    float* yb = LT + NB * DLT;     // [2][NB]
     const int tid = threadIdx.x;
     const int nb = min(NB, P - jb);
     const int r0 = jb + nb + blockIdx.x * RT;
     const float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
     float* yt = yv + (size_t)t * 2 * P;
     {
+        // Linv[c][4 q .. 4 q + 3] -> LT[4 q + i][c]; lanes along c (conflict-free stores)
         float4 v[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = ld4(Dv + (size_t)(tid + 256 * q) * 4);
+        for (int q = 0; q < 16; ++q) {
+            const int e = tid + 256 * q, c = e & (NB - 1), k4 = e >> 7;
+            v[q] = ld4(Dv + (size_t)c * NB + 4 * k4);
+        }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            const int e = tid + 256 * q;
-            *reinterpret_cast<float4*>(Li + (e >> 5) * DSP + 4 * (e & 31)) = v[q];
+            const int e = tid + 256 * q, c = e & (NB - 1), k4 = e >> 7;
+            LT[(4 * k4 + 0) * DLT + c] = v[q].x;
+            LT[(4 * k4 + 1) * DLT + c] = v[q].y;
+            LT[(4 * k4 + 2) * DLT + c] = v[q].z;
+            LT[(4 * k4 + 3) * DLT + c] = v[q].w;
         }
     }
-    if (jb == 0) {
+    {
+        // CT[c][rr] = C[r0 + rr][c]: from the Gram counts (first block column, G[c][i] with i
+        // contiguous) or from the update kernel's transposed output PnT[t][c][i]
         const float* Gt = G + (size_t)t * P * P;
         const double* ob = obar + (size_t)t * P;
         const float inv_ns = 1.0f / (float)ns;
-#pragma unroll 8
-        for (int q = 0; q < (NB * RT) / 256; ++q) {
-            const int e = tid + 256 * q, c = e / RT, rr = e % RT, i = r0 + rr;
-            float v = 0.f;
-            if (i < P && c < nb) v = a_orig(Gt, ob, P, inv_ns, i, c, eps);
-            Ct[rr * DSP + c] = v;
-        }
-    } else {
-        float4 v[8];
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float v[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = tid + 256 * q, rr = e >> 5, c4 = e & 31, i = r0 + rr;
-            v[q] = i < P ? ld4(Pn + ((size_t)t * P + i) * NB + 4 * c4) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+            for (int q = 0; q < 16; ++q) {
+                const int e = tid + 256 * (q + 16 * half), c = e >> 6, rr = e & (RT - 1), i = r0 + rr;
+                float x = 0.f;
+                if (i < P && c < nb) x = jb == 0 ? Gt[(size_t)c * P + i] : Pn[((size_t)t * NB + c) * P + i];
+                v[q] = x;
+            }
+            if (jb == 0) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = tid + 256 * q, rr = e >> 5, c4 = e & 31;
-            float4 w = v[q];
-            if (4 * c4 + 0 >= nb) w.x = 0.f;
-            if (4 * c4 + 1 >= nb) w.y = 0.f;
-            if (4 * c4 + 2 >= nb) w.z = 0.f;
-            if (4 * c4 + 3 >= nb) w.w = 0.f;
-            *reinterpret_cast<float4*>(Ct + rr * DSP + 4 * c4) = w;
+                for (int q = 0; q < 16; ++q) {
+                    const int e = tid + 256 * (q + 16 * half), c = e >> 6, rr = e & (RT - 1), i = r0 + rr;
+                    if (i < P && c < nb) v[q] = v[q] * inv_ns - (float)ob[i] * (float)ob[c];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int e = tid + 256 * (q + 16 * half), c = e >> 6, rr = e & (RT - 1);
+                CT[c * DCT + rr] = v[q];
+            }
         }
     }
     if (tid < 2 * NB) {
@@ -576,17 +596,18 @@ __global__ void __launch_bounds__(256, 2) chol_trsm_kernel(int t0, int P, int LD
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[a][u] = 0.f;
-    const int kq_end = (min(nb, cg * 8 + 8) + 3) >> 2;   // L_dd^-1 is lower triangular
-    for (int kq = 0; kq < kq_end; ++kq) {
-        float4 cv[4], lv[8];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) cv[a] = *reinterpret_cast<const float4*>(Ct + (rg + 16 * a) * DSP + 4 * kq);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) lv[u] = *reinterpret_cast<const float4*>(Li + (cg * 8 + u) * DSP + 4 * kq);
+    const int kend = min(nb, cg * 8 + 8);  // L_dd^-1 is lower triangular
+#pragma unroll 4
+    for (int k = 0; k < kend; ++k) {
+        const float4 cv = *reinterpret_cast<const float4*>(CT + k * DCT + 4 * rg);
+        const float4 l0 = *reinterpret_cast<const float4*>(LT + k * DLT + 8 * cg);
+        const float4 l1 = *reinterpret_cast<const float4*>(LT + k * DLT + 8 * cg + 4);
+        const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+        const float l8[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc[a][u] = dot4(cv[a], lv[u], acc[a][u]);
+            for (int u = 0; u < 8; ++u) acc[a][u] = fmaf(c4[a], l8[u], acc[a][u]);
     }
     const LbLayout lay{(P + NB - 1) / NB, LD / 32};
     float* Lft = Lf + (size_t)t * P * LD;
@@ -595,7 +616,7 @@ __global__ void __launch_bounds__(256, 2) chol_trsm_kernel(int t0, int P, int LD
     float pr[4][2];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int i = r0 + rg + 16 * a;
+        const int i = r0 + 4 * rg + a;
         if (i < P && nv > 0) store_L8(Lft, Lbt, lay, LD, i, jb + cg * 8, acc[a], nv);
         float s0 = 0.f, s1 = 0.f;
 #pragma unroll
@@ -606,12 +627,12 @@ __global__ void __launch_bounds__(256, 2) chol_trsm_kernel(int t0, int P, int LD
         pr[a][0] = s0;
         pr[a][1] = s1;
     }
-    __syncthreads();   // C is no longer read
-    float* red = Ct;   // [16][RT][2]
+    __syncthreads();   // CT is no longer read
+    float* red = CT;   // [16][RT][2]
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        red[(cg * RT + rg + 16 * a) * 2] = pr[a][0];
-        red[(cg * RT + rg + 16 * a) * 2 + 1] = pr[a][1];
+        red[(cg * RT + 4 * rg + a) * 2] = pr[a][0];
+        red[(cg * RT + 4 * rg + a) * 2 + 1] = pr[a][1];
     }
     __syncthreads();
     if (tid < 2 * RT) {
