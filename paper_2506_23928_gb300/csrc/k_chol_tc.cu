@@ -285,29 +285,172 @@ __device__ __forceinline__ int reduce8_index(int lane) {
 }
 
 // ----------------------------------------------------------------------- diagonal block
-// Cholesky factor of the 128 x 128 diagonal block of block column jb and the inverse of that
-// factor, in one pass of right-looking elimination over its 128 columns; one CTA per
-// trajectory.  The block is held in registers as 8 x 8 tiles: threads 0..135 own the 136
-// lower tiles of A (becoming L), threads 136..271 the lower tiles of X (starting at I,
-// becoming L^-1).  Step m publishes column m of A and row m of X through shared memory,
-// then every tile applies its rank-one update:
-//     A[i][j] -= A[i][m] A[j][m] / A[m][m]      (i, j > m)
-//     X[i][j] -= A[i][m] X[m][j] / A[m][m]      (i > m)
-// with L[i][m] = A[i][m] / sqrt(A[m][m]) and (L^-1)[m][j] = X[m][j] / sqrt(A[m][m]).
-// The forward substitution of the solve is fused in: the block's right-hand sides (D for
-// the first block, else the running residual that the TRSM kernels of earlier block
-// columns left behind) are multiplied by L_dd^-1 here.  Rows and columns beyond nb are
-// padded with the identity.
-constexpr int T8 = NB / 8;                  // 16 tile rows
-constexpr int NTRI8 = T8 * (T8 + 1) / 2;    // 136 lower tiles
+// Cholesky factor L_dd of the 128 x 128 diagonal block of block column jb and its inverse
+// X = L_dd^-1, one CTA per trajectory, by 2 x 2 blocks of 64:
+//     L11 X11 <- factor64(A11);  L21 = A21 X11^T;  A22 -= L21 L21^T;  L22 X22 <- factor64(A22);
+//     X21 = -X22 (L21 X11)
+// (the block form of the factor and of the inverse of a lower-triangular matrix).  factor64
+// is one pass of right-looking elimination over register-held 4 x 4 tiles: threads 0..135
+// own the lower tiles of A (becoming L), threads 136..271 those of X (starting at I); step m
+// publishes column m of A and row m of X through shared memory and every tile applies
+//     A[i][j] -= A[i][m] A[j][m] / A[m][m]  (i, j > m),   X[i][j] -= A[i][m] X[m][j] / A[m][m]  (i > m),
+// with L[i][m] = A[i][m] / sqrt(A[m][m]) and X[m][j] = X[m][j] / sqrt(A[m][m]).  The four 64^3
+// products run as register-tiled SIMT GEMMs on float4 shared-memory operands.  The forward
+// substitution of the solve is fused in: the block's right-hand sides (D for the first block,
+// else the running residual that the TRSM kernels of earlier block columns left behind) are
+// multiplied by X here.  Rows and columns beyond nb are padded with the identity.
 constexpr int DIAG_THREADS = 288;
+constexpr int HB = 64;                      // half block
+constexpr int T4 = HB / 4;                  // 16 tile rows of a half block
+constexpr int NTRI4 = T4 * (T4 + 1) / 2;    // 136 lower 4 x 4 tiles
+constexpr int DSD = NB + 4;                 // shared row of the 128-wide block (16-byte aligned)
+constexpr int DIAG_SMEM = (2 * NB * DSD + 4 * HB + 2 * NB) * (int)sizeof(float) + 16;
 
-__device__ __forceinline__ void tri8_index(int q, int& bi, int& bj) {
+__device__ __forceinline__ void tri_index(int q, int& bi, int& bj) {
     int b = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
     while ((b + 1) * (b + 2) / 2 <= q) ++b;
     while (b * (b + 1) / 2 > q) --b;
     bi = b;
     bj = q - b * (b + 1) / 2;
+}
+
+// Factor the 64 x 64 lower block at A (row stride DSD) in place into L and write its inverse
+// into X (lower, zeros above the diagonal).  Returns false (uniformly) on a bad pivot.
+__device__ bool factor64(float* A, float* X, float* cbuf, float* rbuf) {
+    const int tid = threadIdx.x;
+    const bool isA = tid < NTRI4, isX = tid >= NTRI4 && tid < 2 * NTRI4;
+    int bi = 0, bj = 0;
+    if (isA || isX) tri_index(isA ? tid : tid - NTRI4, bi, bj);
+    float a[4][4];
+    if (isA) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a[r][c] = A[(bi * 4 + r) * DSD + bj * 4 + c];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a[r][c] = (bi == bj && r == c) ? 1.f : 0.f;
+    }
+    bool ok = true;
+#pragma unroll 1
+    for (int bm = 0; bm < T4; ++bm) {
+#pragma unroll
+        for (int mm = 0; mm < 4; ++mm) {
+            const int m = bm * 4 + mm;
+            float* cb = cbuf + (mm & 1) * HB;
+            float* rb = rbuf + (mm & 1) * HB;
+            if (isA && bj == bm) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) cb[bi * 4 + r] = a[r][mm];
+            }
+            if (isX && bi == bm) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) rb[bj * 4 + c] = a[mm][c];
+            }
+            __syncthreads();
+            const float d = cb[m];
+            ok = ok && d > 0.f && isfinite(d);
+            const float dd = ok ? d : 1.f;
+            const float isd = 1.0f / sqrtf(dd), id = 1.0f / dd;
+            if (isA && bj >= bm) {
+                float li[4], lj[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) li[r] = bi * 4 + r > m ? cb[bi * 4 + r] * id : 0.f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) lj[c] = bj * 4 + c > m ? cb[bj * 4 + c] : 0.f;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) a[r][c] = fmaf(-li[r], lj[c], a[r][c]);
+                if (bj == bm) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (bi * 4 + r >= m) a[r][mm] = cb[bi * 4 + r] * isd;
+                }
+            }
+            if (isX && bi >= bm && bj <= bm) {
+                float li[4], xm[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) li[r] = bi * 4 + r > m ? cb[bi * 4 + r] * id : 0.f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) xm[c] = rb[bj * 4 + c];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) a[r][c] = fmaf(-li[r], xm[c], a[r][c]);
+                if (bi == bm) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) a[mm][c] = xm[c] * isd;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (isA || isX) {
+        float* dst = isA ? A : X;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dst[(bi * 4 + r) * DSD + bj * 4 + c] = (bi == bj && c > r) ? 0.f : a[r][c];
+            if (bi != bj) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dst[(bj * 4 + r) * DSD + bi * 4 + c] = 0.f;  // upper tile
+            }
+        }
+    }
+    __syncthreads();
+    return ok;
+}
+
+// 64 x 64 x 64 products on shared-memory operands (row stride DSD), threads 0..255; thread
+// (ti, tj) = (tid / 16, tid % 16).
+// NT: out[i][j] = sum_k A[i][k] B[j][k]; rows ti + 16 a, columns tj + 16 b.
+__device__ __forceinline__ void gemm64_nt(const float* A, const float* B, float (&acc)[4][4]) {
+    const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < HB; k += 4) {
+        float4 av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (ti + 16 * a) * DSD + k);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = ld4(B + (tj + 16 * b) * DSD + k);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = dot4(av[a], bv[b], acc[a][b]);
+    }
+}
+// NN: out[i][j] = sum_k A[i][k] B[k][j]; rows ti + 16 a, columns 4 tj .. 4 tj + 3.
+__device__ __forceinline__ void gemm64_nn(const float* A, const float* B, float (&acc)[4][4]) {
+    const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < HB; k += 4) {
+        float4 av[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (ti + 16 * a) * DSD + k);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const float4 bv = ld4(B + (k + kk) * DSD + 4 * tj);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float x = kk == 0 ? av[a].x : kk == 1 ? av[a].y : kk == 2 ? av[a].z : av[a].w;
+                acc[a][0] = fmaf(x, bv.x, acc[a][0]);
+                acc[a][1] = fmaf(x, bv.y, acc[a][1]);
+                acc[a][2] = fmaf(x, bv.z, acc[a][2]);
+                acc[a][3] = fmaf(x, bv.w, acc[a][3]);
+            }
+        }
+    }
 }
 
 __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, int LD, int ns, int jb, float eps,
@@ -320,20 +463,21 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
                                                                     int* __restrict__ fail) {
     const int t = t0 + blockIdx.x;
     if (fail[t]) return;
-    __shared__ float colbuf[2][NB], rowbuf[2][NB], rhs[2][NB];
-    __shared__ float fpart[NTRI8][8][2];
+    extern __shared__ __align__(16) float dsm[];
+    float* A = dsm;                 // [NB][DSD] the block, becoming L (lower); upper-right quarter scratch
+    float* X = A + NB * DSD;        // [NB][DSD] the inverse (lower, zeros above)
+    float* cbuf = X + NB * DSD;     // [2][HB]
+    float* rbuf = cbuf + 2 * HB;    // [2][HB]
+    float* rhs = rbuf + 2 * HB;     // [2][NB]
     const int tid = threadIdx.x;
     const int nb = min(NB, P - jb);
-    const bool isA = tid < NTRI8, isX = tid >= NTRI8 && tid < 2 * NTRI8;
-    int bi = 0, bj = 0;
-    if (isA || isX) tri8_index(isA ? tid : tid - NTRI8, bi, bj);
     float* yt = yv + (size_t)t * 2 * P;
     const double2* Dt = D + (size_t)t * P;
     if (tid < 2 * NB) {
         const int h = tid >> 7, i = tid & (NB - 1);
         float v = 0.f;
         if (i < nb) v = jb == 0 ? (float)(h ? Dt[i].y : Dt[i].x) : yt[h * P + jb + i];
-        rhs[h][i] = v;
+        rhs[h * NB + i] = v;
     }
     if (jb == 0)
         for (int k = NB + tid; k < P; k += blockDim.x) {
@@ -341,172 +485,107 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
             yt[k] = (float)d.x;
             yt[P + k] = (float)d.y;
         }
-
-    float a[8][8];
-    if (isA) {
-        if (jb == 0) {
-            const float* Gt = G + (size_t)t * P * P;
-            const double* ob = obar + (size_t)t * P;
-            const float inv_ns = 1.0f / (float)ns;
-            float obi[8], obj[8];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const int i = bi * 8 + r, j = bj * 8 + r;
-                obi[r] = i < nb ? (float)ob[i] : 0.f;
-                obj[r] = j < nb ? (float)ob[j] : 0.f;
-            }
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int i = bi * 8 + r, j = bj * 8 + c;
-                    float v = i == j ? 1.f : 0.f;
-                    if (i < nb && j < nb && j <= i) {
-                        v = Gt[(size_t)j * P + i] * inv_ns - obi[r] * obj[c];
-                        if (i == j) v += eps;
-                    }
-                    a[r][c] = v;
+    // the lower block (with the diagonal), identity padding beyond nb; lanes along rows i
+    {
+        const float* Gt = G + (size_t)t * P * P;
+        const double* ob = obar + (size_t)t * P;
+        const float inv_ns = 1.0f / (float)ns;
+        for (int e = tid; e < NB * NB; e += blockDim.x) {
+            const int c = e >> 7, i = e & (NB - 1);
+            float v = i == c ? 1.f : 0.f;
+            if (i < nb && c < nb && c <= i) {
+                if (jb == 0) {
+                    v = Gt[(size_t)c * P + i] * inv_ns - (float)ob[i] * (float)ob[c];
+                    if (i == c) v += eps;
+                } else {
+                    v = Pn[((size_t)t * NB + c) * P + jb + i];
                 }
-        } else {
-            // C of the update kernel, stored transposed: PnT[t][c][i]
-            const float* pcol = Pn + ((size_t)t * NB + bj * 8) * P + jb + bi * 8;
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-#pragma unroll
-                for (int r = 0; r < 8; ++r) a[r][c] = bi * 8 + r < nb ? pcol[(size_t)c * P + r] : 0.f;
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int i = bi * 8 + r, j = bj * 8 + c;
-                    if (i >= nb || j >= nb) a[r][c] = i == j ? 1.f : 0.f;
-                    else if (j > i) a[r][c] = 0.f;
-                }
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) a[r][c] = (bi == bj && r == c) ? 1.f : 0.f;
-    }
-
-    bool ok = true;
-#pragma unroll 1
-    for (int bm = 0; bm < T8; ++bm) {
-#pragma unroll
-        for (int mm = 0; mm < 8; ++mm) {
-            const int m = bm * 8 + mm;
-            float* cb = colbuf[mm & 1];
-            float* rb = rowbuf[mm & 1];
-            if (isA && bj == bm) {
-#pragma unroll
-                for (int r = 0; r < 8; ++r) cb[bi * 8 + r] = a[r][mm];
+            } else if (c > i) {
+                v = 0.f;
             }
-            if (isX && bi == bm) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) rb[bj * 8 + c] = a[mm][c];
-            }
-            __syncthreads();
-            const float d = cb[m];
-            ok = ok && d > 0.f && isfinite(d);
-            const float dd = ok ? d : 1.f;
-            const float isd = 1.0f / sqrtf(dd), id = 1.0f / dd;
-            if (isA && bj >= bm) {
-                float li[8], lj[8];
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const int i = bi * 8 + r;
-                    li[r] = i > m ? cb[i] * id : 0.f;
-                }
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int j = bj * 8 + c;
-                    lj[c] = j > m ? cb[j] : 0.f;
-                }
-#pragma unroll
-                for (int r = 0; r < 8; ++r)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-li[r], lj[c], a[r][c]);
-                if (bj == bm) {
-#pragma unroll
-                    for (int r = 0; r < 8; ++r)
-                        if (bi * 8 + r >= m) a[r][mm] = cb[bi * 8 + r] * isd;
-                }
-            }
-            if (isX && bi >= bm && bj <= bm) {
-                float li[8], xm[8];
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const int i = bi * 8 + r;
-                    li[r] = i > m ? cb[i] * id : 0.f;
-                }
-#pragma unroll
-                for (int c = 0; c < 8; ++c) xm[c] = rb[bj * 8 + c];
-#pragma unroll
-                for (int r = 0; r < 8; ++r)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-li[r], xm[c], a[r][c]);
-                if (bi == bm) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) a[mm][c] = xm[c] * isd;
-                }
-            }
-        }
-    }
-    // every thread saw the same pivots, so this exit is uniform
-    if (!ok) {
-        if (tid == 0) fail[t] = 1;
-        return;
-    }
-    const LbLayout lay{(P + NB - 1) / NB, LD / 32};
-    if (isA) {
-        float* Lft = Lf + (size_t)t * P * LD;
-        __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
-        const int nv = nb - bj * 8;
-        if (nv > 0) {
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const int i = bi * 8 + r;
-                if (i >= nb) break;
-                float v[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) v[c] = (bi == bj && c > r) ? 0.f : a[r][c];
-                store_L8(Lft, Lbt, lay, LD, jb + i, jb + bj * 8, v, nv);
-            }
-        }
-    }
-    if (isX) {
-        float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
-        const int q = tid - NTRI8;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int i = bi * 8 + r;
-            float v[8];
-            float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int j = bj * 8 + c;
-                v[c] = (i < nb && j < nb) ? a[r][c] : 0.f;
-                s0 = fmaf(v[c], rhs[0][j], s0);
-                s1 = fmaf(v[c], rhs[1][j], s1);
-            }
-            float4* dst = reinterpret_cast<float4*>(Dv + (size_t)i * NB + bj * 8);
-            dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-            dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-            if (bi != bj) {
-                float4* up = reinterpret_cast<float4*>(Dv + (size_t)(bj * 8 + r) * NB + bi * 8);
-                up[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                up[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            fpart[q][r][0] = s0;
-            fpart[q][r][1] = s1;
+            A[i * DSD + c] = v;
         }
     }
     __syncthreads();
+    // L11, X11
+    bool ok = factor64(A, X, cbuf, rbuf);
+    float acc[4][4];
+    const int ti = tid >> 4, tj = tid & 15;
+    if (ok) {
+        // L21 = A21 X11^T (in place, after all reads)
+        if (tid < 256) gemm64_nt(A + HB * DSD, X, acc);
+        __syncthreads();
+        if (tid < 256) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) A[(HB + ti + 16 * a) * DSD + tj + 16 * b] = acc[a][b];
+        }
+        __syncthreads();
+        // A22 -= L21 L21^T
+        if (tid < 256) {
+            gemm64_nt(A + HB * DSD, A + HB * DSD, acc);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) A[(HB + ti + 16 * a) * DSD + HB + tj + 16 * b] -= acc[a][b];
+        }
+        __syncthreads();
+        // L22, X22
+        ok = factor64(A + HB * DSD + HB, X + HB * DSD + HB, cbuf, rbuf);
+    }
+    if (!ok) {  // uniform: every thread saw the same pivots
+        if (tid == 0) fail[t] = 1;
+        return;
+    }
+    // T = L21 X11 into the unused upper-right quarter of A, then X21 = -X22 T
+    float* Tm = A + HB;
+    if (tid < 256) {
+        gemm64_nn(A + HB * DSD, X, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Tm[(ti + 16 * a) * DSD + 4 * tj + b] = acc[a][b];
+    }
+    __syncthreads();
+    if (tid < 256) {
+        gemm64_nn(X + HB * DSD + HB, Tm, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) X[(HB + ti + 16 * a) * DSD + 4 * tj + b] = -acc[a][b];
+    }
+    // X12 = 0
+    for (int e = tid; e < HB * HB; e += blockDim.x) X[(e >> 6) * DSD + HB + (e & (HB - 1))] = 0.f;
+    __syncthreads();
+    // outputs: L (FP32 and BF16 pieces), X (padded rows / columns zero), y_b = X rhs
+    const LbLayout lay{(P + NB - 1) / NB, LD / 32};
+    float* Lft = Lf + (size_t)t * P * LD;
+    __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
+    for (int e = tid; e < NB * (NB / 8); e += blockDim.x) {
+        const int i = e >> 4, c8 = e & 15;
+        if (i >= nb || c8 * 8 > i) continue;
+        const int nv = nb - c8 * 8;
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = c8 * 8 + u <= i ? A[i * DSD + c8 * 8 + u] : 0.f;
+        store_L8(Lft, Lbt, lay, LD, jb + i, jb + c8 * 8, v, nv);
+    }
+    float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
+    for (int e = tid; e < NB * (NB / 4); e += blockDim.x) {
+        const int i = e >> 5, c4 = e & 31;
+        float4 v = ld4(X + i * DSD + 4 * c4);
+        if (i >= nb) v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * c4 + 0 >= nb) v.x = 0.f;
+        if (4 * c4 + 1 >= nb) v.y = 0.f;
+        if (4 * c4 + 2 >= nb) v.z = 0.f;
+        if (4 * c4 + 3 >= nb) v.w = 0.f;
+        *reinterpret_cast<float4*>(Dv + (size_t)i * NB + 4 * c4) = v;
+    }
     if (tid < 2 * NB) {
-        const int h = tid >> 7, i = tid & (NB - 1), b = i >> 3, r = i & 7;
+        const int h = tid >> 7, i = tid & (NB - 1);
         float s = 0.f;
-        for (int c = 0; c <= b; ++c) s += fpart[b * (b + 1) / 2 + c][r][h];
+        for (int k = 0; k <= i; ++k) s = fmaf(X[i * DSD + k], rhs[h * NB + k], s);
         if (i < nb) yt[h * P + jb + i] = s;
     }
 }
@@ -1110,6 +1189,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
 
     cudaError_t e = cudaMemsetAsync(fail, 0, (size_t)ntraj * 4, s);
     if (e != cudaSuccess) return chol_fail(e, "memset");
+    e = cudaFuncSetAttribute(chol_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DIAG_SMEM);
+    if (e != cudaSuccess) return chol_fail(e, "diag attribute");
     e = cudaFuncSetAttribute(chol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TRSM_SMEM);
     if (e != cudaSuccess) return chol_fail(e, "trsm attribute");
     e = cudaFuncSetAttribute(chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_U);
@@ -1143,7 +1224,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
             }
             {
                 ProfScope pd(OTVMC_K_CHOLD, gsm);
-                chol_diag_kernel<<<nt, DIAG_THREADS, 0, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, D, Pn, Lf, Lb, Dv, yv,
+                chol_diag_kernel<<<nt, DIAG_THREADS, DIAG_SMEM, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, D, Pn, Lf, Lb, Dv, yv,
                                                                fail);
                 count_launch();
             }
