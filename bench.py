@@ -198,7 +198,8 @@ def main():
     model, ans = build_model(w)
     P = ans.P
     seed = 20260603
-    traj0 = rank * T
+    from paper_2506_23928_gb300.sharding import shard
+    traj0, _ = shard(T * world, rank, world)   # weak scaling: T trajectories per rank
     W = (w.n + 63) // 64
     stream = torch.cuda.current_stream()
 
