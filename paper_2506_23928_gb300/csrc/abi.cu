@@ -823,15 +823,27 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
     }
     if (d->measure_final && moments_d) {
         const int64_t ev = 2 * (d->step0 + d->n_steps);
-        CK(launch_sample_jastrow(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, nullptr, status, s),
-           "sample launch");
+        const bool rbm = a->kind == OTVMC_RBM;
+        if (rbm)
+            CK(launch_sample_rbm(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, r.gam, r.lcr, nullptr,
+                                 s),
+               "sample launch");
+        else
+            CK(launch_sample_jastrow(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, nullptr, status,
+                                     s),
+               "sample launch");
         const bool fp32 = d->precision == OTVMC_PREC_MIXED;
         otvmc_status st = run_estimators(a, theta, spins_d, T, d->ns, nullptr, 0.0, fp32, r.eb, r.lpl, nullptr,
                                          nullptr, status, s);
         if (st) return st;
-        CK(launch_obs_prep(a, theta, T, fp32, r.eb, s), "obs prep launch");
-        CK(launch_observables(a, spins_d, T, d->ns, fp32, r.eb, moments_d + (size_t)row * T * OTVMC_MOMENTS, s),
-           "observables launch");
+        double* mrow = moments_d + (size_t)row * T * OTVMC_MOMENTS;
+        if (rbm) {
+            CK(launch_obs_rbm(a, theta, spins_d, T, d->ns, r.eb, s), "observables launch");
+            CK(launch_obs_final(a->n, d->ns, T, r.eb, mrow, s), "observables launch");
+        } else {
+            CK(launch_obs_prep(a, theta, T, fp32, r.eb, s), "obs prep launch");
+            CK(launch_observables(a, spins_d, T, d->ns, fp32, r.eb, mrow, s), "observables launch");
+        }
     }
     return OTVMC_OK;
 }

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -1111,23 +1112,23 @@ struct GroupStreams {
     cudaEvent_t fork;
     cudaEvent_t join[CHOL_GROUPS];
 };
-// Streams of the current device for the trajectory groups, created once per device.
-inline GroupStreams& group_streams() {
+// Streams for the trajectory groups: one set per (device, calling stream), created on first
+// use, so that solves issued from different streams (the run's pipelines) do not share them.
+inline GroupStreams& group_streams(cudaStream_t caller) {
     static std::mutex mu;
-    static GroupStreams per_dev[16];
-    static bool made[16] = {};
+    static std::map<std::pair<int, uintptr_t>, GroupStreams> sets;
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
-    GroupStreams& g = per_dev[dev & 15];
-    if (!made[dev & 15]) {
-        for (int i = 0; i < CHOL_GROUPS; ++i) {
-            cudaStreamCreateWithFlags(&g.s[i], cudaStreamNonBlocking);
-            cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming);
-        }
-        cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
-        made[dev & 15] = true;
+    auto key = std::make_pair(dev, (uintptr_t)caller);
+    auto it = sets.find(key);
+    if (it != sets.end()) return it->second;
+    GroupStreams& g = sets[key];
+    for (int i = 0; i < CHOL_GROUPS; ++i) {
+        cudaStreamCreateWithFlags(&g.s[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming);
     }
+    cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
     return g;
 }
 
@@ -1203,7 +1204,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     // trajectory groups on forked streams: one group's latency-bound kernels overlap the
     // others' (fork and join by events, so the call stays ordered on `s`)
     const int ng = ntraj >= 16 ? CHOL_GROUPS : 1;
-    GroupStreams& gs = group_streams();
+    GroupStreams& gs = group_streams(s);
     if (ng > 1) {
         e = cudaEventRecord(gs.fork, s);
         if (e != cudaSuccess) return chol_fail(e, "fork record");

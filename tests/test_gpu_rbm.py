@@ -153,16 +153,18 @@ def test_rbm_observables(n, m, ns):
                                           (6, 4, 24, abi.OTVMC_MIDPOINT),   # T path, P = 34 > ns
                                           (5, 6, 16, abi.OTVMC_HEUN)])      # T path, P = 41
 def test_rbm_run_matches_oracle(n, m, ns, scheme):
-    """Whole trajectories from theta = 0 with decay and dephasing: bit-identical chains and
-    parameters within 1e-8 of the oracle, whose solve always goes through S; on the T path
-    the push-through identity gives the same delta."""
+    """Whole trajectories with decay and dephasing from a random theta_0 (from theta = 0 the
+    hidden biases and weights of an RBM stay zero: tanh 0 = 0 makes their log-derivatives
+    vanish), bit-identical chains and parameters within 1e-8 of the oracle, whose solve
+    always goes through S; on the T path the push-through identity gives the same delta."""
     c = RbmCase(n, m, gamma=0.05)
     T, steps, dt, seed, eps = 2, 3, 0.01, 4242, 1e-3
+    theta0 = synth.random_theta(77, 1, c.P, 0.1)[0]
     desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=scheme,
                        precision=FP64, reg=abi.OTVMC_REG_SHIFT, eps=eps, snr_thresh=4.0, seed=seed,
                        measure_every=1, measure_final=1, use_graph=0)
     nmeas = abi.otvmc_run_n_meas(desc)
-    theta = torch.zeros((T, c.P, 2), dtype=torch.float64, device="cuda")
+    theta = to_dev_complex(np.tile(theta0, (T, 1))).reshape(T, c.P, 2)
     spins = torch.zeros((T, ns, c.W), dtype=torch.int64, device="cuda")
     check(abi.otvmc_init_chains(c.ans.handle, T, 0, ns, seed, spins))
     nb = abi.otvmc_run_workspace_bytes(c.ans.handle, desc)
@@ -171,7 +173,9 @@ def test_rbm_run_matches_oracle(n, m, ns, scheme):
     mom = torch.zeros((nmeas, T, 9), dtype=torch.float64, device="cuda")
     check(abi.otvmc_run_trajectories(c.ans.handle, desc, theta, spins, mom, work, nb))
     sname = "heun" if scheme == abi.OTVMC_HEUN else "midpoint"
-    oth, osig, om, oq = tr.run_mc(c.omodel, c.oans, T, ns, steps, dt, seed, sname, n_sweep=2, eps=eps)
+    oth, osig, om, oq = tr.run_mc(c.omodel, c.oans, T, ns, steps, dt, seed, sname, n_sweep=2, eps=eps,
+                                  theta0=theta0)
+    assert np.abs(oth[:, c.n + c.m:] - theta0[c.n + c.m:]).max() > 1e-6  # the weights moved
     assert np.array_equal(unpack(spins, c.n), osig)
     assert rel_err(from_dev_complex(theta)[..., 0], oth) < 1e-8
     want = np.concatenate([om, oq[..., [0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]]], axis=-1)
