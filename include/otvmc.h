@@ -302,7 +302,8 @@ typedef struct otvmc_run_desc {
     uint64_t seed;
     int measure_every;   /* 0: never */
     int measure_final;   /* 1: add a row at the final time */
-    int use_graph;       /* 1: capture one step as a CUDA graph and replay it */
+    int use_graph;       /* reserved, must be 0 (graph replay of a step is not built:
+                            the step's counter-based draws change every step) */
 } otvmc_run_desc;
 
 OTVMC_API size_t otvmc_run_workspace_bytes(const otvmc_ansatz* ansatz, const otvmc_run_desc* desc);

@@ -729,6 +729,7 @@ static otvmc_status check_run(const otvmc_ansatz* a, const otvmc_run_desc* d) {
     if (d->precision == OTVMC_PREC_MIXED && (d->ns % 8 != 0 || d->ns >= (1 << 24)))
         return fail(OTVMC_ERR_INVALID, "mixed precision needs ns % 8 == 0 and ns < 2^24");
     if (d->reg != OTVMC_REG_SHIFT && d->reg != OTVMC_REG_SNR) return fail(OTVMC_ERR_INVALID, "unknown regulariser");
+    if (d->use_graph != 0) return fail(OTVMC_ERR_UNSUPPORTED, "run: use_graph is reserved and must be 0");
     if ((st = rbm_precision(a, d->precision))) return st;
     if (a->kind == OTVMC_RBM && d->reg != OTVMC_REG_SHIFT)
         return fail(OTVMC_ERR_UNSUPPORTED, "the SNR regulariser is built for the Jastrow ansatz");
