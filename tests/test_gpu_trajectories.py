@@ -135,3 +135,66 @@ def test_full_size_chain64_sampled():
         assert rel_err(S_gpu, ev["S"].real) < 1e-12
         assert rel_err(Dg[t], ev["D"]) < 1e-5
         assert rel_err(dg[t], tvmc.solve_shift(ev["S"], ev["D"], eps)) < 1e-4
+
+
+def test_full_size_square10_sampled():
+    """The 10 x 10 lattice workload at full size (N = 100, P = 5050, ns = 8192: 40 block
+    columns, the last 58 wide; two spin words): sampled chains bit for bit, E_eff and v on
+    sampled trajectories, sampled entries of G, obar and D from their definitions, and the
+    mixed solve against an FP64 Cholesky solve of the same system."""
+    import scipy.linalg
+    c = Case((10, 10), alpha=3.0, h=0.5, kappa=0.05)
+    T, ns, dt, eps, seed = 4, 8192, 0.005, 1e-4, 2027
+    assert c.P == 5050 and c.W == 2
+    th, th_d = c.theta(81, T, 0.02)
+    sig0, sp = c.spins(82, T, ns)
+    work, nb = c.work(T, ns, MIXED)
+    check(abi.otvmc_sample(c.ans.handle, th_d, T, 0, ns, 2, seed, 0, sp, None, work, nb))
+    sig = unpack(sp, c.n)
+    ids = np.arange(0, ns, ns // 32)[:32]
+    for t in (1, 3):
+        want, _ = tvmc.metropolis(c.oans, th[t], sig0[t][ids], seed, t, 0, 2, chain_ids=ids)
+        assert np.array_equal(sig[t][ids], want)
+    dW = synth.random_normals(83, (T, c.nops), np.sqrt(dt))
+    dW_d = torch.from_numpy(dW).cuda()
+    E = torch.zeros((T, ns, 2), dtype=torch.float64, device="cuda")
+    v = torch.zeros_like(E)
+    check(abi.otvmc_local_estimators(c.ans.handle, th_d, sp, T, ns, dW_d, dt, MIXED, E, v, None, work, nb))
+    vv = from_dev_complex(v)[..., 0]
+    w = tvmc.mc_weights(ns)
+    t = 2
+    terms = tvmc.local_terms(c.omodel, c.oans, th[t], sig[t])
+    lpl = tvmc.expectation(w, terms["LpLd"]).real
+    want_v = -1j * dt * tvmc.effective_energy(terms, lpl) + terms["B"] @ dW[t]
+    assert rel_err(vv[t], want_v) < 1e-5
+    G = torch.zeros((T, c.P, c.P), dtype=torch.float32, device="cuda")
+    ob = torch.zeros((T, c.P), dtype=torch.float64, device="cuda")
+    D = torch.zeros((T, c.P, 2), dtype=torch.float64, device="cuda")
+    check(abi.otvmc_build_S_F(c.ans.handle, None, sp, v, T, ns, MIXED, None, G, ob, D, work, nb))
+    delta = torch.zeros((T, c.P, 2), dtype=torch.float64, device="cuda")
+    del work
+    work, nb = c.work(T, ns, MIXED)
+    check(abi.otvmc_solve_step(c.ans.handle, T, ns, MIXED, abi.OTVMC_REG_SHIFT, eps, 4.0, None, G, ob, D, delta,
+                               None, work, nb))
+    check(abi.otvmc_check(work))
+    Gt, obt, Dt = G[t].cpu().numpy().astype(np.float64), ob[t].cpu().numpy(), from_dev_complex(D)[t, :, 0]
+    # O columns from the spins (sites, then pairs j < k in row-major order)
+    s = sig[t].astype(np.float64)
+    pairs = c.oans.pairs
+    rng = np.random.default_rng(5)
+    ks = np.unique(np.concatenate([rng.integers(0, c.P, 40), [0, c.n - 1, c.n, c.P - 58, c.P - 1]]))
+
+    def col(k):
+        return s[:, k] if k < c.n else s[:, pairs[k - c.n, 0]] * s[:, pairs[k - c.n, 1]]
+
+    vc = vv[t] - vv[t].mean()
+    for i in ks:
+        oi = col(i)
+        assert obt[i] == oi.mean()
+        assert abs(Dt[i] - (oi * vc).mean()) <= 1e-9 * np.abs(Dt).max()
+        for j in ks[ks >= i]:
+            assert Gt[i, j] == float(oi @ col(j))
+    Gs = np.triu(Gt) + np.triu(Gt, 1).T
+    A = Gs / ns - np.outer(obt, obt) + eps * np.eye(c.P)
+    want_delta = scipy.linalg.cho_solve(scipy.linalg.cho_factor(A, lower=True), Dt)
+    assert rel_err(from_dev_complex(delta)[t, :, 0], want_delta) < 1e-4
