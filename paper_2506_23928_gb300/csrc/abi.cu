@@ -114,9 +114,18 @@ static otvmc_status check_batch(const otvmc_ansatz* a, int ntraj, int ns) {
     return OTVMC_OK;
 }
 static otvmc_status rbm_precision(const otvmc_ansatz* a, int precision) {
-    if (a->kind == OTVMC_RBM && precision != OTVMC_PREC_FP64)
-        return fail(OTVMC_ERR_UNSUPPORTED, "the RBM ansatz is built on the FP64 path only");
+    if (a->kind == OTVMC_RBM && precision == OTVMC_PREC_MIXED && a->m > RBM_MIXED_MAX_M)
+        return fail(OTVMC_ERR_UNSUPPORTED, "the mixed RBM path is built for n_hidden <= 256");
     return OTVMC_OK;
+}
+// RBM sampling: the FP32 warp-per-chain sampler (its decisions equal the FP64 ones) when the
+// hidden layer fits it, else the FP64 thread-per-chain sampler with its scratch.
+static cudaError_t sample_rbm_any(const otvmc_ansatz* a, const double2* theta, int T, int traj0, int ns, int n_sweep,
+                                  uint64_t seed, int64_t ev, uint64_t* spins, double2* gam, double* lcr,
+                                  unsigned long long* accepted, cudaStream_t s) {
+    if (a->m <= RBM_MIXED_MAX_M)
+        return launch_sample_rbm_mixed(a, theta, T, traj0, ns, n_sweep, seed, ev, spins, accepted, s);
+    return launch_sample_rbm(a, theta, T, traj0, ns, n_sweep, seed, ev, spins, gam, lcr, accepted, s);
 }
 
 }  // namespace otvmc
@@ -401,7 +410,7 @@ otvmc_status otvmc_sample(const otvmc_ansatz* a, const double* theta_d, int ntra
         double2* gam = c.take<double2>((size_t)ntraj * a->m * ns);
         double* lcr = c.take<double>((size_t)ntraj * a->m * ns);
         if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
-        CK(launch_sample_rbm(a, (const double2*)theta_d, ntraj, traj0, ns, n_sweep, seed, eval_index, spins_d, gam, lcr,
+        CK(sample_rbm_any(a, (const double2*)theta_d, ntraj, traj0, ns, n_sweep, seed, eval_index, spins_d, gam, lcr,
                              (unsigned long long*)accepted_d, (cudaStream_t)stream),
            "sample launch");
         return OTVMC_OK;
@@ -417,7 +426,8 @@ static otvmc_status run_estimators(const otvmc_ansatz* a, const double2* theta, 
                                    const double* dW, double dt, bool fp32, const EvalBufs& b, double* lpl,
                                    double2* Eeff, double2* v, int* status, cudaStream_t s) {
     if (a->kind == OTVMC_RBM) {
-        CK(launch_est_rbm(a, theta, spins, T, ns, b, s), "est rbm launch");
+        if (fp32) CK(launch_est_rbm_mixed(a, theta, spins, T, ns, b, s), "est rbm launch");
+        else CK(launch_est_rbm(a, theta, spins, T, ns, b, s), "est rbm launch");
     } else {
         CK(launch_jastrow_prep(a, theta, T, b, status, s), "prep launch");
         CK(launch_est1_jastrow(a, spins, T, ns, fp32, b, status, s), "est1 launch");
@@ -585,7 +595,7 @@ otvmc_status otvmc_observables(const otvmc_ansatz* a, const double* theta_d, con
                         (int*)work_d, s);
     if (st) return st;
     if (a->kind == OTVMC_RBM) {
-        CK(launch_obs_rbm(a, (const double2*)theta_d, spins_d, ntraj, ns, b, s), "observables launch");
+        CK(launch_obs_rbm(a, (const double2*)theta_d, spins_d, ntraj, ns, fp32, b, s), "observables launch");
         CK(launch_obs_final(a->n, ns, ntraj, b, moments_d, s), "observables launch");
         return OTVMC_OK;
     }
@@ -763,13 +773,13 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     const int T = d->ntraj, ns = d->ns;
     const bool fp32 = d->precision == OTVMC_PREC_MIXED;
     if (a->kind == OTVMC_RBM) {
-        CK(launch_sample_rbm(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, r.gam, r.lcr, nullptr, s),
+        CK(sample_rbm_any(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, r.gam, r.lcr, nullptr, s),
            "sample launch");
         otvmc_status st =
-            run_estimators(a, theta, spins, T, ns, r.dW, d->dt, false, r.eb, r.lpl, r.Eeff, r.v, status, s);
+            run_estimators(a, theta, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s);
         if (st) return st;
         if (moments_row) {
-            CK(launch_obs_rbm(a, theta, spins, T, ns, r.eb, s), "observables launch");
+            CK(launch_obs_rbm(a, theta, spins, T, ns, fp32, r.eb, s), "observables launch");
             CK(launch_obs_final(a->n, ns, T, r.eb, moments_row, s), "observables launch");
         }
         CK(launch_vquant(T, ns, r.v, r.eb, s), "vquant launch");
@@ -826,7 +836,7 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
         const int64_t ev = 2 * (d->step0 + d->n_steps);
         const bool rbm = a->kind == OTVMC_RBM;
         if (rbm)
-            CK(launch_sample_rbm(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, r.gam, r.lcr, nullptr,
+            CK(sample_rbm_any(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, r.gam, r.lcr, nullptr,
                                  s),
                "sample launch");
         else
@@ -839,7 +849,7 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
         if (st) return st;
         double* mrow = moments_d + (size_t)row * T * OTVMC_MOMENTS;
         if (rbm) {
-            CK(launch_obs_rbm(a, theta, spins_d, T, d->ns, r.eb, s), "observables launch");
+            CK(launch_obs_rbm(a, theta, spins_d, T, d->ns, fp32, r.eb, s), "observables launch");
             CK(launch_obs_final(a->n, d->ns, T, r.eb, mrow, s), "observables launch");
         } else {
             CK(launch_obs_prep(a, theta, T, fp32, r.eb, s), "obs prep launch");

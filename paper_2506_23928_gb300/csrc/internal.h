@@ -150,7 +150,14 @@ cudaError_t launch_sample_rbm(const otvmc_ansatz* an, const double2* theta, int 
 cudaError_t launch_est_rbm(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int ntraj, int ns,
                            const EvalBufs& b, cudaStream_t s);
 cudaError_t launch_obs_rbm(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int ntraj, int ns,
-                           const EvalBufs& b, cudaStream_t s);
+                           bool fp32, const EvalBufs& b, cudaStream_t s);
+// RBM, FP32 sampling (decisions equal to FP64) and estimators (k_rbm_mixed.cu); M <= 256
+constexpr int RBM_MIXED_MAX_M = 256;
+cudaError_t launch_sample_rbm_mixed(const otvmc_ansatz* an, const double2* theta, int ntraj, int traj0, int ns,
+                                    int n_sweep, uint64_t seed, int64_t eval, uint64_t* spins,
+                                    unsigned long long* accepted, cudaStream_t s);
+cudaError_t launch_est_rbm_mixed(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int ntraj,
+                                 int ns, const EvalBufs& b, cudaStream_t s);
 cudaError_t launch_obs_final(int n, int ns, int ntraj, const EvalBufs& b, double* moments, cudaStream_t s);
 size_t rbm_build_bytes(const otvmc_ansatz* a, int ntraj, int ns);
 size_t rbm_solve_bytes(int ntraj, int P);

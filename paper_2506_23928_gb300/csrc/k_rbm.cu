@@ -431,10 +431,11 @@ __global__ void rbm_embed_D_kernel(int P, const double2* __restrict__ D, double2
 // The moments of the Jastrow observables kernel, with the two-flip ratios computed directly:
 // log r_jk = -2 a_j s_j - 2 a_k s_k + sum_m [lc(gamma_m - 2 W_jm s_j - 2 W_km s_k) - lc(gamma_m)].
 // Thread (g, j), samples blk * SB + g + q SPP, SB = SPP * spt.
+template <typename R2>
 __global__ void __launch_bounds__(256) obs_rbm_kernel(int n, int M, int W, int P, int ns, int spt,
                                                       const double2* __restrict__ theta,
                                                       const uint64_t* __restrict__ spins,
-                                                      const double2* __restrict__ r, double* __restrict__ part_obs) {
+                                                      const R2* __restrict__ r, double* __restrict__ part_obs) {
     const int NT = ((n + 31) / 32) * 32;
     const int SPP = 256 / NT;
     const int SB = SPP * spt;
@@ -493,7 +494,8 @@ __global__ void __launch_bounds__(256) obs_rbm_kernel(int n, int M, int W, int P
             A = cadd(A, rjk);
             B = cadd(B, cscale(rjk, sk));
         }
-        const double2 rj = r[((size_t)t * ns + s) * n + j];
+        const R2 rr = r[((size_t)t * ns + s) * n + j];
+        const double2 rj = make_double2((double)rr.x, (double)rr.y);
         acc[0] += rj.x;
         acc[1] += sj * rj.y;
         acc[2] += sj;
@@ -516,16 +518,24 @@ __global__ void __launch_bounds__(256) obs_rbm_kernel(int n, int M, int W, int P
 }
 
 cudaError_t launch_obs_rbm(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int ntraj, int ns,
-                           const EvalBufs& b, cudaStream_t s) {
+                           bool fp32, const EvalBufs& b, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_OBS, s);
     const int n = a->n, M = a->m, W = (n + 63) / 64;
     const int NT = ((n + 31) / 32) * 32, SPP = 256 / NT;
     const size_t smem = (size_t)2 * SPP * M * 16 + (size_t)SPP * W * 8 + 64;
-    cudaError_t e = cudaFuncSetAttribute(obs_rbm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     dim3 grid(obs_blocks(n, ns), ntraj);
-    obs_rbm_kernel<<<grid, 256, smem, s>>>(n, M, W, (int)a->P, ns, obs_samples_per_thread(), theta, spins, b.r,
-                                           b.part_obs);
+    cudaError_t e;
+    if (fp32) {
+        e = cudaFuncSetAttribute(obs_rbm_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        obs_rbm_kernel<float2><<<grid, 256, smem, s>>>(n, M, W, (int)a->P, ns, obs_samples_per_thread(), theta, spins,
+                                                       reinterpret_cast<const float2*>(b.r), b.part_obs);
+    } else {
+        e = cudaFuncSetAttribute(obs_rbm_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        obs_rbm_kernel<double2><<<grid, 256, smem, s>>>(n, M, W, (int)a->P, ns, obs_samples_per_thread(), theta,
+                                                        spins, b.r, b.part_obs);
+    }
     count_launch();
     return cudaGetLastError();
 }
