@@ -118,8 +118,12 @@ OTVMC_API int otvmc_model_nops(const otvmc_model* model);
  *   theta = [a_0..a_{N-1}, eta_jk for j<k row-major].  n_hidden ignored.
  * OTVMC_RBM: log psi = sum a_i s_i + sum_m log 2cosh(b_m + sum_i W_im s_i),
  *   P = N + M + N M, theta = [a (N), b (M), W (N x M row-major)], M = n_hidden in
- *   [1, 4096].  Built on the FP64 path (sample, local_estimators, build_S_F, solve_step,
- *   observables, run_trajectories); MIXED calls return OTVMC_ERR_UNSUPPORTED.
+ *   [1, 4096].  Sampling uses an FP32 warp-per-chain kernel whose decisions equal the FP64
+ *   ones (M <= 256; an FP64 kernel beyond).  MIXED (M <= 256): FP32 log 2cosh in the
+ *   estimators and observables; in run_trajectories, S (P <= ns) or T (P > ns) from
+ *   split-BF16 tensor-core products accumulated in FP32 and the tensor-core Cholesky with
+ *   refinement against that matrix (delta within ~1e-4 relative of the FP64 path at eps 1e-3);
+ *   build_S_F / solve_step of an RBM run in FP64 for either precision.
  * The ansatz keeps a pointer to the model, which must outlive it. */
 OTVMC_API otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, int n_hidden,
                                  otvmc_ansatz** out);

@@ -711,8 +711,13 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
         r.obuf = nullptr;
         r.gam = c.take<double2>((size_t)T * a->m * ns);
         r.lcr = c.take<double>((size_t)T * a->m * ns);
-        r.rbm = c.take<char>(rbm_build_bytes(a, T, ns));
-        r.chol = c.take<char>(chol_ws_bytes(T, 2 * (int)(P <= (size_t)ns ? P : (size_t)ns), OTVMC_PREC_FP64));
+        if (d->precision == OTVMC_PREC_MIXED) {
+            r.rbm = c.take<char>(rbm_mixed_bytes(a, T, ns));
+            r.chol = nullptr;
+        } else {
+            r.rbm = c.take<char>(rbm_build_bytes(a, T, ns));
+            r.chol = c.take<char>(chol_ws_bytes(T, 2 * (int)(P <= (size_t)ns ? P : (size_t)ns), OTVMC_PREC_FP64));
+        }
         return r;
     }
     if (d->precision == OTVMC_PREC_FP64) {
@@ -783,8 +788,13 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
             CK(launch_obs_final(a->n, ns, T, r.eb, moments_row, s), "observables launch");
         }
         CK(launch_vquant(T, ns, r.v, r.eb, s), "vquant launch");
-        CK(launch_rbm_build_solve(a, theta, spins, r.v, r.eb.vinfo, T, ns, d->eps, r.rbm, r.chol, delta, status, s),
-           "rbm build/solve launch");
+        if (fp32)
+            CK(launch_rbm_build_solve_mixed(a, theta, spins, r.v, r.eb.vinfo, T, ns, d->eps, r.rbm, delta, status, s),
+               "rbm build/solve launch");
+        else
+            CK(launch_rbm_build_solve(a, theta, spins, r.v, r.eb.vinfo, T, ns, d->eps, r.rbm, r.chol, delta, status,
+                                      s),
+               "rbm build/solve launch");
         return OTVMC_OK;
     }
     CK(launch_sample_jastrow(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, nullptr, status, s),

@@ -169,6 +169,12 @@ cudaError_t launch_rbm_solve_S(const otvmc_ansatz* a, int T, int ns, double eps,
 cudaError_t launch_rbm_build_solve(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, const double2* v,
                                    const double* vinfo, int T, int ns, double eps, void* ws, void* chol,
                                    double2* delta, int* status, cudaStream_t s);
+size_t rbm_mixed_bytes(const otvmc_ansatz* a, int ntraj, int ns);
+cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
+                                         const double2* v, const double* vinfo, int T, int ns, double eps, void* ws,
+                                         double2* delta, int* status, cudaStream_t s);
+cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16_t* Xs, float* G, int* status,
+                              cudaStream_t s);
 inline size_t rbm_sample_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
     return (size_t)ntraj * a->m * ns * (16 + 8) + 512;
 }

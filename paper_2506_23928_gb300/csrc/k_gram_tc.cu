@@ -34,9 +34,27 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 256;
 
+// Split operands: X = [X_h | X_m | X_l] stacked along k (piece stride kpad); the k loop runs
+// over the products (h,h) (h,m) (m,h) (h,l) (m,m) (l,h) of a piece of the A rows with a piece
+// of the B rows, whose FP32 sum reproduces the product of the unsplit operand to ~2^-24.
+__constant__ int c_pair_a[6] = {0, 0, 1, 0, 1, 2};
+__constant__ int c_pair_b[6] = {0, 1, 0, 2, 1, 0};
+
+// (mb, nb) of upper-triangle tile q, enumerated in the order of gram_tiles()
+__device__ __forceinline__ int2 tile_of(int q, int P) {
+    const int MT = (P + BM - 1) / BM, NT = (P + BN - 1) / BN;
+    for (int mb = 0; mb < MT; ++mb) {
+        const int first = (mb * BM) / BN;  // smallest nb with (nb + 1) BN > mb BM
+        const int cnt = NT - first;
+        if (q < cnt) return make_int2(mb, first + q);
+        q -= cnt;
+    }
+    return make_int2(MT, NT);
+}
+
 __global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
-                                                          const int2* __restrict__ tiles, float* __restrict__ G,
-                                                          int* status) {
+                                                          int kpad, int npairs, const int2* __restrict__ tiles,
+                                                          float* __restrict__ G, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
@@ -49,9 +67,10 @@ __global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int t = blockIdx.y;
-    const int2 tl = tiles[blockIdx.x];
+    const int2 tl = tiles ? tiles[blockIdx.x] : tile_of(blockIdx.x, P);
     const int i0 = tl.x * BM, j0 = tl.y * BN;
-    const int nk = (ns + BK - 1) / BK;
+    const int nks = (ns + BK - 1) / BK;  // k slices of one piece
+    const int nk = nks * npairs;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -83,9 +102,11 @@ __global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__
                     break;
                 }
                 mbar_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_3d(sA + s * A_BYTES, &tmap, &full[s], kb * BK, i0, t);
-                tma_load_3d(sB + s * B_BYTES, &tmap, &full[s], kb * BK, j0, t);
-                tma_load_3d(sB + s * B_BYTES + BOX_BYTES, &tmap, &full[s], kb * BK, j0 + 128, t);
+                const int pr = kb / nks, kk = kb - pr * nks;
+                const int ka = c_pair_a[pr] * kpad + kk * BK, kbx = c_pair_b[pr] * kpad + kk * BK;
+                tma_load_3d(sA + s * A_BYTES, &tmap, &full[s], ka, i0, t);
+                tma_load_3d(sB + s * B_BYTES, &tmap, &full[s], kbx, j0, t);
+                tma_load_3d(sB + s * B_BYTES + BOX_BYTES, &tmap, &full[s], kbx, j0 + 128, t);
                 ++issued;
             }
             // drain: every issued stage must have landed before the CTA may exit
@@ -184,7 +205,35 @@ cudaError_t launch_gram_tc(int ntraj, int P, int ns, const uint16_t* Ot, const i
                                          tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid(ntiles, ntraj);
-    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, P, ns, tiles, G, status);
+    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, P, ns, ns, 1, tiles, G, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// G = X X^T (upper triangle, FP32) for X = X_h + X_m + X_l given as the three BF16 pieces
+// stacked along k: Xs[t][row][piece * kpad + k], rows x K per piece (K <= kpad, kpad a multiple
+// of 64, the columns K..kpad zero), six piece products.
+cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16_t* Xs, float* G, int* status,
+                              cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_GRAM, s);
+    if (kpad % tc::BK != 0 || K > kpad) return cudaErrorInvalidValue;
+    auto encode = tc::get_encode();
+    if (!encode) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)3 * kpad, (cuuint64_t)rows, (cuuint64_t)ntraj};
+    const cuuint64_t strides[2] = {(cuuint64_t)3 * kpad * 2, (cuuint64_t)rows * 3 * kpad * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)tc::BK, 128u, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Xs, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(tc::gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (int)gram_tiles(rows).size();
+    dim3 grid(ntiles, ntraj);
+    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, rows, kpad, kpad, 6, nullptr, G, status);
     count_launch();
     return cudaGetLastError();
 }

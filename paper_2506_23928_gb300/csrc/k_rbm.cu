@@ -15,6 +15,8 @@
 // [Re D; Im D] for D = O_c^+ v_c / ns, and R^T [yr; yi] / ns = [Re; Im] of O_c^+ y / ns.  So
 // (S + eps I) delta = D is a real symmetric solve of size 2P, and the push-through form
 // delta = O_c^+ (T + eps I)^-1 v_c / ns (same delta) one of size 2 ns.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace otvmc {
@@ -701,6 +703,194 @@ cudaError_t launch_rbm_build_solve(const otvmc_ansatz* a, const double2* theta, 
         ProfScope prof_(OTVMC_K_D, s);
         rbm_gemv_kernel<<<dim3((2 * P + 255) / 256, T), 256, 0, s>>>(P, ns, 0, 1.0 / ns, rb.R, rb.sol, rb.rhs);
         rbm_unpack_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(P, rb.rhs, delta);
+        count_launch(2);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ mixed build and solve
+// R (as above) in FP32, written as three BF16 pieces r = h + m + l stacked along the row:
+// kmajor: Xs[t][k'][p * kpad + x'] (rows = 2P parameters, K = 2 ns samples), else
+// Xs[t][x'][p * kpad + k'] (rows = 2 ns samples, K = 2P parameters); columns K .. kpad zero.
+__device__ __forceinline__ void split3(float v, uint16_t& h, uint16_t& m, uint16_t& l) {
+    const __nv_bfloat16 bh = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(bh);
+    const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 bl = __float2bfloat16_rn(r1 - __bfloat162float(bm));
+    h = __bfloat16_as_ushort(bh);
+    m = __bfloat16_as_ushort(bm);
+    l = __bfloat16_as_ushort(bl);
+}
+
+__global__ void __launch_bounds__(256) rbm_Xsplit_kernel(int n, int M, int W, int P, int ns, int kmajor, int kpad,
+                                                         const uint64_t* __restrict__ spins,
+                                                         const double2* __restrict__ Th,
+                                                         const double2* __restrict__ obar, uint16_t* __restrict__ Xs) {
+    const int t = blockIdx.y;
+    const uint64_t* sp = spins + (size_t)t * ns * W;
+    const double2* Tht = Th + (size_t)t * M * ns;
+    const int rows = kmajor ? 2 * P : 2 * ns, K = kmajor ? 2 * ns : 2 * P;
+    uint16_t* X = Xs + (size_t)t * rows * 3 * kpad;
+    const size_t rs = (size_t)3 * kpad;  // row stride
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)P * ns; e += (size_t)gridDim.x * blockDim.x) {
+        int k, x;
+        if (kmajor) {
+            k = (int)(e / ns);
+            x = (int)(e - (size_t)k * ns);
+        } else {
+            x = (int)(e / P);
+            k = (int)(e - (size_t)x * P);
+        }
+        const double2 o = csub(rbm_O(sp, W, n, M, ns, Tht, k, x), obar[(size_t)t * P + k]);
+        // the four entries of R for (x, k): (x, k) = Re, (x, P+k) = -Im, (ns+x, k) = Im, (ns+x, P+k) = Re
+        const float vr = (float)o.x, vi = (float)o.y;
+        uint16_t hr, mr, lr, hi, mi, li, hn, mn, ln;
+        split3(vr, hr, mr, lr);
+        split3(vi, hi, mi, li);
+        split3(-vi, hn, mn, ln);
+        size_t a0, a1, a2, a3;  // (row, column) of the four entries
+        if (kmajor) {  // rows parameters, columns samples
+            a0 = (size_t)k * rs + x;
+            a1 = (size_t)(P + k) * rs + x;
+            a2 = (size_t)k * rs + ns + x;
+            a3 = (size_t)(P + k) * rs + ns + x;
+        } else {
+            a0 = (size_t)x * rs + k;
+            a1 = (size_t)x * rs + P + k;
+            a2 = (size_t)(ns + x) * rs + k;
+            a3 = (size_t)(ns + x) * rs + P + k;
+        }
+        X[a0] = hr; X[a0 + kpad] = mr; X[a0 + 2 * kpad] = lr;
+        X[a1] = hn; X[a1 + kpad] = mn; X[a1 + 2 * kpad] = ln;
+        X[a2] = hi; X[a2 + kpad] = mi; X[a2 + 2 * kpad] = li;
+        X[a3] = hr; X[a3 + kpad] = mr; X[a3 + 2 * kpad] = lr;
+    }
+    const int padc = kpad - K;
+    if (padc > 0)
+        for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)rows * 3 * padc;
+             e += (size_t)gridDim.x * blockDim.x) {
+            const size_t r = e / (3 * padc), q = e - r * 3 * padc, pc = q / padc, c = q - pc * padc;
+            X[r * rs + pc * kpad + K + c] = 0;
+        }
+}
+
+__device__ __forceinline__ float bf16v(uint16_t u) { return __bfloat162float(__ushort_as_bfloat16(u)); }
+
+// out[k'] = inv sum_x' R[x'][k'] u[x'].x over the split pieces (k' < 2P); kmajor: one warp per
+// k' along the contiguous samples, else one thread per k'.  Runs of FP32 products, FP64 sums.
+__global__ void __launch_bounds__(256) rbm_split_gemv_kernel(int P, int ns, int kmajor, int kpad, double inv,
+                                                             const uint16_t* __restrict__ Xs,
+                                                             const double2* __restrict__ u, double2* __restrict__ out) {
+    const int t = blockIdx.y;
+    const size_t NS2 = 2 * (size_t)ns, P2 = 2 * (size_t)P, rs = (size_t)3 * kpad;
+    const size_t rows = kmajor ? P2 : NS2;
+    const uint16_t* X = Xs + (size_t)t * rows * rs;
+    const double2* ut = u + (size_t)t * NS2;
+    if (kmajor) {
+        const int k = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x & 31;
+        if (k >= 2 * P) return;
+        const uint16_t* row = X + (size_t)k * rs;
+        double a = 0.0;
+        for (size_t x = lane; x < NS2; x += 32) {
+            const float r = bf16v(row[x]) + bf16v(row[kpad + x]) + bf16v(row[2 * kpad + x]);
+            a = fma((double)r, ut[x].x, a);
+        }
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) out[(size_t)t * P2 + k] = make_double2(a * inv, 0.0);
+    } else {
+        const int k = blockIdx.x * blockDim.x + threadIdx.x;
+        if (k >= 2 * P) return;
+        double a = 0.0;
+        for (size_t x0 = 0; x0 < NS2; x0 += 64) {
+            float f = 0.f;
+            const size_t xe = x0 + 64 < NS2 ? x0 + 64 : NS2;
+            for (size_t x = x0; x < xe; ++x) {
+                const uint16_t* e = X + x * rs + k;
+                const float r = bf16v(e[0]) + bf16v(e[kpad]) + bf16v(e[2 * kpad]);
+                f = fmaf(r, (float)ut[x].x, f);
+            }
+            a += (double)f;
+        }
+        out[(size_t)t * P2 + k] = make_double2(a * inv, 0.0);
+    }
+}
+
+static size_t rup(size_t b) { return (b + 255) & ~(size_t)255; }
+static int kpad64(int k) { return (k + 63) / 64 * 64; }
+
+size_t chol_ws_bytes(int ntraj, int P, int precision);
+
+size_t rbm_mixed_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
+    const size_t P = (size_t)a->P, M = (size_t)a->m, T = (size_t)ntraj;
+    const bool tpath = P > (size_t)ns;
+    const size_t rows = tpath ? 2 * (size_t)ns : 2 * P, K = tpath ? 2 * P : 2 * (size_t)ns;
+    const size_t kp = (size_t)kpad64((int)K);
+    const size_t mx = P > (size_t)ns ? P : (size_t)ns;
+    return rup(T * M * ns * 16) + rup(T * P * 16) + rup(T * rows * 3 * kp * 2) + rup(T * rows * rows * 4) +
+           rup(T * rows * 8) + 2 * rup(T * 2 * mx * 16) + chol_ws_bytes(ntraj, (int)rows, OTVMC_PREC_MIXED) + 1024;
+}
+
+cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16_t* Xs, float* G, int* status,
+                              cudaStream_t s);
+
+// Whole evaluation's build + solve on the tensor cores: R in three BF16 pieces, the split Gram
+// R^T R or R R^T in FP32 (six piece products), the mixed Cholesky of size 2P or 2 ns with it as
+// its matrix (obar = 0: R is centred) and its refinement against it, then delta from R^T.
+cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
+                                         const double2* v, const double* vinfo, int T, int ns, double eps, void* ws,
+                                         double2* delta, int* status, cudaStream_t s) {
+    const int P = (int)a->P, n = a->n, M = a->m, W = (n + 63) / 64;
+    const bool tpath = P > ns;
+    const int rows = tpath ? 2 * ns : 2 * P, K = tpath ? 2 * P : 2 * ns, kp = kpad64(K);
+    const size_t mx = (size_t)(P > ns ? P : ns);
+    char* q = (char*)ws;
+    auto take = [&](size_t b) {
+        char* r = q;
+        q += rup(b);
+        return (void*)r;
+    };
+    double2* Th = (double2*)take((size_t)T * M * ns * 16);
+    double2* obar = (double2*)take((size_t)T * P * 16);
+    uint16_t* Xs = (uint16_t*)take((size_t)T * rows * 3 * kp * 2);
+    float* Gs = (float*)take((size_t)T * rows * rows * 4);
+    double* zero = (double*)take((size_t)T * rows * 8);
+    double2* rhs = (double2*)take((size_t)T * 2 * mx * 16);
+    double2* sol = (double2*)take((size_t)T * 2 * mx * 16);
+    void* chol = q;
+    {
+        ProfScope prof_(OTVMC_K_OBUILD, s);
+        rbm_tanh_kernel<<<dim3((ns + 255) / 256, M, T), 256, 0, s>>>(n, M, W, P, ns, theta, spins, Th);
+        rbm_obar_kernel<<<dim3((P + 7) / 8, T), 256, 0, s>>>(n, M, W, P, ns, spins, Th, obar);
+        rbm_Xsplit_kernel<<<dim3(1024, T), 256, 0, s>>>(n, M, W, P, ns, tpath ? 0 : 1, kp, spins, Th, obar, Xs);
+        rbm_vtilde_kernel<<<dim3((2 * ns + 255) / 256, T), 256, 0, s>>>(ns, v, vinfo, rhs);
+        count_launch(4);
+    }
+    cudaError_t e = cudaMemsetAsync(zero, 0, (size_t)T * rows * 8, s);
+    if (e != cudaSuccess) return e;
+    e = launch_gram_split(T, rows, K, kp, Xs, Gs, status, s);
+    if (e != cudaSuccess) return e;
+    if (!tpath) {
+        {
+            ProfScope prof_(OTVMC_K_D, s);
+            rbm_split_gemv_kernel<<<dim3((2 * P + 7) / 8, T), 256, 0, s>>>(P, ns, 1, kp, 1.0 / ns, Xs, rhs, sol);
+            count_launch();
+        }
+        // (S~ + eps I) x = [Re D; Im D], S~ = Gs / ns
+        e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, sol, rhs, nullptr, chol, 1,
+                              status, s);
+        if (e != cudaSuccess) return e;
+        rbm_unpack_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(P, rhs, delta);
+        count_launch();
+        return cudaGetLastError();
+    }
+    // (T~ + eps I) y = v~, T~ = Gs / ns; delta~ = R^T y / ns
+    e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, rhs, sol, nullptr, chol, 1, status,
+                          s);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope prof_(OTVMC_K_D, s);
+        rbm_split_gemv_kernel<<<dim3((2 * P + 255) / 256, T), 256, 0, s>>>(P, ns, 0, kp, 1.0 / ns, Xs, sol, rhs);
+        rbm_unpack_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(P, rhs, delta);
         count_launch(2);
     }
     return cudaGetLastError();

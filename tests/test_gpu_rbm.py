@@ -190,10 +190,12 @@ def test_rbm_run_matches_oracle(n, m, ns, scheme, precision):
                                   theta0=theta0)
     assert np.abs(oth[:, c.n + c.m:] - theta0[c.n + c.m:]).max() > 1e-6  # the weights moved
     assert np.array_equal(unpack(spins, c.n), osig)
-    tol = 1e-8 if precision == FP64 else 1e-5
+    # the mixed path's S or T is an FP32 sum of split-BF16 products (not exact as for the
+    # Jastrow +-1 counts), so its solve carries ~kappa x 1e-7 relative error: 3e-4 of max|theta|
+    tol = 1e-8 if precision == FP64 else 3e-4
     assert rel_err(from_dev_complex(theta)[..., 0], oth) < tol
     want = np.concatenate([om, oq[..., [0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]]], axis=-1)
-    assert rel_err(mom.cpu().numpy(), want) < tol
+    assert rel_err(mom.cpu().numpy(), want) < (1e-8 if precision == FP64 else 1e-4)
 
 
 def test_rbm_mixed_run_rejected_beyond_256_hidden():
@@ -204,3 +206,33 @@ def test_rbm_mixed_run_rejected_beyond_256_hidden():
     assert abi.otvmc_run_workspace_bytes(c.ans.handle, desc) == 0
     desc.precision = FP64
     assert abi.otvmc_run_workspace_bytes(c.ans.handle, desc) > 0
+
+
+def _run(c, precision, T, ns, steps, dt, seed, eps, theta0):
+    desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=abi.OTVMC_MIDPOINT,
+                       precision=precision, reg=abi.OTVMC_REG_SHIFT, eps=eps, snr_thresh=4.0, seed=seed,
+                       measure_every=1, measure_final=0, use_graph=0)
+    theta = to_dev_complex(np.tile(theta0, (T, 1))).reshape(T, c.P, 2)
+    spins = torch.zeros((T, ns, c.W), dtype=torch.int64, device="cuda")
+    check(abi.otvmc_init_chains(c.ans.handle, T, 0, ns, seed, spins))
+    nb = abi.otvmc_run_workspace_bytes(c.ans.handle, desc)
+    assert nb > 0
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    mom = torch.zeros((abi.otvmc_run_n_meas(desc), T, 9), dtype=torch.float64, device="cuda")
+    check(abi.otvmc_run_trajectories(c.ans.handle, desc, theta, spins, mom, work, nb))
+    return from_dev_complex(theta)[..., 0], unpack(spins, c.n), mom.cpu().numpy()
+
+
+@pytest.mark.parametrize("ns", [256, 96])
+def test_rbm_mixed_tensor_core_path_chain64_shape(ns):
+    """The chain64_rbm shape (N = 64, M = 128, P = 8384 > ns: the T path, factored at size
+    2 ns): the mixed path (FP32 sampling and estimators, T from the split-BF16 tensor-core
+    product, tensor-core Cholesky with refinement) against the FP64 path on the same draws."""
+    c = RbmCase(64, 128, gamma=0.05)
+    T, steps, dt, seed, eps = 2, 1, 0.005, 99, 1e-3
+    theta0 = synth.random_theta(5, 1, c.P, 0.01)[0]
+    th_m, sp_m, mo_m = _run(c, MIXED, T, ns, steps, dt, seed, eps, theta0)
+    th_f, sp_f, mo_f = _run(c, FP64, T, ns, steps, dt, seed, eps, theta0)
+    # the parameter change of one step (measured ~2e-4 relative: FP32-accumulated T, eps 1e-3)
+    assert rel_err(th_m - theta0, th_f - theta0) < 1e-3
+    assert rel_err(mo_m, mo_f) < 1e-5  # moments of the predictor samples (identical chains at theta_0)
