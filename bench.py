@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rbm-path", action="store_true")
     return ap.parse_args()
 
 
@@ -128,6 +129,55 @@ def run_desc(w, ntraj, traj0, step0, n_steps, precision, seed):
                        scheme=abi.OTVMC_HEUN if w.scheme == "heun" else abi.OTVMC_MIDPOINT, precision=precision,
                        reg=abi.OTVMC_REG_SHIFT, eps=w.eps, snr_thresh=4.0, seed=seed, measure_every=1,
                        measure_final=0, use_graph=0)
+
+
+def rbm_path(stream, fp64_value):
+    """The mixed batched RBM path on the chain64_rbm shape (N = 64, M = 128 hidden units,
+    P = 8384 > ns: the T path), on a reduced batch that fits beside the main run: 16
+    trajectories at ns = 2048 (the smallest of the workload's sample counts), hidden weights
+    drawn N(0, 0.01) in real and imaginary part, a = b = 0, no observables in the timed steps.
+    Reported next to the plain FP64 per-trajectory Jastrow path of the same GPU."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2506_23928_gb300 as pkg
+    from paper_2506_23928_gb300 import abi
+    from paper_2506_23928_gb300.abi import check
+    w = synth.WORKLOADS["chain64_rbm"]
+    T, ns, seed = 16, 2048, 7
+    J = pkg.lattice_couplings(w.extent, w.J, w.alpha, w.kac, w.pbc)
+    model = pkg.Model(J, w.h, np.full(w.n, w.kappa), np.full(w.n, w.gamma))
+    ans = pkg.Ansatz(model, kind=abi.OTVMC_RBM, n_hidden=w.n_hidden)
+    P, M = ans.P, w.n_hidden
+    g = synth.rng(11)
+    th = np.zeros((T, P), complex)
+    th[:, w.n + M:] = g.normal(0, 0.01, (T, w.n * M)) + 1j * g.normal(0, 0.01, (T, w.n * M))
+    theta = torch.from_numpy(th.view(np.float64).copy()).cuda().reshape(T, P, 2)
+    spins = torch.zeros((T, ns, 1), dtype=torch.int64, device="cuda")
+    check(abi.otvmc_init_chains(ans.handle, T, 0, ns, seed, spins, stream))
+
+    def desc(step0):
+        return abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=1, step0=step0, n_sweep=w.n_sweep, dt=w.dt,
+                           scheme=abi.OTVMC_MIDPOINT, precision=abi.OTVMC_PREC_MIXED, reg=abi.OTVMC_REG_SHIFT,
+                           eps=w.eps, snr_thresh=4.0, seed=seed, measure_every=0, measure_final=0, use_graph=0)
+    nb = abi.otvmc_run_workspace_bytes(ans.handle, desc(0))
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    check(abi.otvmc_run_trajectories(ans.handle, desc(0), theta, spins, None, work, nb, stream))
+    torch.cuda.synchronize()
+    steps = 2
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        check(abi.otvmc_run_trajectories(ans.handle, desc(1 + k), theta, spins, None, work, nb, stream))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    value = T * steps / (e0.elapsed_time(e1) / 1000.0)
+    del work
+    return {"value": value, "unit": METRIC, "precision": "mixed (FP32 ratios, split-BF16 T on tensor cores, "
+            "tensor-core Cholesky + refinement)",
+            "config": {"workload": w.name, "N": w.n, "M": M, "P": P, "ns": ns, "ntraj": T, "solve": "T path (2 ns)",
+                       "steps_timed": steps, "observables": "off"},
+            "vs_fp64_jastrow_path": (value / fp64_value) if fp64_value else None}
 
 
 def cpu_baseline(w, steps=1):
@@ -341,6 +391,10 @@ def main():
                 "sample": f"{Tf} trajectories x 1 step, same workload, FP64 O / S / Cholesky"}
         del wf
 
+    rbm = None
+    if not args.no_rbm_path and world == 1:
+        rbm = rbm_path(stream, fp64["value"] if fp64 else None)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, 1)
@@ -357,7 +411,8 @@ def main():
                        "parallelism": f"trajectories sharded over {world} GPU(s)",
                        "l2": "no flush: per-step working set (O, G, L of 256 trajectories, ~14 GB) exceeds L2"},
             "roofline": rl, "roofline_by_kernel": roof, "dominant_kernel": dominant,
-            "stage_ms_per_step": stage_ms, "cpu_baseline": cpu, "fp64_path": fp64, "clocks": clk, "e2e": e2e,
+            "stage_ms_per_step": stage_ms, "cpu_baseline": cpu, "fp64_path": fp64, "rbm_mixed_path": rbm,
+            "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
     if world > 1:
