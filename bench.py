@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rbm-path", action="store_true")
+    ap.add_argument("--no-rbm-workloads", action="store_true")
     return ap.parse_args()
 
 
@@ -131,11 +132,13 @@ def run_desc(w, ntraj, traj0, step0, n_steps, precision, seed):
                        measure_final=0, use_graph=0)
 
 
-def rbm_path(stream, fp64_value):
+def rbm_path(stream, fp64_value, peaks_):
     """The mixed batched RBM path on the chain64_rbm shape (N = 64, M = 128 hidden units,
     P = 8384 > ns: the T path), on a reduced batch that fits beside the main run: 16
     trajectories at ns = 2048 (the smallest of the workload's sample counts), hidden weights
     drawn N(0, 0.01) in real and imaginary part, a = b = 0, no observables in the timed steps.
+    Timed with T formed from the factorised kernel (the default) and from materialised O on
+    the tensor cores (split BF16); the second also gives the T-GEMM's tensor throughput.
     Reported next to the plain FP64 per-trajectory Jastrow path of the same GPU."""
     import numpy as np
     import torch
@@ -144,40 +147,135 @@ def rbm_path(stream, fp64_value):
     from paper_2506_23928_gb300 import abi
     from paper_2506_23928_gb300.abi import check
     w = synth.WORKLOADS["chain64_rbm"]
-    T, ns, seed = 16, 2048, 7
+    T, ns, seed, steps = 16, 2048, 7, 2
     J = pkg.lattice_couplings(w.extent, w.J, w.alpha, w.kac, w.pbc)
     model = pkg.Model(J, w.h, np.full(w.n, w.kappa), np.full(w.n, w.gamma))
     ans = pkg.Ansatz(model, kind=abi.OTVMC_RBM, n_hidden=w.n_hidden)
     P, M = ans.P, w.n_hidden
     g = synth.rng(11)
-    th = np.zeros((T, P), complex)
-    th[:, w.n + M:] = g.normal(0, 0.01, (T, w.n * M)) + 1j * g.normal(0, 0.01, (T, w.n * M))
-    theta = torch.from_numpy(th.view(np.float64).copy()).cuda().reshape(T, P, 2)
-    spins = torch.zeros((T, ns, 1), dtype=torch.int64, device="cuda")
-    check(abi.otvmc_init_chains(ans.handle, T, 0, ns, seed, spins, stream))
+    th0 = np.zeros((T, P), complex)
+    th0[:, w.n + M:] = g.normal(0, 0.01, (T, w.n * M)) + 1j * g.normal(0, 0.01, (T, w.n * M))
 
     def desc(step0):
         return abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=1, step0=step0, n_sweep=w.n_sweep, dt=w.dt,
                            scheme=abi.OTVMC_MIDPOINT, precision=abi.OTVMC_PREC_MIXED, reg=abi.OTVMC_REG_SHIFT,
                            eps=w.eps, snr_thresh=4.0, seed=seed, measure_every=0, measure_final=0, use_graph=0)
-    nb = abi.otvmc_run_workspace_bytes(ans.handle, desc(0))
+
+    def measure(mode):
+        check(abi.otvmc_ansatz_set_rbm_t_build(ans.handle, mode))
+        theta = torch.from_numpy(th0.view(np.float64).copy()).cuda().reshape(T, P, 2)
+        spins = torch.zeros((T, ns, 1), dtype=torch.int64, device="cuda")
+        check(abi.otvmc_init_chains(ans.handle, T, 0, ns, seed, spins, stream))
+        nb = abi.otvmc_run_workspace_bytes(ans.handle, desc(0))
+        work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+        check(abi.otvmc_run_trajectories(ans.handle, desc(0), theta, spins, None, work, nb, stream))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            check(abi.otvmc_run_trajectories(ans.handle, desc(1 + k), theta, spins, None, work, nb, stream))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        value = T * steps / (e0.elapsed_time(e1) / 1000.0)
+        # one more step with per-class kernel timing (outside the timed steps)
+        abi.otvmc_profile_enable(1)
+        check(abi.otvmc_run_trajectories(ans.handle, desc(1 + steps), theta, spins, None, work, nb, stream))
+        torch.cuda.synchronize()
+        prof = abi.profile_summary()
+        abi.otvmc_profile_enable(0)
+        del work
+        return value, {k: v[0] for k, v in prof.items()}, nb
+
+    v_f, st_f, nb_f = measure(abi.OTVMC_RBM_T_FACTORED)
+    v_m, st_m, nb_m = measure(abi.OTVMC_RBM_T_MATERIALISED)
+    check(abi.otvmc_ansatz_set_rbm_t_build(ans.handle, abi.OTVMC_RBM_T_FACTORED))
+    rows, K = 2 * ns, 2 * P
+    # BF16 product flops of the split T-GEMM: six piece products of the upper triangle of the
+    # embedded T (size 2 ns) over K = 2P, for T trajectories x 2 evaluations of the profiled step
+    gemm_flops = 6 * 2.0 * K * rows * (rows + 1) / 2 * T * 2
+    gram_ms = st_m.get("gram")
+    t_gemm = None
+    if gram_ms:
+        ach = gemm_flops / (gram_ms / 1000.0) / 1e12
+        t_gemm = {"bound": "tensor", "achieved": ach, "peak": peaks_["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                  "frac": ach / peaks_["bf16_tflops_sustained"], "ms_per_step": gram_ms}
+    return {"value": v_f, "unit": METRIC,
+            "precision": "mixed (FP32 ratios; T factorised: integer A, FP32 B, FP64 column sums; "
+                         "tensor-core Cholesky + refinement)",
+            "config": {"workload": w.name, "N": w.n, "M": M, "P": P, "ns": ns, "ntraj": T,
+                       "solve": "T path (2 ns)", "steps_timed": steps, "observables": "off",
+                       "workspace_bytes": nb_f},
+            "stage_ms_per_step": st_f,
+            "vs_fp64_jastrow_path": (v_f / fp64_value) if fp64_value else None,
+            "materialised_T": {"value": v_m, "unit": METRIC, "workspace_bytes": nb_m, "stage_ms_per_step": st_m,
+                               "t_gemm_roofline": t_gemm,
+                               "vs_fp64_jastrow_path": (v_m / fp64_value) if fp64_value else None}}
+
+
+def rbm_workload(name, stream, fp64_value, steps=1, warmup=1):
+    """A whole RBM workload at its full size on the mixed path (T formed from the factorised
+    kernel): chain64_rbm = 128 trajectories whose sample counts go round-robin over
+    2048 / 4096 / 8192 (one batch per sample count, the batches run one after another in a
+    step); square16_rbm = 64 trajectories at 4096 samples.  Hidden weights N(0, 0.01) in real
+    and imaginary part, a = b = 0; observables off (the RBM's pair terms cost N^2 M per sample).
+    Each step is every trajectory of the workload advanced once."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2506_23928_gb300 as pkg
+    from paper_2506_23928_gb300 import abi
+    from paper_2506_23928_gb300.abi import check
+    w = synth.WORKLOADS[name]
+    ns_mix = (2048, 4096, 8192) if name == "chain64_rbm" else (w.ns,)
+    counts = [len(range(k, w.ntraj, len(ns_mix))) for k in range(len(ns_mix))]
+    J = pkg.lattice_couplings(w.extent, w.J, w.alpha, w.kac, w.pbc)
+    model = pkg.Model(J, w.h, np.full(w.n, w.kappa), np.full(w.n, w.gamma))
+    ans = pkg.Ansatz(model, kind=abi.OTVMC_RBM, n_hidden=w.n_hidden)
+    check(abi.otvmc_ansatz_set_rbm_t_build(ans.handle, abi.OTVMC_RBM_T_FACTORED))
+    P, M, Wd = ans.P, w.n_hidden, (w.n + 63) // 64
+    seed = 20261203
+
+    def desc(k, step0):
+        return abi.RunDesc(ntraj=counts[k], traj0=sum(counts[:k]), ns=ns_mix[k], n_steps=1, step0=step0,
+                           n_sweep=w.n_sweep, dt=w.dt, scheme=abi.OTVMC_MIDPOINT, precision=abi.OTVMC_PREC_MIXED,
+                           reg=abi.OTVMC_REG_SHIFT, eps=w.eps, snr_thresh=4.0, seed=seed, measure_every=0,
+                           measure_final=0, use_graph=0)
+    nb = max(abi.otvmc_run_workspace_bytes(ans.handle, desc(k, 0)) for k in range(len(ns_mix)))
+    if nb == 0:
+        return {"unavailable": "run descriptor rejected"}
     work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
-    check(abi.otvmc_run_trajectories(ans.handle, desc(0), theta, spins, None, work, nb, stream))
-    torch.cuda.synchronize()
-    steps = 2
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(steps):
-        check(abi.otvmc_run_trajectories(ans.handle, desc(1 + k), theta, spins, None, work, nb, stream))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    value = T * steps / (e0.elapsed_time(e1) / 1000.0)
-    del work
-    return {"value": value, "unit": METRIC, "precision": "mixed (FP32 ratios, split-BF16 T on tensor cores, "
-            "tensor-core Cholesky + refinement)",
-            "config": {"workload": w.name, "N": w.n, "M": M, "P": P, "ns": ns, "ntraj": T, "solve": "T path (2 ns)",
-                       "steps_timed": steps, "observables": "off"},
-            "vs_fp64_jastrow_path": (value / fp64_value) if fp64_value else None}
+    g = synth.rng(13)
+    batches = []
+    for k, (T, ns) in enumerate(zip(counts, ns_mix)):
+        th = np.zeros((T, P), complex)
+        th[:, w.n + M:] = g.normal(0, 0.01, (T, w.n * M)) + 1j * g.normal(0, 0.01, (T, w.n * M))
+        theta = torch.from_numpy(th.view(np.float64).copy()).cuda().reshape(T, P, 2)
+        spins = torch.zeros((T, ns, Wd), dtype=torch.int64, device="cuda")
+        check(abi.otvmc_init_chains(ans.handle, T, sum(counts[:k]), ns, seed, spins, stream))
+        batches.append((theta, spins))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(ns_mix) + 1)] for _ in range(steps)]
+    for i in range(warmup + steps):
+        marks = ev[i - warmup] if i >= warmup else None
+        if marks:
+            marks[0].record(stream)
+        for k in range(len(ns_mix)):
+            theta, spins = batches[k]
+            check(abi.otvmc_run_trajectories(ans.handle, desc(k, i), theta, spins, None, work, nb, stream))
+            if marks:
+                marks[k + 1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(m[0].elapsed_time(m[-1]) for m in ev)
+    per_ns = {str(ns_mix[k]): {"ntraj": counts[k],
+                               "ms_per_step": sum(m[k].elapsed_time(m[k + 1]) for m in ev) / steps}
+              for k in range(len(ns_mix))}
+    del work, batches
+    torch.cuda.empty_cache()
+    value = w.ntraj * steps / (total_ms / 1000.0)
+    return {"value": value, "unit": METRIC, "ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup,
+            "precision": "mixed (FP32 ratios; T factorised; tensor-core Cholesky + refinement)",
+            "config": {"workload": name, "N": w.n, "M": M, "P": P, "ntraj": w.ntraj, "ns": list(ns_mix),
+                       "solve": "T path (2 ns)", "observables": "off", "workspace_bytes": nb},
+            "per_ns": per_ns, "vs_fp64_jastrow_path": (value / fp64_value) if fp64_value else None}
 
 
 def cpu_baseline(w, steps=1):
@@ -393,7 +491,12 @@ def main():
 
     rbm = None
     if not args.no_rbm_path and world == 1:
-        rbm = rbm_path(stream, fp64["value"] if fp64 else None)
+        rbm = rbm_path(stream, fp64["value"] if fp64 else None, pk)
+
+    rbm_full = None
+    if not args.no_rbm_workloads and world == 1:
+        rbm_full = {name: rbm_workload(name, stream, fp64["value"] if fp64 else None)
+                    for name in ("chain64_rbm", "square16_rbm")}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -412,6 +515,7 @@ def main():
                        "l2": "no flush: per-step working set (O, G, L of 256 trajectories, ~14 GB) exceeds L2"},
             "roofline": rl, "roofline_by_kernel": roof, "dominant_kernel": dominant,
             "stage_ms_per_step": stage_ms, "cpu_baseline": cpu, "fp64_path": fp64, "rbm_mixed_path": rbm,
+            "rbm_workloads": rbm_full,
             "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)

@@ -123,12 +123,27 @@ OTVMC_API int otvmc_model_nops(const otvmc_model* model);
  *   estimators and observables; in run_trajectories, S (P <= ns) or T (P > ns) from
  *   split-BF16 tensor-core products accumulated in FP32 and the tensor-core Cholesky with
  *   refinement against that matrix (delta within ~1e-4 relative of the FP64 path at eps 1e-3);
+ *   on the T path T is by default formed without O (otvmc_ansatz_set_rbm_t_build);
  *   build_S_F / solve_step of an RBM run in FP64 for either precision.
  * The ansatz keeps a pointer to the model, which must outlive it. */
 OTVMC_API otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, int n_hidden,
                                  otvmc_ansatz** out);
 OTVMC_API void otvmc_ansatz_destroy(otvmc_ansatz* ansatz);
 OTVMC_API int64_t otvmc_ansatz_nparams(const otvmc_ansatz* ansatz);
+
+/* How the MIXED path of run_trajectories forms T = O_c O_c^+ / ns of an RBM on the T path
+ * (P > ns; the push-through solve of the otVMC procedure).
+ * OTVMC_RBM_T_FACTORED (default): from the exact factorisation of the RBM's log-derivatives,
+ *   sum_k O_k(x) O_k(x')^* = A + B + A B with A = sum_i s_i s_i' (an integer) and
+ *   B = sum_m tanh gamma_m(x) tanh gamma_m(x')^* (FP32), centred with obar (FP64 column sums);
+ *   O(ns^2 (N + M)) work and no O in memory.  delta = O_c^+ z / ns likewise from N x (M + 1)
+ *   column sums.  Same delta as the materialised form up to rounding.
+ * OTVMC_RBM_T_MATERIALISED: O_c materialised (real embedding, three BF16 pieces) and T from
+ *   the split-BF16 tensor-core product (O(ns^2 N M) work, 12 ns N M bytes per trajectory).
+ * Returns OTVMC_ERR_INVALID for another mode or a Jastrow ansatz.  Not synchronised with
+ * calls in flight on the same ansatz: set it before launching them. */
+enum { OTVMC_RBM_T_FACTORED = 0, OTVMC_RBM_T_MATERIALISED = 1 };
+OTVMC_API otvmc_status otvmc_ansatz_set_rbm_t_build(otvmc_ansatz* ansatz, int mode);
 
 /* Bytes of work_d needed by any stage entry point below for this batch shape. */
 OTVMC_API size_t otvmc_workspace_bytes(const otvmc_ansatz* ansatz, int ntraj, int ns, int precision);
@@ -337,7 +352,7 @@ enum {
     OTVMC_K_OBS = 5,     /* observables */
     OTVMC_K_D = 6,       /* D = Cov(O^*, v) and column means */
     OTVMC_K_OBUILD = 7,  /* O in BF16 / FP64 */
-    OTVMC_K_GRAM = 8,    /* tensor-core Gram G = O^T O */
+    OTVMC_K_GRAM = 8,    /* Gram G = O^T O (tensor cores); the RBM T of the mixed T path */
     OTVMC_K_SYRK = 9,    /* FP64 S (plain path) */
     OTVMC_K_SOLVE = 10,  /* Cholesky solve (FP64 path) / triangular substitutions and refinement */
     OTVMC_K_SDE = 11,    /* predictor-corrector combination */

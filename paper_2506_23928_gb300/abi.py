@@ -24,6 +24,7 @@ OTVMC_JASTROW, OTVMC_RBM = 0, 1
 OTVMC_PREC_FP64, OTVMC_PREC_MIXED = 0, 1
 OTVMC_REG_SHIFT, OTVMC_REG_SNR = 0, 1
 OTVMC_HEUN, OTVMC_MIDPOINT = 0, 1
+OTVMC_RBM_T_FACTORED, OTVMC_RBM_T_MATERIALISED = 0, 1
 OTVMC_MOMENTS = 9
 KERNEL_CLASSES = ["sample", "prep", "est1", "est2", "reduce", "obs", "D", "obuild", "gram", "syrk", "solve", "sde",
                   "noise", "chol_update", "chol_trsm", "chol_diag", "chol_resid"]
@@ -53,6 +54,7 @@ SIGNATURES = {
     "otvmc_ansatz_create": (c_int, [P, c_int, c_int, P]),
     "otvmc_ansatz_destroy": (None, [P]),
     "otvmc_ansatz_nparams": (c_int64, [P]),
+    "otvmc_ansatz_set_rbm_t_build": (c_int, [P, c_int]),
     "otvmc_workspace_bytes": (c_size_t, [P, c_int, c_int, c_int]),
     "otvmc_check": (c_int, [P, P]),
     "otvmc_draw_noise": (c_int, [P, c_int, c_int, c_uint64, c_int64, c_double, P, P]),
@@ -160,6 +162,10 @@ def otvmc_ansatz_destroy(ansatz):
 
 def otvmc_ansatz_nparams(ansatz):
     return _call("otvmc_ansatz_nparams", ansatz)
+
+
+def otvmc_ansatz_set_rbm_t_build(ansatz, mode):
+    return _call("otvmc_ansatz_set_rbm_t_build", ansatz, mode)
 
 
 def otvmc_workspace_bytes(ansatz, ntraj, ns, precision):

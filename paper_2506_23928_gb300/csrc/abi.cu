@@ -342,6 +342,14 @@ void otvmc_ansatz_destroy(otvmc_ansatz* a) {
 
 int64_t otvmc_ansatz_nparams(const otvmc_ansatz* a) { return a ? a->P : 0; }
 
+otvmc_status otvmc_ansatz_set_rbm_t_build(otvmc_ansatz* a, int mode) {
+    if (!a || a->kind != OTVMC_RBM) return fail(OTVMC_ERR_INVALID, "set_rbm_t_build: not an RBM ansatz");
+    if (mode != OTVMC_RBM_T_FACTORED && mode != OTVMC_RBM_T_MATERIALISED)
+        return fail(OTVMC_ERR_INVALID, "set_rbm_t_build: unknown mode");
+    a->rbm_t_build = mode;
+    return OTVMC_OK;
+}
+
 size_t otvmc_workspace_bytes(const otvmc_ansatz* a, int ntraj, int ns, int precision) {
     if (!valid_ansatz(a) || ntraj < 1 || ns < 1) return 0;
     const size_t ev = eval_bufs_bytes(a, ntraj, ns);

@@ -32,6 +32,7 @@ struct otvmc_ansatz {
     int* pairs_d = nullptr;  // Jastrow: [P - n][2] sites (j, k), j < k
     int2* tiles_d = nullptr; // upper-triangle tiles of the tensor-core Gram kernel
     int ntiles = 0;
+    int rbm_t_build = 0;     // OTVMC_RBM_T_FACTORED or OTVMC_RBM_T_MATERIALISED
 };
 
 namespace otvmc {
@@ -175,6 +176,11 @@ cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* t
                                          double2* delta, int* status, cudaStream_t s);
 cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16_t* Xs, float* G, int* status,
                               cudaStream_t s);
+// RBM T path of the mixed path without materialised O (k_rbm_factored.cu)
+size_t rbm_factored_bytes(const otvmc_ansatz* a, int ntraj, int ns);
+cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
+                                            const double2* v, const double* vinfo, int T, int ns, double eps,
+                                            void* ws, double2* delta, int* status, cudaStream_t s);
 inline size_t rbm_sample_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
     return (size_t)ntraj * a->m * ns * (16 + 8) + 512;
 }

@@ -486,25 +486,39 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
             yt[k] = (float)d.x;
             yt[P + k] = (float)d.y;
         }
-    // the lower block (with the diagonal), identity padding beyond nb; lanes along rows i
+    // the lower block (with the diagonal), identity padding beyond nb; lanes along rows i.
+    // Loads are issued in batches of 16 per thread before any of them is used.
     {
         const float* Gt = G + (size_t)t * P * P;
-        const double* ob = obar + (size_t)t * P;
         const float inv_ns = 1.0f / (float)ns;
-        for (int e = tid; e < NB * NB; e += blockDim.x) {
-            const int c = e >> 7, i = e & (NB - 1);
-            float v = i == c ? 1.f : 0.f;
-            if (i < nb && c < nb && c <= i) {
-                if (jb == 0) {
-                    v = Gt[(size_t)c * P + i] * inv_ns - (float)ob[i] * (float)ob[c];
-                    if (i == c) v += eps;
-                } else {
-                    v = Pn[((size_t)t * NB + c) * P + jb + i];
-                }
-            } else if (c > i) {
-                v = 0.f;
+        float* obs = X;  // the block's column means (first block column only), X not yet in use
+        if (jb == 0 && tid < NB) obs[tid] = tid < nb ? (float)obar[(size_t)t * P + tid] : 0.f;
+        __syncthreads();
+#pragma unroll 1
+        for (int base = 0; base < NB * NB; base += 16 * DIAG_THREADS) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int e = base + tid + DIAG_THREADS * q, c = e >> 7, i = e & (NB - 1);
+                float x = 0.f;
+                if (e < NB * NB && i < nb && c < nb && c <= i)
+                    x = jb == 0 ? Gt[(size_t)c * P + i] : Pn[((size_t)t * NB + c) * P + jb + i];
+                v[q] = x;
             }
-            A[i * DSD + c] = v;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int e = base + tid + DIAG_THREADS * q, c = e >> 7, i = e & (NB - 1);
+                if (e >= NB * NB) continue;
+                float x = i == c ? 1.f : 0.f;
+                if (i < nb && c < nb && c <= i) {
+                    x = v[q];
+                    if (jb == 0) {
+                        x = x * inv_ns - obs[i] * obs[c];
+                        if (i == c) x += eps;
+                    }
+                }
+                A[i * DSD + c] = x;
+            }
         }
     }
     __syncthreads();

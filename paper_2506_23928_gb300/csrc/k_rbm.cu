@@ -823,6 +823,7 @@ size_t chol_ws_bytes(int ntraj, int P, int precision);
 size_t rbm_mixed_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
     const size_t P = (size_t)a->P, M = (size_t)a->m, T = (size_t)ntraj;
     const bool tpath = P > (size_t)ns;
+    if (tpath && a->rbm_t_build == OTVMC_RBM_T_FACTORED) return rbm_factored_bytes(a, ntraj, ns);
     const size_t rows = tpath ? 2 * (size_t)ns : 2 * P, K = tpath ? 2 * P : 2 * (size_t)ns;
     const size_t kp = (size_t)kpad64((int)K);
     const size_t mx = P > (size_t)ns ? P : (size_t)ns;
@@ -836,11 +837,14 @@ cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16
 // Whole evaluation's build + solve on the tensor cores: R in three BF16 pieces, the split Gram
 // R^T R or R R^T in FP32 (six piece products), the mixed Cholesky of size 2P or 2 ns with it as
 // its matrix (obar = 0: R is centred) and its refinement against it, then delta from R^T.
+// On the T path the ansatz's default (OTVMC_RBM_T_FACTORED) forms T without R instead.
 cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
                                          const double2* v, const double* vinfo, int T, int ns, double eps, void* ws,
                                          double2* delta, int* status, cudaStream_t s) {
     const int P = (int)a->P, n = a->n, M = a->m, W = (n + 63) / 64;
     const bool tpath = P > ns;
+    if (tpath && a->rbm_t_build == OTVMC_RBM_T_FACTORED)
+        return launch_rbm_build_solve_factored(a, theta, spins, v, vinfo, T, ns, eps, ws, delta, status, s);
     const int rows = tpath ? 2 * ns : 2 * P, K = tpath ? 2 * P : 2 * ns, kp = kpad64(K);
     const size_t mx = (size_t)(P > ns ? P : ns);
     char* q = (char*)ws;

@@ -1,0 +1,453 @@
+// RBM (Eq. 11) push-through solve on the mixed path without materialising O.
+//
+// For the RBM the log-derivatives are O_a_i = s_i, O_b_m = t_m, O_W_im = s_i t_m (t = tanh
+// gamma), so the uncentred kernel over samples factorises exactly:
+//     sum_k O_k(x) O_k(x')^* = A + B + A B,
+//     A(x, x') = sum_i s_i(x) s_i(x')  (an integer, n - 2 popcount(x xor x')),
+//     B(x, x') = sum_m t_m(x) t_m(x')^*.
+// Centring with obar (definitions after Eq. 8):
+//     T_c(x, x') = sum_k (O_k(x) - obar_k)(O_k(x') - obar_k)^*
+//                = A + B + A B - u(x) - u(x')^* + c,
+//     u(x) = sum_k O_k(x) obar_k^*  =  s.abar^* + sum_m t_m (bbar_m^* + sum_i s_i Wbar_im^*),
+//     c = sum_k |obar_k|^2.
+// With u'(x) = u(x) - c/2 the last three terms are -u'(x) - u'(x')^*.  T_c costs
+// O(ns^2 (N + M)) instead of the O(ns^2 N M) of the product of materialised rows, and the
+// back-projection delta = O_c^+ z / ns of the push-through identity (z the complex solution of
+// the size-2 ns system) is, per parameter,
+//     a_i: sum_x s_i z - abar_i^* Z,   b_m: sum_x t_m^* z - bbar_m^* Z,
+//     W_im: sum_x s_i t_m^* z - Wbar_im^* Z,   Z = sum_x z,   all divided by ns,
+// an N x (M+1) product over the samples.  The column means obar are the same product with
+// z = 1 and t unconjugated.  The real embedding written for the Cholesky is the one of
+// k_rbm.cu: rows x and ns + x, [[Re T_c, -Im T_c], [Im T_c, Re T_c]], upper triangle.
+#include "common.cuh"
+
+namespace otvmc {
+namespace rbmf {
+
+constexpr int TB = 64;   // complex tile of T_c (samples x samples)
+constexpr int MC = 32;   // hidden units per shared-memory chunk
+constexpr int XC = 64;   // samples per chunk of the column sums
+
+// tanh z = s (1 - w) / (1 + w), w = exp(-2 s z), s = sign(Re z), in FP32
+__device__ __forceinline__ float2 ctanh_f(float2 z) {
+    const float s = z.x >= 0.f ? 1.f : -1.f;
+    const float e = expf(-2.f * s * z.x);
+    float sn, cs;
+    sincosf(2.f * z.y, &sn, &cs);
+    const float wr = e * cs, wi = -s * e * sn;
+    const float nr = 1.f - wr, ni = -wi, dr = 1.f + wr, di = wi;
+    const float inv = 1.f / (dr * dr + di * di);
+    return make_float2(s * (nr * dr + ni * di) * inv, s * (ni * dr - nr * di) * inv);
+}
+
+__device__ __forceinline__ bool spin_up(const uint64_t* w, int i) { return (w[i >> 6] >> (i & 63)) & 1ull; }
+
+// t_m(x) = tanh(b_m + sum_i W_im s_i(x)) in FP32, laid out [t][m][x]
+__global__ void __launch_bounds__(256) tanh_f32_kernel(int n, int M, int W, int P, int ns,
+                                                       const double2* __restrict__ theta,
+                                                       const uint64_t* __restrict__ spins, float2* __restrict__ Tf) {
+    const int t = blockIdx.z, m = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= ns) return;
+    const double2* th = theta + (size_t)t * P;
+    const uint64_t* w = spins + ((size_t)t * ns + x) * W;
+    const double2 b = th[n + m];
+    float gr = (float)b.x, gi = (float)b.y;
+    for (int i = 0; i < n; ++i) {
+        const double2 wim = th[n + M + (size_t)i * M + m];
+        const float sg = spin_up(w, i) ? 1.f : -1.f;
+        gr = fmaf(sg, (float)wim.x, gr);
+        gi = fmaf(sg, (float)wim.y, gi);
+    }
+    Tf[((size_t)t * M + m) * ns + x] = ctanh_f(make_float2(gr, gi));
+}
+
+// Column sums over the samples, for columns c = 0..M (c = M stands for the constant 1):
+//     Wsum[t][i][c] = sum_x s_i(x) f_c(x) z(x),   csum[t][c] = sum_x f_c(x) z(x),
+// with f_c = t_c^* (conj = 1) or t_c (conj = 0), and z = 1 when zr is null, else
+// z(x) = zr[x].x + i zr[ns + x].x (real parts of the double2 solution of the embedded system).
+// One CTA per (32 columns, 64 sites, trajectory); lane = column, warp = site residue mod 8.
+// Runs of 64 samples are summed in FP32, the runs in FP64, in a fixed order.
+__global__ void __launch_bounds__(256) colsum_kernel(int n, int M, int W, int ns, int conj,
+                                                     const uint64_t* __restrict__ spins,
+                                                     const float2* __restrict__ Tf, const double2* __restrict__ zr,
+                                                     double2* __restrict__ Wsum, double2* __restrict__ csum) {
+    const int t = blockIdx.z, ib = blockIdx.y, c0 = blockIdx.x * 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ float2 fz[XC][33];
+    __shared__ uint64_t sb[XC];
+    __shared__ float2 zs[XC];
+    const float2* Tt = Tf + (size_t)t * M * ns;
+    const uint64_t* sp = spins + (size_t)t * ns * W;
+    const int c = c0 + lane;
+    double ar[8], ai[8], sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ar[r] = ai[r] = 0.0;
+    for (int x0 = 0; x0 < ns; x0 += XC) {
+        if (tid < XC) {
+            const int x = x0 + tid;
+            float2 z = make_float2(0.f, 0.f);
+            uint64_t word = 0ull;
+            if (x < ns) {
+                z = zr ? make_float2((float)zr[(size_t)t * 2 * ns + x].x, (float)zr[(size_t)t * 2 * ns + ns + x].x)
+                       : make_float2(1.f, 0.f);
+                word = sp[(size_t)x * W + ib];
+            }
+            zs[tid] = z;
+            sb[tid] = word;
+        }
+        __syncthreads();
+        // f_c(x) z(x) for the chunk: consecutive threads take consecutive samples of a column
+        for (int e = tid; e < XC * 32; e += 256) {
+            const int l = e / XC, xs = e - l * XC;
+            const int cc = c0 + l, x = x0 + xs;
+            float2 f = make_float2(0.f, 0.f);
+            if (x < ns && cc <= M) {
+                f = cc < M ? Tt[(size_t)cc * ns + x] : make_float2(1.f, 0.f);
+                if (conj) f.y = -f.y;
+            }
+            const float2 z = zs[xs];
+            fz[xs][l] = make_float2(f.x * z.x - f.y * z.y, f.x * z.y + f.y * z.x);
+        }
+        __syncthreads();
+        float fr[8], fi[8], gr = 0.f, gi = 0.f;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) fr[r] = fi[r] = 0.f;
+        const int xe = ns - x0 < XC ? ns - x0 : XC;
+        for (int xs = 0; xs < xe; ++xs) {
+            const float2 v = fz[xs][lane];
+            const uint64_t word = sb[xs] >> warp;
+            gr += v.x;
+            gi += v.y;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const bool up = (word >> (8 * r)) & 1ull;
+                fr[r] += up ? v.x : -v.x;
+                fi[r] += up ? v.y : -v.y;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            ar[r] += (double)fr[r];
+            ai[r] += (double)fi[r];
+        }
+        sr += (double)gr;
+        si += (double)gi;
+        __syncthreads();
+    }
+    if (c > M) return;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int i = ib * 64 + warp + 8 * r;
+        if (i < n) Wsum[((size_t)t * n + i) * (M + 1) + c] = make_double2(ar[r], ai[r]);
+    }
+    if (ib == 0 && warp == 0) csum[(size_t)t * (M + 1) + c] = make_double2(sr, si);
+}
+
+// obar from the sums with z = 1 (conj = 0): a_i = Wsum[i][M], b_m = csum[m], W_im = Wsum[i][m]
+// (delta_mode = 0), or delta from the sums with z the solution (conj = 1): the same entries
+// minus obar_k^* Z, Z = csum[M] (delta_mode = 1).  Both divided by ns.
+__global__ void finish_kernel(int n, int M, int P, int ns, int delta_mode, const double2* __restrict__ Wsum,
+                              const double2* __restrict__ csum, const double2* __restrict__ obar,
+                              double2* __restrict__ out) {
+    const int t = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const double2* Ws = Wsum + (size_t)t * n * (M + 1);
+    const double2* cs = csum + (size_t)t * (M + 1);
+    double2 v;
+    if (k < n) v = Ws[(size_t)k * (M + 1) + M];
+    else if (k < n + M) v = cs[k - n];
+    else {
+        const int q = k - n - M, i = q / M, m = q - i * M;
+        v = Ws[(size_t)i * (M + 1) + m];
+    }
+    if (delta_mode) {
+        const double2 Z = cs[M], o = obar[(size_t)t * P + k];
+        // v - conj(o) Z
+        v.x -= o.x * Z.x + o.y * Z.y;
+        v.y -= o.x * Z.y - o.y * Z.x;
+    }
+    const double inv = 1.0 / ns;
+    out[(size_t)t * P + k] = make_double2(v.x * inv, v.y * inv);
+}
+
+// u'(x) = sum_k O_k(x) obar_k^* - c/2 for 32 samples per CTA, thread = hidden unit m (M <= 256):
+// h_m = bbar_m^* + sum_i s_i Wbar_im^*, then sum_m t_m h_m (warp shuffles, then over warps),
+// plus s.abar^* and - c/2 (c summed in FP64 in a fixed order by every CTA alike).
+__global__ void __launch_bounds__(256) center_kernel(int n, int M, int W, int P, int ns,
+                                                     const uint64_t* __restrict__ spins,
+                                                     const float2* __restrict__ Tf, const double2* __restrict__ obar,
+                                                     float2* __restrict__ up) {
+    const int t = blockIdx.y, x0 = blockIdx.x * 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ uint64_t sb[32][4];
+    __shared__ double cred[256];
+    __shared__ float2 red[8][32];
+    const double2* ob = obar + (size_t)t * P;
+    const uint64_t* sp = spins + (size_t)t * ns * W;
+    double cp = 0.0;
+    for (int k = tid; k < P; k += 256) cp += ob[k].x * ob[k].x + ob[k].y * ob[k].y;
+    cred[tid] = cp;
+    if (tid < 32 * W) {
+        const int s = tid / W, w = tid - s * W;
+        sb[s][w] = x0 + s < ns ? sp[(size_t)(x0 + s) * W + w] : 0ull;
+    }
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (tid < h) cred[tid] += cred[tid + h];
+        __syncthreads();
+    }
+    const double c = cred[0];
+    const int m = tid;
+    float2 acc[32];
+    if (m < M) {
+        const double2 bb = ob[n + m];
+#pragma unroll
+        for (int s = 0; s < 32; ++s) acc[s] = make_float2((float)bb.x, -(float)bb.y);
+        for (int i = 0; i < n; ++i) {
+            const double2 wb = ob[n + M + (size_t)i * M + m];
+            const float wr = (float)wb.x, wi = -(float)wb.y;
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const bool u = (sb[s][i >> 6] >> (i & 63)) & 1ull;
+                acc[s].x += u ? wr : -wr;
+                acc[s].y += u ? wi : -wi;
+            }
+        }
+        const float2* Tm = Tf + ((size_t)t * M + m) * ns;
+#pragma unroll
+        for (int s = 0; s < 32; ++s) {
+            const float2 tv = x0 + s < ns ? Tm[x0 + s] : make_float2(0.f, 0.f);
+            acc[s] = make_float2(tv.x * acc[s].x - tv.y * acc[s].y, tv.x * acc[s].y + tv.y * acc[s].x);
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < 32; ++s) acc[s] = make_float2(0.f, 0.f);
+    }
+    // reduce over the 32 hidden units of each warp: lane s ends with sample s's partial sum
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+        float vr = acc[s].x, vi = acc[s].y;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            vr += __shfl_xor_sync(0xffffffffu, vr, off);
+            vi += __shfl_xor_sync(0xffffffffu, vi, off);
+        }
+        if (lane == s) red[warp][s] = make_float2(vr, vi);
+    }
+    __syncthreads();
+    if (tid < 32 && x0 + tid < ns) {
+        float ur = 0.f, ui = 0.f;
+        for (int w = 0; w < 8; ++w) {
+            ur += red[w][tid].x;
+            ui += red[w][tid].y;
+        }
+        float arr = 0.f, aii = 0.f;
+        for (int i = 0; i < n; ++i) {
+            const double2 ab = ob[i];
+            const bool u = (sb[tid][i >> 6] >> (i & 63)) & 1ull;
+            arr += u ? (float)ab.x : -(float)ab.x;
+            aii += u ? -(float)ab.y : (float)ab.y;
+        }
+        up[(size_t)t * ns + x0 + tid] = make_float2((float)((double)(ur + arr) - 0.5 * c), ui + aii);
+    }
+}
+
+// Upper tiles I <= J (64 x 64 samples) of the embedded T_c, one per CTA:
+//   Re T_c at (x, x') and (ns + x, ns + x'); -Im T_c at (x, ns + x'); for I < J also
+//   -Im T_c(x', x) = Im T_c(x, x') at (x', ns + x) (through a shared-memory transpose).
+// Thread (ty, tx) owns rows 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3 of the tile.
+__global__ void __launch_bounds__(256) tc_kernel(int n, int M, int W, int ns, const uint64_t* __restrict__ spins,
+                                                 const float2* __restrict__ Tf, const float2* __restrict__ up,
+                                                 float* __restrict__ G) {
+    const int t = blockIdx.y;
+    int J = (int)((sqrtf(8.f * (float)blockIdx.x + 1.f) - 1.f) * 0.5f);
+    while ((J + 1) * (J + 2) / 2 <= (int)blockIdx.x) ++J;
+    while (J * (J + 1) / 2 > (int)blockIdx.x) --J;
+    const int I = blockIdx.x - J * (J + 1) / 2;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    // the two t chunks, and after the products the transposed imaginary parts, share memory
+    constexpr int RAW = 4 * MC * TB > TB * (TB + 1) ? 4 * MC * TB : TB * (TB + 1);
+    __shared__ __align__(16) float raw[RAW];
+    float2(*tr)[TB] = reinterpret_cast<float2(*)[TB]>(raw);
+    float2(*tcl)[TB] = reinterpret_cast<float2(*)[TB]>(raw + 2 * MC * TB);
+    float(*tim)[TB + 1] = reinterpret_cast<float(*)[TB + 1]>(raw);
+    __shared__ uint64_t sbr[TB][4], sbc[TB][4];
+    __shared__ float2 ur[TB], uc[TB];
+    const float2* Tt = Tf + (size_t)t * M * ns;
+    const uint64_t* sp = spins + (size_t)t * ns * W;
+    const int xr0 = I * TB, xc0 = J * TB;
+    for (int e = tid; e < TB * W; e += 256) {
+        const int s = e / W, w = e - s * W;
+        sbr[s][w] = xr0 + s < ns ? sp[(size_t)(xr0 + s) * W + w] : 0ull;
+        sbc[s][w] = xc0 + s < ns ? sp[(size_t)(xc0 + s) * W + w] : 0ull;
+    }
+    if (tid < TB) {
+        ur[tid] = xr0 + tid < ns ? up[(size_t)t * ns + xr0 + tid] : make_float2(0.f, 0.f);
+        uc[tid] = xc0 + tid < ns ? up[(size_t)t * ns + xc0 + tid] : make_float2(0.f, 0.f);
+    }
+    float br[4][4], bi[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) br[a][b] = bi[a][b] = 0.f;
+    for (int m0 = 0; m0 < M; m0 += MC) {
+        __syncthreads();
+        for (int e = tid; e < MC * TB; e += 256) {
+            const int mm = e / TB, xs = e - mm * TB, m = m0 + mm;
+            tr[mm][xs] = (m < M && xr0 + xs < ns) ? Tt[(size_t)m * ns + xr0 + xs] : make_float2(0.f, 0.f);
+            tcl[mm][xs] = (m < M && xc0 + xs < ns) ? Tt[(size_t)m * ns + xc0 + xs] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int mm = 0; mm < MC; ++mm) {
+            const float4 r01 = *reinterpret_cast<const float4*>(&tr[mm][4 * ty]);
+            const float4 r23 = *reinterpret_cast<const float4*>(&tr[mm][4 * ty + 2]);
+            const float4 c01 = *reinterpret_cast<const float4*>(&tcl[mm][4 * tx]);
+            const float4 c23 = *reinterpret_cast<const float4*>(&tcl[mm][4 * tx + 2]);
+            const float rx[4] = {r01.x, r01.z, r23.x, r23.z}, ry[4] = {r01.y, r01.w, r23.y, r23.w};
+            const float cx[4] = {c01.x, c01.z, c23.x, c23.z}, cy[4] = {c01.y, c01.w, c23.y, c23.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    // t(x) t(x')^*
+                    br[a][b] = fmaf(rx[a], cx[b], fmaf(ry[a], cy[b], br[a][b]));
+                    bi[a][b] = fmaf(ry[a], cx[b], fmaf(-rx[a], cy[b], bi[a][b]));
+                }
+        }
+    }
+    const size_t ld = 2 * (size_t)ns;
+    float* Gt = G + (size_t)t * ld * ld;
+    float vre[4][4], vim[4][4];
+    __syncthreads();  // the last chunk's reads are done before tim overwrites it
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = 4 * ty + a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int cc = 4 * tx + b;
+            int pc = 0;
+            for (int w = 0; w < W; ++w) {
+                const int lo = 64 * w, valid = n - lo < 64 ? n - lo : 64;
+                const uint64_t mask = valid == 64 ? ~0ull : ((1ull << valid) - 1ull);
+                pc += __popcll((sbr[r][w] ^ sbc[cc][w]) & mask);
+            }
+            const float A = (float)(n - 2 * pc);
+            vre[a][b] = fmaf(A, 1.f + br[a][b], br[a][b]) - ur[r].x - uc[cc].x;
+            vim[a][b] = fmaf(A, bi[a][b], bi[a][b]) - ur[r].y + uc[cc].y;
+            tim[cc][r] = vim[a][b];
+        }
+    }
+    const bool vec = (ns & 3) == 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int x = xr0 + 4 * ty + a, xc = xc0 + 4 * tx;
+        if (x >= ns) continue;
+        float* row0 = Gt + (size_t)x * ld;
+        float* row1 = Gt + (size_t)(ns + x) * ld + ns;
+        float* row2 = Gt + (size_t)x * ld + ns;
+        if (vec && xc + 3 < ns) {
+            *reinterpret_cast<float4*>(row0 + xc) = make_float4(vre[a][0], vre[a][1], vre[a][2], vre[a][3]);
+            *reinterpret_cast<float4*>(row1 + xc) = make_float4(vre[a][0], vre[a][1], vre[a][2], vre[a][3]);
+            *reinterpret_cast<float4*>(row2 + xc) = make_float4(-vim[a][0], -vim[a][1], -vim[a][2], -vim[a][3]);
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (xc + b < ns) {
+                    row0[xc + b] = vre[a][b];
+                    row1[xc + b] = vre[a][b];
+                    row2[xc + b] = -vim[a][b];
+                }
+        }
+    }
+    if (I == J) return;
+    __syncthreads();
+    // (x', ns + x) = Im T_c(x, x') for x' in tile J, x in tile I: rows along x'
+    for (int e = tid; e < TB * TB; e += 256) {
+        const int cc = e / TB, r = e - cc * TB;
+        const int xp = xc0 + cc, x = xr0 + r;
+        if (xp < ns && x < ns) Gt[(size_t)xp * ld + ns + x] = tim[cc][r];
+    }
+}
+
+// [Re v_c; Im v_c] as real parts of double2 (the embedded right-hand side of the T system)
+__global__ void rhs_kernel(int ns, const double2* __restrict__ v, const double* __restrict__ vinfo,
+                           double2* __restrict__ u) {
+    const int t = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= 2 * ns) return;
+    const double2 vv = v[(size_t)t * ns + (x < ns ? x : x - ns)];
+    const double val = x < ns ? vv.x - vinfo[4 * t] : vv.y - vinfo[4 * t + 1];
+    u[(size_t)t * 2 * ns + x] = make_double2(val, 0.0);
+}
+
+static size_t rup(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace rbmf
+
+size_t rbm_factored_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
+    using rbmf::rup;
+    const size_t P = (size_t)a->P, M = (size_t)a->m, n = (size_t)a->n, T = (size_t)ntraj, S = (size_t)ns;
+    return rup(T * M * S * 8) + rup(T * P * 16) + rup(T * S * 8) + rup(T * 4 * S * S * 4) + rup(T * 2 * S * 8) +
+           2 * rup(T * 2 * S * 16) + rup(T * n * (M + 1) * 16) + rup(T * (M + 1) * 16) +
+           chol_ws_bytes(ntraj, (int)(2 * S), OTVMC_PREC_MIXED) + 1024;
+}
+
+// Build + solve of one evaluation on the T path (P > ns) of the mixed RBM path, factored:
+// t in FP32, obar (FP64 sums), u', the embedded T_c, the tensor-core Cholesky of size 2 ns with
+// refinement, then delta from the column sums of the solution.
+cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
+                                            const double2* v, const double* vinfo, int T, int ns, double eps,
+                                            void* ws, double2* delta, int* status, cudaStream_t s) {
+    using namespace rbmf;
+    const int P = (int)a->P, n = a->n, M = a->m, W = (n + 63) / 64;
+    char* q = (char*)ws;
+    auto take = [&](size_t b) {
+        char* r = q;
+        q += rup(b);
+        return (void*)r;
+    };
+    float2* Tf = (float2*)take((size_t)T * M * ns * 8);
+    double2* obar = (double2*)take((size_t)T * P * 16);
+    float2* up = (float2*)take((size_t)T * ns * 8);
+    float* G = (float*)take((size_t)T * 4 * ns * ns * 4);
+    double* zero = (double*)take((size_t)T * 2 * ns * 8);
+    double2* rhs = (double2*)take((size_t)T * 2 * ns * 16);
+    double2* sol = (double2*)take((size_t)T * 2 * ns * 16);
+    double2* Wsum = (double2*)take((size_t)T * n * (M + 1) * 16);
+    double2* csum = (double2*)take((size_t)T * (M + 1) * 16);
+    void* chol = q;
+    const dim3 cs_grid((M + 1 + 31) / 32, W, T);
+    {
+        ProfScope prof_(OTVMC_K_OBUILD, s);
+        tanh_f32_kernel<<<dim3((ns + 255) / 256, M, T), 256, 0, s>>>(n, M, W, P, ns, theta, spins, Tf);
+        colsum_kernel<<<cs_grid, 256, 0, s>>>(n, M, W, ns, 0, spins, Tf, nullptr, Wsum, csum);
+        finish_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(n, M, P, ns, 0, Wsum, csum, nullptr, obar);
+        center_kernel<<<dim3((ns + 31) / 32, T), 256, 0, s>>>(n, M, W, P, ns, spins, Tf, obar, up);
+        rhs_kernel<<<dim3((2 * ns + 255) / 256, T), 256, 0, s>>>(ns, v, vinfo, rhs);
+        count_launch(5);
+    }
+    {
+        ProfScope prof_(OTVMC_K_GRAM, s);
+        const int nt = (ns + TB - 1) / TB;
+        tc_kernel<<<dim3(nt * (nt + 1) / 2, T), 256, 0, s>>>(n, M, W, ns, spins, Tf, up, G);
+        count_launch();
+    }
+    cudaError_t e = cudaMemsetAsync(zero, 0, (size_t)T * 2 * ns * 8, s);
+    if (e != cudaSuccess) return e;
+    // (T~ + eps I) y = v~ with T~ = G / ns
+    e = launch_chol_solve(T, 2 * ns, ns, OTVMC_PREC_MIXED, eps, nullptr, G, zero, rhs, sol, nullptr, chol, 1, status,
+                          s);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope prof_(OTVMC_K_D, s);
+        colsum_kernel<<<cs_grid, 256, 0, s>>>(n, M, W, ns, 1, spins, Tf, sol, Wsum, csum);
+        finish_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(n, M, P, ns, 1, Wsum, csum, obar, delta);
+        count_launch(2);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace otvmc

@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(256) sample_rbm_mixed_kernel(const double2* __
         err = __shfl_sync(0xffffffffu, err, 0);
         const float aj = (float)a[j].x;
         const float lr = -2.f * aj * sj + s;  // Re log r_j; accept iff log u < 2 Re log r_j
-        const double u = u01(wu);
-        const float lu = logf((float)u);
+        // u = (wu + 1/2) 2^-32 in FP32 (relative error <= 2^-24, inside the guard band below)
+        const float lu = logf(fmaf((float)wu, 0x1.0p-32f, 0x1.0p-33f));
         const float guard = 4.f * (err + 1.2e-7f * fabsf(aj)) + 1e-6f + 4e-7f * fabsf(lu) + 2e-6f * fabsf(lr);
         const float d = 2.f * lr - lu;
         bool acc;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) sample_rbm_mixed_kernel(const double2* __
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, off);
             s64 = __shfl_sync(0xffffffffu, s64, 0);
-            acc = u < exp(2.0 * (-2.0 * a[j].x * sj + s64));
+            acc = u01(wu) < exp(2.0 * (-2.0 * a[j].x * sj + s64));
         }
         if (acc) {
 #pragma unroll

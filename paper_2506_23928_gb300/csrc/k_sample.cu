@@ -99,9 +99,9 @@ __global__ void __launch_bounds__(256) sample_jastrow_kernel(const double2* __re
         const int j = (int)(((unsigned long long)wsite * (unsigned long long)n) >> 32);
         const int sj = spin_sel(wd, j);
         const float fj = fm[j * TPB];
-        const double u = u01(wu);
+        // u = (wu + 1/2) 2^-32 in FP32 (relative error <= 2^-24, inside the guard band below)
+        const float lu = logf(fmaf((float)wu, 0x1.0p-32f, 0x1.0p-33f));
         const float l32 = -4.f * (float)sj * fj;
-        const float lu = logf((float)u);
         const float guard = 4.f * (float)(n + 3 + m) * ulp * R[j] * 1.01f + 1e-6f + 4e-7f * fabsf(lu);
         const float d = l32 - lu;
         bool acc;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) sample_jastrow_kernel(const double2* __re
             for (int k = 0; k < n; ++k)
                 if (k != j) part += th[n + pair_index(min(j, k), max(j, k), n)].x * (double)spin_sel(wd, k);
             const double ell = -4.0 * (double)sj * (th[j].x + part);
-            acc = u < exp(ell);
+            acc = u01(wu) < exp(ell);
         }
         if (acc) {
             const float c = -2.f * (float)sj;
@@ -204,9 +204,9 @@ __global__ void __launch_bounds__(256) sample_jastrow_reg_kernel(const double2* 
         const int j = (int)(((unsigned long long)wsite * (unsigned long long)n) >> 32);
         const int sj = ((wd >> j) & 1ull) ? 1 : -1;
         const float fj = pick_field<NF>(f, j);
-        const double u = u01(wu);
+        // u = (wu + 1/2) 2^-32 in FP32 (relative error <= 2^-24, inside the guard band below)
+        const float lu = logf(fmaf((float)wu, 0x1.0p-32f, 0x1.0p-33f));
         const float l32 = -4.f * (float)sj * fj;
-        const float lu = logf((float)u);
         const float guard = 4.f * (float)(n + 3 + m) * ulp * R[j] * 1.01f + 1e-6f + 4e-7f * fabsf(lu);
         const float d = l32 - lu;
         bool acc;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) sample_jastrow_reg_kernel(const double2* 
             for (int k = 0; k < n; ++k)
                 if (k != j) part += th[n + pair_index(min(j, k), max(j, k), n)].x * (((wd >> k) & 1ull) ? 1.0 : -1.0);
             const double ell = -4.0 * (double)sj * (th[j].x + part);
-            acc = u < exp(ell);
+            acc = u01(wu) < exp(ell);
         }
         if (acc) {
             const float c = -2.f * (float)sj;

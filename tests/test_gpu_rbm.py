@@ -15,6 +15,7 @@ from paper_2506_23928_gb300.abi import check
 
 pytestmark = pytest.mark.gpu
 FP64, MIXED = abi.OTVMC_PREC_FP64, abi.OTVMC_PREC_MIXED
+FACT, MAT = abi.OTVMC_RBM_T_FACTORED, abi.OTVMC_RBM_T_MATERIALISED
 TOL = 1e-10
 
 
@@ -164,13 +165,15 @@ def test_rbm_observables(precision, n, m, ns):
 @pytest.mark.parametrize("n,m,ns,scheme", [(6, 4, 128, abi.OTVMC_HEUN),     # S path, P = 34 <= ns
                                           (6, 4, 24, abi.OTVMC_MIDPOINT),   # T path, P = 34 > ns
                                           (5, 6, 16, abi.OTVMC_HEUN)])      # T path, P = 41
-@pytest.mark.parametrize("precision", [FP64, MIXED])
-def test_rbm_run_matches_oracle(n, m, ns, scheme, precision):
+@pytest.mark.parametrize("precision,tbuild", [(FP64, FACT), (MIXED, FACT), (MIXED, MAT)])
+def test_rbm_run_matches_oracle(n, m, ns, scheme, precision, tbuild):
     """Whole trajectories with decay and dephasing from a random theta_0 (from theta = 0 the
     hidden biases and weights of an RBM stay zero: tanh 0 = 0 makes their log-derivatives
     vanish), bit-identical chains and parameters within 1e-8 of the oracle, whose solve
-    always goes through S; on the T path the push-through identity gives the same delta."""
+    always goes through S; on the T path the push-through identity gives the same delta,
+    with T formed from the factorised kernel or from materialised O on the mixed path."""
     c = RbmCase(n, m, gamma=0.05)
+    check(abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, tbuild))
     T, steps, dt, seed, eps = 2, 3, 0.01, 4242, 1e-3
     theta0 = synth.random_theta(77, 1, c.P, 0.1)[0]
     desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=scheme,
@@ -223,12 +226,15 @@ def _run(c, precision, T, ns, steps, dt, seed, eps, theta0):
     return from_dev_complex(theta)[..., 0], unpack(spins, c.n), mom.cpu().numpy()
 
 
+@pytest.mark.parametrize("tbuild", [FACT, MAT])
 @pytest.mark.parametrize("ns", [256, 96])
-def test_rbm_mixed_tensor_core_path_chain64_shape(ns):
+def test_rbm_mixed_tensor_core_path_chain64_shape(ns, tbuild):
     """The chain64_rbm shape (N = 64, M = 128, P = 8384 > ns: the T path, factored at size
-    2 ns): the mixed path (FP32 sampling and estimators, T from the split-BF16 tensor-core
-    product, tensor-core Cholesky with refinement) against the FP64 path on the same draws."""
+    2 ns): the mixed path (FP32 sampling and estimators, T from the factorised kernel or the
+    split-BF16 tensor-core product of materialised O, tensor-core Cholesky with refinement)
+    against the FP64 path on the same draws."""
     c = RbmCase(64, 128, gamma=0.05)
+    check(abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, tbuild))
     T, steps, dt, seed, eps = 2, 1, 0.005, 99, 1e-3
     theta0 = synth.random_theta(5, 1, c.P, 0.01)[0]
     th_m, sp_m, mo_m = _run(c, MIXED, T, ns, steps, dt, seed, eps, theta0)
@@ -236,3 +242,33 @@ def test_rbm_mixed_tensor_core_path_chain64_shape(ns):
     # the parameter change of one step (measured ~2e-4 relative: FP32-accumulated T, eps 1e-3)
     assert rel_err(th_m - theta0, th_f - theta0) < 1e-3
     assert rel_err(mo_m, mo_f) < 1e-5  # moments of the predictor samples (identical chains at theta_0)
+
+
+def test_rbm_t_build_option_validation():
+    c = RbmCase(4, 3)
+    assert abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, 2) == abi.OTVMC_ERR_INVALID
+    assert abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, MAT) == abi.OTVMC_OK
+    from gpu_helpers import Case
+    j = Case((4,))
+    assert abi.otvmc_ansatz_set_rbm_t_build(j.ans.handle, FACT) == abi.OTVMC_ERR_INVALID
+
+
+@pytest.mark.parametrize("n,m,ns", [(64, 128, 200), (70, 20, 136), (5, 9, 40)])
+def test_rbm_factored_t_equals_materialised(n, m, ns):
+    """One evaluation's parameter change on the T path from the factorised T (no O in memory)
+    and from the split-BF16 product of materialised O, both against the FP64 path on the same
+    draws (two words of spins for N = 70, ragged sample tiles for ns = 136, 200, 40)."""
+    c = RbmCase(n, m, gamma=0.05)
+    assert c.P > ns
+    T, dt, seed, eps = 3, 0.005, 31, 1e-3
+    theta0 = synth.random_theta(8, 1, c.P, 0.05)[0]
+    res = {}
+    for tb in (FACT, MAT):
+        check(abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, tb))
+        res[tb] = _run(c, MIXED, T, ns, 1, dt, seed, eps, theta0)
+    th_d, sp_d, _ = _run(c, FP64, T, ns, 1, dt, seed, eps, theta0)
+    th_f, sp_f, _ = res[FACT]
+    th_m, sp_m, _ = res[MAT]
+    assert np.array_equal(sp_f, sp_d) and np.array_equal(sp_m, sp_d)
+    assert rel_err(th_f - theta0, th_d - theta0) < 1e-3
+    assert rel_err(th_m - theta0, th_d - theta0) < 1e-3
