@@ -268,6 +268,14 @@ def rbm_workload(name, stream, fp64_value, steps=1, warmup=1):
     per_ns = {str(ns_mix[k]): {"ntraj": counts[k],
                                "ms_per_step": sum(m[k].elapsed_time(m[k + 1]) for m in ev) / steps}
               for k in range(len(ns_mix))}
+    # one more step with per-class kernel timing (outside the timed steps)
+    abi.otvmc_profile_enable(1)
+    for k in range(len(ns_mix)):
+        theta, spins = batches[k]
+        check(abi.otvmc_run_trajectories(ans.handle, desc(k, warmup + steps), theta, spins, None, work, nb, stream))
+    torch.cuda.synchronize()
+    stage = {c: v[0] for c, v in abi.profile_summary().items()}
+    abi.otvmc_profile_enable(0)
     del work, batches
     torch.cuda.empty_cache()
     value = w.ntraj * steps / (total_ms / 1000.0)
@@ -275,7 +283,8 @@ def rbm_workload(name, stream, fp64_value, steps=1, warmup=1):
             "precision": "mixed (FP32 ratios; T factorised; tensor-core Cholesky + refinement)",
             "config": {"workload": name, "N": w.n, "M": M, "P": P, "ntraj": w.ntraj, "ns": list(ns_mix),
                        "solve": "T path (2 ns)", "observables": "off", "workspace_bytes": nb},
-            "per_ns": per_ns, "vs_fp64_jastrow_path": (value / fp64_value) if fp64_value else None}
+            "per_ns": per_ns, "stage_ms_per_step": stage,
+            "vs_fp64_jastrow_path": (value / fp64_value) if fp64_value else None}
 
 
 def cpu_baseline(w, steps=1):
@@ -438,8 +447,8 @@ def main():
         "gram": ("tensor", 2.0 * ns * P * (P + 1) / 2),
         # BF16 tensor flops of the Cholesky block-column updates: six BF16 products per FP32 product
         "chol_update": ("tensor", 6 * 2.0 * sum((P - jb) * NBK * jb for jb in jbs if jb > 0)),
-        # FP32 flops of the panel solves X = C L_dd^-T (triangular: 128*129/2 multiply-adds per row)
-        "chol_trsm": ("alu", 2.0 * sum(max(0, P - jb - NBK) * NBK * (NBK + 1) / 2 for jb in jbs)),
+        # BF16 tensor flops of the panel products X = C L_dd^-T: six BF16 products per FP32 product
+        "chol_trsm": ("tensor", 6 * 2.0 * sum(max(0, P - jb - NBK) * NBK * NBK for jb in jbs)),
         # bytes the triangular substitutions must read: the lower factor (FP32) once for the
         # backward pass after the factorization (its forward pass is fused into it) and twice
         # for the correction of the refinement step

@@ -10,11 +10,12 @@
 //           32-column k slices (64-byte swizzle) in a 2-stage ring, two CTAs per SM.
 //   diag    (SIMT)     factor the 128 x 128 diagonal block and invert its factor in one pass of
 //           right-looking elimination over register-held 8 x 8 tiles;
-//   trsm    (SIMT)     the rows below as a register-tiled GEMM X = C L_dd^-T, one 64-row tile
-//           per CTA; both write L in FP32 (for the triangular solves) and as BF16 pieces
-//           (for later updates), and the diagonal kernel writes L_dd^-1.
+//   panel   (tcgen05)  the rows below, X = C L_dd^-T, with C (written by the update kernel as
+//           BF16 pieces) and L_dd^-1 (written by the diagonal kernel as BF16 pieces) through the
+//           same six piece products over K = 128, one 128-row tile per CTA; diag and panel
+//           write L in FP32 (for the triangular solves) and as BF16 pieces (for later updates).
 //   The forward substitution L y = D rides along: diag applies L_dd^-1 to its block of the
-//   right-hand side, trsm subtracts the block's contribution from the rows below.
+//   right-hand side, the panel kernel subtracts the block's contribution from the rows below.
 // solve     (SIMT)     backward substitution x = L^-T y by blocks through the stored inverses,
 //           then iterative refinement: the residual D - (S + eps I) x from the exact Gram
 //           counts (S = G/ns - obar obar^T) in double-float arithmetic, tile-parallel over
@@ -42,7 +43,6 @@ constexpr int STAGE = 2 * NPC * BOX;     // A pieces + B pieces: 48 KB
 constexpr int STAGES = 2;                // about 97 KB of shared memory: two CTAs per SM
 constexpr int SMEM_U = STAGES * STAGE + 1024 + 256;
 constexpr uint32_t TCOLS = 128;
-constexpr int RT = 64;                   // panel rows per tile
 
 __device__ __forceinline__ float a_orig(const float* Gt, const double* ob, int P, float inv_ns, int i, int j,
                                         float eps) {
@@ -51,11 +51,55 @@ __device__ __forceinline__ float a_orig(const float* Gt, const double* ob, int P
     return i == j ? v + eps : v;
 }
 
+// ------------------------------------------------------------------ BF16 piece layout
+// BF16 pieces of L are stored tiled: for piece p of trajectory t, the 128-row tile i / 128
+// and the 32-column chunk k / 32 form one contiguous 8 KB block [i % 128][k % 32] laid out
+// exactly as the update kernel's shared-memory operand box: rows of 64 bytes with the
+// 64-byte swizzle (16-byte unit u of row r stored at unit u ^ ((r / 2) mod 4)), so that one
+// box is one contiguous bulk copy.
+struct LbLayout {
+    int NT;  // row tiles, ceil(P / 128)
+    int KC;  // 32-column chunks, LD / 32
+    __host__ __device__ __forceinline__ size_t plane() const { return (size_t)NT * KC * 128 * 32; }
+    __device__ __forceinline__ size_t at(int i, int k) const {
+        const int r = i & 127, u = (k & 31) >> 3;
+        return (((size_t)(i >> 7) * KC + (k >> 5)) * 128 + r) * 32 + ((u ^ ((r >> 1) & 3)) << 3) + (k & 7);
+    }
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// The three BF16 pieces of eight consecutive entries (a 16-byte unit of each piece's plane).
+__device__ __forceinline__ void store_P8(__nv_bfloat16* Bt, size_t pl, size_t idx, const float (&v)[8]) {
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        __nv_bfloat16 hp[2], mp[2], lp[2];
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            const float x = v[2 * u + w];
+            hp[w] = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(hp[w]);
+            mp[w] = __float2bfloat16_rn(r1);
+            lp[w] = __float2bfloat16_rn(r1 - __bfloat162float(mp[w]));
+        }
+        h[u] = pack_bf16x2(hp[0], hp[1]);
+        m[u] = pack_bf16x2(mp[0], mp[1]);
+        l[u] = pack_bf16x2(lp[0], lp[1]);
+    }
+    *reinterpret_cast<uint4*>(Bt + idx) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(Bt + pl + idx) = make_uint4(m[0], m[1], m[2], m[3]);
+    *reinterpret_cast<uint4*>(Bt + 2 * pl + idx) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 // ------------------------------------------------------------------------- update (tcgen05)
 __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16* __restrict__ Lb, size_t plane,
                                                              int KC, int t0, int P, int ns, int jb, float eps,
                                                              const float* __restrict__ G,
                                                              const double* __restrict__ obar, float* __restrict__ Pn,
+                                                             __nv_bfloat16* __restrict__ Cb, size_t planeC,
                                                              const int* __restrict__ fail, int* status) {
     using namespace tc;
     const int t = t0 + blockIdx.y;
@@ -142,8 +186,10 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
         }
         __syncwarp();
     } else {
-        // epilogue: C = A - acc, written transposed (PnT[t][c][i]) so that the lanes of a warp
-        // (consecutive rows i) store consecutive addresses
+        // epilogue: C = A - acc.  The diagonal tile (blockIdx.x = 0) goes to PnT[t][c][i]
+        // (FP32, transposed, so that the lanes of a warp store consecutive addresses) for the
+        // diagonal-block kernel; the tiles below go out as three BF16 pieces in the operand-box
+        // layout of the panel kernel (one 16-byte unit of each piece per 8 columns of a row).
         const int q = warp & 3;
         const float* Gt = G + (size_t)t * P * P;
         const double* ob = obar + (size_t)t * P;
@@ -169,13 +215,29 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                 if (i >= P) continue;
+                if (blockIdx.x == 0) {
 #pragma unroll
-                for (int u = 0; u < 32; ++u) {
-                    const int j = jb + c0 + u;
-                    if (j < P && j <= i) {
-                        float a = g[u] * inv_ns - obi * obj_s[c0 + u];
-                        if (i == j) a += eps;
-                        pcol[(size_t)(c0 + u) * P] = a - __uint_as_float(v[u]);
+                    for (int u = 0; u < 32; ++u) {
+                        const int j = jb + c0 + u;
+                        if (j < P && j <= i) {
+                            float a = g[u] * inv_ns - obi * obj_s[c0 + u];
+                            if (i == j) a += eps;
+                            pcol[(size_t)(c0 + u) * P] = a - __uint_as_float(v[u]);
+                        }
+                    }
+                } else {
+                    // rows below the diagonal block: every column j = jb + c0 + u < i
+                    const LbLayout layC{(P + NB - 1) / NB, NB / BK};
+                    __nv_bfloat16* Cbt = Cb + (size_t)t * NPC * planeC;
+#pragma unroll
+                    for (int u8 = 0; u8 < 4; ++u8) {
+                        float c8[8];
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) {
+                            const int u = 8 * u8 + w;
+                            c8[w] = g[u] * inv_ns - obi * obj_s[c0 + u] - __uint_as_float(v[u]);
+                        }
+                        store_P8(Cbt, planeC, layC.at(i, c0 + 8 * u8), c8);
                     }
                 }
             }
@@ -189,26 +251,6 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
     }
-}
-
-// --------------------------------------------------------------------------- panel (SIMT)
-// BF16 pieces of L are stored tiled: for piece p of trajectory t, the 128-row tile i / 128
-// and the 32-column chunk k / 32 form one contiguous 8 KB block [i % 128][k % 32] laid out
-// exactly as the update kernel's shared-memory operand box: rows of 64 bytes with the
-// 64-byte swizzle (16-byte unit u of row r stored at unit u ^ ((r / 2) mod 4)), so that one
-// box is one contiguous bulk copy.
-struct LbLayout {
-    int NT;  // row tiles, ceil(P / 128)
-    int KC;  // 32-column chunks, LD / 32
-    __host__ __device__ __forceinline__ size_t plane() const { return (size_t)NT * KC * 128 * 32; }
-    __device__ __forceinline__ size_t at(int i, int k) const {
-        const int r = i & 127, u = (k & 31) >> 3;
-        return (((size_t)(i >> 7) * KC + (k >> 5)) * 128 + r) * 32 + ((u ^ ((r >> 1) & 3)) << 3) + (k & 7);
-    }
-};
-
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
 // Eight consecutive entries L[i][k0 .. k0+8) (k0 a multiple of 8): FP32 copy for the
@@ -460,8 +502,9 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
                                                                     const double2* __restrict__ D,
                                                                     const float* __restrict__ Pn, float* __restrict__ Lf,
                                                                     __nv_bfloat16* __restrict__ Lb,
-                                                                    float* __restrict__ Dinv, float* __restrict__ yv,
-                                                                    int* __restrict__ fail) {
+                                                                    float* __restrict__ Dinv,
+                                                                    __nv_bfloat16* __restrict__ Db,
+                                                                    float* __restrict__ yv, int* __restrict__ fail) {
     const int t = t0 + blockIdx.x;
     if (fail[t]) return;
     extern __shared__ __align__(16) float dsm[];
@@ -597,6 +640,22 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         if (4 * c4 + 3 >= nb) v.w = 0.f;
         *reinterpret_cast<float4*>(Dv + (size_t)i * NB + 4 * c4) = v;
     }
+    {
+        // L_dd^-1 as three BF16 pieces in the operand-box layout of the panel kernel
+        const LbLayout layD{1, NB / BK};
+        const size_t pl = layD.plane();
+        __nv_bfloat16* Dbt = Db + (size_t)t * NPC * pl;
+        for (int e = tid; e < NB * (NB / 8); e += blockDim.x) {
+            const int i = e >> 4, c8 = e & 15;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = 8 * c8 + u;
+                v[u] = (i < nb && c < nb) ? X[i * DSD + c] : 0.f;
+            }
+            store_P8(Dbt, pl, layD.at(i, 8 * c8), v);
+        }
+    }
     if (tid < 2 * NB) {
         const int h = tid >> 7, i = tid & (NB - 1);
         float s = 0.f;
@@ -605,138 +664,178 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     }
 }
 
-// ---------------------------------------------------------------------------------- trsm
-// Rows below the diagonal block: X = C L_dd^-T, one 64-row tile per CTA, both operands held
-// transposed in shared memory (CT[k][row], LT[k][col]).  Thread (rg, cg) owns rows
-// 4 rg .. 4 rg + 3 and columns 8 cg .. 8 cg + 7; per k it reads one float4 of C^T and two of
-// L_dd^-T (3 loads per 32 multiply-adds).  The forward substitution is fused in: each row i
-// below loses its component along this block column, y_i -= X[i, :] . y_b.
-constexpr int DCT = RT + 4;              // CT row: 64 rows + pad (16-byte aligned)
-constexpr int DLT = NB + 4;              // LT row: 128 columns + pad
-constexpr int TRSM_SMEM = (NB * DCT + NB * DLT + 2 * NB) * (int)sizeof(float);
+// ---------------------------------------------------------------------------------- panel
+// Rows below the diagonal block, X = C L_dd^-T, on the tensor cores: one CTA = 128 rows of one
+// trajectory, A = the rows of C (three BF16 pieces written by the update kernel, or for the
+// first block column by chol_cb0_kernel from the Gram counts), B = L_dd^-1 (three pieces
+// written by the diagonal kernel), the six piece products of the update kernel over K = 128
+// (four 32-column slices), FP32 accumulators in TMEM.  The epilogue (one row per thread)
+// writes L (FP32 + pieces) and subtracts the row's component along the block from the
+// forward-substitution vector, y_i -= X[i, :] . y_b.
 
-__global__ void __launch_bounds__(256, 2) chol_trsm_kernel(int t0, int P, int LD, int ns, int jb, float eps,
-                                                           const float* __restrict__ G, const double* __restrict__ obar,
-                                                           const float* __restrict__ Pn, float* __restrict__ Lf,
-                                                           __nv_bfloat16* __restrict__ Lb,
-                                                           const float* __restrict__ Dinv, float* __restrict__ yv,
-                                                           const int* __restrict__ fail) {
+// C of the first block column for the rows below it: (S + eps I)_ic = G[c][i]/ns - obar_i obar_c
+// (i >= 128 > c), as BF16 pieces.  Thread: row r = tid % 128 of the tile, column groups
+// tid / 128 + 2 g (g < 8) of eight columns; rows beyond P are written as zeros.
+__global__ void __launch_bounds__(256) chol_cb0_kernel(int t0, int P, int ns, const float* __restrict__ G,
+                                                       const double* __restrict__ obar, __nv_bfloat16* __restrict__ Cb,
+                                                       size_t planeC, const int* __restrict__ fail) {
     const int t = t0 + blockIdx.y;
     if (fail[t]) return;
-    extern __shared__ __align__(16) float tsm[];
-    float* CT = tsm;               // [NB][DCT]  C^T (k = column of C, then row)
-    float* LT = CT + NB * DCT;     // [NB][DLT]  (L_dd^-1)^T: LT[k][c] = Linv[c][k]
-    float* yb = LT + NB * DLT;     // [2][NB]
-    const int tid = threadIdx.x;
-    const int nb = min(NB, P - jb);
-    const int r0 = jb + nb + blockIdx.x * RT;
-    const float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
-    float* yt = yv + (size_t)t * 2 * P;
-    {
-        // Linv[c][4 q .. 4 q + 3] -> LT[4 q + i][c]; lanes along c (conflict-free stores)
-        float4 v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int e = tid + 256 * q, c = e & (NB - 1), k4 = e >> 7;
-            v[q] = ld4(Dv + (size_t)c * NB + 4 * k4);
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int e = tid + 256 * q, c = e & (NB - 1), k4 = e >> 7;
-            LT[(4 * k4 + 0) * DLT + c] = v[q].x;
-            LT[(4 * k4 + 1) * DLT + c] = v[q].y;
-            LT[(4 * k4 + 2) * DLT + c] = v[q].z;
-            LT[(4 * k4 + 3) * DLT + c] = v[q].w;
-        }
-    }
-    {
-        // CT[c][rr] = C[r0 + rr][c]: from the Gram counts (first block column, G[c][i] with i
-        // contiguous) or from the update kernel's transposed output PnT[t][c][i]
-        const float* Gt = G + (size_t)t * P * P;
-        const double* ob = obar + (size_t)t * P;
-        const float inv_ns = 1.0f / (float)ns;
+    const int r = threadIdx.x & (NB - 1), i = NB * (1 + blockIdx.x) + r;
+    const float* Gt = G + (size_t)t * P * P;
+    const double* ob = obar + (size_t)t * P;
+    const LbLayout layC{(P + NB - 1) / NB, NB / BK};
+    __nv_bfloat16* Cbt = Cb + (size_t)t * NPC * planeC;
+    const float inv_ns = 1.0f / (float)ns;
+    const float obi = i < P ? (float)ob[i] : 0.f;
 #pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            float v[16];
+    for (int g = 0; g < 8; ++g) {
+        const int c0 = 8 * ((threadIdx.x >> 7) + 2 * g);
+        float v[8];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int e = tid + 256 * (q + 16 * half), c = e >> 6, rr = e & (RT - 1), i = r0 + rr;
-                float x = 0.f;
-                if (i < P && c < nb) x = jb == 0 ? Gt[(size_t)c * P + i] : Pn[((size_t)t * NB + c) * P + i];
-                v[q] = x;
+        for (int u = 0; u < 8; ++u) v[u] = i < P ? Gt[(size_t)(c0 + u) * P + i] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = i < P ? v[u] * inv_ns - obi * (float)ob[c0 + u] : 0.f;
+        store_P8(Cbt, planeC, layC.at(i, c0), v);
+    }
+}
+
+__global__ void __launch_bounds__(192, 2) chol_panel_kernel(const __nv_bfloat16* __restrict__ Cb, size_t planeC,
+                                                            const __nv_bfloat16* __restrict__ Db, int t0, int P,
+                                                            int LD, int jb, float* __restrict__ Lf,
+                                                            __nv_bfloat16* __restrict__ Lb, float* __restrict__ yv,
+                                                            const int* __restrict__ fail, int* status) {
+    using namespace tc;
+    const int t = t0 + blockIdx.y;
+    if (fail[t]) return;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ float yb_s[2][NB];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int i0 = jb + NB * (1 + blockIdx.x);
+    constexpr int nk = NB / BK;
+    const size_t planeD = (size_t)NB * NB;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int st = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (kb >= STAGES && !mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                uint8_t* sb = smem + st * STAGE;
+                mbar_expect_tx(&full[st], STAGE);
+                for (int p = 0; p < NPC; ++p) {
+                    const __nv_bfloat16* pa = Cb + (size_t)(t * NPC + p) * planeC;
+                    const __nv_bfloat16* pb = Db + (size_t)(t * NPC + p) * planeD;
+                    bulk_load(sb + p * BOX, pa + ((size_t)(i0 >> 7) * nk + kb) * (BOX / 2), BOX, &full[st]);
+                    bulk_load(sb + (NPC + p) * BOX, pb + (size_t)kb * (BOX / 2), BOX, &full[st]);
+                }
+                ++issued;
             }
-            if (jb == 0) {
+            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+                mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, nullptr);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const int pa[6] = {0, 0, 1, 0, 1, 2};
+            const int pb[6] = {0, 1, 0, 2, 1, 0};
+            constexpr uint32_t ID = idesc_bf16(128, NB);
+            for (int kb = 0; kb < nk; ++kb) {
+                const int st = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (!mbar_wait(&full[st], ph, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t sa = su32(smem + st * STAGE);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int e = tid + 256 * (q + 16 * half), c = e >> 6, rr = e & (RT - 1), i = r0 + rr;
-                    if (i < P && c < nb) v[q] = v[q] * inv_ns - (float)ob[i] * (float)ob[c];
+                for (int k = 0; k < BK / 16; ++k)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q)
+                        umma(tmem, smem_desc_sw64(sa + pa[q] * BOX + k * 32),
+                             smem_desc_sw64(sa + (NPC + pb[q]) * BOX + k * 32), ID, (kb > 0 || k > 0 || q > 0) ? 1u : 0u);
+                umma_commit(&empty[st]);
+            }
+            umma_commit(done);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        float* yt = yv + (size_t)t * 2 * P;
+        for (int c = threadIdx.x - 64; c < NB; c += 128) {
+            yb_s[0][c] = yt[jb + c];
+            yb_s[1][c] = yt[P + jb + c];
+        }
+        int ok = 0;
+        if (lane == 0) ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        fence_after();
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // yb_s written by the four epilogue warps
+        if (ok) {
+            const int i = i0 + q * 32 + lane;
+            const LbLayout lay{(P + NB - 1) / NB, LD / 32};
+            float* Lft = Lf + (size_t)t * P * LD;
+            __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll 1
+            for (int c0 = 0; c0 < NB; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                if (i >= P) continue;
+#pragma unroll
+                for (int u8 = 0; u8 < 4; ++u8) {
+                    float x8[8];
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) {
+                        x8[w] = __uint_as_float(v[8 * u8 + w]);
+                        s0 = fmaf(x8[w], yb_s[0][c0 + 8 * u8 + w], s0);
+                        s1 = fmaf(x8[w], yb_s[1][c0 + 8 * u8 + w], s1);
+                    }
+                    store_L8(Lft, Lbt, lay, LD, i, jb + c0 + 8 * u8, x8, 8);
                 }
             }
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int e = tid + 256 * (q + 16 * half), c = e >> 6, rr = e & (RT - 1);
-                CT[c * DCT + rr] = v[q];
+            if (i < P) {
+                yt[i] -= s0;
+                yt[P + i] -= s1;
             }
         }
     }
-    if (tid < 2 * NB) {
-        const int h = tid >> 7, c = tid & (NB - 1);
-        yb[h * NB + c] = c < nb ? yt[h * P + jb + c] : 0.f;
-    }
     __syncthreads();
-    const int rg = tid & 15, cg = tid >> 4;
-    float acc[4][8];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc[a][u] = 0.f;
-    const int kend = min(nb, cg * 8 + 8);  // L_dd^-1 is lower triangular
-#pragma unroll 4
-    for (int k = 0; k < kend; ++k) {
-        const float4 cv = *reinterpret_cast<const float4*>(CT + k * DCT + 4 * rg);
-        const float4 l0 = *reinterpret_cast<const float4*>(LT + k * DLT + 8 * cg);
-        const float4 l1 = *reinterpret_cast<const float4*>(LT + k * DLT + 8 * cg + 4);
-        const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
-        const float l8[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[a][u] = fmaf(c4[a], l8[u], acc[a][u]);
-    }
-    const LbLayout lay{(P + NB - 1) / NB, LD / 32};
-    float* Lft = Lf + (size_t)t * P * LD;
-    __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
-    const int nv = nb - cg * 8;
-    float pr[4][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = r0 + 4 * rg + a;
-        if (i < P && nv > 0) store_L8(Lft, Lbt, lay, LD, i, jb + cg * 8, acc[a], nv);
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            s0 = fmaf(acc[a][u], yb[cg * 8 + u], s0);
-            s1 = fmaf(acc[a][u], yb[NB + cg * 8 + u], s1);
-        }
-        pr[a][0] = s0;
-        pr[a][1] = s1;
-    }
-    __syncthreads();   // CT is no longer read
-    float* red = CT;   // [16][RT][2]
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        red[(cg * RT + 4 * rg + a) * 2] = pr[a][0];
-        red[(cg * RT + 4 * rg + a) * 2 + 1] = pr[a][1];
-    }
-    __syncthreads();
-    if (tid < 2 * RT) {
-        const int rr = tid >> 1, h = tid & 1, i = r0 + rr;
-        if (i < P) {
-            float s = 0.f;
-#pragma unroll
-            for (int g = 0; g < 16; ++g) s += red[(g * RT + rr) * 2 + h];
-            yt[h * P + i] -= s;
-        }
+    if (threadIdx.x == 0 && *abort_flag) record_error(status, OTVMC_ERR_TIMEOUT, t);
+    if (warp == 1) {
+        if (lane == 0) mbar_wait(done, 0, nullptr);
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
     }
 }
 
@@ -1162,6 +1261,8 @@ size_t chol_tc_ws_bytes(int ntraj, int P) {
     add((size_t)ntraj * 4 * P * 8);          // x (and the fallback's residual)
     add((size_t)ntraj * 2 * P * 4);          // forward-substitution vector
     add((size_t)ntraj * nblk * nblk * 2 * NB * 8);  // residual slots
+    add((size_t)ntraj * NPC * nblk * NB * NB * 2);  // C of the panel rows, BF16 pieces
+    add((size_t)ntraj * NPC * NB * NB * 2);         // L_dd^-1, BF16 pieces
     return b + 256;
 }
 
@@ -1198,6 +1299,9 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     double* x = (double*)take((size_t)ntraj * 4 * P * 8);
     float* yv = (float*)take((size_t)ntraj * 2 * P * 4);
     double* part = (double*)take((size_t)ntraj * nblk * nblk * 2 * NB * 8);
+    const size_t planeC = LbLayout{NT, NB / BK}.plane();
+    __nv_bfloat16* Cb = (__nv_bfloat16*)take((size_t)ntraj * NPC * planeC * 2);
+    __nv_bfloat16* Db = (__nv_bfloat16*)take((size_t)ntraj * NPC * NB * NB * 2);
 
     const LbLayout lay{NT, LD / 32};
     const size_t plane = lay.plane();
@@ -1206,8 +1310,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     if (e != cudaSuccess) return chol_fail(e, "memset");
     e = cudaFuncSetAttribute(chol_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DIAG_SMEM);
     if (e != cudaSuccess) return chol_fail(e, "diag attribute");
-    e = cudaFuncSetAttribute(chol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TRSM_SMEM);
-    if (e != cudaSuccess) return chol_fail(e, "trsm attribute");
+    e = cudaFuncSetAttribute(chol_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_U);
+    if (e != cudaSuccess) return chol_fail(e, "panel attribute");
     e = cudaFuncSetAttribute(chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_U);
     if (e != cudaSuccess) return chol_fail(e, "update attribute");
     const float feps = (float)eps;
@@ -1234,21 +1338,24 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
                 ProfScope pu(OTVMC_K_CHOLU, gsm);
                 dim3 grid((P - jb + 127) / 128, nt);
                 chol_update_kernel<<<grid, 192, SMEM_U, gsm>>>(Lb, plane, LD / 32, ta, P, ns, jb, feps, G, obar, Pn,
-                                                               fail, status);
+                                                               Cb, planeC, fail, status);
                 count_launch();
             }
             {
                 ProfScope pd(OTVMC_K_CHOLD, gsm);
-                chol_diag_kernel<<<nt, DIAG_THREADS, DIAG_SMEM, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, D, Pn, Lf, Lb, Dv, yv,
-                                                               fail);
+                chol_diag_kernel<<<nt, DIAG_THREADS, DIAG_SMEM, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, D, Pn, Lf, Lb, Dv,
+                                                                       Db, yv, fail);
                 count_launch();
             }
             const int nrows = P - jb - min(NB, P - jb);
             if (nrows > 0) {
                 ProfScope pp(OTVMC_K_CHOLP, gsm);
-                dim3 grid((nrows + RT - 1) / RT, nt);
-                chol_trsm_kernel<<<grid, 256, TRSM_SMEM, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, Pn, Lf, Lb, Dv, yv,
-                                                                fail);
+                dim3 grid((nrows + NB - 1) / NB, nt);
+                if (jb == 0) {
+                    chol_cb0_kernel<<<grid, 256, 0, gsm>>>(ta, P, ns, G, obar, Cb, planeC, fail);
+                    count_launch();
+                }
+                chol_panel_kernel<<<grid, 192, SMEM_U, gsm>>>(Cb, planeC, Db, ta, P, LD, jb, Lf, Lb, yv, fail, status);
                 count_launch();
             }
         }

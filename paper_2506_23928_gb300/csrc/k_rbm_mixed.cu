@@ -7,8 +7,8 @@
 //     Re lc(x + iy) = log |2 cosh(x + iy)| = |x| + log1p(e (2 cos 2y + e)) / 2,  e = exp(-2|x|).
 // Each term carries an error bound: rounding of |x|, of the transcendentals and of
 // t = e (2 cos 2y + e) (amplified by 1 / (1 + t) near a zero of cosh), plus the error of the
-// FP32 angles (at most (N + 2 + 2 m) 2^-24 Gmax after m accepted flips, Gmax the largest
-// |b_m| + sum_i |W_im| per component) times |tanh gamma| (the derivative of Re lc).  When
+// FP32 angles (a per-unit bound summed as the angle is formed and updated: 2^-24 of every
+// rounded parameter and of every rounded sum) times |tanh gamma| (the derivative of Re lc).  When
 // |Re log r_j - log u| is within twice the summed bound the proposal is decided in FP64 from
 // the parameters, so every accept/reject equals the FP64 decision.
 //
@@ -47,40 +47,23 @@ __device__ __forceinline__ double relc_d(double x, double y) {
     return ax + 0.5 * log1p(e * (2.0 * cos(2.0 * y) + e));
 }
 
+// WS: the weights W_jm as float2 in shared memory ([n][M], when they fit), else read from theta.
+// MQ: hidden units per lane (M <= 32 MQ).
+template <bool WS, int MQ>
 __global__ void __launch_bounds__(256) sample_rbm_mixed_kernel(const double2* __restrict__ theta, int P, int n, int M,
                                                                int W, int ns, int n_sweep, uint32_t k0, uint32_t k1,
                                                                uint32_t evtag, int traj0, uint64_t* __restrict__ spins,
                                                                unsigned long long* __restrict__ accepted) {
-    __shared__ float gmax_s;
-    __shared__ float red_s[8];
+    extern __shared__ float2 wsm[];
     const int t = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double2* th = theta + (size_t)t * P;
     const double2* a = th;
     const double2* b = th + n;
     const double2* Wt = th + n + M;
-    // Gmax over the hidden units (per component), for the angle error bound
-    {
-        float g = 0.f;
-        for (int m = threadIdx.x; m < M; m += blockDim.x) {
-            double gx = fabs(b[m].x), gy = fabs(b[m].y);
-            for (int i = 0; i < n; ++i) {
-                gx += fabs(Wt[(size_t)i * M + m].x);
-                gy += fabs(Wt[(size_t)i * M + m].y);
-            }
-            g = fmaxf(g, (float)fmax(gx, gy));
-        }
-        for (int off = 16; off > 0; off >>= 1) g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, off));
-        if (lane == 0) red_s[warp] = g;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float mx = 0.f;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red_s[w]);
-            gmax_s = mx * 1.0001f + 1e-30f;
-        }
-        __syncthreads();
-    }
-    const float gmax = gmax_s;
+    if (WS)
+        for (int e = threadIdx.x; e < n * M; e += blockDim.x) wsm[e] = make_float2((float)Wt[e].x, (float)Wt[e].y);
+    if (WS) __syncthreads();
     const int chain = blockIdx.x * (blockDim.x >> 5) + warp;
     if (chain >= ns) return;
     uint64_t* sp = spins + ((size_t)t * ns + chain) * W;
@@ -92,22 +75,36 @@ __global__ void __launch_bounds__(256) sample_rbm_mixed_kernel(const double2* __
         const uint64_t v = w == 0 ? wd[0] : w == 1 ? wd[1] : w == 2 ? wd[2] : wd[3];
         return ((v >> (i & 63)) & 1ull) ? 1.f : -1.f;
     };
-    float gx[RBM_MQ], gy[RBM_MQ], l0[RBM_MQ];
+    // angles, and Re lc with its error bound and |tanh| at the current angles (kept across
+    // proposals, replaced on acceptance by the values of the accepted angles).  eb bounds the
+    // error of either FP32 angle component against the exact angle: the rounding of b and of
+    // every W_im taken (2^-24 of each), of every FP32 sum formed (2^-24 of the result), summed
+    // as they happen.
+    constexpr float U = 5.9604645e-8f * 1.001f;  // 2^-24, rounded up
+    float gx[MQ], gy[MQ], l0[MQ], e0[MQ], d0[MQ], eb[MQ];
 #pragma unroll
-    for (int q = 0; q < RBM_MQ; ++q) {
+    for (int q = 0; q < MQ; ++q) {
         const int m = lane + 32 * q;
-        gx[q] = gy[q] = l0[q] = 0.f;
+        gx[q] = gy[q] = l0[q] = e0[q] = d0[q] = eb[q] = 0.f;
         if (m < M) {
             float zx = (float)b[m].x, zy = (float)b[m].y;
+            float ex = U * fabsf(zx), ey = U * fabsf(zy);
             for (int i = 0; i < n; ++i) {
                 const float si = spin(i);
                 const double2 w = Wt[(size_t)i * M + m];
-                zx = fmaf((float)w.x, si, zx);
-                zy = fmaf((float)w.y, si, zy);
+                const float wx = (float)w.x, wy = (float)w.y;
+                zx = fmaf(wx, si, zx);
+                zy = fmaf(wy, si, zy);
+                ex += U * (fabsf(zx) + fabsf(wx));
+                ey += U * (fabsf(zy) + fabsf(wy));
             }
             gx[q] = zx;
             gy[q] = zy;
-            l0[q] = relc_f(zx, zy).v;
+            eb[q] = fmaxf(ex, ey) * 1.001f;
+            const RelcF r0 = relc_f(zx, zy);
+            l0[q] = r0.v;
+            e0[q] = r0.err;
+            d0[q] = r0.dtn;
         }
     }
     const int nprop = n_sweep * n;
@@ -119,26 +116,37 @@ __global__ void __launch_bounds__(256) sample_rbm_mixed_kernel(const double2* __
         const uint32_t wu = (p & 1) ? draw.w : draw.y;
         const int j = (int)(((unsigned long long)wsite * (unsigned long long)n) >> 32);
         const float sj = spin(j);
-        const float eg = 5.9604645e-8f * (float)(n + 2 + 2 * nacc) * gmax;  // angle error bound
         float s = 0.f, err = 0.f;
-        float wjx[RBM_MQ], wjy[RBM_MQ], l1[RBM_MQ];
+        float nx[MQ], ny[MQ], l1[MQ], e1[MQ], d1[MQ], eb1[MQ];
 #pragma unroll
-        for (int q = 0; q < RBM_MQ; ++q) {
+        for (int q = 0; q < MQ; ++q) {
             const int m = lane + 32 * q;
-            wjx[q] = wjy[q] = l1[q] = 0.f;
+            nx[q] = gx[q];
+            ny[q] = gy[q];
+            l1[q] = e1[q] = d1[q] = eb1[q] = 0.f;
             if (m < M) {
-                const double2 w = Wt[(size_t)j * M + m];
-                wjx[q] = (float)w.x;
-                wjy[q] = (float)w.y;
-                const RelcF r1 = relc_f(gx[q] - 2.f * wjx[q] * sj, gy[q] - 2.f * wjy[q] * sj);
-                const RelcF r0 = relc_f(gx[q], gy[q]);
+                float2 w;
+                if (WS) {
+                    w = wsm[j * M + m];
+                } else {
+                    const double2 wd2 = Wt[(size_t)j * M + m];
+                    w = make_float2((float)wd2.x, (float)wd2.y);
+                }
+                // the angles after the flip: -2 s_j w is exact, so one rounding of the sum,
+                // plus the rounding of W_jm to FP32 (twice, through the factor 2)
+                nx[q] = fmaf(-2.f * sj, w.x, gx[q]);
+                ny[q] = fmaf(-2.f * sj, w.y, gy[q]);
+                eb1[q] = eb[q] + U * (fmaxf(fabsf(nx[q]), fabsf(ny[q])) + 2.f * fmaxf(fabsf(w.x), fabsf(w.y)));
+                const RelcF r1 = relc_f(nx[q], ny[q]);
                 l1[q] = r1.v;
+                e1[q] = r1.err;
+                d1[q] = r1.dtn;
                 const float term = r1.v - l0[q];
                 s += term;
                 // evaluation and angle errors, plus the rounding of the term and of the
-                // summation (at most RBM_MQ + 6 roundings on the way to the total)
-                err += r1.err + r0.err + 2.f * eg * (r1.dtn + r0.dtn) +
-                       5.9604645e-8f * (float)(RBM_MQ + 6) * (fabsf(term) + fabsf(r1.v) + fabsf(l0[q]));
+                // summation (at most MQ + 6 roundings on the way to the total)
+                err += r1.err + e0[q] + 2.f * (eb1[q] * r1.dtn + eb[q] * d0[q]) +
+                       5.9604645e-8f * (float)(MQ + 6) * (fabsf(term) + fabsf(r1.v) + fabsf(l0[q]));
             }
         }
 #pragma unroll
@@ -164,7 +172,7 @@ __global__ void __launch_bounds__(256) sample_rbm_mixed_kernel(const double2* __
         } else {
             // FP64 from the parameters
             double s64 = 0.0;
-            for (int q = 0; q < RBM_MQ; ++q) {
+            for (int q = 0; q < MQ; ++q) {
                 const int m = lane + 32 * q;
                 if (m < M) {
                     double zx = b[m].x, zy = b[m].y;
@@ -184,10 +192,13 @@ __global__ void __launch_bounds__(256) sample_rbm_mixed_kernel(const double2* __
         }
         if (acc) {
 #pragma unroll
-            for (int q = 0; q < RBM_MQ; ++q) {
-                gx[q] -= 2.f * wjx[q] * sj;
-                gy[q] -= 2.f * wjy[q] * sj;
+            for (int q = 0; q < MQ; ++q) {
+                gx[q] = nx[q];
+                gy[q] = ny[q];
                 l0[q] = l1[q];
+                e0[q] = e1[q];
+                d0[q] = d1[q];
+                eb[q] = eb1[q];
             }
             const uint64_t bit = 1ull << (j & 63);
             const int w = j >> 6;
@@ -209,9 +220,20 @@ cudaError_t launch_sample_rbm_mixed(const otvmc_ansatz* an, const double2* theta
     if (an->m > 32 * RBM_MQ) return cudaErrorInvalidValue;
     const int n = an->n, W = (n + 63) / 64;
     const uint32_t evtag = (TAG_SAMPLE << 28) | ((uint32_t)eval & 0x0FFFFFFFu);
-    dim3 grid((ns + 7) / 8, ntraj);
-    sample_rbm_mixed_kernel<<<grid, 256, 0, s>>>(theta, (int)an->P, n, an->m, W, ns, n_sweep, (uint32_t)seed,
-                                                 (uint32_t)(seed >> 32), evtag, traj0, spins, accepted);
+    const size_t wbytes = (size_t)n * an->m * sizeof(float2);
+    const bool ws = wbytes <= 64 * 1024, small = an->m <= 128;
+    // eight chains per CTA with four hidden units per lane; four with eight (more registers)
+    const int cpb = small ? 8 : 4;
+    dim3 grid((ns + cpb - 1) / cpb, ntraj);
+    auto kern = ws ? (small ? sample_rbm_mixed_kernel<true, 4> : sample_rbm_mixed_kernel<true, RBM_MQ>)
+                   : (small ? sample_rbm_mixed_kernel<false, 4> : sample_rbm_mixed_kernel<false, RBM_MQ>);
+    const size_t smem = ws ? wbytes : 0;
+    if (ws) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, 32 * cpb, smem, s>>>(theta, (int)an->P, n, an->m, W, ns, n_sweep, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                 evtag, traj0, spins, accepted);
     count_launch();
     return cudaGetLastError();
 }

@@ -57,6 +57,9 @@ class RbmCase:
 @pytest.mark.parametrize("n,m,ns,scale", [(6, 4, 150, 0.3), (9, 7, 64, 0.3), (70, 3, 40, 0.3),
                                           (64, 128, 48, 0.05),   # the chain64_rbm shape (FP32 warp sampler)
                                           (12, 40, 200, 1.0),    # large parameters: many decisions near the band
+                                          (9, 200, 40, 0.1),     # 8 hidden units per lane, W in shared memory
+                                          (200, 100, 24, 0.05),  # 4 per lane, W (160 KB) read from theta
+                                          (256, 256, 16, 0.02),  # the square16_rbm shape
                                           (4, 300, 64, 0.2)])    # M > 256: the FP64 sampler
 def test_rbm_sample_bit_exact(n, m, ns, scale):
     """Every accept/reject equals the FP64 decision (FP32 sampler with its error bound and
@@ -66,7 +69,10 @@ def test_rbm_sample_bit_exact(n, m, ns, scale):
     th, th_d = c.theta(1, T, scale)
     sig, sp = c.spins(2, T, ns)
     acc = torch.zeros(T, dtype=torch.int64, device="cuda")
-    work, nb = c.work(T, ns)
+    # the sampler's own scratch (the FP64 sampler's angles and Re lc), not the all-stage size,
+    # which for the 16 x 16 shape holds the FP64 S of P = 66048 parameters
+    nb = T * m * ns * 24 + 4096
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     check(abi.otvmc_sample(c.ans.handle, th_d, T, traj0, ns, sweeps, seed, ev, sp, acc, work, nb))
     check(abi.otvmc_check(work))
     got = unpack(sp, n)
