@@ -96,6 +96,7 @@ EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.vinfo = c.take<double>((size_t)T * 4);
     b.qsum = c.take<long long>((size_t)T * 2);
     b.Epm = c.take<double2>((size_t)T * 2 * n * n);
+    b.rtab = a->kind == OTVMC_RBM ? (float4*)c.take<char>(rbm_tab_bytes(a, T)) : nullptr;
     b.part_obs = c.take<double>((size_t)T * (nblk > (size_t)obs_blocks(n, ns) ? nblk : obs_blocks(n, ns)) * 9);
     b.dsum = c.take<long long>((size_t)T * a->P * 3);
     return b;
@@ -121,10 +122,10 @@ static otvmc_status rbm_precision(const otvmc_ansatz* a, int precision) {
 // RBM sampling: the FP32 warp-per-chain sampler (its decisions equal the FP64 ones) when the
 // hidden layer fits it, else the FP64 thread-per-chain sampler with its scratch.
 static cudaError_t sample_rbm_any(const otvmc_ansatz* a, const double2* theta, int T, int traj0, int ns, int n_sweep,
-                                  uint64_t seed, int64_t ev, uint64_t* spins, double2* gam, double* lcr,
+                                  uint64_t seed, int64_t ev, uint64_t* spins, double2* gam, double* lcr, float4* tab,
                                   unsigned long long* accepted, cudaStream_t s) {
     if (a->m <= RBM_MIXED_MAX_M)
-        return launch_sample_rbm_mixed(a, theta, T, traj0, ns, n_sweep, seed, ev, spins, accepted, s);
+        return launch_sample_rbm_mixed(a, theta, T, traj0, ns, n_sweep, seed, ev, tab, spins, accepted, s);
     return launch_sample_rbm(a, theta, T, traj0, ns, n_sweep, seed, ev, spins, gam, lcr, accepted, s);
 }
 
@@ -417,9 +418,10 @@ otvmc_status otvmc_sample(const otvmc_ansatz* a, const double* theta_d, int ntra
         Carver c(work_d, work_bytes);
         double2* gam = c.take<double2>((size_t)ntraj * a->m * ns);
         double* lcr = c.take<double>((size_t)ntraj * a->m * ns);
+        float4* tab = (float4*)c.take<char>(rbm_tab_bytes(a, ntraj));
         if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
         CK(sample_rbm_any(a, (const double2*)theta_d, ntraj, traj0, ns, n_sweep, seed, eval_index, spins_d, gam, lcr,
-                             (unsigned long long*)accepted_d, (cudaStream_t)stream),
+                             tab, (unsigned long long*)accepted_d, (cudaStream_t)stream),
            "sample launch");
         return OTVMC_OK;
     }
@@ -692,6 +694,7 @@ struct RunBufs {
     void* chol;
     double2* gam;  // RBM sampler scratch
     double* lcr;
+    float4* tab;   // RBM flip table of the FP32 sampler
     void* rbm;     // RBM build scratch
     EvalBufs eb;
 };
@@ -712,6 +715,7 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
     r.D = c.take<double2>(T * P);
     r.gam = nullptr;
     r.lcr = nullptr;
+    r.tab = nullptr;
     r.rbm = nullptr;
     if (a->kind == OTVMC_RBM) {
         r.S = nullptr;
@@ -719,6 +723,7 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
         r.obuf = nullptr;
         r.gam = c.take<double2>((size_t)T * a->m * ns);
         r.lcr = c.take<double>((size_t)T * a->m * ns);
+        r.tab = (float4*)c.take<char>(rbm_tab_bytes(a, T));
         if (d->precision == OTVMC_PREC_MIXED) {
             r.rbm = c.take<char>(rbm_mixed_bytes(a, T, ns));
             r.chol = nullptr;
@@ -786,7 +791,7 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     const int T = d->ntraj, ns = d->ns;
     const bool fp32 = d->precision == OTVMC_PREC_MIXED;
     if (a->kind == OTVMC_RBM) {
-        CK(sample_rbm_any(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, r.gam, r.lcr, nullptr, s),
+        CK(sample_rbm_any(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, r.gam, r.lcr, r.tab, nullptr, s),
            "sample launch");
         otvmc_status st =
             run_estimators(a, theta, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s);
@@ -854,7 +859,7 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
         const int64_t ev = 2 * (d->step0 + d->n_steps);
         const bool rbm = a->kind == OTVMC_RBM;
         if (rbm)
-            CK(sample_rbm_any(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, r.gam, r.lcr, nullptr,
+            CK(sample_rbm_any(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, r.gam, r.lcr, r.tab, nullptr,
                                  s),
                "sample launch");
         else

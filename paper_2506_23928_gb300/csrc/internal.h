@@ -106,6 +106,7 @@ struct EvalBufs {
     double2* Epm;        // [T][2][n][n] exp(+-4 eta) for observables
     double* part_obs;    // [T][obs_blocks][9]
     long long* dsum;     // [T][P][3] exact sums behind D and obar
+    float4* rtab;        // RBM only: the mixed kernels' FP32 tables (rbm_tab_bytes)
 };
 
 size_t eval_bufs_bytes(const otvmc_ansatz* a, int ntraj, int ns);
@@ -155,7 +156,7 @@ cudaError_t launch_obs_rbm(const otvmc_ansatz* a, const double2* theta, const ui
 // RBM, FP32 sampling (decisions equal to FP64) and estimators (k_rbm_mixed.cu); M <= 256
 constexpr int RBM_MIXED_MAX_M = 256;
 cudaError_t launch_sample_rbm_mixed(const otvmc_ansatz* an, const double2* theta, int ntraj, int traj0, int ns,
-                                    int n_sweep, uint64_t seed, int64_t eval, uint64_t* spins,
+                                    int n_sweep, uint64_t seed, int64_t eval, float4* tab, uint64_t* spins,
                                     unsigned long long* accepted, cudaStream_t s);
 cudaError_t launch_est_rbm_mixed(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int ntraj,
                                  int ns, const EvalBufs& b, cudaStream_t s);
@@ -181,8 +182,15 @@ size_t rbm_factored_bytes(const otvmc_ansatz* a, int ntraj, int ns);
 cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
                                             const double2* v, const double* vinfo, int T, int ns, double eps,
                                             void* ws, double2* delta, int* status, cudaStream_t s);
+// FP32 tables of the mixed RBM kernels, one buffer: flip factors [T][N][M] and [T][M][N]
+// float4, then W [T][N][M] float2, then a [T][N] float2 (k_rbm_mixed.cu: rbm_flip_table_kernel)
+inline size_t rbm_tab_bytes(const otvmc_ansatz* a, int ntraj) {
+    return (size_t)ntraj * ((size_t)a->n * a->m * 40 + (size_t)a->n * 8) + 256;
+}
+// scratch of RBM sampling: the FP64 sampler's angles and Re lc [T][M][ns], then the FP32
+// sampler's tables
 inline size_t rbm_sample_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
-    return (size_t)ntraj * a->m * ns * (16 + 8) + 512;
+    return (size_t)ntraj * a->m * ns * (16 + 8) + rbm_tab_bytes(a, ntraj) + 1024;
 }
 
 // SNR-filtered eigen pseudo-inverse (one CTA per trajectory, P <= SNR_PMAX)

@@ -69,9 +69,10 @@ def test_rbm_sample_bit_exact(n, m, ns, scale):
     th, th_d = c.theta(1, T, scale)
     sig, sp = c.spins(2, T, ns)
     acc = torch.zeros(T, dtype=torch.int64, device="cuda")
-    # the sampler's own scratch (the FP64 sampler's angles and Re lc), not the all-stage size,
-    # which for the 16 x 16 shape holds the FP64 S of P = 66048 parameters
-    nb = T * m * ns * 24 + 4096
+    # the sampler's own scratch (the FP64 sampler's angles and Re lc, the FP32 sampler's tables
+    # of flip factors, W and a), not the all-stage size, which for the 16 x 16 shape holds the
+    # FP64 S of P = 66048
+    nb = T * m * ns * 24 + T * n * (40 * m + 8) + 65536
     work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     check(abi.otvmc_sample(c.ans.handle, th_d, T, traj0, ns, sweeps, seed, ev, sp, acc, work, nb))
     check(abi.otvmc_check(work))
