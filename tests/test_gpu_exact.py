@@ -1,0 +1,93 @@
+"""Whole GPU trajectories against exact results that do not come from the oracle's tVMC:
+the exact Jastrow state of the unitary Ising chain (eta = -i t J), the closed form of App. D
+for the dissipative chain at h = 0 (any N, periodic), and the exact Lindblad solution of the
+8-spin benchmark workload (Eq. 1).  Ensemble observables are compared within three standard
+errors (plus 1e-3 for the O(1/N_s) bias of the estimated <L + L^+>) at times where the
+Jastrow ansatz still represents the state; beyond them the variational error of the ansatz
+dominates (the oracle's enumeration tVMC, which has no sampling error, shows the same
+drift), so those times are not a test of the implementation."""
+import numpy as np
+import pytest
+
+from gpu_helpers import Case, require_gpu, from_dev_complex, torch
+import synth
+from oracle import fossfeig, lindblad
+from oracle.model import dense_hamiltonian, dense_jump_ops, coherent_x_state
+from oracle.observables import ensemble, moments_from_rho
+from paper_2506_23928_gb300 import abi
+from paper_2506_23928_gb300.abi import check
+
+pytestmark = pytest.mark.gpu
+FP64, MIXED = abi.OTVMC_PREC_FP64, abi.OTVMC_PREC_MIXED
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _run(c, T, ns, steps, dt, seed, precision, every):
+    desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=abi.OTVMC_HEUN,
+                       precision=precision, reg=abi.OTVMC_REG_SHIFT, eps=1e-4, snr_thresh=4.0, seed=seed,
+                       measure_every=every, measure_final=1, use_graph=0)
+    nm = abi.otvmc_run_n_meas(desc)
+    theta = torch.zeros((T, c.P, 2), dtype=torch.float64, device="cuda")
+    spins = torch.zeros((T, ns, c.W), dtype=torch.int64, device="cuda")
+    check(abi.otvmc_init_chains(c.ans.handle, T, 0, ns, seed, spins))
+    nb = abi.otvmc_run_workspace_bytes(c.ans.handle, desc)
+    assert nb > 0
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    mom = torch.zeros((nm, T, 9), dtype=torch.float64, device="cuda")
+    check(abi.otvmc_run_trajectories(c.ans.handle, desc, theta, spins, mom, work, nb))
+    check(abi.otvmc_check(work))
+    return from_dev_complex(theta)[..., 0], mom.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+@pytest.mark.parametrize("n", [16, 32])
+def test_unitary_ising_is_exact_jastrow(n, precision):
+    """h = 0 and no dissipation: exp(-i t H) of the coherent state is the Jastrow state
+    eta_jk = -i t J_jk, a = 0.  After t = 1 (100 Heun steps) the parameters stay within the
+    sampling error of 4096 samples of it, and every trajectory's <sigma^x> matches
+    prod_k cos(2 J_jk t) (the same for every site of the ring)."""
+    c = Case((n,), alpha=1.5, h=0.0, kappa=0.0, gamma=0.0, pbc=True)
+    steps, dt = 100, 0.01
+    th, mom = _run(c, 4, 4096, steps, dt, 5, precision, 0)
+    iu = np.triu_indices(n, 1)
+    eta_exact = -1j * steps * dt * c.J[iu]
+    assert np.abs(th[:, n:] - eta_exact[None, :]).max() < 3e-4
+    assert np.abs(th[:, :n]).max() < 1e-5
+    mx_exact = np.prod(np.cos(2 * steps * dt * c.J[0, 1:]))
+    assert np.abs(mom[-1, :, 0] - mx_exact).max() < 0.01
+
+
+def test_decay_ring_matches_closed_form():
+    """h = 0 ring of 16 spins with decay (kappa = 0.1, alpha = 1.5): the ensemble of 256
+    trajectories against App. D's closed form at t = 0.1, 0.2, 0.3, and M_z = e^{-kappa t} - 1."""
+    n, kappa, alpha = 16, 0.1, 1.5
+    c = Case((n,), alpha=alpha, h=0.0, kappa=kappa, gamma=0.0, pbc=True)
+    Jd = fossfeig.ring_couplings(n, 1.0, alpha, kac=False)
+    steps, every, dt = 30, 10, 0.01
+    _, mom = _run(c, 256, 1024, steps, dt, 5, MIXED, every)
+    for i in range(1, mom.shape[0]):
+        t = min(i * every, steps) * dt
+        Mf, _ = fossfeig.fossfeig(Jd, kappa, t)
+        assert abs(Mf[2] - (np.exp(-kappa * t) - 1)) < 1e-12
+        M, _, dM = ensemble(mom[i, :, :3], np.zeros((mom.shape[1], 3, 3)))
+        assert np.all(np.abs(M - Mf) <= 3 * dM + 1e-3), (t, M, Mf, dM)
+
+
+def test_chain8_workload_matches_exact_lindblad():
+    """The 8-spin benchmark workload (h = 1, decay 0.1, open chain, Heun, dt = 0.01, 1024
+    samples) with 512 trajectories against the exact 256 x 256 density matrix of Eq. 1 at
+    t = 0.1, 0.2, 0.3."""
+    w = synth.WORKLOADS["chain8_jastrow"]
+    c = Case(w.extent, alpha=w.alpha, h=w.h, kappa=w.kappa, gamma=w.gamma)
+    steps, every = 30, 10
+    _, mom = _run(c, 512, w.ns, steps, w.dt, 11, MIXED, every)
+    psi = coherent_x_state(w.n)
+    _, recs = lindblad.evolve(np.outer(psi, psi.conj()), dense_hamiltonian(c.omodel), dense_jump_ops(c.omodel),
+                              steps * w.dt, w.dt, observe=lambda r: moments_from_rho(r, w.n)[0], every=every)
+    for i in range(1, mom.shape[0]):
+        M, _, dM = ensemble(mom[i, :, :3], np.zeros((mom.shape[1], 3, 3)))
+        assert np.all(np.abs(M - recs[i]) <= 3 * dM + 1e-3), (i, M, recs[i], dM)
