@@ -89,9 +89,18 @@ __global__ void __launch_bounds__(256) est1_jastrow_kernel(
         sw[i] = (s < ns) ? spins[((size_t)t * ns + s) * W + w] : 0ull;
     }
 
+    // Real and J fields: exact int64 on the FP64 path, FP32 sums on the mixed path (staged as
+    // FP32 in the same shared-memory rows).  The imaginary field stays exact int64 on both, for
+    // the phase reduction modulo 2 pi.
     long long ar[SPT], ai[SPT], aj[SPT];
+    float arf[SPT], ajf[SPT];
 #pragma unroll
-    for (int q = 0; q < SPT; ++q) ar[q] = ai[q] = aj[q] = 0;
+    for (int q = 0; q < SPT; ++q) {
+        ar[q] = ai[q] = aj[q] = 0;
+        arf[q] = ajf[q] = 0.f;
+    }
+    float* qr_f = reinterpret_cast<float*>(qr_s);
+    float* qj_f = reinterpret_cast<float*>(qj_s);
 
     const long long* QrT = Qre + (size_t)t * n * n;
     const long long* QiT = Qim + (size_t)t * n * n;
@@ -99,9 +108,14 @@ __global__ void __launch_bounds__(256) est1_jastrow_kernel(
         __syncthreads();
         const int rows = min(EST_KC, n - kc);
         for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
-            qr_s[i] = QrT[(size_t)kc * n + i];
             qi_s[i] = QiT[(size_t)kc * n + i];
-            qj_s[i] = QJ[(size_t)kc * n + i];
+            if constexpr (FP32T) {
+                qr_f[i] = fx_to_float(QrT[(size_t)kc * n + i]);
+                qj_f[i] = fx_to_float(QJ[(size_t)kc * n + i]);
+            } else {
+                qr_s[i] = QrT[(size_t)kc * n + i];
+                qj_s[i] = QJ[(size_t)kc * n + i];
+            }
         }
         __syncthreads();
         if (active) {
@@ -109,13 +123,26 @@ __global__ void __launch_bounds__(256) est1_jastrow_kernel(
 #pragma unroll
             for (int q = 0; q < SPT; ++q) wq[q] = sw[(g + q * SPP) * W + (kc >> 6)] >> (kc & 63);
             for (int kk = 0; kk < rows; ++kk) {
-                const long long vr = qr_s[kk * n + j], vi = qi_s[kk * n + j], vj = qj_s[kk * n + j];
+                const long long vi = qi_s[kk * n + j];
+                if constexpr (FP32T) {
+                    const float vr = qr_f[kk * n + j], vj = qj_f[kk * n + j];
 #pragma unroll
-                for (int q = 0; q < SPT; ++q) {
-                    if ((wq[q] >> kk) & 1ull) {
-                        ar[q] += vr;
-                        ai[q] += vi;
-                        aj[q] += vj;
+                    for (int q = 0; q < SPT; ++q) {
+                        if ((wq[q] >> kk) & 1ull) {
+                            arf[q] += vr;
+                            ai[q] += vi;
+                            ajf[q] += vj;
+                        }
+                    }
+                } else {
+                    const long long vr = qr_s[kk * n + j], vj = qj_s[kk * n + j];
+#pragma unroll
+                    for (int q = 0; q < SPT; ++q) {
+                        if ((wq[q] >> kk) & 1ull) {
+                            ar[q] += vr;
+                            ai[q] += vi;
+                            aj[q] += vj;
+                        }
                     }
                 }
             }
@@ -132,21 +159,21 @@ __global__ void __launch_bounds__(256) est1_jastrow_kernel(
         float2* rf = reinterpret_cast<float2*>(r_out);
         float2 prf = make_float2(0.f, 0.f), psrf = make_float2(0.f, 0.f);
         int psi = 0;
+        const float bre = active ? fx_to_float(base_re[(size_t)t * n + j]) : 0.f;
+        const float bj = active ? fx_to_float(baseJ[j]) : 0.f;
 #pragma unroll
         for (int q = 0; q < SPT; ++q) {
             const int sl = g + q * SPP;
             const int s = s0 + sl;
-            float hrx = 0.f, hry = 0.f;
-            long long isg = 0;
+            float hrx = 0.f, hry = 0.f, fsg = 0.f;
             if (active && s < ns) {
                 const bool up = (sw[sl * W + (j >> 6)] >> (j & 63)) & 1ull;
-                const long long fre = base_re[(size_t)t * n + j] + 2 * ar[q];
+                const float fre = fmaf(2.f, arf[q], bre);
                 const long long fim = base_im[(size_t)t * n + j] + 2 * ai[q];
-                const long long fj = baseJ[j] + 2 * aj[q];
+                const float fj = fmaf(2.f, ajf[q], bj);
                 // log r_j = -2 sigma_j f_j
-                const long long lre = up ? -2 * fre : 2 * fre;
                 const long long lim = up ? -2 * fim : 2 * fim;
-                const float e = expf(fx_to_float(lre));
+                const float e = expf(up ? -2.f * fre : 2.f * fre);
                 const int kq = __float2int_rn(fx_to_float(lim) * 0.15915494309189535f);
                 const long long red = lim - (long long)kq * FX_TWO_PI;
                 float sn, cs;
@@ -155,7 +182,7 @@ __global__ void __launch_bounds__(256) est1_jastrow_kernel(
                 rf[((size_t)t * ns + s) * n + j] = r;
                 hrx = r.x;
                 hry = r.y;
-                isg = (up ? fj : -fj) >> 8;  // sigma_j f^J_j in units of 2^-40 (no overflow for n <= 256)
+                fsg = up ? fj : -fj;  // sigma_j f^J_j
                 prf.x += r.x;
                 prf.y += r.y;
                 psrf.x += up ? r.x : -r.x;
@@ -166,11 +193,10 @@ __global__ void __launch_bounds__(256) est1_jastrow_kernel(
             for (int off = 16; off > 0; off >>= 1) {
                 hrx += __shfl_xor_sync(0xffffffffu, hrx, off);
                 hry += __shfl_xor_sync(0xffffffffu, hry, off);
-                isg += __shfl_xor_sync(0xffffffffu, isg, off);
+                fsg += __shfl_xor_sync(0xffffffffu, fsg, off);
             }
             if (lane == 0 && g < SPP)
-                ered[sl * (NT / 32) + wis] =
-                    make_double2(0.5 * (double)isg * 0x1.0p-40 + h * (double)hrx, h * (double)hry);
+                ered[sl * (NT / 32) + wis] = make_double2(0.5 * (double)fsg + h * (double)hrx, h * (double)hry);
         }
         pr = make_double2((double)prf.x, (double)prf.y);
         psr = make_double2((double)psrf.x, (double)psrf.y);
