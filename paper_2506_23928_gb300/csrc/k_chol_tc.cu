@@ -347,7 +347,10 @@ constexpr int HB = 64;                      // half block
 constexpr int T4 = HB / 4;                  // 16 tile rows of a half block
 constexpr int NTRI4 = T4 * (T4 + 1) / 2;    // 136 lower 4 x 4 tiles
 constexpr int DSD = NB + 4;                 // shared row of the 128-wide block (16-byte aligned)
-constexpr int DIAG_SMEM = (2 * NB * DSD + 4 * HB + 2 * NB) * (int)sizeof(float) + 16;
+constexpr int DSX = HB + 4;                 // shared row of a 64-wide quarter of the inverse
+// The inverse is kept as its three nonzero 64 x 64 quarters X11, X21, X22 (X12 = 0), so that the
+// kernel's ~119 KB of shared memory leaves room for an update-kernel CTA on the same SM.
+constexpr int DIAG_SMEM = (NB * DSD + 3 * HB * DSX + 4 * HB + 2 * NB) * (int)sizeof(float) + 16;
 
 __device__ __forceinline__ void tri_index(int q, int& bi, int& bj) {
     int b = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
@@ -357,9 +360,9 @@ __device__ __forceinline__ void tri_index(int q, int& bi, int& bj) {
     bj = q - b * (b + 1) / 2;
 }
 
-// Factor the 64 x 64 lower block at A (row stride DSD) in place into L and write its inverse
-// into X (lower, zeros above the diagonal).  Returns false (uniformly) on a bad pivot.
-__device__ bool factor64(float* A, float* X, float* cbuf, float* rbuf) {
+// Factor the 64 x 64 lower block at A (row stride lda) in place into L and write its inverse
+// into X (row stride ldx; lower, zeros above the diagonal).  Returns false (uniformly) on a bad pivot.
+__device__ bool factor64(float* A, int lda, float* X, int ldx, float* cbuf, float* rbuf) {
     const int tid = threadIdx.x;
     const bool isA = tid < NTRI4, isX = tid >= NTRI4 && tid < 2 * NTRI4;
     int bi = 0, bj = 0;
@@ -369,7 +372,7 @@ __device__ bool factor64(float* A, float* X, float* cbuf, float* rbuf) {
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) a[r][c] = A[(bi * 4 + r) * DSD + bj * 4 + c];
+            for (int c = 0; c < 4; ++c) a[r][c] = A[(bi * 4 + r) * lda + bj * 4 + c];
     } else {
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -433,13 +436,14 @@ __device__ bool factor64(float* A, float* X, float* cbuf, float* rbuf) {
     __syncthreads();
     if (isA || isX) {
         float* dst = isA ? A : X;
+        const int ld = isA ? lda : ldx;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) dst[(bi * 4 + r) * DSD + bj * 4 + c] = (bi == bj && c > r) ? 0.f : a[r][c];
+            for (int c = 0; c < 4; ++c) dst[(bi * 4 + r) * ld + bj * 4 + c] = (bi == bj && c > r) ? 0.f : a[r][c];
             if (bi != bj) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) dst[(bj * 4 + r) * DSD + bi * 4 + c] = 0.f;  // upper tile
+                for (int c = 0; c < 4; ++c) dst[(bj * 4 + r) * ld + bi * 4 + c] = 0.f;  // upper tile
             }
         }
     }
@@ -447,10 +451,10 @@ __device__ bool factor64(float* A, float* X, float* cbuf, float* rbuf) {
     return ok;
 }
 
-// 64 x 64 x 64 products on shared-memory operands (row stride DSD), threads 0..255; thread
+// 64 x 64 x 64 products on shared-memory operands (row strides lda, ldb), threads 0..255; thread
 // (ti, tj) = (tid / 16, tid % 16).
 // NT: out[i][j] = sum_k A[i][k] B[j][k]; rows ti + 16 a, columns tj + 16 b.
-__device__ __forceinline__ void gemm64_nt(const float* A, const float* B, float (&acc)[4][4]) {
+__device__ __forceinline__ void gemm64_nt(const float* A, int lda, const float* B, int ldb, float (&acc)[4][4]) {
     const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -460,9 +464,9 @@ __device__ __forceinline__ void gemm64_nt(const float* A, const float* B, float 
     for (int k = 0; k < HB; k += 4) {
         float4 av[4], bv[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (ti + 16 * a) * DSD + k);
+        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (ti + 16 * a) * lda + k);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = ld4(B + (tj + 16 * b) * DSD + k);
+        for (int b = 0; b < 4; ++b) bv[b] = ld4(B + (tj + 16 * b) * ldb + k);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -470,7 +474,7 @@ __device__ __forceinline__ void gemm64_nt(const float* A, const float* B, float 
     }
 }
 // NN: out[i][j] = sum_k A[i][k] B[k][j]; rows ti + 16 a, columns 4 tj .. 4 tj + 3.
-__device__ __forceinline__ void gemm64_nn(const float* A, const float* B, float (&acc)[4][4]) {
+__device__ __forceinline__ void gemm64_nn(const float* A, int lda, const float* B, int ldb, float (&acc)[4][4]) {
     const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -480,10 +484,10 @@ __device__ __forceinline__ void gemm64_nn(const float* A, const float* B, float 
     for (int k = 0; k < HB; k += 4) {
         float4 av[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (ti + 16 * a) * DSD + k);
+        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (ti + 16 * a) * lda + k);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-            const float4 bv = ld4(B + (k + kk) * DSD + 4 * tj);
+            const float4 bv = ld4(B + (k + kk) * ldb + 4 * tj);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const float x = kk == 0 ? av[a].x : kk == 1 ? av[a].y : kk == 2 ? av[a].z : av[a].w;
@@ -509,8 +513,15 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     if (fail[t]) return;
     extern __shared__ __align__(16) float dsm[];
     float* A = dsm;                 // [NB][DSD] the block, becoming L (lower); upper-right quarter scratch
-    float* X = A + NB * DSD;        // [NB][DSD] the inverse (lower, zeros above)
-    float* cbuf = X + NB * DSD;     // [2][HB]
+    float* X11 = A + NB * DSD;      // [HB][DSX] quarters of the inverse (lower)
+    float* X21 = X11 + HB * DSX;    // [HB][DSX]
+    float* X22 = X21 + HB * DSX;    // [HB][DSX]
+    float* cbuf = X22 + HB * DSX;   // [2][HB]
+    // entry (i, c) of the inverse (zero above the diagonal and in the upper-right quarter)
+    auto xat = [&](int i, int c) -> float {
+        if (i < HB) return c < HB ? X11[i * DSX + c] : 0.f;
+        return c < HB ? X21[(i - HB) * DSX + c] : X22[(i - HB) * DSX + c - HB];
+    };
     float* rbuf = cbuf + 2 * HB;    // [2][HB]
     float* rhs = rbuf + 2 * HB;     // [2][NB]
     const int tid = threadIdx.x;
@@ -534,7 +545,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     {
         const float* Gt = G + (size_t)t * P * P;
         const float inv_ns = 1.0f / (float)ns;
-        float* obs = X;  // the block's column means (first block column only), X not yet in use
+        float* obs = X11;  // the block's column means (first block column only), X not yet in use
         if (jb == 0 && tid < NB) obs[tid] = tid < nb ? (float)obar[(size_t)t * P + tid] : 0.f;
         __syncthreads();
 #pragma unroll 1
@@ -566,12 +577,12 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     }
     __syncthreads();
     // L11, X11
-    bool ok = factor64(A, X, cbuf, rbuf);
+    bool ok = factor64(A, DSD, X11, DSX, cbuf, rbuf);
     float acc[4][4];
     const int ti = tid >> 4, tj = tid & 15;
     if (ok) {
         // L21 = A21 X11^T (in place, after all reads)
-        if (tid < 256) gemm64_nt(A + HB * DSD, X, acc);
+        if (tid < 256) gemm64_nt(A + HB * DSD, DSD, X11, DSX, acc);
         __syncthreads();
         if (tid < 256) {
 #pragma unroll
@@ -582,7 +593,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         __syncthreads();
         // A22 -= L21 L21^T
         if (tid < 256) {
-            gemm64_nt(A + HB * DSD, A + HB * DSD, acc);
+            gemm64_nt(A + HB * DSD, DSD, A + HB * DSD, DSD, acc);
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -590,7 +601,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         }
         __syncthreads();
         // L22, X22
-        ok = factor64(A + HB * DSD + HB, X + HB * DSD + HB, cbuf, rbuf);
+        ok = factor64(A + HB * DSD + HB, DSD, X22, DSX, cbuf, rbuf);
     }
     if (!ok) {  // uniform: every thread saw the same pivots
         if (tid == 0) fail[t] = 1;
@@ -599,7 +610,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     // T = L21 X11 into the unused upper-right quarter of A, then X21 = -X22 T
     float* Tm = A + HB;
     if (tid < 256) {
-        gemm64_nn(A + HB * DSD, X, acc);
+        gemm64_nn(A + HB * DSD, DSD, X11, DSX, acc);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -607,14 +618,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     }
     __syncthreads();
     if (tid < 256) {
-        gemm64_nn(X + HB * DSD + HB, Tm, acc);
+        gemm64_nn(X22, DSX, Tm, DSD, acc);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) X[(HB + ti + 16 * a) * DSD + 4 * tj + b] = -acc[a][b];
+            for (int b = 0; b < 4; ++b) X21[(ti + 16 * a) * DSX + 4 * tj + b] = -acc[a][b];
     }
     // X12 = 0
-    for (int e = tid; e < HB * HB; e += blockDim.x) X[(e >> 6) * DSD + HB + (e & (HB - 1))] = 0.f;
     __syncthreads();
     // outputs: L (FP32 and BF16 pieces), X (padded rows / columns zero), y_b = X rhs
     const LbLayout lay{(P + NB - 1) / NB, LD / 32};
@@ -632,7 +642,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
     for (int e = tid; e < NB * (NB / 4); e += blockDim.x) {
         const int i = e >> 5, c4 = e & 31;
-        float4 v = ld4(X + i * DSD + 4 * c4);
+        float4 v = make_float4(xat(i, 4 * c4), xat(i, 4 * c4 + 1), xat(i, 4 * c4 + 2), xat(i, 4 * c4 + 3));
         if (i >= nb) v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (4 * c4 + 0 >= nb) v.x = 0.f;
         if (4 * c4 + 1 >= nb) v.y = 0.f;
@@ -651,7 +661,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int c = 8 * c8 + u;
-                v[u] = (i < nb && c < nb) ? X[i * DSD + c] : 0.f;
+                v[u] = (i < nb && c < nb) ? xat(i, c) : 0.f;
             }
             store_P8(Dbt, pl, layD.at(i, 8 * c8), v);
         }
@@ -659,7 +669,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     if (tid < 2 * NB) {
         const int h = tid >> 7, i = tid & (NB - 1);
         float s = 0.f;
-        for (int k = 0; k <= i; ++k) s = fmaf(X[i * DSD + k], rhs[h * NB + k], s);
+        for (int k = 0; k <= i; ++k) s = fmaf(xat(i, k), rhs[h * NB + k], s);
         if (i < nb) yt[h * P + jb + i] = s;
     }
 }
