@@ -7,7 +7,8 @@
 //
 // One CTA computes one 128 x 256 tile of the upper triangle of G for one trajectory:
 //   warp 0      TMA producer: three 128-row boxes (A rows i, B rows j, j+128) of 64 samples
-//               per stage into a 4-stage ring, 128-byte swizzled, completing on mbarriers;
+//               per stage into a 2-stage ring, 128-byte swizzled, completing on mbarriers (two
+//               CTAs per SM, so that one CTA's epilogue overlaps the other's MMAs);
 //   warp 1      allocates 256 TMEM columns; one lane issues tcgen05.mma (M=128, N=256,
 //               K=16, BF16 in, FP32 accumulate in TMEM) and commits each stage back;
 //   warps 2..5  epilogue: tcgen05.ld of their 32 TMEM lanes, FP32 stores of the j >= i part.
@@ -26,7 +27,7 @@ namespace otvmc {
 namespace tc {
 
 constexpr int BM = 128, BN = 256, BK = 64;
-constexpr int STAGES = 4;
+constexpr int STAGES = 2;  // two CTAs per SM: one's epilogue overlaps the other's MMAs
 constexpr int BOX_BYTES = 128 * BK * 2;  // 16 KB: one 128-row box
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
@@ -52,7 +53,7 @@ __device__ __forceinline__ int2 tile_of(int q, int P) {
     return make_int2(MT, NT);
 }
 
-__global__ void __launch_bounds__(192, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
+__global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
                                                           int kpad, int npairs, const int2* __restrict__ tiles,
                                                           float* __restrict__ G, int* status) {
     extern __shared__ uint8_t smem_raw[];
