@@ -31,9 +31,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one gram_tc_kernel launch per trajectory at this workload, from
-# the ncu capture summarised in profiles/gram_tc_chain64_32traj.md (798.5 MB for 32 trajectories;
+# the ncu capture summarised in profiles/gram_tc_chain64_32traj.md (799.1 MB for 32 trajectories;
 # traffic grows in proportion to the trajectories of a launch).
-GRAM_DRAM_BYTES_PER_TRAJ = 798.5e6 / 32
+GRAM_DRAM_BYTES_PER_TRAJ = 799.1e6 / 32
 
 
 def parse():
