@@ -119,8 +119,10 @@ OTVMC_API int otvmc_model_nops(const otvmc_model* model);
  * OTVMC_RBM: log psi = sum a_i s_i + sum_m log 2cosh(b_m + sum_i W_im s_i),
  *   P = N + M + N M, theta = [a (N), b (M), W (N x M row-major)], M = n_hidden in
  *   [1, 4096].  Sampling uses an FP32 warp-per-chain kernel whose decisions equal the FP64
- *   ones (M <= 256; an FP64 kernel beyond).  MIXED (M <= 256): FP32 log 2cosh in the
- *   estimators and observables; in run_trajectories, S (P <= ns) or T (P > ns) from
+ *   ones (M <= 256; an FP64 kernel beyond); its ratios are products of flip factors
+ *   cosh(g - 2 s W) / cosh g = 1 + (cosh 2W - 1) - s tanh(g) sinh 2W, tabulated per call in
+ *   the workspace.  MIXED (M <= 256): the same flip factors for the estimators' ratios, FP32
+ *   log 2cosh in the observables; in run_trajectories, S (P <= ns) or T (P > ns) from
  *   split-BF16 tensor-core products accumulated in FP32 and the tensor-core Cholesky with
  *   refinement against that matrix (delta within ~1e-4 relative of the FP64 path at eps 1e-3);
  *   on the T path T is by default formed without O (otvmc_ansatz_set_rbm_t_build);
@@ -139,7 +141,7 @@ OTVMC_API int64_t otvmc_ansatz_nparams(const otvmc_ansatz* ansatz);
  *   O(ns^2 (N + M)) work and no O in memory.  delta = O_c^+ z / ns likewise from N x (M + 1)
  *   column sums.  Same delta as the materialised form up to rounding.
  * OTVMC_RBM_T_MATERIALISED: O_c materialised (real embedding, three BF16 pieces) and T from
- *   the split-BF16 tensor-core product (O(ns^2 N M) work, 12 ns N M bytes per trajectory).
+ *   the split-BF16 tensor-core product (O(ns^2 N M) work, 24 ns P bytes per trajectory).
  * Returns OTVMC_ERR_INVALID for another mode or a Jastrow ansatz.  Not synchronised with
  * calls in flight on the same ansatz: set it before launching them. */
 enum { OTVMC_RBM_T_FACTORED = 0, OTVMC_RBM_T_MATERIALISED = 1 };
