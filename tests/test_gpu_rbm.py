@@ -279,3 +279,23 @@ def test_rbm_factored_t_equals_materialised(n, m, ns):
     assert np.array_equal(sp_f, sp_d) and np.array_equal(sp_m, sp_d)
     assert rel_err(th_f - theta0, th_d - theta0) < 1e-3
     assert rel_err(th_m - theta0, th_d - theta0) < 1e-3
+
+
+def test_rbm_mixed_full_size_chain64_rbm():
+    """The chain64_rbm configuration the benchmark times (N = 64, M = 128, P = 8384, N_s = 2048,
+    T path of size 4096, weights N(0, 0.01^2), shift 1e-4 as in the workload): one trajectory step of
+    the mixed path (factorised T) against the FP64 path on the same draws, on two trajectories:
+    identical chains, parameter change within 1e-3, moments within 1e-5."""
+    w = synth.WORKLOADS["chain64_rbm"]
+    c = RbmCase(w.n, w.n_hidden, h=w.h, kappa=w.kappa, gamma=w.gamma, alpha=w.alpha)
+    check(abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, FACT))
+    T, ns, seed = 2, 2048, 7
+    g = synth.rng(11)
+    theta0 = np.zeros(c.P, complex)
+    theta0[c.n + c.m:] = g.normal(0, 0.01, c.n * c.m) + 1j * g.normal(0, 0.01, c.n * c.m)
+    th_m, sp_m, mo_m = _run(c, MIXED, T, ns, 1, w.dt, seed, w.eps, theta0)
+    th_f, sp_f, mo_f = _run(c, FP64, T, ns, 1, w.dt, seed, w.eps, theta0)
+    assert np.array_equal(sp_m, sp_f)
+    e = rel_err(th_m - theta0, th_f - theta0)
+    assert e < 1e-3, e
+    assert rel_err(mo_m, mo_f) < 1e-5
