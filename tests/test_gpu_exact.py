@@ -145,3 +145,44 @@ def test_rbm_gains_over_jastrow_at_later_times():
     assert err_r[late].mean() < 0.6 * err_j[late].mean()
     assert err_j[late].mean() - err_r[late].mean() > 5 * max(se)
     assert err_j[:3].max() < 0.01 and err_r[:3].max() < 0.01
+
+
+def test_paper_fig1_setup_matches_closed_form():
+    """The setup of the paper's N = 10 benchmark (LITF paragraph, Fig. 1): periodic ring,
+    alpha = 1 with the Kac factor, the LITF sign of Eq. 10 (J_ij = -J_d), kappa = 0.5, h = 0,
+    400 trajectories, midpoint; full Jastrow ansatz with 4096 samples, dt = 0.005, shift 1e-3.
+    Against App. D's closed form (its y components flipped for the LITF sign): M within 3
+    standard errors (+1e-3) at t = 0.1, 0.2, 0.3, and the squeezing parameter xi^2 (which falls
+    from 1 to about 0.58 over this time) within 5 %."""
+    import paper_2506_23928_gb300 as pkg
+    from oracle.observables import squeezing
+    n, alpha, kappa = 10, 1.0, 0.5
+    Jd = fossfeig.ring_couplings(n, 1.0, alpha, kac=True)
+    Jij = np.array([[0.0 if i == j else -Jd[(i - j) % n] for j in range(n)] for i in range(n)])
+    model = pkg.Model(Jij, 0.0, np.full(n, kappa), np.zeros(n))
+    ans = pkg.Ansatz(model)
+    T, ns, steps, every, dt = 400, 4096, 60, 20, 0.005
+    desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=abi.OTVMC_MIDPOINT,
+                       precision=MIXED, reg=abi.OTVMC_REG_SHIFT, eps=1e-3, snr_thresh=4.0, seed=3,
+                       measure_every=every, measure_final=1, use_graph=0)
+    nm = abi.otvmc_run_n_meas(desc)
+    theta = torch.zeros((T, ans.P, 2), dtype=torch.float64, device="cuda")
+    spins = torch.zeros((T, ns, 1), dtype=torch.int64, device="cuda")
+    check(abi.otvmc_init_chains(ans.handle, T, 0, ns, 3, spins))
+    nb = abi.otvmc_run_workspace_bytes(ans.handle, desc)
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    mom = torch.zeros((nm, T, 9), dtype=torch.float64, device="cuda")
+    check(abi.otvmc_run_trajectories(ans.handle, desc, theta, spins, mom, work, nb))
+    mom = mom.cpu().numpy()
+    flip = np.array([1, -1, 1])
+    for i in range(1, nm):
+        t = min(i * every, steps) * dt
+        Mf, Cf = fossfeig.fossfeig(Jd, kappa, t)
+        Mf, Cf = Mf * flip, Cf * np.outer(flip, flip)
+        q = np.zeros((T, 3, 3))
+        for (a, b), col in zip([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)], range(3, 9)):
+            q[:, a, b] = q[:, b, a] = mom[i, :, col]
+        M, C, dM = ensemble(mom[i, :, :3], q)
+        assert np.all(np.abs(M - Mf) <= 3 * dM + 1e-3), (t, M, Mf, dM)
+        xi, xif = squeezing(M, C, n), squeezing(Mf, Cf, n)
+        assert abs(xi - xif) < 0.05 * xif, (t, xi, xif)
