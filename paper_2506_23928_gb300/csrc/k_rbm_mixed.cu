@@ -97,7 +97,7 @@ __device__ __forceinline__ void tanh_bound(float gx, float gy, float eb, float& 
 // entries and of the arithmetic.  WS: W_jm (needed on acceptance) as float2 in shared memory.
 // MQ: hidden units per lane (M <= 32 MQ).
 template <bool WS, int MQ>
-__global__ void __launch_bounds__(256, MQ == 4 ? 3 : 1) sample_rbm_mixed_kernel(const double2* __restrict__ theta, int P, int n, int M,
+__global__ void __launch_bounds__(MQ == 4 ? 256 : 128, MQ == 4 ? 3 : 4) sample_rbm_mixed_kernel(const double2* __restrict__ theta, int P, int n, int M,
                                                                int W, int ns, int n_sweep, uint32_t k0, uint32_t k1,
                                                                uint32_t evtag, int traj0, const float4* __restrict__ tab,
                                                                const float2* __restrict__ wtab,
