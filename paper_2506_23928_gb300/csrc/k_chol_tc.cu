@@ -1094,12 +1094,13 @@ __device__ void sweep_backward(int P, int PY, int LD, const float* Lt, const flo
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.f;
         int i = jb + NB + warp;
-        for (; i + 7 * SW_WARPS < P; i += 8 * SW_WARPS) {
-            float4 l[8];
+        // sixteen rows per warp in flight (the pass is bound by the loads' latency)
+        for (; i + 15 * SW_WARPS < P; i += 16 * SW_WARPS) {
+            float4 l[16];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) l[a] = ld4(Lt + (size_t)(i + a * SW_WARPS) * LD + jb + 4 * lane);
+            for (int a = 0; a < 16; ++a) l[a] = ld4(Lt + (size_t)(i + a * SW_WARPS) * LD + jb + 4 * lane);
 #pragma unroll
-            for (int a = 0; a < 8; ++a) acc_col4(acc, l[a], y[i + a * SW_WARPS], y[PY + i + a * SW_WARPS]);
+            for (int a = 0; a < 16; ++a) acc_col4(acc, l[a], y[i + a * SW_WARPS], y[PY + i + a * SW_WARPS]);
         }
         for (; i < P; i += SW_WARPS) acc_col4(acc, ld4(Lt + (size_t)i * LD + jb + 4 * lane), y[i], y[PY + i]);
         put_col4(red, warp, lane, acc);
