@@ -399,7 +399,8 @@ __device__ bool factor64(float* A, int lda, float* X, int ldx, float* cbuf, floa
             const float d = cb[m];
             ok = ok && d > 0.f && isfinite(d);
             const float dd = ok ? d : 1.f;
-            const float isd = 1.0f / sqrtf(dd), id = 1.0f / dd;
+            // a few ulps suffice here: the factor is refined against the exact matrix later
+            const float isd = rsqrtf(dd), id = isd * isd;
             if (isA && bj >= bm) {
                 float li[4], lj[4];
 #pragma unroll
@@ -668,8 +669,17 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     }
     if (tid < 2 * NB) {
         const int h = tid >> 7, i = tid & (NB - 1);
+        const float* rh = rhs + h * NB;
         float s = 0.f;
-        for (int k = 0; k <= i; ++k) s = fmaf(xat(i, k), rhs[h * NB + k], s);
+        if (i < HB) {
+            for (int k = 0; k <= i; ++k) s = fmaf(X11[i * DSX + k], rh[k], s);
+        } else {
+            const float* x21 = X21 + (i - HB) * DSX;
+            const float* x22 = X22 + (i - HB) * DSX;
+#pragma unroll 8
+            for (int k = 0; k < HB; ++k) s = fmaf(x21[k], rh[k], s);
+            for (int k = HB; k <= i; ++k) s = fmaf(x22[k - HB], rh[k], s);
+        }
         if (i < nb) yt[h * P + jb + i] = s;
     }
 }
