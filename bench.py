@@ -178,7 +178,7 @@ def rbm_path(stream, fp64_value, peaks_):
         torch.cuda.synchronize()
         value = T * steps / (e0.elapsed_time(e1) / 1000.0)
         # one more step with per-class kernel timing (outside the timed steps)
-        abi.otvmc_profile_enable(1)
+        abi.otvmc_profile_enable(abi.OTVMC_PROFILE_SERIAL)
         check(abi.otvmc_run_trajectories(ans.handle, desc(1 + steps), theta, spins, None, work, nb, stream))
         torch.cuda.synchronize()
         prof = abi.profile_summary()
@@ -269,7 +269,7 @@ def rbm_workload(name, stream, fp64_value, steps=1, warmup=1):
                                "ms_per_step": sum(m[k].elapsed_time(m[k + 1]) for m in ev) / steps}
               for k in range(len(ns_mix))}
     # one more step with per-class kernel timing (outside the timed steps)
-    abi.otvmc_profile_enable(1)
+    abi.otvmc_profile_enable(abi.OTVMC_PROFILE_SERIAL)
     for k in range(len(ns_mix)):
         theta, spins = batches[k]
         check(abi.otvmc_run_trajectories(ans.handle, desc(k, warmup + steps), theta, spins, None, work, nb, stream))
@@ -381,7 +381,6 @@ def main():
     if clocks:
         clocks.start()
         time.sleep(0.3)
-    abi.otvmc_profile_enable(1)
     l0 = abi.otvmc_launch_count()
     if world > 1:
         dist.barrier()
@@ -396,8 +395,6 @@ def main():
         dist.barrier()
     launches = abi.otvmc_launch_count() - l0
     el_ms = ev0.elapsed_time(ev1)
-    prof = abi.profile_summary()
-    abi.otvmc_profile_enable(0)
     clk = clocks.stop() if clocks else None
     t = torch.tensor([el_ms], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -428,17 +425,29 @@ def main():
         e2e = {"value": total_units / float(e2e_s.item()), "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # per-kernel durations: the same steps once more, outside the timed region, with every launch
+    # bracketed by CUDA events on its own stream and the solver's trajectory groups run one after
+    # another (in the timed steps they overlap on forked streams, where a launch's event time
+    # would include the time it shares the GPU with the other groups' kernels)
+    prof_steps = max(1, min(args.steps, 2))
+    abi.otvmc_profile_enable(abi.OTVMC_PROFILE_SERIAL)
+    for k in range(prof_steps):
+        step(args.warmup + 2 * args.steps + k)
+    torch.cuda.synchronize()
+    prof = abi.profile_summary()
+    abi.otvmc_profile_enable(abi.OTVMC_PROFILE_OFF)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
     pk, pk_kind = peaks()
-    stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
+    stage_ms = {k: v[0] / prof_steps for k, v in prof.items()}
     dominant = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     ns = w.ns
     roof = {}
-    evals = 2 * args.steps                                            # evaluations per trajectory in the timed region
+    evals = 2 * prof_steps                                            # evaluations per trajectory in the profiled steps
     NBK = 128
     jbs = list(range(0, P, NBK))
     # algorithmic work per trajectory-evaluation of each kernel class
@@ -523,6 +532,8 @@ def main():
                        "parallelism": f"trajectories sharded over {world} GPU(s)",
                        "l2": "no flush: per-step working set (O, G, L of 256 trajectories, ~14 GB) exceeds L2"},
             "roofline": rl, "roofline_by_kernel": roof, "dominant_kernel": dominant,
+            "kernel_timing": f"CUDA events per launch over {prof_steps} more step(s) after the timed region, "
+                             "solver trajectory groups serialised (launch durations not shared)",
             "stage_ms_per_step": stage_ms, "cpu_baseline": cpu, "fp64_path": fp64, "rbm_mixed_path": rbm,
             "rbm_workloads": rbm_full,
             "clocks": clk, "e2e": e2e,

@@ -344,7 +344,14 @@ OTVMC_API otvmc_status otvmc_run_trajectories_host(const otvmc_ansatz* ansatz, c
 /* ------------------------------------------------------------------ kernel timing
  * When enabled, every kernel launch of the library is bracketed by two CUDA events on
  * its own stream; otvmc_profile_read sums the elapsed times per kernel class.  Enabling
- * clears earlier records.  Not for use inside CUDA graph capture. */
+ * clears earlier records.  Not for use inside CUDA graph capture.
+ * otvmc_profile_enable(OTVMC_PROFILE_ON) keeps the normal schedule, in which the Cholesky
+ * solver's trajectory groups run concurrently on forked streams, so that a launch's elapsed
+ * time includes the time it shares the GPU with the other groups' kernels.
+ * OTVMC_PROFILE_SERIAL runs those groups one after another on the calling stream (the same
+ * launches, no overlap), so that each elapsed time is the launch's own duration; results are
+ * identical, only the schedule differs.  OTVMC_PROFILE_OFF (0) stops recording. */
+enum { OTVMC_PROFILE_OFF = 0, OTVMC_PROFILE_ON = 1, OTVMC_PROFILE_SERIAL = 2 };
 enum {
     OTVMC_K_SAMPLE = 0,  /* Metropolis sweeps */
     OTVMC_K_PREP = 1,    /* fixed-point parameter tables */

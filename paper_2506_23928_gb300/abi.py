@@ -25,6 +25,7 @@ OTVMC_PREC_FP64, OTVMC_PREC_MIXED = 0, 1
 OTVMC_REG_SHIFT, OTVMC_REG_SNR = 0, 1
 OTVMC_HEUN, OTVMC_MIDPOINT = 0, 1
 OTVMC_RBM_T_FACTORED, OTVMC_RBM_T_MATERIALISED = 0, 1
+OTVMC_PROFILE_OFF, OTVMC_PROFILE_ON, OTVMC_PROFILE_SERIAL = 0, 1, 2
 OTVMC_MOMENTS = 9
 KERNEL_CLASSES = ["sample", "prep", "est1", "est2", "reduce", "obs", "D", "obuild", "gram", "syrk", "solve", "sde",
                   "noise", "chol_update", "chol_trsm", "chol_diag", "chol_resid"]

@@ -1,6 +1,7 @@
 // C ABI of libotvmc: handles, argument checks, workspace carving, stage entry points and
 // the batched trajectory driver (otVMC procedure paragraph, App. C).
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <cmath>
 #include <cstdio>
@@ -23,10 +24,12 @@ struct ProfRec {
 };
 static std::mutex g_prof_mu;
 static std::atomic<bool> g_prof_on{false};
+static std::atomic<bool> g_prof_serial{false};
 static std::vector<ProfRec> g_prof;
 static std::vector<cudaEvent_t> g_prof_pool;
 
 bool profiling() { return g_prof_on.load(std::memory_order_relaxed); }
+bool profiling_serial() { return g_prof_serial.load(std::memory_order_relaxed); }
 
 void prof_record(int cls, cudaStream_t s, bool start) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -145,6 +148,7 @@ void otvmc_profile_enable(int on) {
     }
     g_prof.clear();
     g_prof_on.store(on != 0);
+    g_prof_serial.store(on == OTVMC_PROFILE_SERIAL);
 }
 
 otvmc_status otvmc_profile_read(int cls, double* total_ms, uint64_t* launches) {
@@ -777,11 +781,74 @@ int otvmc_run_n_meas(const otvmc_run_desc* d) {
     return n;
 }
 
+// Trajectory pipelines: a batch of at least RUN_PIPE_MIN trajectories runs as RUN_PIPES
+// contiguous sub-batches, each advanced through all its steps on a stream of its own forked
+// from the caller's, so that the sub-batches' launches overlap one another's tails and
+// gaps (the sub-batches start together; a start staggered by one evaluation's sampling and
+// Gram phase measured slower on the 64-spin benchmark).  Trajectories are independent
+// and every random draw is keyed by the global trajectory id, so the split leaves every
+// result unchanged.  Each sub-batch carves its own region of the workspace; all share the
+// status word at its head.
+constexpr int RUN_PIPES = 2;
+constexpr int RUN_PIPE_MIN = 32;
+
+// (Jastrow only: with the RBM's T path the solve of size 2 ns dominates, and sub-batches
+// whose solves compete measured slower.)
+static int run_pipes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    return a->kind == OTVMC_JASTROW && d->ntraj >= RUN_PIPE_MIN ? RUN_PIPES : 1;
+}
+
+// Sub-batch p of np: its descriptor and the offset of its first trajectory in the batch.
+static otvmc_run_desc pipe_desc(const otvmc_run_desc* d, int p, int np, int* first) {
+    const int ta = (int)((long long)d->ntraj * p / np), tb = (int)((long long)d->ntraj * (p + 1) / np);
+    otvmc_run_desc q = *d;
+    q.ntraj = tb - ta;
+    q.traj0 = d->traj0 + ta;
+    *first = ta;
+    return q;
+}
+
+// Workspace bytes of one sub-batch (256-byte head included, rounded to 256).
+static size_t pipe_bytes(const otvmc_ansatz* a, const otvmc_run_desc* q) {
+    Carver c(nullptr, (size_t)-1);
+    carve_run(c, a, q);
+    return (c.off + 255) & ~(size_t)255;
+}
+
+struct PipeStreams {
+    cudaStream_t s[RUN_PIPES];
+    cudaEvent_t fork;
+    cudaEvent_t join[RUN_PIPES];
+};
+// One set per (device, calling stream), created on first use.
+static PipeStreams& pipe_streams(cudaStream_t caller) {
+    static std::mutex mu;
+    static std::map<std::pair<int, uintptr_t>, PipeStreams> sets;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, (uintptr_t)caller);
+    auto it = sets.find(key);
+    if (it != sets.end()) return it->second;
+    PipeStreams& g = sets[key];
+    for (int i = 0; i < RUN_PIPES; ++i) {
+        cudaStreamCreateWithFlags(&g.s[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming);
+    }
+    cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
+    return g;
+}
+
 size_t otvmc_run_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
     if (check_run(a, d)) return 0;
-    Carver c(nullptr, (size_t)-1);
-    carve_run(c, a, d);
-    return c.off + 256;
+    const int np = run_pipes(a, d);
+    size_t total = 0;
+    for (int p = 0; p < np; ++p) {
+        int first = 0;
+        const otvmc_run_desc q = pipe_desc(d, p, np, &first);
+        total += pipe_bytes(a, &q);
+    }
+    return total + 256;
 }
 
 // One evaluation at theta (eval index ev): sample, estimators, [observables], S/D, solve.
@@ -832,12 +899,14 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     return OTVMC_OK;
 }
 
+// All steps of one (sub-)batch on stream s; moments rows hold mstride trajectories, of which
+// this batch's come first in moments_d.
 static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d, uint64_t* spins_d,
-                              double* moments_d, void* work_d, size_t work_bytes, cudaStream_t s) {
+                              double* moments_d, int mstride, void* work_d, size_t work_bytes, int* status,
+                              cudaStream_t s) {
     Carver c(work_d, work_bytes);
     RunBufs r = carve_run(c, a, d);
     if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
-    int* status = (int*)work_d;
     const int T = d->ntraj;
     const int64_t P = a->P;
     double2* theta = (double2*)theta_d;
@@ -847,7 +916,7 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
         CK(launch_noise(a->model, T, d->traj0, d->seed, step, d->dt, r.dW, s), "noise launch");
         double* mrow = nullptr;
         if (d->measure_every > 0 && i % d->measure_every == 0 && moments_d)
-            mrow = moments_d + (size_t)(row++) * T * OTVMC_MOMENTS;
+            mrow = moments_d + (size_t)(row++) * mstride * OTVMC_MOMENTS;
         otvmc_status st = run_eval(a, d, r, theta, spins_d, 2 * step, mrow, r.d0, status, s);
         if (st) return st;
         CK(launch_sde(T, P, d->scheme, 0, theta, r.d0, nullptr, r.theta_c, nullptr, status, s), "sde launch");
@@ -870,7 +939,7 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
         otvmc_status st = run_estimators(a, theta, spins_d, T, d->ns, nullptr, 0.0, fp32, r.eb, r.lpl, nullptr,
                                          nullptr, status, s);
         if (st) return st;
-        double* mrow = moments_d + (size_t)row * T * OTVMC_MOMENTS;
+        double* mrow = moments_d + (size_t)row * mstride * OTVMC_MOMENTS;
         if (rbm) {
             CK(launch_obs_rbm(a, theta, spins_d, T, d->ns, fp32, r.eb, s), "observables launch");
             CK(launch_obs_final(a->n, d->ns, T, r.eb, mrow, s), "observables launch");
@@ -878,6 +947,40 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
             CK(launch_obs_prep(a, theta, T, fp32, r.eb, s), "obs prep launch");
             CK(launch_observables(a, spins_d, T, d->ns, fp32, r.eb, mrow, s), "observables launch");
         }
+    }
+    return OTVMC_OK;
+}
+
+// The batch as sub-batches on forked streams (one after another on s under serial profiling).
+static otvmc_status run_pipelined(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d, uint64_t* spins_d,
+                                  double* moments_d, void* work_d, size_t work_bytes, cudaStream_t s) {
+    int* status = (int*)work_d;
+    const int np = run_pipes(a, d);
+    if (np == 1) return run_steps(a, d, theta_d, spins_d, moments_d, d->ntraj, work_d, work_bytes, status, s);
+    const bool forked = !profiling_serial();
+    PipeStreams& ps = pipe_streams(s);
+    if (forked) CK(cudaEventRecord(ps.fork, s), "pipeline fork");
+    const size_t W = (size_t)((a->n + 63) / 64);
+    char* w = (char*)work_d;
+    size_t left = work_bytes;
+    for (int p = 0; p < np; ++p) {
+        int first = 0;
+        const otvmc_run_desc q = pipe_desc(d, p, np, &first);
+        const size_t need = pipe_bytes(a, &q);
+        if (need > left) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+        cudaStream_t sp = forked ? ps.s[p] : s;
+        if (forked) CK(cudaStreamWaitEvent(sp, ps.fork, 0), "pipeline fork");
+        otvmc_status st = run_steps(a, &q, theta_d + (size_t)first * a->P * 2, spins_d + (size_t)first * d->ns * W,
+                                    moments_d ? moments_d + (size_t)first * OTVMC_MOMENTS : nullptr, d->ntraj, w, need,
+                                    status, sp);
+        if (forked) {
+            // joined also after an error, so that the caller's stream stays ordered after it
+            CK(cudaEventRecord(ps.join[p], sp), "pipeline join");
+            CK(cudaStreamWaitEvent(s, ps.join[p], 0), "pipeline join");
+        }
+        if (st) return st;
+        w += need;
+        left -= need;
     }
     return OTVMC_OK;
 }
@@ -890,7 +993,7 @@ otvmc_status otvmc_run_trajectories(const otvmc_ansatz* a, const otvmc_run_desc*
     if (!theta_d || !spins_d || !work_d) return fail(OTVMC_ERR_INVALID, "run: null buffer");
     if (otvmc_run_n_meas(d) > 0 && !moments_d) return fail(OTVMC_ERR_INVALID, "run: moments_d needed");
     cudaStream_t s = (cudaStream_t)stream;
-    st = run_steps(a, d, theta_d, spins_d, moments_d, work_d, work_bytes, s);
+    st = run_pipelined(a, d, theta_d, spins_d, moments_d, work_d, work_bytes, s);
     if (st) return st;
     return otvmc_check(work_d, stream);
 }
@@ -924,7 +1027,7 @@ otvmc_status otvmc_run_trajectories_host(const otvmc_ansatz* a, const otvmc_run_
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(th_d, theta_h, th_bytes, cudaMemcpyHostToDevice, s), "theta upload");
     CK(cudaMemcpyAsync(sp_d, spins_h, sp_bytes, cudaMemcpyHostToDevice, s), "spins upload");
-    st = run_steps(a, d, th_d, sp_d, nmeas ? mo_d : nullptr, work_d, base, s);
+    st = run_pipelined(a, d, th_d, sp_d, nmeas ? mo_d : nullptr, work_d, base, s);
     if (st) return st;
     CK(cudaMemcpyAsync(theta_h, th_d, th_bytes, cudaMemcpyDeviceToHost, s), "theta download");
     CK(cudaMemcpyAsync(spins_h, sp_d, sp_bytes, cudaMemcpyDeviceToHost, s), "spins download");

@@ -43,6 +43,7 @@ void count_launch(int n = 1);
 
 // Kernel timing (otvmc_profile_enable): records a CUDA event pair around a launch.
 bool profiling();
+bool profiling_serial();  // profiling with the solver's trajectory groups on the calling stream
 void prof_record(int cls, cudaStream_t s, bool start);
 struct ProfScope {
     int cls;

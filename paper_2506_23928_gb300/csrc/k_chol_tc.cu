@@ -1241,6 +1241,13 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
 inline int ldim(int P) { return ((P + 63) / 64) * 64; }
 
 constexpr int CHOL_GROUPS = 4;
+// Trajectory groups of one call: groups of 64 once the call has 128 trajectories or more
+// (each launch then fills the GPU by itself), else CHOL_GROUPS groups from 16 trajectories.
+inline int chol_groups(int ntraj) {
+    if (ntraj < 16) return 1;
+    if (ntraj >= 128) return ntraj / 64 < CHOL_GROUPS ? ntraj / 64 : CHOL_GROUPS;
+    return CHOL_GROUPS;
+}
 struct GroupStreams {
     cudaStream_t s[CHOL_GROUPS];
     cudaEvent_t fork;
@@ -1342,9 +1349,11 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     if (e != cudaSuccess) return chol_fail(e, "sweep attribute");
     // trajectory groups on forked streams: one group's latency-bound kernels overlap the
     // others' (fork and join by events, so the call stays ordered on `s`)
-    const int ng = ntraj >= 16 ? CHOL_GROUPS : 1;
+    // (under serial profiling the groups keep their launches but run one after another on s)
+    const int ng = chol_groups(ntraj);
+    const bool forked = ng > 1 && !profiling_serial();
     GroupStreams& gs = group_streams(s);
-    if (ng > 1) {
+    if (forked) {
         e = cudaEventRecord(gs.fork, s);
         if (e != cudaSuccess) return chol_fail(e, "fork record");
     }
@@ -1352,8 +1361,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
         const int ta = (int)((long long)ntraj * g / ng), tb = (int)((long long)ntraj * (g + 1) / ng);
         const int nt = tb - ta;
         if (nt <= 0) continue;
-        cudaStream_t gsm = ng > 1 ? gs.s[g] : s;
-        if (ng > 1 && (e = cudaStreamWaitEvent(gsm, gs.fork, 0)) != cudaSuccess) return e;
+        cudaStream_t gsm = forked ? gs.s[g] : s;
+        if (forked && (e = cudaStreamWaitEvent(gsm, gs.fork, 0)) != cudaSuccess) return e;
         for (int jb = 0; jb < P; jb += NB) {
             if (jb > 0) {
                 ProfScope pu(OTVMC_K_CHOLU, gsm);
@@ -1398,7 +1407,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
                                                                   obar, D, Lf, Dv, yv, part, x, delta, shift_used, fail);
             count_launch();
         }
-        if (ng > 1) {
+        if (forked) {
             if ((e = cudaEventRecord(gs.join[g], gsm)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, gs.join[g], 0)) != cudaSuccess) return e;
         }

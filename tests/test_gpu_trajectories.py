@@ -92,6 +92,32 @@ def test_batching_does_not_change_results():
     assert np.array_equal(full[1], np.concatenate([lo[1], hi[1]]))
 
 
+def test_pipelined_batch_equals_separate_batches():
+    """A batch of 40 trajectories runs as two sub-batches of 20 on forked streams (the solver's
+    trajectory groups forked again inside each); it equals a batch of 24 and a batch of 16 run
+    apart, in theta, spins and every measured moment, with device and host buffers, and with the
+    sub-batches serialised on the caller's stream (serial profiling)."""
+    c = Case((10,), kappa=0.1)
+    args = (64, 2, 0.01, 3, abi.OTVMC_HEUN, MIXED)
+    full = run_gpu(c, 40, *args)
+    lo = run_gpu(c, 24, *args, traj0=0)
+    hi = run_gpu(c, 16, *args, traj0=24)
+    assert np.array_equal(full[0], np.concatenate([lo[0], hi[0]]))
+    assert np.array_equal(full[1], np.concatenate([lo[1], hi[1]]))
+    assert np.array_equal(full[2], np.concatenate([lo[2], hi[2]], axis=1))
+    host = run_gpu(c, 40, *args, host=True)
+    abi.otvmc_profile_enable(abi.OTVMC_PROFILE_SERIAL)
+    try:
+        ser = run_gpu(c, 40, *args)
+        prof = abi.profile_summary()
+    finally:
+        abi.otvmc_profile_enable(abi.OTVMC_PROFILE_OFF)
+    for k in range(3):
+        assert np.array_equal(full[k], host[k])
+        assert np.array_equal(full[k], ser[k])
+    assert prof["sample"][1] > 0
+
+
 def test_full_size_chain64_sampled():
     """The benchmark launch shape (N = 64, P = 2080, ns = 4096, 256 trajectories): one
     evaluation's sampler, S, D and solve, checked on sampled trajectories and entries."""
