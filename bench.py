@@ -34,6 +34,10 @@ FP32_LANES_PER_SM = 128
 # the ncu capture summarised in profiles/gram_tc_chain64_32traj.md (799.1 MB for 32 trajectories;
 # traffic grows in proportion to the trajectories of a launch).
 GRAM_DRAM_BYTES_PER_TRAJ = 799.1e6 / 32
+# DRAM bytes (read + write) of the block-column update kernel per trajectory-evaluation, from an
+# ncu capture of all 64 update launches of one evaluation of 32 trajectories (four groups of 8;
+# 44.28 MB per launch), chain64_jastrow shape
+UPDATE_DRAM_BYTES_PER_TRAJ_EVAL = 44.28e6 * 64 / 32
 
 
 def parse():
@@ -480,7 +484,9 @@ def main():
         else:
             ach, peak, unit = total / (ms / 1000.0) / 1e9, pk["hbm_gbs"], "GB/s"
             kind = f"HBM copy, {pk_kind}"
-        traffic = GRAM_DRAM_BYTES_PER_TRAJ * T if (cls == "gram" and w.name == "chain64_jastrow") else None
+        # DRAM bytes per launch from the ncu capture, scaled by the trajectories one launch covers
+        per_te = {"gram": GRAM_DRAM_BYTES_PER_TRAJ, "chol_update": UPDATE_DRAM_BYTES_PER_TRAJ_EVAL}.get(cls)
+        traffic = per_te * T * evals / cnt if (per_te and w.name == "chain64_jastrow") else None
         roof[cls] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
                      "traffic": traffic, "peak_kind": kind, "launches": cnt, "ms_total": ms}
     # the dominant kernel class among those with a roofline (largest total event time)
