@@ -952,21 +952,27 @@ __global__ void __launch_bounds__(256) chol_resid_kernel(int t0, int P, const fl
     DF cs[4][2];
 #pragma unroll
     for (int u = 0; u < 4; ++u) cs[u][0] = cs[u][1] = DF{0.f, 0.f};
-#pragma unroll 1
-    for (int g = 0; g < 4; ++g) {
-        float gv[4][4];
+    // the four rows of group g (rows warp*16 + 4g .. +3 of the tile, columns j0 .. j0+3)
+    auto load_group = [&](int g, float (&dst)[4][4]) {
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int i = I * NB + warp * 16 + 4 * g + a;
             const float* row = Gt + (size_t)i * P;
             if (i < P && vec) {
                 const float4 q = ld4(row + j0);
-                gv[a][0] = q.x; gv[a][1] = q.y; gv[a][2] = q.z; gv[a][3] = q.w;
+                dst[a][0] = q.x; dst[a][1] = q.y; dst[a][2] = q.z; dst[a][3] = q.w;
             } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) gv[a][u] = (i < P && j0 + u < P) ? row[j0 + u] : 0.f;
+                for (int u = 0; u < 4; ++u) dst[a][u] = (i < P && j0 + u < P) ? row[j0 + u] : 0.f;
             }
         }
+    };
+    // loads of group g + 1 are issued before the arithmetic of group g
+    float gv[4][4], gn[4][4];
+    load_group(0, gv);
+#pragma unroll 1
+    for (int g = 0; g < 4; ++g) {
+        if (g + 1 < 4) load_group(g + 1, gn);
         DF rs[8];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -989,6 +995,10 @@ __global__ void __launch_bounds__(256) chol_resid_kernel(int t0, int P, const fl
             const int idx = reduce8_index(lane);
             rowacc[idx & 1][warp * 16 + 4 * g + (idx >> 1)] = (double)s.s + (double)s.c;
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) gv[a][u] = gn[a][u];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
