@@ -118,6 +118,23 @@ def test_pipelined_batch_equals_separate_batches():
     assert prof["sample"][1] > 0
 
 
+def test_full_size_run_is_batch_invariant():
+    """The benchmark's launch configuration: 256 trajectories of the 64-spin workload (P = 2080,
+    N_s = 4096) through otvmc_run_trajectories, i.e. two sub-batches of 128 whose solves run as
+    groups of 64.  The same trajectories run as a batch of 128 (two sub-batches of 64, four
+    solver groups of 16 each) and as a batch of 16 (one batch, four groups of 4) give the same
+    theta, chains and moments bit for bit."""
+    c = Case((64,), alpha=1.5, h=1.0, kappa=0.1, gamma=0.05)
+    args = (4096, 1, 0.005, 2026, abi.OTVMC_MIDPOINT, MIXED)
+    full = run_gpu(c, 256, *args)
+    for T, t0 in ((128, 0), (16, 240)):
+        part = run_gpu(c, T, *args, traj0=t0)
+        assert np.array_equal(full[0][t0:t0 + T], part[0])
+        assert np.array_equal(full[1][t0:t0 + T], part[1])
+        assert np.array_equal(full[2][:, t0:t0 + T], part[2])
+    assert np.all(np.isfinite(full[0])) and np.abs(full[0]).max() > 0
+
+
 def test_full_size_chain64_sampled():
     """The benchmark launch shape (N = 64, P = 2080, ns = 4096, 256 trajectories): one
     evaluation's sampler, S, D and solve, checked on sampled trajectories and entries."""
