@@ -33,7 +33,10 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one gram_tc_kernel launch per trajectory at this workload, from
 # the ncu capture summarised in profiles/gram_tc_chain64_32traj.md (799.1 MB for 32 trajectories;
 # traffic grows in proportion to the trajectories of a launch).
-GRAM_DRAM_BYTES_PER_TRAJ = 799.1e6 / 32
+# DRAM bytes (read + write) of the Gram kernel per trajectory-evaluation, from an ncu capture of
+# one launch of 16 trajectories (O with its 17 extra rows: 283.8 MB read, 105.8 MB written),
+# chain64_jastrow shape
+GRAM_DRAM_BYTES_PER_TRAJ = (283.8e6 + 105.8e6) / 16
 # DRAM bytes (read + write) of the block-column update kernel per trajectory-evaluation, from an
 # ncu capture of all 64 update launches of one evaluation of 32 trajectories (four groups of 8;
 # 44.28 MB per launch), chain64_jastrow shape

@@ -227,7 +227,11 @@ OTVMC_API otvmc_status otvmc_local_estimators_noalloc(const otvmc_ansatz* ansatz
  *          gamma), S_d is [ntraj][P][P] double2 (complex Hermitian, full), obar_d (optional)
  *          [ntraj][P] double2; built as R^T R / ns with R = [[Re O_c, -Im O_c], [Im O_c, Re O_c]]
  *          (the real embedding of S), G_d unused.
- * D_d: [ntraj][P] double2.  Inputs v_d from otvmc_local_estimators. */
+ * D_d: [ntraj][P] double2.  Inputs v_d from otvmc_local_estimators.  Jastrow: D and obar are
+ *          exact integer sums of O against v quantised to 64-bit fixed point (one scale per
+ *          trajectory), converted once to FP64; on the mixed path with ns <= 2^17 the sums come
+ *          out of the same tensor-core pass as G (the digits of the quantised v as extra
+ *          operand rows), with identical results. */
 OTVMC_API otvmc_status otvmc_build_S_F(const otvmc_ansatz* ansatz, const double* theta_d,
                              const uint64_t* spins_d, const double* v_d, int ntraj, int ns,
                              int precision, double* S_d, float* G_d, double* obar_d,

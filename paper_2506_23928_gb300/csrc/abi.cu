@@ -102,12 +102,13 @@ EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.rtab = a->kind == OTVMC_RBM ? (float4*)c.take<char>(rbm_tab_bytes(a, T)) : nullptr;
     b.part_obs = c.take<double>((size_t)T * (nblk > (size_t)obs_blocks(n, ns) ? nblk : obs_blocks(n, ns)) * 9);
     b.dsum = c.take<long long>((size_t)T * a->P * 3);
+    b.dx = a->kind == OTVMC_JASTROW ? c.take<float>((size_t)T * a->P * D_XROWS) : nullptr;
     return b;
 }
 
 static size_t obuf_bytes(const otvmc_ansatz* a, int T, int ns, int precision) {
-    const size_t el = precision == OTVMC_PREC_FP64 ? 8 : 2;
-    return (size_t)T * a->P * ns * el + 256;
+    if (precision == OTVMC_PREC_FP64) return (size_t)T * a->P * ns * 8 + 256;
+    return (size_t)T * (a->P + D_XROWS) * ns * 2 + 256;  // BF16 O and its extra rows
 }
 
 static bool valid_ansatz(const otvmc_ansatz* a) { return a != nullptr && a->model != nullptr && a->P > 0; }
@@ -322,7 +323,7 @@ otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, int n_hidde
             pairs.push_back(j);
             pairs.push_back(k);
         }
-    std::vector<int2> tiles = gram_tiles((int)a->P);
+    std::vector<int2> tiles = gram_tiles_x((int)a->P, (int)a->P + D_XROWS);
     a->ntiles = (int)tiles.size();
     bool ok = true;
     if (!pairs.empty())
@@ -476,16 +477,23 @@ static otvmc_status run_build(const otvmc_ansatz* a, const uint64_t* spins, cons
     const int P = (int)a->P;
     if (!v_parts_ready) CK(launch_vpart(T, ns, v, b, s), "vpart launch");
     CK(launch_vquant(T, ns, v, b, s), "vquant launch");
-    CK(launch_D_fixed_jastrow(a, spins, T, ns, b, obar, D, s), "D launch");
     if (precision == OTVMC_PREC_FP64) {
+        CK(launch_D_fixed_jastrow(a, spins, T, ns, b, obar, D, s), "D launch");
         double* Oc = (double*)obuf;
         CK(launch_obuild_f64_jastrow(a, spins, T, ns, obar, Oc, s), "obuild f64 launch");
         CK(launch_syrk_f64(T, P, ns, Oc, S, s), "syrk launch");
         CK(launch_gemv_D_f64(T, P, ns, Oc, v, b, D, s), "gemv launch");
     } else {
+        // D and obar from the Gram pass (the digits of q as extra rows of O) while the digit
+        // sums stay exact in FP32; else by the integer sums
+        const bool dx = b.dx != nullptr && ns <= D_XROWS_MAX_NS;
+        if (!dx) CK(launch_D_fixed_jastrow(a, spins, T, ns, b, obar, D, s), "D launch");
         uint16_t* Ot = (uint16_t*)obuf;
-        CK(launch_obuild_bf16_jastrow(a, spins, T, ns, Ot, s), "obuild bf16 launch");
-        CK(launch_gram_tc(T, P, ns, Ot, a->tiles_d, a->ntiles, G, status, s), "gram launch");
+        CK(launch_obuild_bf16_jastrow(a, spins, T, ns, dx ? b.qv : nullptr, Ot, s), "obuild bf16 launch");
+        CK(launch_gram_tc(T, P, dx ? P + D_XROWS : P, ns, Ot, a->tiles_d, a->ntiles, G, dx ? b.dx : nullptr, status,
+                          s),
+           "gram launch");
+        if (dx) CK(launch_D_from_gram(a, T, ns, b, obar, D, s), "D launch");
         if (S) CK(launch_expand_S(T, P, ns, G, obar, S, s), "expand launch");
     }
     return OTVMC_OK;

@@ -2,6 +2,8 @@
 // Jastrow ansatz (definitions after Eq. 8: S = <O^* O> - <O^*><O>, F and N^n likewise;
 // D = -i F dt + sum_n N^n dW_n = Cov(O^*, v) with v = -i dt E_eff + sum_n dW_n B^n).
 // Jastrow log-derivatives are real: O_{a_j} = sigma_j, O_{eta_jk} = sigma_j sigma_k (Eq. 12).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace otvmc {
@@ -105,6 +107,42 @@ __global__ void __launch_bounds__(256) D_final_kernel(int P, int ns, const long 
     D[(size_t)t * P + k] = make_double2(dr, di);
 }
 
+// D and obar from the Gram kernel's side output X[t][k][17] (the sums of O_k against the
+// extra rows): sum_x O_k q = sum_p X[p] 256^p for the real (p < 8) and imaginary (8 <= p < 16)
+// digits, in wrapping 64-bit arithmetic (the true sum fits in 64 bits), and c_k = X[16] =
+// sum_x O_k; then the formula of D_final_kernel with 2 a_r - Q_r = sum_x O_k q_r.
+__global__ void __launch_bounds__(256) D_from_gram_kernel(int P, int ns, const float* __restrict__ X,
+                                                          const double* __restrict__ vinfo,
+                                                          const long long* __restrict__ qsum, double* __restrict__ obar,
+                                                          double2* __restrict__ D) {
+    const int t = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const float* x = X + ((size_t)t * P + k) * D_XROWS;
+    unsigned long long sr = 0ull, si = 0ull;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        sr += (unsigned long long)(long long)x[p] << (8 * p);
+        si += (unsigned long long)(long long)x[8 + p] << (8 * p);
+    }
+    const long long c = (long long)x[16];
+    const long long Qr = qsum[2 * t], Qi = qsum[2 * t + 1];
+    const double inv = vinfo[4 * t + 2] / ns;
+    const double dr = ((double)(long long)sr - (double)c * (double)Qr / ns) * inv;
+    const double di = ((double)(long long)si - (double)c * (double)Qi / ns) * inv;
+    obar[(size_t)t * P + k] = (double)c / ns;
+    D[(size_t)t * P + k] = make_double2(dr, di);
+}
+
+cudaError_t launch_D_from_gram(const otvmc_ansatz* a, int ntraj, int ns, const EvalBufs& b, double* obar, double2* D,
+                               cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_D, s);
+    const int P = (int)a->P;
+    D_from_gram_kernel<<<dim3((P + 255) / 256, ntraj), 256, 0, s>>>(P, ns, b.dx, b.vinfo, b.qsum, obar, D);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_D_fixed_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
                                    const EvalBufs& b, double* obar, double2* D, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_D, s);
@@ -138,9 +176,16 @@ __device__ __forceinline__ uint4 bf16_pm1x8(uint32_t e) {
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-__global__ void __launch_bounds__(256) obuild_bf16_jastrow_kernel(int n, int W, int P, int ns,
+__device__ __forceinline__ uint32_t bf16_int_pair(int lo, int hi) {
+    // two small integers (|d| <= 128, exact in BF16) packed as BF16 bits
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)hi)) << 16);
+}
+
+__global__ void __launch_bounds__(256) obuild_bf16_jastrow_kernel(int n, int W, int P, int rows, int ns,
                                                                   const uint64_t* __restrict__ spins,
                                                                   const int* __restrict__ pairs,
+                                                                  const long long* __restrict__ qv,
                                                                   uint16_t* __restrict__ Ot) {
     extern __shared__ uint8_t msk[];  // [n][256]: site masks of each thread's samples
     const int t = blockIdx.y, tid = threadIdx.x;
@@ -159,7 +204,7 @@ __global__ void __launch_bounds__(256) obuild_bf16_jastrow_kernel(int n, int W, 
     }
     __syncthreads();
     if (x0 >= ns) return;
-    uint16_t* base = Ot + (size_t)t * P * ns + x0;
+    uint16_t* base = Ot + (size_t)t * rows * ns + x0;
     const bool vec = (ns % OB_SPT) == 0;  // rows start on 16-byte boundaries and hold whole groups
     for (int k = 0; k < P; ++k) {
         uint32_t e;
@@ -180,12 +225,37 @@ __global__ void __launch_bounds__(256) obuild_bf16_jastrow_kernel(int n, int W, 
                 if (x0 + q < ns) dst[q] = (uint16_t)(wv[q >> 1] >> (16 * (q & 1)));
         }
     }
+    if (qv == nullptr) return;
+    // extra rows P .. P + 16: the balanced base-256 digits d_p in [-128, 127] of q (real part,
+    // then imaginary part; q = sum_p d_p 256^p), then ones (ns is a multiple of 8 here)
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        long long r[OB_SPT];
+#pragma unroll
+        for (int q = 0; q < OB_SPT; ++q) r[q] = (x0 + q < ns) ? qv[((size_t)t * ns + x0 + q) * 2 + h] : 0ll;
+#pragma unroll 1
+        for (int p = 0; p < 8; ++p) {
+            int d[OB_SPT];
+#pragma unroll
+            for (int q = 0; q < OB_SPT; ++q) {
+                d[q] = (int)((r[q] & 0xFF) ^ 0x80) - 0x80;
+                r[q] = (r[q] - d[q]) >> 8;  // exact: r - d is a multiple of 256
+            }
+            *reinterpret_cast<uint4*>(base + (size_t)(P + 8 * h + p) * ns) =
+                make_uint4(bf16_int_pair(d[0], d[1]), bf16_int_pair(d[2], d[3]), bf16_int_pair(d[4], d[5]),
+                           bf16_int_pair(d[6], d[7]));
+        }
+    }
+    *reinterpret_cast<uint4*>(base + (size_t)(P + 16) * ns) = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u,
+                                                                          0x3F803F80u);
 }
 
 cudaError_t launch_obuild_bf16_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
-                                       uint16_t* Ot, cudaStream_t s) {
+                                       const long long* qv, uint16_t* Ot, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_OBUILD, s);
     const int n = a->n, W = (n + 63) / 64, P = (int)a->P;
+    if (qv != nullptr && ns % OB_SPT != 0) return cudaErrorInvalidValue;
+    const int rows = qv != nullptr ? P + D_XROWS : P;
     const int per_block = 256 * OB_SPT;
     dim3 grid((ns + per_block - 1) / per_block, ntraj);
     const size_t smem = (size_t)n * 256;
@@ -194,7 +264,7 @@ cudaError_t launch_obuild_bf16_jastrow(const otvmc_ansatz* a, const uint64_t* sp
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    obuild_bf16_jastrow_kernel<<<grid, 256, smem, s>>>(n, W, P, ns, spins, a->pairs_d, Ot);
+    obuild_bf16_jastrow_kernel<<<grid, 256, smem, s>>>(n, W, P, rows, ns, spins, a->pairs_d, qv, Ot);
     count_launch();
     return cudaGetLastError();
 }

@@ -11,7 +11,9 @@
 //               CTAs per SM, so that one CTA's epilogue overlaps the other's MMAs);
 //   warp 1      allocates 256 TMEM columns; one lane issues tcgen05.mma (M=128, N=256,
 //               K=16, BF16 in, FP32 accumulate in TMEM) and commits each stage back;
-//   warps 2..5  epilogue: tcgen05.ld of their 32 TMEM lanes, FP32 stores of the j >= i part.
+//   warps 2..5  epilogue: tcgen05.ld of their 32 TMEM lanes, FP32 stores of the j >= i part;
+//               operand rows from P on (the digits of the quantised v and a row of ones, on the
+//               mixed Jastrow path) give the columns of a side output X instead.
 // Every mbarrier wait is bounded (2 s of %globaltimer); on timeout the CTA records
 // OTVMC_ERR_TIMEOUT, drains its own copies and MMAs (bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -55,7 +57,8 @@ __device__ __forceinline__ int2 tile_of(int q, int P) {
 
 __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
                                                           int kpad, int npairs, const int2* __restrict__ tiles,
-                                                          float* __restrict__ G, int* status) {
+                                                          float* __restrict__ G, float* __restrict__ X, int nx,
+                                                          int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
@@ -143,11 +146,20 @@ __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__
             const int row = q * 32 + lane;
             const int gi = i0 + row;
             float* Grow = G + ((size_t)t * P + (gi < P ? gi : 0)) * P;
+            // columns P .. P + nx - 1 (extra rows of the operand) of the rows gi < P go to X
+            float* Xrow = (X != nullptr && gi < P) ? X + ((size_t)t * P + gi) * nx : nullptr;
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
                 const int gj0 = j0 + c;
+                if (Xrow != nullptr && gj0 + 31 >= P && gj0 < P + nx) {
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const int gj = gj0 + u;
+                        if (gj >= P && gj < P + nx) Xrow[gj - P] = __uint_as_float(v[u]);
+                    }
+                }
                 if (gi >= P || gj0 + 31 < gi || gj0 >= P) continue;
                 if (gj0 >= gi && gj0 + 31 < P && ((reinterpret_cast<uintptr_t>(Grow + gj0) & 15u) == 0)) {
                     float4* dst = (float4*)(Grow + gj0);
@@ -179,23 +191,27 @@ __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__
 }  // namespace tc
 
 // Upper-triangle tiles (mb, nb) of 128 x 256 that contain some j >= i.
-std::vector<int2> gram_tiles(int P) {
+std::vector<int2> gram_tiles(int P) { return gram_tiles_x(P, P); }
+
+// Tiles (mb, nb) of 128 rows < P by 256 columns < PC (PC >= P) that contain some column >= row.
+std::vector<int2> gram_tiles_x(int P, int PC) {
     std::vector<int2> v;
-    const int MT = (P + tc::BM - 1) / tc::BM, NT = (P + tc::BN - 1) / tc::BN;
+    const int MT = (P + tc::BM - 1) / tc::BM, NT = (PC + tc::BN - 1) / tc::BN;
     for (int mb = 0; mb < MT; ++mb)
         for (int nb = 0; nb < NT; ++nb)
             if ((nb + 1) * tc::BN > mb * tc::BM) v.push_back(make_int2(mb, nb));
     return v;
 }
 
-cudaError_t launch_gram_tc(int ntraj, int P, int ns, const uint16_t* Ot, const int2* tiles, int ntiles, float* G,
-                           int* status, cudaStream_t s) {
+cudaError_t launch_gram_tc(int ntraj, int P, int rows, int ns, const uint16_t* Ot, const int2* tiles, int ntiles,
+                           float* G, float* X, int* status, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_GRAM, s);
+    if (rows < P || (X != nullptr && rows == P)) return cudaErrorInvalidValue;
     auto encode = tc::get_encode();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)ns, (cuuint64_t)P, (cuuint64_t)ntraj};
-    const cuuint64_t strides[2] = {(cuuint64_t)ns * 2, (cuuint64_t)P * ns * 2};
+    const cuuint64_t dims[3] = {(cuuint64_t)ns, (cuuint64_t)rows, (cuuint64_t)ntraj};
+    const cuuint64_t strides[2] = {(cuuint64_t)ns * 2, (cuuint64_t)rows * ns * 2};
     const cuuint32_t box[3] = {(cuuint32_t)tc::BK, 128u, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Ot, dims, strides, box, estr,
@@ -206,7 +222,7 @@ cudaError_t launch_gram_tc(int ntraj, int P, int ns, const uint16_t* Ot, const i
                                          tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid(ntiles, ntraj);
-    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, P, ns, ns, 1, tiles, G, status);
+    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, P, ns, ns, 1, tiles, G, X, X ? rows - P : 0, status);
     count_launch();
     return cudaGetLastError();
 }
@@ -234,7 +250,7 @@ cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16
     if (e != cudaSuccess) return e;
     const int ntiles = (int)gram_tiles(rows).size();
     dim3 grid(ntiles, ntraj);
-    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, rows, kpad, kpad, 6, nullptr, G, status);
+    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, rows, kpad, kpad, 6, nullptr, G, nullptr, 0, status);
     count_launch();
     return cudaGetLastError();
 }

@@ -145,6 +145,31 @@ def test_build_S_F_many_tiles(precision):
         assert rel_err(D[t], evs[t]["D"]) < 1e-10
 
 
+@pytest.mark.parametrize("n,ns", [(22, 136), (22, 4096), (64, 4096)])
+def test_D_from_gram_pass(n, ns):
+    """On the mixed path D and obar come out of the Gram kernel: the quantised centred v enters as
+    extra rows of O (balanced base-256 digits, exact in BF16, digit sums exact in FP32) and a row
+    of ones.  P = 253 needs one more column tile for those rows, P = 2080 has room in its last
+    tile.  obar equals the FP64 path's (exact counts) bit for bit, D agrees with the FP64 path's
+    GEMV to rounding (a digit lost or misplaced would show at 1e-10 or above), and G stays the
+    exact count matrix."""
+    c = Case((n,), h=0.7, kappa=0.1, gamma=0.05)
+    T = 3
+    sig, sp = c.spins(41, T, ns)
+    g = synth.rng(42)
+    v = g.normal(0, 1, (T, ns)) + 1j * g.normal(0, 1, (T, ns))
+    _, G, ob_m, D_m = _build(c, MIXED, T, ns, v, sp, want_S=False)
+    _, _, ob_f, D_f = _build(c, FP64, T, ns, v, sp)
+    assert torch.equal(ob_m, ob_f)
+    D_m, D_f = from_dev_complex(D_m)[..., 0], from_dev_complex(D_f)[..., 0]
+    for t in range(T):
+        assert rel_err(D_m[t], D_f[t]) < 1e-13
+    O = np.concatenate([sig[0].astype(np.float64), np.stack([sig[0][:, j] * sig[0][:, k] for j in range(n)
+                                                             for k in range(j + 1, n)], axis=1)], axis=1)
+    iu = np.triu_indices(c.P)
+    assert np.array_equal(G.cpu().numpy()[0][iu], (O.T @ O)[iu])
+
+
 @pytest.mark.parametrize("precision", [FP64, MIXED])
 def test_solve_step(precision):
     c = Case((16,), kappa=0.1, gamma=0.05)
