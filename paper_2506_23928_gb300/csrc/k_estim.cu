@@ -696,10 +696,11 @@ __global__ void __launch_bounds__(256) observables_kernel(int n, int W, int ns, 
     const bool active = (g < SPP) && (j < n);
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nE = SMEM_E ? n * n : 0;
-    R2* E0 = (R2*)smraw;                     // [n][n] exp(+4 eta) (shared-memory copy)
+    R2* rs = (R2*)smraw;                     // [SPP][NT]
+    unsigned char* un = smraw + (size_t)SPP * NT * sizeof(R2);
+    R2* E0 = (R2*)un;                        // [n][n] exp(+4 eta) (shared-memory copy)
     R2* E1 = E0 + nE;                        // [n][n] exp(-4 eta)
-    R2* rs = E1 + nE;                        // [SPP][NT]
-    double* red = (double*)(rs + SPP * NT);  // [256][9]
+    double* red = (double*)un;               // [256][9], over the tables once the samples are done
     const double2* G0 = Epm + (size_t)t * 2 * n * n;
     const double2* G1 = G0 + n * n;
     if (SMEM_E)
@@ -803,8 +804,11 @@ cudaError_t launch_observables(const otvmc_ansatz* a, const uint64_t* spins, int
     const int nblk = obs_blocks(n, ns);
     dim3 grid(nblk, ntraj);
     const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
-    const size_t base = (size_t)SPP * NT * el + 256 * 9 * 8 + 64;
-    const size_t full = base + 2 * (size_t)n * n * el;
+    // the sample staging, then one region for the exp(+-4 eta) tables and, after them, the
+    // final reduction (at N = 64 in FP32: 66 KB, three CTAs per SM)
+    const size_t red_b = 256 * 9 * 8, tab_b = 2 * (size_t)n * n * el;
+    const size_t base = (size_t)SPP * NT * el + red_b + 64;
+    const size_t full = (size_t)SPP * NT * el + (tab_b > red_b ? tab_b : red_b) + 64;
     const bool sm = full <= 200 * 1024;
     const size_t smem = sm ? full : base;
 #define OTVMC_OBS_LAUNCH(R2, R, SM)                                                                          \
