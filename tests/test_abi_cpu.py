@@ -40,6 +40,18 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(names) == set(abi.SIGNATURES)
 
 
+def test_binding_constants_match_header():
+    """Every enum value the header defines and the binding names has the header's value."""
+    text = open(HEADER).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(OTVMC_\w+)\s*=\s*(\d+)", text)}
+    named = [k for k in consts if hasattr(abi, k)]
+    assert len(named) >= 20
+    for k in named:
+        assert getattr(abi, k) == consts[k], k
+    for k in ("OTVMC_PROFILE_OFF", "OTVMC_PROFILE_ON", "OTVMC_PROFILE_SERIAL", "OTVMC_RBM_T_FACTORED"):
+        assert k in named
+
+
 @pytest.mark.parametrize("extent,alpha,kac,pbc", [((8,), 1.5, False, False), ((10,), 1.0, True, True),
                                                    ((4, 5), 3.0, False, False), ((4, 4), 1.5, False, True)])
 def test_lattice_couplings_match_oracle(lib, extent, alpha, kac, pbc):
