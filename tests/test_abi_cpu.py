@@ -50,6 +50,10 @@ def test_binding_constants_match_header():
         assert getattr(abi, k) == consts[k], k
     for k in ("OTVMC_PROFILE_OFF", "OTVMC_PROFILE_ON", "OTVMC_PROFILE_SERIAL", "OTVMC_RBM_T_FACTORED"):
         assert k in named
+    # kernel classes: the binding lists one name per class, in the header's order
+    classes = sorted((v, k) for k, v in consts.items() if k.startswith("OTVMC_K_") and k != "OTVMC_K_CLASSES")
+    assert [v for v, _ in classes] == list(range(consts["OTVMC_K_CLASSES"]))
+    assert len(abi.KERNEL_CLASSES) == consts["OTVMC_K_CLASSES"]
 
 
 @pytest.mark.parametrize("extent,alpha,kac,pbc", [((8,), 1.5, False, False), ((10,), 1.0, True, True),
