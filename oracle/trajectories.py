@@ -16,8 +16,12 @@ from .model import dense_hamiltonian, dense_jump_ops, coherent_x_state
 
 
 def run_mc(model, ans, ntraj, ns, n_steps, dt, seed, scheme="heun", n_sweep=2, eps=1e-4,
-           traj0=0, theta0=None, measure=True, reg="shift"):
-    """MC otVMC; returns theta (ntraj, P), spins, moments m (n_meas, ntraj, 3), q (.., 3, 3)."""
+           traj0=0, theta0=None, measure=True, reg="shift", push=False):
+    """MC otVMC; returns theta (ntraj, P), spins, moments m (n_meas, ntraj, 3), q (.., 3, 3).
+
+    push=True solves the diagonal-shift system through its Ns x Ns form (tvmc.solve_shift_push,
+    the same delta) and never forms S: for parameter counts far above Ns.
+    """
     P, n = ans.P, ans.n
     n_ops = model.n_ops
     thetas, sigs, ms, qs = [], [], [], []
@@ -37,7 +41,9 @@ def run_mc(model, ans, ntraj, ns, n_steps, dt, seed, scheme="heun", n_sweep=2, e
                     m, q = moments_from_samples(ans, th, sig, w)
                     m_t.append(m)
                     q_t.append(q)
-                ev = tvmc.evaluate(model, ans, th, sig, w, dW, dt)
+                ev = tvmc.evaluate(model, ans, th, sig, w, dW, dt, with_S=not push)
+                if reg == "shift" and push:
+                    return tvmc.solve_shift_push(ev["O"], tvmc.local_v(ev, dW, dt), w, eps)
                 if reg == "shift":
                     return tvmc.solve_shift(ev["S"], ev["D"], eps)
                 return tvmc.solve_snr(ev["S"], ev["D"], ev["O"], tvmc.local_v(ev, dW, dt), w)

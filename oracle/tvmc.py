@@ -81,16 +81,18 @@ def covariance(w, A, B):
     return Ac.T @ (w[:, None] * B) - np.outer(expectation(w, Ac), expectation(w, B))
 
 
-def evaluate(model, ans, theta, sig, w, dW, dt):
+def evaluate(model, ans, theta, sig, w, dW, dt, with_S=True):
     """S, F, N^n and D at theta from configurations sig with weights w.
 
-    D = -i F dt + sum_n N^n dW_n (otVMC procedure paragraph, hbar = 1).
+    D = -i F dt + sum_n N^n dW_n (otVMC procedure paragraph, hbar = 1).  with_S=False skips
+    the P x P matrix S (S is None then), for parameter counts where only the push-through
+    solve below is affordable.
     """
     terms = local_terms(model, ans, theta, sig)
     lpl = expectation(w, terms["LpLd"]).real
     E = effective_energy(terms, lpl)
     O = ans.O(theta, sig)
-    S = covariance(w, O, O)
+    S = covariance(w, O, O) if with_S else None
     F = covariance(w, O, E[:, None])[:, 0]
     N = covariance(w, O, terms["B"])
     D = -1j * F * dt + N @ np.asarray(dW, dtype=np.float64)
@@ -125,6 +127,22 @@ def solve_shift(S, D, eps):
     A = S + eps * np.eye(S.shape[0])
     c = scipy.linalg.cho_factor(A, lower=True)
     return scipy.linalg.cho_solve(c, D)
+
+
+def solve_shift_push(O, v, w, eps):
+    """The same delta as solve_shift(S, D, eps), through a system of size Ns.
+
+    With A = W^(1/2) O_c (rows scaled by sqrt(w), O_c centred) and b = W^(1/2) v_c, the
+    covariances are S = A^+ A and D = A^+ b, and (A^+ A + eps I)^-1 A^+ = A^+ (A A^+ + eps I)^-1
+    (push-through identity), so delta = A^+ (A A^+ + eps I)^-1 b: a Cholesky of Ns x Ns instead
+    of P x P.  For MC weights A A^+ = O_c O_c^+ / Ns.
+    """
+    sw = np.sqrt(np.asarray(w, dtype=np.float64))
+    A = sw[:, None] * (O - expectation(w, O)[None, :])
+    b = sw * (v - expectation(w, v))
+    K = A @ A.conj().T + eps * np.eye(A.shape[0])
+    c = scipy.linalg.cho_factor(K, lower=True)
+    return A.conj().T @ scipy.linalg.cho_solve(c, b)
 
 
 def solve_snr(S, D, O, v, w, snr_thresh=4.0, eps_svd=1e-12):

@@ -143,6 +143,25 @@ def test_shift_solve_residual_and_snr_limit():
     assert np.abs(y - np.linalg.pinv(S) @ D).max() < 1e-10
 
 
+@pytest.mark.parametrize("ns,P,mc", [(40, 90, True), (120, 30, True), (64, 200, False)])
+def test_push_through_solve_equals_shift_solve(ns, P, mc):
+    """The Ns x Ns form of the diagonal-shift solve gives the P x P solve's delta, with P above
+    and below Ns and with non-uniform (exact-expectation) weights."""
+    g = np.random.default_rng(ns + P)
+    O = g.normal(size=(ns, P)) + 1j * g.normal(size=(ns, P))
+    v = g.normal(size=ns) + 1j * g.normal(size=ns)
+    w = tvmc.mc_weights(ns) if mc else g.random(ns)
+    w = w / w.sum()
+    eps = 1e-3
+    S = tvmc.covariance(w, O, O)
+    D = tvmc.covariance(w, O, v[:, None])[:, 0]
+    want = tvmc.solve_shift(S, D, eps)
+    got = tvmc.solve_shift_push(O, v, w, eps)
+    assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
+    # and it solves the P x P system
+    assert np.abs((S + eps * np.eye(P)) @ got - D).max() < 1e-10 * np.abs(D).max()
+
+
 def test_enumeration_tvmc_unitary_ising_is_exact():
     """gamma = 0, h = 0: psi(t) is the Jastrow state eta = -i t J, a = 0."""
     n = 5
