@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rbm-path", action="store_true")
     ap.add_argument("--no-rbm-workloads", action="store_true")
+    ap.add_argument("--no-jastrow-workloads", action="store_true")
     return ap.parse_args()
 
 
@@ -219,7 +220,7 @@ def rbm_path(stream, fp64_value, peaks_):
                                "vs_fp64_jastrow_path": (v_m / fp64_value) if fp64_value else None}}
 
 
-def rbm_workload(name, stream, fp64_value, steps=1, warmup=1):
+def rbm_workload(name, stream, fp64_value, steps=3, warmup=2):
     """A whole RBM workload at its full size on the mixed path (T formed from the factorised
     kernel): chain64_rbm = 128 trajectories whose sample counts go round-robin over
     2048 / 4096 / 8192 (one batch per sample count, the batches run one after another in a
@@ -292,6 +293,57 @@ def rbm_workload(name, stream, fp64_value, steps=1, warmup=1):
                        "solve": "T path (2 ns)", "observables": "off", "workspace_bytes": nb},
             "per_ns": per_ns, "stage_ms_per_step": stage,
             "vs_fp64_jastrow_path": (value / fp64_value) if fp64_value else None}
+
+
+def jastrow_workload(name, stream, precision, steps=3, warmup=2):
+    """A whole Jastrow workload at its full size: every trajectory advanced by one trajectory
+    step per step (observables of the predictor samples included, as in the headline step), in
+    waves of contiguous trajectory ids by device-memory footprint when the batch's workspace
+    exceeds the free memory (one workspace of the largest wave, reused; the waves run one after
+    another).  CUDA events around each step."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2506_23928_gb300 import abi, waves as wv
+    from paper_2506_23928_gb300.abi import check
+    w = synth.WORKLOADS[name]
+    model, ans = build_model(w)
+    P, T, Wd = ans.P, w.ntraj, (w.n + 63) // 64
+    seed = 20261204
+
+    def desc(o, c, step0):
+        return run_desc(w, c, o, step0, 1, precision, seed)
+    torch.cuda.empty_cache()
+    free = torch.cuda.mem_get_info()[0]
+    state = T * (P * 16 + w.ns * Wd * 8 + 9 * 8)
+    budget = int(0.85 * free) - state
+    plan = wv.plan(T, lambda c: abi.otvmc_run_workspace_bytes(ans.handle, desc(0, c, 0)), budget)
+    nb = max(abi.otvmc_run_workspace_bytes(ans.handle, desc(o, c, 0)) for o, c in plan)
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    theta = torch.zeros((T, P, 2), dtype=torch.float64, device="cuda")
+    spins = torch.zeros((T, w.ns, Wd), dtype=torch.int64, device="cuda")
+    check(abi.otvmc_init_chains(ans.handle, T, 0, w.ns, seed, spins, stream))
+    cmax = max(c for _, c in plan)
+    mom = torch.zeros((1, cmax, 9), dtype=torch.float64, device="cuda")
+    per = []
+    for i in range(warmup + steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for o, c in plan:
+            check(abi.otvmc_run_trajectories(ans.handle, desc(o, c, i), theta[o:o + c], spins[o:o + c], mom, work,
+                                             nb, stream))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            per.append(e0.elapsed_time(e1))
+    total_ms = sum(per)
+    del work, theta, spins
+    torch.cuda.empty_cache()
+    return {"value": T * steps / (total_ms / 1000.0), "unit": METRIC, "ms_per_step": total_ms / steps,
+            "ms_per_step_min": min(per), "ms_per_step_max": max(per), "steps": steps, "warmup": warmup,
+            "precision": "mixed" if precision == abi.OTVMC_PREC_MIXED else "fp64",
+            "config": {"workload": name, "N": w.n, "P": P, "ns": w.ns, "ntraj": T, "dt": w.dt, "scheme": w.scheme,
+                       "eps": w.eps, "waves": [list(x) for x in plan], "workspace_bytes": nb}}
 
 
 def cpu_baseline(w, steps=1):
@@ -461,10 +513,11 @@ def main():
     work = {
         # useful tensor flops of G = O^T O (upper triangle incl. diagonal)
         "gram": ("tensor", 2.0 * ns * P * (P + 1) / 2),
-        # BF16 tensor flops of the Cholesky block-column updates: six BF16 products per FP32 product
-        "chol_update": ("tensor", 6 * 2.0 * sum((P - jb) * NBK * jb for jb in jbs if jb > 0)),
-        # BF16 tensor flops of the panel products X = C L_dd^-T: six BF16 products per FP32 product
-        "chol_trsm": ("tensor", 6 * 2.0 * sum(max(0, P - jb - NBK) * NBK * NBK for jb in jbs)),
+        # flops of the method in the Cholesky block-column updates, one product per FP32-level
+        # product (the kernel issues six BF16 piece products for each: see issued_bf16_*)
+        "chol_update": ("tensor", 2.0 * sum((P - jb) * NBK * jb for jb in jbs if jb > 0)),
+        # flops of the method in the panel products X = C L_dd^-T (six BF16 piece products issued each)
+        "chol_trsm": ("tensor", 2.0 * sum(max(0, P - jb - NBK) * NBK * NBK for jb in jbs)),
         # bytes the triangular substitutions must read: the lower factor (FP32) once for the
         # backward pass after the factorization (its forward pass is fused into it) and twice
         # for the correction of the refinement step
@@ -492,6 +545,10 @@ def main():
         traffic = per_te * T * evals / cnt if (per_te and w.name == "chain64_jastrow") else None
         roof[cls] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
                      "traffic": traffic, "peak_kind": kind, "launches": cnt, "ms_total": ms}
+        if cls in ("chol_update", "chol_trsm"):
+            # what the tensor pipe executes: six BF16 piece products per FP32-level product
+            roof[cls]["issued_bf16_tflops"] = 6 * ach
+            roof[cls]["issued_bf16_frac"] = 6 * ach / peak
     # the dominant kernel class among those with a roofline (largest total event time)
     dominant = max(roof, key=lambda k: roof[k]["ms_total"]) if roof else dominant
     rl = roof.get(dominant)
@@ -508,12 +565,21 @@ def main():
         mf = torch.zeros((1, Tf, 9), dtype=torch.float64, device="cuda")
         check(abi.otvmc_run_trajectories(ans.handle, df, thf, spf, mf, wf, nbf, stream))
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        df = run_desc(w, Tf, 0, 1, 1, abi.OTVMC_PREC_FP64, seed)
-        check(abi.otvmc_run_trajectories(ans.handle, df, thf, spf, mf, wf, nbf, stream))
-        torch.cuda.synchronize()
-        fp64 = {"value": Tf / (time.perf_counter() - t0), "unit": METRIC,
-                "sample": f"{Tf} trajectories x 1 step, same workload, FP64 O / S / Cholesky"}
+        n_fp64 = 3
+        per = []
+        for k in range(n_fp64):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            df = run_desc(w, Tf, 0, 1 + k, 1, abi.OTVMC_PREC_FP64, seed)
+            e0.record(stream)
+            check(abi.otvmc_run_trajectories(ans.handle, df, thf, spf, mf, wf, nbf, stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per.append(e0.elapsed_time(e1))
+        med = statistics.median(per)
+        fp64 = {"value": Tf / (med / 1000.0), "unit": METRIC, "ms_per_step_median": med,
+                "ms_per_step_min": min(per), "ms_per_step_max": max(per), "steps": n_fp64, "warmup": 1,
+                "sample": f"{Tf} trajectories x {n_fp64} steps (CUDA events, median) after 1 warm-up step, "
+                          "same workload, FP64 O / S / Cholesky"}
         del wf
 
     rbm = None
@@ -524,6 +590,15 @@ def main():
     if not args.no_rbm_workloads and world == 1:
         rbm_full = {name: rbm_workload(name, stream, fp64["value"] if fp64 else None)
                     for name in ("chain64_rbm", "square16_rbm")}
+
+    jw = None
+    if not args.no_jastrow_workloads and world == 1:
+        del work
+        torch.cuda.empty_cache()
+        jw = {"chain8_jastrow": jastrow_workload("chain8_jastrow", stream, abi.OTVMC_PREC_FP64, steps=20, warmup=3),
+              "chain8_jastrow_mixed": jastrow_workload("chain8_jastrow", stream, abi.OTVMC_PREC_MIXED, steps=20,
+                                                       warmup=3),
+              "square10_jastrow": jastrow_workload("square10_jastrow", stream, abi.OTVMC_PREC_MIXED)}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -544,7 +619,7 @@ def main():
             "kernel_timing": f"CUDA events per launch over {prof_steps} more step(s) after the timed region, "
                              "solver trajectory groups serialised (launch durations not shared)",
             "stage_ms_per_step": stage_ms, "cpu_baseline": cpu, "fp64_path": fp64, "rbm_mixed_path": rbm,
-            "rbm_workloads": rbm_full,
+            "rbm_workloads": rbm_full, "jastrow_workloads": jw,
             "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)

@@ -195,13 +195,19 @@ OTVMC_API otvmc_status otvmc_local_estimators(const otvmc_ansatz* ansatz, const 
  * an interface for callers that cannot give the library scratch memory -- code whose device
  * memory belongs to a memory manager with a hard budget it may not allocate outside of, or a
  * latency-sensitive loop where an allocation, which can synchronise the device, is not
- * acceptable).  Same inputs, outputs and results as otvmc_local_estimators, but no work_d:
- * the scratch is a fixed 32 MiB array inside this library's device memory, held by every GPU
+ * acceptable).  Jastrow ansatz only (an RBM ansatz returns OTVMC_ERR_UNSUPPORTED).  Same
+ * inputs, outputs and results (bit for bit) as otvmc_local_estimators, but no work_d: the
+ * scratch is a fixed 32 MiB array inside this library's device memory, held by every GPU
  * that loads the library until the process exits.  Nothing is allocated by this call.
  *   - Batches whose scratch would exceed 32 MiB are rejected with OTVMC_ERR_WORKSPACE before
- *     anything is launched (about ntraj * ns * N * 16 bytes plus small tables).
- *   - status_d (optional device int, caller-cleared) receives device-side errors such as
- *     OTVMC_ERR_RANGE, as the workspace status word does for the other entry points.
+ *     anything is launched.  The scratch of a batch is about
+ *     ntraj * (16 ns (N + 1) + 16 N^2 + 40 N ceil(ns / b)) bytes, b = 8 floor(256 / N32),
+ *     N32 = N rounded up to a multiple of 32 (flip ratios, E_H, the fixed-point parameter
+ *     tables and the per-block site sums): at N = 64 and 4096 samples, 7 trajectories fit.
+ *   - status_d (optional, caller-cleared): device int[2].  Device-side errors are recorded
+ *     there as in the workspace status word of the other entry points: word 0 the first error
+ *     code (e.g. OTVMC_ERR_RANGE when a parameter field leaves the fixed-point range), word 1
+ *     its detail (the trajectory index).  Both words may be written.
  *   - All calls share the one array: calls that overlap on the GPU (different streams or
  *     threads without ordering) race and give wrong results; order them on one stream.
  *     The array keeps the last call's contents; nothing in it needs to start at zero.
@@ -379,6 +385,16 @@ enum {
 OTVMC_API void otvmc_profile_enable(int on);
 /* Synchronises the recorded events; total milliseconds and launch count of one class. */
 OTVMC_API otvmc_status otvmc_profile_read(int kernel_class, double* total_ms, uint64_t* launches);
+
+/* Test hook (the paper has no counterpart): bound, in nanoseconds, of the pipeline waits of
+ * the tensor-core kernels (Gram, Cholesky update and panel) on the current device; 0 restores
+ * the default of 2 s.  A wait that runs out makes its CTA stop issuing work, drain the copies
+ * and products already in flight (those waits keep the 2 s bound), free its tensor memory and
+ * return; OTVMC_ERR_TIMEOUT is then recorded in the status word and the call's results are
+ * unspecified.  A tiny bound lets a test drive that path; it is not for production use.
+ * Synchronous with respect to the device (a symbol copy); do not call while kernels of this
+ * library run. */
+OTVMC_API otvmc_status otvmc_debug_set_wait_limit(uint64_t ns);
 
 /* Thread-local message describing the last error returned on this thread. */
 OTVMC_API const char* otvmc_last_error(void);

@@ -79,6 +79,7 @@ SIGNATURES = {
     "otvmc_profile_read": (c_int, [c_int, P, P]),
     "otvmc_last_error": (ctypes.c_char_p, []),
     "otvmc_launch_count": (c_uint64, []),
+    "otvmc_debug_set_wait_limit": (c_int, [c_uint64]),
 }
 
 _lib = None
@@ -283,3 +284,7 @@ def otvmc_last_error():
 
 def otvmc_launch_count():
     return _call("otvmc_launch_count")
+
+
+def otvmc_debug_set_wait_limit(ns):
+    return _call("otvmc_debug_set_wait_limit", ns)

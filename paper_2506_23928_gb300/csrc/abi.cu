@@ -106,6 +106,27 @@ EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     return b;
 }
 
+EvalBufs carve_est_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
+    const int n = a->n;
+    const size_t nblk = est_blocks(n, ns), vblk = v_blocks(ns);
+    EvalBufs b{};
+    b.Qre = c.take<long long>((size_t)T * n * n);
+    b.Qim = c.take<long long>((size_t)T * n * n);
+    b.base_re = c.take<long long>((size_t)T * n);
+    b.base_im = c.take<long long>((size_t)T * n);
+    b.r = c.take<double2>((size_t)T * ns * n);
+    b.EH = c.take<double2>((size_t)T * ns);
+    b.part_r = c.take<double2>((size_t)T * nblk * n);
+    b.part_sr = c.take<double2>((size_t)T * nblk * n);
+    b.part_s = c.take<double>((size_t)T * nblk * n);
+    b.mean_r = c.take<double2>((size_t)T * n);
+    b.mean_sr = c.take<double2>((size_t)T * n);
+    b.mean_s = c.take<double>((size_t)T * n);
+    b.part_v = c.take<double2>((size_t)T * vblk);
+    b.part_vmax = c.take<double>((size_t)T * vblk);
+    return b;
+}
+
 static size_t obuf_bytes(const otvmc_ansatz* a, int T, int ns, int precision) {
     if (precision == OTVMC_PREC_FP64) return (size_t)T * a->P * ns * 8 + 256;
     return (size_t)T * (a->P + D_XROWS) * ns * 2 + 256;  // BF16 O and its extra rows
@@ -170,6 +191,13 @@ otvmc_status otvmc_profile_read(int cls, double* total_ms, uint64_t* launches) {
     return OTVMC_OK;
 }
 uint64_t otvmc_launch_count(void) { return g_launches.load(); }
+
+otvmc_status otvmc_debug_set_wait_limit(uint64_t ns) {
+    const unsigned long long v = ns == 0 ? 2000000000ull : (unsigned long long)ns;
+    CK(gram_set_wait_limit(v), "set wait limit (Gram kernel)");
+    CK(chol_set_wait_limit(v), "set wait limit (Cholesky kernels)");
+    return OTVMC_OK;
+}
 
 otvmc_status otvmc_lattice_couplings(int dim, const int* extent, double J, double alpha, int kac, int pbc,
                                      double* J_out_h) {

@@ -120,6 +120,9 @@ constexpr int D_XROWS_MAX_NS = 1 << 17;
 
 size_t eval_bufs_bytes(const otvmc_ansatz* a, int ntraj, int ns);
 EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int ntraj, int ns);
+// Only the buffers of the Jastrow local estimators (prep, est1, site means, est2); the others
+// are null.
+EvalBufs carve_est_bufs(Carver& c, const otvmc_ansatz* a, int ntraj, int ns);
 
 // ---- launchers (return cudaGetLastError of the launch)
 cudaError_t launch_noise(const otvmc_model* m, int ntraj, int traj0, uint64_t seed, int64_t step,
@@ -194,6 +197,15 @@ cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16
                               cudaStream_t s);
 // RBM T path of the mixed path without materialised O (k_rbm_factored.cu)
 size_t rbm_factored_bytes(const otvmc_ansatz* a, int ntraj, int ns);
+// FP64 corrections of the push-through solve of the mixed RBM path (k_rbm_factored.cu)
+constexpr int RBM_PUSH_REFINE = 2;
+size_t rbm_refine_bytes(const otvmc_ansatz* a, int ntraj, int ns);
+cudaError_t launch_rbm_refine_push(const otvmc_ansatz* a, int T, int ns, double eps, int iters,
+                                   const uint64_t* spins, const double2* Td, const double2* obar, const double2* rhs,
+                                   double2* z, void* chol, void* ws, double2* delta, cudaStream_t s);
+cudaError_t launch_rbm_refine_S(const otvmc_ansatz* a, int T, int ns, double eps, int iters, const uint64_t* spins,
+                                const double2* Td, const double2* obar, const double2* vemb, double2* xe, void* chol,
+                                void* ws, double2* delta, cudaStream_t s);
 cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
                                             const double2* v, const double* vinfo, int T, int ns, double eps,
                                             void* ws, double2* delta, int* status, cudaStream_t s);
@@ -219,6 +231,11 @@ cudaError_t launch_chol_solve(int ntraj, int P, int ns, int precision, double ep
                               const float* G, const double* obar, const double2* D, double2* delta,
                               double* shift_used, void* ws, int refine_iters, int* status, cudaStream_t s);
 size_t chol_ws_bytes(int ntraj, int P, int precision);
+// bound of the pipeline waits of the tensor-core kernels of one translation unit (current device)
+cudaError_t gram_set_wait_limit(unsigned long long ns);
+cudaError_t chol_set_wait_limit(unsigned long long ns);
+// x += (L L^T)^-1 r with the factor left in ws by the last mixed (tensor-core) solve of this size
+cudaError_t launch_chol_tc_resolve(int ntraj, int P, void* ws, const double2* r, double2* x, cudaStream_t s);
 cudaError_t launch_sde(int ntraj, int64_t P, int scheme, int stage, const double2* theta, const double2* d0,
                        const double2* d1, double2* out, int* failed, int* status, cudaStream_t s);
 cudaError_t launch_obs_prep(const otvmc_ansatz* a, const double2* theta, int ntraj, bool fp32,

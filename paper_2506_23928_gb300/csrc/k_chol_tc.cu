@@ -195,7 +195,10 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
         const double* ob = obar + (size_t)t * P;
         for (int c = threadIdx.x - 64; c < NB; c += 128) obj_s[c] = jb + c < P ? (float)ob[jb + c] : 0.f;
         int ok = 0;
-        if (lane == 0) ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+        if (lane == 0) {
+            ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+            if (!ok) *abort_flag = 1;  // a wait that ran out here is reported as well
+        }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         fence_after();
         asm volatile("bar.sync 1, 128;" ::: "memory");  // obj_s written by the four epilogue warps
@@ -816,7 +819,10 @@ __global__ void __launch_bounds__(192, 2) chol_panel_kernel(const __nv_bfloat16*
             yb_s[1][c] = yt[P + jb + c];
         }
         int ok = 0;
-        if (lane == 0) ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+        if (lane == 0) {
+            ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+            if (!ok) *abort_flag = 1;  // a wait that ran out here is reported as well
+        }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         fence_after();
         asm volatile("bar.sync 1, 128;" ::: "memory");  // yb_s written by the four epilogue warps
@@ -1158,6 +1164,8 @@ __device__ void sweep_backward(int P, int PY, int LD, const float* Lt, const flo
 //   mode 0: x = L^-T y from the forward result y that the factorization left in yv;
 //   mode 1: r = D - (S + eps I) x with S x = (G x) / ns - obar (obar . x), G x summed from the
 //           residual kernel's slots in FP64; then dx = L^-T L^-1 r and x += dx.
+//   mode 2: the right-hand side D is a residual formed by the caller; dx = L^-T L^-1 D is added
+//           to delta (in place, FP64), with the factor left by an earlier call.
 // The last pass writes delta (and the shift used), the others keep x in xw (FP64).
 __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P, int LD, int ns, double eps, int mode,
                                                                     int last, const double* __restrict__ obar,
@@ -1183,6 +1191,21 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
     double* xt = xw + (size_t)t * 2 * P;
     const double2* Dt = D + (size_t)t * P;
     for (int k = P + tid; k < PY; k += blockDim.x) y[k] = y[PY + k] = 0.f;
+    if (mode == 2) {
+        for (int k = tid; k < P; k += blockDim.x) {
+            y[k] = (float)Dt[k].x;
+            y[PY + k] = (float)Dt[k].y;
+        }
+        __syncthreads();
+        sweep_forward(P, PY, LD, Lt, Dv, y, tb);
+        sweep_backward(P, PY, LD, Lt, Dv, y, tb, red);
+        double2* dt = delta + (size_t)t * P;
+        for (int k = tid; k < P; k += blockDim.x) {
+            const double2 o = dt[k];
+            dt[k] = make_double2(o.x + (double)y[k], o.y + (double)y[PY + k]);
+        }
+        return;
+    }
     if (mode == 0) {
         const float* yt = yv + (size_t)t * 2 * P;
         for (int k = tid; k < P; k += blockDim.x) {
@@ -1284,6 +1307,8 @@ inline GroupStreams& group_streams(cudaStream_t caller) {
 }
 
 }  // namespace chol
+
+cudaError_t chol_set_wait_limit(unsigned long long ns) { return tc::set_wait_limit_tu(ns); }
 
 size_t chol_tc_ws_bytes(int ntraj, int P) {
     using namespace chol;
@@ -1427,6 +1452,36 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     // trajectories whose pivot failed: robust solver with shift retries (exits at once for the others)
     return launch_chol_solve_masked(ntraj, P, ns, eps, G, obar, D, delta, shift_used, Lf, yf, x, refine_iters, fail,
                                     status, s);
+}
+
+// One more correction with the factor that the last launch_chol_tc on this workspace left:
+// x += (L L^T)^-1 r for every trajectory whose pivots did not fail (the others were solved by
+// the fallback with a raised shift and keep x).  r, x: [ntraj][P] double2 (two right-hand sides).
+cudaError_t launch_chol_tc_resolve(int ntraj, int P, void* ws, const double2* r, double2* x, cudaStream_t s) {
+    using namespace chol;
+    const int LD = ldim(P);
+    const size_t nblk = (P + NB - 1) / NB;
+    const int NT = (P + NB - 1) / NB;
+    char* p = (char*)ws;
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return (void*)q;
+    };
+    take((size_t)ntraj * NPC * NT * 128 * LD * 2);
+    float* Lf = (float*)take((size_t)ntraj * P * LD * 4);
+    take((size_t)ntraj * P * NB * 4);
+    float* Dv = (float*)take((size_t)ntraj * nblk * NB * NB * 4);
+    int* fail = (int*)take((size_t)ntraj * 4);
+    const int PY = (int)nblk * NB;
+    const int wsmem = (2 * PY + SW_WARPS * NB * 2 + 2 * NB) * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(chol_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
+    if (e != cudaSuccess) return chol_fail(e, "sweep attribute");
+    ProfScope ps(OTVMC_K_SOLVE, s);
+    chol_sweep_kernel<<<ntraj, SWEEP_THREADS, wsmem, s>>>(0, P, LD, 0, 0.0, 2, 0, nullptr, r, Lf, Dv, nullptr, nullptr,
+                                                           nullptr, x, nullptr, fail);
+    count_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace otvmc

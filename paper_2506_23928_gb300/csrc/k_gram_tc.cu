@@ -139,7 +139,10 @@ __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__
     } else {
         const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
         int ok = 0;
-        if (lane == 0) ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+        if (lane == 0) {
+            ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+            if (!ok) *abort_flag = 1;  // a wait that ran out here is reported as well
+        }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         fence_after();
         if (ok) {
@@ -189,6 +192,8 @@ __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__
 }
 
 }  // namespace tc
+
+cudaError_t gram_set_wait_limit(unsigned long long ns) { return tc::set_wait_limit_tu(ns); }
 
 // Upper-triangle tiles (mb, nb) of 128 x 256 that contain some j >= i.
 std::vector<int2> gram_tiles(int P) { return gram_tiles_x(P, P); }

@@ -62,7 +62,7 @@ extern "C" otvmc_status otvmc_local_estimators_noalloc(const otvmc_ansatz* a, co
     }
     // size of the scratch this call needs, before touching the device
     Carver sz(nullptr, (size_t)-1);
-    carve_eval_bufs(sz, a, ntraj, ns);
+    carve_est_bufs(sz, a, ntraj, ns);
     if (!lpl_d) sz.take<double>((size_t)ntraj * (a->model->nops + 1));
     if (sz.off > NOALLOC_SCRATCH_BYTES) {
         set_error("local_estimators_noalloc: this batch needs " + std::to_string(sz.off) +
@@ -74,7 +74,7 @@ extern "C" otvmc_status otvmc_local_estimators_noalloc(const otvmc_ansatz* a, co
     cudaError_t e = noalloc_scratch(&base);
     if (e != cudaSuccess) return cuda_status(e, "local_estimators_noalloc: scratch address");
     Carver c(base, NOALLOC_SCRATCH_BYTES);
-    EvalBufs b = carve_eval_bufs(c, a, ntraj, ns);
+    EvalBufs b = carve_est_bufs(c, a, ntraj, ns);
     double* lpl = lpl_d ? lpl_d : c.take<double>((size_t)ntraj * (a->model->nops + 1));
     // Every buffer the kernels read below is fully written earlier in this call, so nothing in
     // the shared scratch needs clearing between calls.

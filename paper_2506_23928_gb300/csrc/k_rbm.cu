@@ -828,7 +828,8 @@ size_t rbm_mixed_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
     const size_t kp = (size_t)kpad64((int)K);
     const size_t mx = P > (size_t)ns ? P : (size_t)ns;
     return rup(T * M * ns * 16) + rup(T * P * 16) + rup(T * rows * 3 * kp * 2) + rup(T * rows * rows * 4) +
-           rup(T * rows * 8) + 2 * rup(T * 2 * mx * 16) + chol_ws_bytes(ntraj, (int)rows, OTVMC_PREC_MIXED) + 1024;
+           rup(T * rows * 8) + 2 * rup(T * 2 * mx * 16) + rbm_refine_bytes(a, ntraj, ns) +
+           (tpath ? 0 : rup(T * 2 * P * 16)) + chol_ws_bytes(ntraj, (int)rows, OTVMC_PREC_MIXED) + 1024;
 }
 
 cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16_t* Xs, float* G, int* status,
@@ -836,7 +837,8 @@ cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16
 
 // Whole evaluation's build + solve on the tensor cores: R in three BF16 pieces, the split Gram
 // R^T R or R R^T in FP32 (six piece products), the mixed Cholesky of size 2P or 2 ns with it as
-// its matrix (obar = 0: R is centred) and its refinement against it, then delta from R^T.
+// its matrix (obar = 0: R is centred), then corrections against the FP64 operator applied
+// through the factorisation of O (k_rbm_factored.cu) and delta in FP64.
 // On the T path the ansatz's default (OTVMC_RBM_T_FACTORED) forms T without R instead.
 cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
                                          const double2* v, const double* vinfo, int T, int ns, double eps, void* ws,
@@ -860,6 +862,8 @@ cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* t
     double* zero = (double*)take((size_t)T * rows * 8);
     double2* rhs = (double2*)take((size_t)T * 2 * mx * 16);
     double2* sol = (double2*)take((size_t)T * 2 * mx * 16);
+    void* rws = take(rbm_refine_bytes(a, T, ns));
+    double2* xe = tpath ? nullptr : (double2*)take((size_t)T * 2 * P * 16);
     void* chol = q;
     {
         ProfScope prof_(OTVMC_K_OBUILD, s);
@@ -879,25 +883,18 @@ cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* t
             rbm_split_gemv_kernel<<<dim3((2 * P + 7) / 8, T), 256, 0, s>>>(P, ns, 1, kp, 1.0 / ns, Xs, rhs, sol);
             count_launch();
         }
-        // (S~ + eps I) x = [Re D; Im D], S~ = Gs / ns
-        e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, sol, rhs, nullptr, chol, 1,
+        // (S~ + eps I) x = [Re D~; Im D~], S~ = Gs / ns, then corrections against the FP64 operator
+        e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, sol, xe, nullptr, chol, 0,
                               status, s);
         if (e != cudaSuccess) return e;
-        rbm_unpack_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(P, rhs, delta);
-        count_launch();
-        return cudaGetLastError();
+        return launch_rbm_refine_S(a, T, ns, eps, RBM_PUSH_REFINE, spins, Th, obar, rhs, xe, chol, rws, delta, s);
     }
-    // (T~ + eps I) y = v~, T~ = Gs / ns; delta~ = R^T y / ns
-    e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, rhs, sol, nullptr, chol, 1, status,
+    // (T~ + eps I) y = v~, T~ = Gs / ns, then corrections against the FP64 operator (through the
+    // factorisation of O with the FP64 tanh gamma and obar) and delta = O_c^+ y / ns in FP64
+    e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, rhs, sol, nullptr, chol, 0, status,
                           s);
     if (e != cudaSuccess) return e;
-    {
-        ProfScope prof_(OTVMC_K_D, s);
-        rbm_split_gemv_kernel<<<dim3((2 * P + 255) / 256, T), 256, 0, s>>>(P, ns, 0, kp, 1.0 / ns, Xs, sol, rhs);
-        rbm_unpack_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(P, rhs, delta);
-        count_launch(2);
-    }
-    return cudaGetLastError();
+    return launch_rbm_refine_push(a, T, ns, eps, RBM_PUSH_REFINE, spins, Th, obar, rhs, sol, chol, rws, delta, s);
 }
 
 }  // namespace otvmc

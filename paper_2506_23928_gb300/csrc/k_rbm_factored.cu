@@ -26,123 +26,8 @@ namespace rbmf {
 
 constexpr int TB = 64;   // complex tile of T_c (samples x samples)
 constexpr int MC = 32;   // hidden units per shared-memory chunk
-constexpr int XC = 64;   // samples per chunk of the column sums
-
-// tanh z = s (1 - w) / (1 + w), w = exp(-2 s z), s = sign(Re z), in FP32
-__device__ __forceinline__ float2 ctanh_f(float2 z) {
-    const float s = z.x >= 0.f ? 1.f : -1.f;
-    const float e = expf(-2.f * s * z.x);
-    float sn, cs;
-    sincosf(2.f * z.y, &sn, &cs);
-    const float wr = e * cs, wi = -s * e * sn;
-    const float nr = 1.f - wr, ni = -wi, dr = 1.f + wr, di = wi;
-    const float inv = 1.f / (dr * dr + di * di);
-    return make_float2(s * (nr * dr + ni * di) * inv, s * (ni * dr - nr * di) * inv);
-}
 
 __device__ __forceinline__ bool spin_up(const uint64_t* w, int i) { return (w[i >> 6] >> (i & 63)) & 1ull; }
-
-// t_m(x) = tanh(b_m + sum_i W_im s_i(x)) in FP32, laid out [t][m][x]
-__global__ void __launch_bounds__(256) tanh_f32_kernel(int n, int M, int W, int P, int ns,
-                                                       const double2* __restrict__ theta,
-                                                       const uint64_t* __restrict__ spins, float2* __restrict__ Tf) {
-    const int t = blockIdx.z, m = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= ns) return;
-    const double2* th = theta + (size_t)t * P;
-    const uint64_t* w = spins + ((size_t)t * ns + x) * W;
-    const double2 b = th[n + m];
-    float gr = (float)b.x, gi = (float)b.y;
-    for (int i = 0; i < n; ++i) {
-        const double2 wim = th[n + M + (size_t)i * M + m];
-        const float sg = spin_up(w, i) ? 1.f : -1.f;
-        gr = fmaf(sg, (float)wim.x, gr);
-        gi = fmaf(sg, (float)wim.y, gi);
-    }
-    Tf[((size_t)t * M + m) * ns + x] = ctanh_f(make_float2(gr, gi));
-}
-
-// Column sums over the samples, for columns c = 0..M (c = M stands for the constant 1):
-//     Wsum[t][i][c] = sum_x s_i(x) f_c(x) z(x),   csum[t][c] = sum_x f_c(x) z(x),
-// with f_c = t_c^* (conj = 1) or t_c (conj = 0), and z = 1 when zr is null, else
-// z(x) = zr[x].x + i zr[ns + x].x (real parts of the double2 solution of the embedded system).
-// One CTA per (32 columns, 64 sites, trajectory); lane = column, warp = site residue mod 8.
-// Runs of 64 samples are summed in FP32, the runs in FP64, in a fixed order.
-__global__ void __launch_bounds__(256) colsum_kernel(int n, int M, int W, int ns, int conj,
-                                                     const uint64_t* __restrict__ spins,
-                                                     const float2* __restrict__ Tf, const double2* __restrict__ zr,
-                                                     double2* __restrict__ Wsum, double2* __restrict__ csum) {
-    const int t = blockIdx.z, ib = blockIdx.y, c0 = blockIdx.x * 32;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    __shared__ float2 fz[XC][33];
-    __shared__ uint64_t sb[XC];
-    __shared__ float2 zs[XC];
-    const float2* Tt = Tf + (size_t)t * M * ns;
-    const uint64_t* sp = spins + (size_t)t * ns * W;
-    const int c = c0 + lane;
-    double ar[8], ai[8], sr = 0.0, si = 0.0;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) ar[r] = ai[r] = 0.0;
-    for (int x0 = 0; x0 < ns; x0 += XC) {
-        if (tid < XC) {
-            const int x = x0 + tid;
-            float2 z = make_float2(0.f, 0.f);
-            uint64_t word = 0ull;
-            if (x < ns) {
-                z = zr ? make_float2((float)zr[(size_t)t * 2 * ns + x].x, (float)zr[(size_t)t * 2 * ns + ns + x].x)
-                       : make_float2(1.f, 0.f);
-                word = sp[(size_t)x * W + ib];
-            }
-            zs[tid] = z;
-            sb[tid] = word;
-        }
-        __syncthreads();
-        // f_c(x) z(x) for the chunk: consecutive threads take consecutive samples of a column
-        for (int e = tid; e < XC * 32; e += 256) {
-            const int l = e / XC, xs = e - l * XC;
-            const int cc = c0 + l, x = x0 + xs;
-            float2 f = make_float2(0.f, 0.f);
-            if (x < ns && cc <= M) {
-                f = cc < M ? Tt[(size_t)cc * ns + x] : make_float2(1.f, 0.f);
-                if (conj) f.y = -f.y;
-            }
-            const float2 z = zs[xs];
-            fz[xs][l] = make_float2(f.x * z.x - f.y * z.y, f.x * z.y + f.y * z.x);
-        }
-        __syncthreads();
-        float fr[8], fi[8], gr = 0.f, gi = 0.f;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) fr[r] = fi[r] = 0.f;
-        const int xe = ns - x0 < XC ? ns - x0 : XC;
-        for (int xs = 0; xs < xe; ++xs) {
-            const float2 v = fz[xs][lane];
-            const uint64_t word = sb[xs] >> warp;
-            gr += v.x;
-            gi += v.y;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const bool up = (word >> (8 * r)) & 1ull;
-                fr[r] += up ? v.x : -v.x;
-                fi[r] += up ? v.y : -v.y;
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            ar[r] += (double)fr[r];
-            ai[r] += (double)fi[r];
-        }
-        sr += (double)gr;
-        si += (double)gi;
-        __syncthreads();
-    }
-    if (c > M) return;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int i = ib * 64 + warp + 8 * r;
-        if (i < n) Wsum[((size_t)t * n + i) * (M + 1) + c] = make_double2(ar[r], ai[r]);
-    }
-    if (ib == 0 && warp == 0) csum[(size_t)t * (M + 1) + c] = make_double2(sr, si);
-}
 
 // obar from the sums with z = 1 (conj = 0): a_i = Wsum[i][M], b_m = csum[m], W_im = Wsum[i][m]
 // (delta_mode = 0), or delta from the sums with z the solution (conj = 1): the same entries
@@ -383,21 +268,352 @@ __global__ void rhs_kernel(int ns, const double2* __restrict__ v, const double* 
     u[(size_t)t * 2 * ns + x] = make_double2(val, 0.0);
 }
 
+// ------------------------------------------------------------------ FP64 refinement
+// The FP32 T_c (and the FP32-level factor of T_c + eps I) carry errors of ~1e-7 of |T_c|, which
+// the solve amplifies by up to |T_c| / eps.  The solution is therefore refined against the
+// exact operator, applied through the same factorisation of O in FP64 without forming T:
+//     y = O_c^+ z / ns   (column sums, as for delta),
+//     r = v_c - eps z - O_c y,   z += (L L^T)^-1 r.
+
+// tanh z = s (1 - w) / (1 + w), w = exp(-2 s z), s = sign(Re z), in FP64
+__device__ __forceinline__ double2 ctanh_d(double2 z) {
+    const double s = z.x >= 0.0 ? 1.0 : -1.0;
+    const double e = exp(-2.0 * s * z.x);
+    double sn, cs;
+    sincos(2.0 * z.y, &sn, &cs);
+    const double wr = e * cs, wi = -s * e * sn;
+    const double nr = 1.0 - wr, ni = -wi, dr = 1.0 + wr, di = wi;
+    const double inv = 1.0 / (dr * dr + di * di);
+    return make_double2(s * (nr * dr + ni * di) * inv, s * (ni * dr - nr * di) * inv);
+}
+
+// t_m(x) = tanh(b_m + sum_i W_im s_i(x)) with gamma summed in FP64, laid out [t][m][x] in FP64,
+// and (Tf not null) its FP32 rounding for the FP32 kernels.
+__global__ void __launch_bounds__(256) tanh_f64_kernel(int n, int M, int W, int P, int ns,
+                                                       const double2* __restrict__ theta,
+                                                       const uint64_t* __restrict__ spins, double2* __restrict__ Td,
+                                                       float2* __restrict__ Tf) {
+    const int t = blockIdx.z, m = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= ns) return;
+    const double2* th = theta + (size_t)t * P;
+    const uint64_t* w = spins + ((size_t)t * ns + x) * W;
+    double2 g = th[n + m];
+    for (int i = 0; i < n; ++i) {
+        const double2 wim = th[n + M + (size_t)i * M + m];
+        if (spin_up(w, i)) {
+            g.x += wim.x;
+            g.y += wim.y;
+        } else {
+            g.x -= wim.x;
+            g.y -= wim.y;
+        }
+    }
+    const double2 tv = ctanh_d(g);
+    const size_t o = ((size_t)t * M + m) * ns + x;
+    Td[o] = tv;
+    if (Tf) Tf[o] = make_float2((float)tv.x, (float)tv.y);
+}
+
+constexpr int XD = 32;  // samples per chunk of the FP64 column sums
+
+// Column sums over the samples in FP64, for columns c = 0..M (c = M stands for the constant 1):
+//     Wsum[t][i][c] = sum_x s_i(x) f_c(x) z(x),   csum[t][c] = sum_x f_c(x) z(x),
+// with f_c = t_c^* (conj = 1) or t_c (conj = 0), and z = 1 when zr is null, else
+// z(x) = zr[x].x + i zr[ns + x].x (real parts of the double2 solution of the embedded system).
+// One CTA per (32 columns, 64 sites, trajectory); lane = column, warp = site residue mod 8;
+// a fixed summation order.  Per site the sum is
+// taken as (sum over all samples) - 2 (sum over the samples where s_i = -1): the lanes of a warp
+// share sample and site, so the test does not diverge and half the additions are skipped.
+__global__ void __launch_bounds__(256) colsum_f64_kernel(int n, int M, int W, int ns, int conj,
+                                                         const uint64_t* __restrict__ spins,
+                                                         const double2* __restrict__ Td, const double2* __restrict__ zr,
+                                                         double2* __restrict__ Wsum, double2* __restrict__ csum) {
+    const int t = blockIdx.z, ib = blockIdx.y, c0 = blockIdx.x * 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ double2 fz[XD][33];
+    __shared__ uint64_t sb[XD];
+    __shared__ double2 zs[XD];
+    const double2* Tt = Td + (size_t)t * M * ns;
+    const uint64_t* sp = spins + (size_t)t * ns * W;
+    const int c = c0 + lane;
+    double dr[8], di[8], tr = 0.0, ti = 0.0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) dr[r] = di[r] = 0.0;
+    for (int x0 = 0; x0 < ns; x0 += XD) {
+        if (tid < XD) {
+            const int x = x0 + tid;
+            double2 z = make_double2(0.0, 0.0);
+            uint64_t word = 0ull;
+            if (x < ns) {
+                z = zr ? make_double2(zr[(size_t)t * 2 * ns + x].x, zr[(size_t)t * 2 * ns + ns + x].x)
+                       : make_double2(1.0, 0.0);
+                word = sp[(size_t)x * W + ib];
+            }
+            zs[tid] = z;
+            sb[tid] = word;
+        }
+        __syncthreads();
+        for (int e = tid; e < XD * 32; e += 256) {
+            const int l = e / XD, xs = e - l * XD;
+            const int cc = c0 + l, x = x0 + xs;
+            double2 f = make_double2(0.0, 0.0);
+            if (x < ns && cc <= M) {
+                f = cc < M ? Tt[(size_t)cc * ns + x] : make_double2(1.0, 0.0);
+                if (conj) f.y = -f.y;
+            }
+            fz[xs][l] = cmul(f, zs[xs]);
+        }
+        __syncthreads();
+        const int xe = ns - x0 < XD ? ns - x0 : XD;
+        for (int xs = 0; xs < xe; ++xs) {
+            const double2 v = fz[xs][lane];
+            const uint64_t word = sb[xs] >> warp;
+            tr += v.x;
+            ti += v.y;
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (!((word >> (8 * r)) & 1ull)) {
+                    dr[r] += v.x;
+                    di[r] += v.y;
+                }
+        }
+        __syncthreads();
+    }
+    if (c > M) return;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int i = ib * 64 + warp + 8 * r;
+        if (i < n) Wsum[((size_t)t * n + i) * (M + 1) + c] = make_double2(tr - 2.0 * dr[r], ti - 2.0 * di[r]);
+    }
+    if (ib == 0 && warp == 0) csum[(size_t)t * (M + 1) + c] = make_double2(tr, ti);
+}
+
+constexpr int AS = 16;  // samples per CTA of the residual kernel
+
+// r(x) = v_c(x) - eps z(x) - sum_k (O_k(x) - obar_k) y_k for AS samples per CTA, thread = hidden
+// unit m (M <= 256), in FP64:  sum_k O_k(x) y_k = s.y_a + sum_m t_m(x) (y_b_m + sum_i s_i y_W_im),
+// the site sum taken as (sum_i y_W_im) - 2 (sum over the sites where s_i = -1) (the lanes of a
+// warp share the sample: no divergence).  v_c, z and r are the embedded vectors: .x of
+// [Re; Im] with ns entries each.
+__global__ void __launch_bounds__(256) resid_f64_kernel(int n, int M, int W, int P, int ns, double eps,
+                                                        const uint64_t* __restrict__ spins,
+                                                        const double2* __restrict__ Td, const double2* __restrict__ obar,
+                                                        const double2* __restrict__ y, const double2* __restrict__ rhs,
+                                                        const double2* __restrict__ z, double2* __restrict__ r) {
+    const int t = blockIdx.y, x0 = blockIdx.x * AS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ uint64_t sb[AS][4];
+    __shared__ double cr[256], ci[256];
+    __shared__ double2 red[8][AS];
+    const double2* yt = y + (size_t)t * P;
+    const double2* ob = obar + (size_t)t * P;
+    const uint64_t* sp = spins + (size_t)t * ns * W;
+    double pr = 0.0, pi = 0.0;
+    for (int k = tid; k < P; k += 256) {
+        const double2 o = ob[k], v = yt[k];
+        pr += o.x * v.x - o.y * v.y;
+        pi += o.x * v.y + o.y * v.x;
+    }
+    cr[tid] = pr;
+    ci[tid] = pi;
+    if (tid < AS * W) {
+        const int sI = tid / W, w = tid - sI * W;
+        sb[sI][w] = x0 + sI < ns ? sp[(size_t)(x0 + sI) * W + w] : 0ull;
+    }
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (tid < h) {
+            cr[tid] += cr[tid + h];
+            ci[tid] += ci[tid + h];
+        }
+        __syncthreads();
+    }
+    const int m = tid;
+    double2 acc[AS];
+    if (m < M) {
+        double2 base = yt[n + m];
+        double dnr[AS], dni[AS];
+#pragma unroll
+        for (int q = 0; q < AS; ++q) dnr[q] = dni[q] = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double2 yw = yt[n + M + (size_t)i * M + m];
+            base.x += yw.x;
+            base.y += yw.y;
+#pragma unroll
+            for (int q = 0; q < AS; ++q)
+                if (!((sb[q][i >> 6] >> (i & 63)) & 1ull)) {
+                    dnr[q] += yw.x;
+                    dni[q] += yw.y;
+                }
+        }
+        const double2* Tm = Td + ((size_t)t * M + m) * ns;
+#pragma unroll
+        for (int q = 0; q < AS; ++q) {
+            const double2 tv = x0 + q < ns ? Tm[x0 + q] : make_double2(0.0, 0.0);
+            acc[q] = cmul(tv, make_double2(base.x - 2.0 * dnr[q], base.y - 2.0 * dni[q]));
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < AS; ++q) acc[q] = make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int q = 0; q < AS; ++q) {
+        double vr = acc[q].x, vi = acc[q].y;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            vr += __shfl_xor_sync(0xffffffffu, vr, off);
+            vi += __shfl_xor_sync(0xffffffffu, vi, off);
+        }
+        if (lane == q) red[warp][q] = make_double2(vr, vi);
+    }
+    __syncthreads();
+    if (tid < AS && x0 + tid < ns) {
+        const int x = x0 + tid;
+        double orr = -cr[0], oi = -ci[0];
+        for (int w = 0; w < 8; ++w) {
+            orr += red[w][tid].x;
+            oi += red[w][tid].y;
+        }
+        for (int i = 0; i < n; ++i) {
+            const double2 ya = yt[i];
+            if ((sb[tid][i >> 6] >> (i & 63)) & 1ull) {
+                orr += ya.x;
+                oi += ya.y;
+            } else {
+                orr -= ya.x;
+                oi -= ya.y;
+            }
+        }
+        const size_t b = (size_t)t * 2 * ns;
+        r[b + x] = make_double2(rhs[b + x].x - eps * z[b + x].x - orr, 0.0);
+        r[b + ns + x] = make_double2(rhs[b + ns + x].x - eps * z[b + ns + x].x - oi, 0.0);
+    }
+}
+
+// S path (P <= ns): the embedded right-hand side of a correction, [Re; Im] of g - eps delta
+// (g = O_c^+ w / ns with w = v_c - O_c delta), and the complex delta from the embedded solution.
+__global__ void sres_kernel(int P, double eps, const double2* __restrict__ g, const double2* __restrict__ delta,
+                            double2* __restrict__ r) {
+    const int t = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const double2 gv = g[(size_t)t * P + k], d = delta[(size_t)t * P + k];
+    r[(size_t)t * 2 * P + k] = make_double2(gv.x - eps * d.x, 0.0);
+    r[(size_t)t * 2 * P + P + k] = make_double2(gv.y - eps * d.y, 0.0);
+}
+__global__ void unembed_kernel(int P, const double2* __restrict__ xe, double2* __restrict__ delta) {
+    const int t = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    delta[(size_t)t * P + k] = make_double2(xe[(size_t)t * 2 * P + k].x, xe[(size_t)t * 2 * P + P + k].x);
+}
+
 static size_t rup(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace rbmf
 
+size_t rbm_refine_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
+    using rbmf::rup;
+    const size_t P = (size_t)a->P, M = (size_t)a->m, n = (size_t)a->n, T = (size_t)ntraj, S = (size_t)ns;
+    return rup(T * 2 * S * 16) + rup(T * P * 16) + rup(T * n * (M + 1) * 16) + rup(T * (M + 1) * 16) +
+           rup(T * 2 * P * 16) + 256;
+}
+
+// FP64 refinement of the push-through solve (see above) and delta = O_c^+ z / ns: z [T][2 ns] the
+// embedded solution of the FP32 system (in/out), rhs the embedded v_c, Td the FP64 tanh gamma
+// [T][M][ns], obar the FP64 column means, chol the workspace of the solve that produced z.
+cudaError_t launch_rbm_refine_push(const otvmc_ansatz* a, int T, int ns, double eps, int iters,
+                                   const uint64_t* spins, const double2* Td, const double2* obar, const double2* rhs,
+                                   double2* z, void* chol, void* ws, double2* delta, cudaStream_t s) {
+    using namespace rbmf;
+    const int P = (int)a->P, n = a->n, M = a->m, W = (n + 63) / 64;
+    char* q = (char*)ws;
+    auto take = [&](size_t b) {
+        char* r = q;
+        q += rup(b);
+        return (void*)r;
+    };
+    double2* r = (double2*)take((size_t)T * 2 * ns * 16);
+    double2* y = (double2*)take((size_t)T * P * 16);
+    double2* Wsum = (double2*)take((size_t)T * n * (M + 1) * 16);
+    double2* csum = (double2*)take((size_t)T * (M + 1) * 16);
+    const dim3 cs_grid((M + 1 + 31) / 32, W, T);
+    for (int it = 0; it <= iters; ++it) {
+        double2* out = it == iters ? delta : y;
+        {
+            ProfScope prof_(OTVMC_K_D, s);
+            colsum_f64_kernel<<<cs_grid, 256, 0, s>>>(n, M, W, ns, 1, spins, Td, z, Wsum, csum);
+            finish_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(n, M, P, ns, 1, Wsum, csum, obar, out);
+            count_launch(2);
+        }
+        if (it == iters) break;
+        {
+            ProfScope prof_(OTVMC_K_RESID, s);
+            resid_f64_kernel<<<dim3((ns + AS - 1) / AS, T), 256, 0, s>>>(n, M, W, P, ns, eps, spins, Td, obar, y, rhs,
+                                                                         z, r);
+            count_launch();
+        }
+        cudaError_t e = launch_chol_tc_resolve(T, 2 * ns, chol, r, z, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
 size_t rbm_factored_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
     using rbmf::rup;
     const size_t P = (size_t)a->P, M = (size_t)a->m, n = (size_t)a->n, T = (size_t)ntraj, S = (size_t)ns;
-    return rup(T * M * S * 8) + rup(T * P * 16) + rup(T * S * 8) + rup(T * 4 * S * S * 4) + rup(T * 2 * S * 8) +
-           2 * rup(T * 2 * S * 16) + rup(T * n * (M + 1) * 16) + rup(T * (M + 1) * 16) +
-           chol_ws_bytes(ntraj, (int)(2 * S), OTVMC_PREC_MIXED) + 1024;
+    return rup(T * M * S * 8) + rup(T * M * S * 16) + rup(T * P * 16) + rup(T * S * 8) + rup(T * 4 * S * S * 4) +
+           rup(T * 2 * S * 8) + 2 * rup(T * 2 * S * 16) + rup(T * n * (M + 1) * 16) + rup(T * (M + 1) * 16) +
+           rbm_refine_bytes(a, ntraj, ns) + chol_ws_bytes(ntraj, (int)(2 * S), OTVMC_PREC_MIXED) + 1024;
 }
 
 // Build + solve of one evaluation on the T path (P > ns) of the mixed RBM path, factored:
-// t in FP32, obar (FP64 sums), u', the embedded T_c, the tensor-core Cholesky of size 2 ns with
-// refinement, then delta from the column sums of the solution.
+// t in FP64 (and its FP32 rounding), obar (FP64 column sums), u', the embedded T_c in FP32, the
+// tensor-core Cholesky of size 2 ns, then RBM_PUSH_REFINE corrections against the FP64 operator
+// and delta from the FP64 column sums of the solution.
+// The same corrections on the S path (P <= ns): the solve is (S + eps I) delta = D with
+// S = O_c^+ O_c / ns, D = O_c^+ v_c / ns, so the residual D - (S + eps I) delta is
+// O_c^+ (v_c - O_c delta) / ns - eps delta.  xe [T][2P] is the embedded solution of the FP32
+// system (in/out), vemb [T][2 ns] the embedded v_c; delta receives the refined solution.
+cudaError_t launch_rbm_refine_S(const otvmc_ansatz* a, int T, int ns, double eps, int iters, const uint64_t* spins,
+                                const double2* Td, const double2* obar, const double2* vemb, double2* xe, void* chol,
+                                void* ws, double2* delta, cudaStream_t s) {
+    using namespace rbmf;
+    const int P = (int)a->P, n = a->n, M = a->m, W = (n + 63) / 64;
+    char* q = (char*)ws;
+    auto take = [&](size_t b) {
+        char* r = q;
+        q += rup(b);
+        return (void*)r;
+    };
+    double2* w = (double2*)take((size_t)T * 2 * ns * 16);
+    double2* g = (double2*)take((size_t)T * P * 16);
+    double2* Wsum = (double2*)take((size_t)T * n * (M + 1) * 16);
+    double2* csum = (double2*)take((size_t)T * (M + 1) * 16);
+    double2* re = (double2*)take((size_t)T * 2 * P * 16);
+    const dim3 cs_grid((M + 1 + 31) / 32, W, T);
+    const dim3 pg((P + 255) / 256, T);
+    for (int it = 0; it <= iters; ++it) {
+        unembed_kernel<<<pg, 256, 0, s>>>(P, xe, delta);
+        count_launch();
+        if (it == iters) break;
+        {
+            ProfScope prof_(OTVMC_K_RESID, s);
+            // w = v_c - O_c delta (eps = 0: the z term vanishes)
+            resid_f64_kernel<<<dim3((ns + AS - 1) / AS, T), 256, 0, s>>>(n, M, W, P, ns, 0.0, spins, Td, obar, delta,
+                                                                         vemb, vemb, w);
+            colsum_f64_kernel<<<cs_grid, 256, 0, s>>>(n, M, W, ns, 1, spins, Td, w, Wsum, csum);
+            finish_kernel<<<pg, 256, 0, s>>>(n, M, P, ns, 1, Wsum, csum, obar, g);
+            sres_kernel<<<pg, 256, 0, s>>>(P, eps, g, delta, re);
+            count_launch(4);
+        }
+        cudaError_t e = launch_chol_tc_resolve(T, 2 * P, chol, re, xe, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
                                             const double2* v, const double* vinfo, int T, int ns, double eps,
                                             void* ws, double2* delta, int* status, cudaStream_t s) {
@@ -410,6 +626,7 @@ cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2
         return (void*)r;
     };
     float2* Tf = (float2*)take((size_t)T * M * ns * 8);
+    double2* Td = (double2*)take((size_t)T * M * ns * 16);
     double2* obar = (double2*)take((size_t)T * P * 16);
     float2* up = (float2*)take((size_t)T * ns * 8);
     float* G = (float*)take((size_t)T * 4 * ns * ns * 4);
@@ -418,12 +635,13 @@ cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2
     double2* sol = (double2*)take((size_t)T * 2 * ns * 16);
     double2* Wsum = (double2*)take((size_t)T * n * (M + 1) * 16);
     double2* csum = (double2*)take((size_t)T * (M + 1) * 16);
+    void* rws = take(rbm_refine_bytes(a, T, ns));
     void* chol = q;
     const dim3 cs_grid((M + 1 + 31) / 32, W, T);
     {
         ProfScope prof_(OTVMC_K_OBUILD, s);
-        tanh_f32_kernel<<<dim3((ns + 255) / 256, M, T), 256, 0, s>>>(n, M, W, P, ns, theta, spins, Tf);
-        colsum_kernel<<<cs_grid, 256, 0, s>>>(n, M, W, ns, 0, spins, Tf, nullptr, Wsum, csum);
+        tanh_f64_kernel<<<dim3((ns + 255) / 256, M, T), 256, 0, s>>>(n, M, W, P, ns, theta, spins, Td, Tf);
+        colsum_f64_kernel<<<cs_grid, 256, 0, s>>>(n, M, W, ns, 0, spins, Td, nullptr, Wsum, csum);
         finish_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(n, M, P, ns, 0, Wsum, csum, nullptr, obar);
         center_kernel<<<dim3((ns + 31) / 32, T), 256, 0, s>>>(n, M, W, P, ns, spins, Tf, obar, up);
         rhs_kernel<<<dim3((2 * ns + 255) / 256, T), 256, 0, s>>>(ns, v, vinfo, rhs);
@@ -437,17 +655,12 @@ cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2
     }
     cudaError_t e = cudaMemsetAsync(zero, 0, (size_t)T * 2 * ns * 8, s);
     if (e != cudaSuccess) return e;
-    // (T~ + eps I) y = v~ with T~ = G / ns
-    e = launch_chol_solve(T, 2 * ns, ns, OTVMC_PREC_MIXED, eps, nullptr, G, zero, rhs, sol, nullptr, chol, 1, status,
+    // (T~ + eps I) y = v~ with T~ = G / ns (no refinement against the FP32 G: the corrections
+    // below are taken against the FP64 operator)
+    e = launch_chol_solve(T, 2 * ns, ns, OTVMC_PREC_MIXED, eps, nullptr, G, zero, rhs, sol, nullptr, chol, 0, status,
                           s);
     if (e != cudaSuccess) return e;
-    {
-        ProfScope prof_(OTVMC_K_D, s);
-        colsum_kernel<<<cs_grid, 256, 0, s>>>(n, M, W, ns, 1, spins, Tf, sol, Wsum, csum);
-        finish_kernel<<<dim3((P + 255) / 256, T), 256, 0, s>>>(n, M, P, ns, 1, Wsum, csum, obar, delta);
-        count_launch(2);
-    }
-    return cudaGetLastError();
+    return launch_rbm_refine_push(a, T, ns, eps, RBM_PUSH_REFINE, spins, Td, obar, rhs, sol, chol, rws, delta, s);
 }
 
 }  // namespace otvmc

@@ -11,6 +11,14 @@ namespace otvmc {
 namespace tc {
 
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // bound of every mbarrier wait
+// Bound of the pipeline waits (those that can abort the CTA), normally WAIT_NS; lowered only by
+// otvmc_debug_set_wait_limit, to exercise the timeout path.  The drain waits after an abort
+// (no abort flag) always keep WAIT_NS, so that no copy or MMA is left in flight at exit.
+// One copy per translation unit (no relocatable device code): set through set_wait_limit_tu.
+static __device__ unsigned long long g_wait_limit_ns = WAIT_NS;
+static inline cudaError_t set_wait_limit_tu(unsigned long long ns) {
+    return cudaMemcpyToSymbol(g_wait_limit_ns, &ns, sizeof(ns));
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ unsigned long long gtime() {
@@ -37,11 +45,12 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 }
 // Bounded wait for the phase of the given parity; false on timeout or abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    const unsigned long long lim = abort_flag != nullptr ? g_wait_limit_ns : WAIT_NS;
     const unsigned long long t0 = gtime();
     while (true) {
         if (mbar_try(b, parity)) return true;
         if (abort_flag != nullptr && *abort_flag) return false;
-        if (gtime() - t0 > WAIT_NS) return false;
+        if (gtime() - t0 > lim) return false;
     }
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {

@@ -93,7 +93,8 @@ def _evaluate(c, T, ns, seed, scale, dt):
 
 
 @pytest.mark.parametrize("precision", [FP64, MIXED])
-@pytest.mark.parametrize("n,m,ns,gamma", [(7, 5, 300, 0.0), (10, 12, 96, 0.05), (64, 128, 40, 0.05)])
+@pytest.mark.parametrize("n,m,ns,gamma", [(7, 5, 300, 0.0), (10, 12, 96, 0.05), (64, 128, 40, 0.05),
+                                         (256, 256, 32, 0.0)])  # the square16_rbm shape
 def test_rbm_local_estimators(precision, n, m, ns, gamma):
     """E_eff, v and <L+L^+> against the oracle's local terms (FP64 1e-10, mixed 1e-5)."""
     c = RbmCase(n, m, gamma=gamma)
@@ -200,10 +201,11 @@ def test_rbm_run_matches_oracle(n, m, ns, scheme, precision, tbuild):
                                   theta0=theta0)
     assert np.abs(oth[:, c.n + c.m:] - theta0[c.n + c.m:]).max() > 1e-6  # the weights moved
     assert np.array_equal(unpack(spins, c.n), osig)
-    # the mixed path's S or T is an FP32 sum of split-BF16 products (not exact as for the
-    # Jastrow +-1 counts), so its solve carries ~kappa x 1e-7 relative error: 3e-4 of max|theta|
-    tol = 1e-8 if precision == FP64 else 3e-4
-    assert rel_err(from_dev_complex(theta)[..., 0], oth) < tol
+    # the parameter change over the run, per element against its largest entry: 1e-8 on the
+    # FP64 path, 1e-4 on the mixed path (the theta-dot tolerance of FP32-class paths)
+    got = from_dev_complex(theta)[..., 0]
+    tol = 1e-8 if precision == FP64 else 1e-4
+    assert rel_err(got - theta0, oth - theta0) < tol
     want = np.concatenate([om, oq[..., [0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]]], axis=-1)
     assert rel_err(mom.cpu().numpy(), want) < (1e-8 if precision == FP64 else 1e-4)
 
@@ -233,22 +235,80 @@ def _run(c, precision, T, ns, steps, dt, seed, eps, theta0):
     return from_dev_complex(theta)[..., 0], unpack(spins, c.n), mom.cpu().numpy()
 
 
+def _oracle_step(c, T, ns, dt, seed, eps, theta0):
+    """One midpoint step of the oracle from theta0 on the same draws, the diagonal-shift solve
+    taken through its Ns x Ns form (the same delta; S of P = 8384 or 66048 is not formed)."""
+    oth, osig, _, _ = tr.run_mc(c.omodel, c.oans, T, ns, 1, dt, seed, "midpoint", n_sweep=2, eps=eps,
+                                theta0=theta0, measure=False, push=True)
+    return oth, osig
+
+
+def _oracle_moments(c, theta, sig, chunk=8):
+    """The oracle's per-trajectory moments, summed over chunks of samples (the two-flip ratios
+    of an RBM take (chunk, N, N, M) entries); each chunk carries its weight 1/ns."""
+    ns = sig.shape[0]
+    w = np.full(ns, 1.0 / ns)
+    m = np.zeros(3)
+    q = np.zeros((3, 3))
+    k = 0
+    for x0 in range(0, ns, chunk):
+        mm, qq = moments_from_samples(c.oans, theta, sig[x0:x0 + chunk], w[x0:x0 + chunk])
+        m += mm
+        q += qq
+        k += 1
+    q -= (k - 1) * np.eye(3) / c.n  # the same-site term 2 delta_ab is added once per call
+    return np.concatenate([m, q[[0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]]])
+
+
+def _workload_theta0(c, seed, sd=0.01):
+    """a = b = 0 and W ~ N(0, sd^2) in real and imaginary part, as the RBM workloads start."""
+    g = synth.rng(seed)
+    theta0 = np.zeros(c.P, complex)
+    theta0[c.n + c.m:] = g.normal(0, sd, c.n * c.m) + 1j * g.normal(0, sd, c.n * c.m)
+    return theta0
+
+
 @pytest.mark.parametrize("tbuild", [FACT, MAT])
 @pytest.mark.parametrize("ns", [256, 96])
-def test_rbm_mixed_tensor_core_path_chain64_shape(ns, tbuild):
+def test_rbm_mixed_chain64_shape_matches_oracle(ns, tbuild):
     """The chain64_rbm shape (N = 64, M = 128, P = 8384 > ns: the T path, factored at size
-    2 ns): the mixed path (FP32 sampling and estimators, T from the factorised kernel or the
-    split-BF16 tensor-core product of materialised O, tensor-core Cholesky with refinement)
-    against the FP64 path on the same draws."""
+    2 ns) with dephasing: one midpoint step of the mixed path (FP32 sampling and estimators, T
+    from the factorised kernel or the split-BF16 tensor-core product of materialised O,
+    tensor-core Cholesky, FP64 corrections) against the oracle on the same draws: identical
+    chains, parameter change within 1e-4 of its largest entry, moments of the predictor samples
+    within 1e-5."""
     c = RbmCase(64, 128, gamma=0.05)
     check(abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, tbuild))
-    T, steps, dt, seed, eps = 2, 1, 0.005, 99, 1e-3
+    T, dt, seed, eps = 2, 0.005, 99, 1e-4
     theta0 = synth.random_theta(5, 1, c.P, 0.01)[0]
-    th_m, sp_m, mo_m = _run(c, MIXED, T, ns, steps, dt, seed, eps, theta0)
-    th_f, sp_f, mo_f = _run(c, FP64, T, ns, steps, dt, seed, eps, theta0)
-    # the parameter change of one step (measured ~2e-4 relative: FP32-accumulated T, eps 1e-3)
-    assert rel_err(th_m - theta0, th_f - theta0) < 1e-3
-    assert rel_err(mo_m, mo_f) < 1e-5  # moments of the predictor samples (identical chains at theta_0)
+    th_m, sp_m, mo_m = _run(c, MIXED, T, ns, 1, dt, seed, eps, theta0)
+    oth, osig = _oracle_step(c, T, ns, dt, seed, eps, theta0)
+    assert np.array_equal(sp_m, osig)
+    e = rel_err(th_m - theta0, oth - theta0)
+    assert e < 1e-4, e
+    if ns <= 96:
+        from oracle.philox import initial_spins
+        for t in range(T):
+            sig0, _ = tvmc.metropolis(c.oans, theta0, initial_spins(seed, t, ns, c.n), seed, t, 0, 2)
+            assert rel_err(mo_m[0, t], _oracle_moments(c, theta0, sig0)) < 1e-5
+
+
+@pytest.mark.parametrize("n,m,ns", [(64, 128, 200), (70, 20, 136), (5, 9, 40)])
+def test_rbm_factored_and_materialised_t_match_oracle(n, m, ns):
+    """One step's parameter change on the T path from the factorised T (no O in memory) and
+    from the split-BF16 product of materialised O, both against the oracle on the same draws
+    (two words of spins for N = 70, ragged sample tiles for ns = 136, 200, 40), within 1e-4."""
+    c = RbmCase(n, m, gamma=0.05)
+    assert c.P > ns
+    T, dt, seed, eps = 3, 0.005, 31, 1e-4
+    theta0 = synth.random_theta(8, 1, c.P, 0.05)[0]
+    oth, osig = _oracle_step(c, T, ns, dt, seed, eps, theta0)
+    for tb in (FACT, MAT):
+        check(abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, tb))
+        th, sp, _ = _run(c, MIXED, T, ns, 1, dt, seed, eps, theta0)
+        assert np.array_equal(sp, osig)
+        e = rel_err(th - theta0, oth - theta0)
+        assert e < 1e-4, (tb, e)
 
 
 def test_rbm_t_build_option_validation():
@@ -260,42 +320,29 @@ def test_rbm_t_build_option_validation():
     assert abi.otvmc_ansatz_set_rbm_t_build(j.ans.handle, FACT) == abi.OTVMC_ERR_INVALID
 
 
-@pytest.mark.parametrize("n,m,ns", [(64, 128, 200), (70, 20, 136), (5, 9, 40)])
-def test_rbm_factored_t_equals_materialised(n, m, ns):
-    """One evaluation's parameter change on the T path from the factorised T (no O in memory)
-    and from the split-BF16 product of materialised O, both against the FP64 path on the same
-    draws (two words of spins for N = 70, ragged sample tiles for ns = 136, 200, 40)."""
-    c = RbmCase(n, m, gamma=0.05)
-    assert c.P > ns
-    T, dt, seed, eps = 3, 0.005, 31, 1e-3
-    theta0 = synth.random_theta(8, 1, c.P, 0.05)[0]
-    res = {}
-    for tb in (FACT, MAT):
-        check(abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, tb))
-        res[tb] = _run(c, MIXED, T, ns, 1, dt, seed, eps, theta0)
-    th_d, sp_d, _ = _run(c, FP64, T, ns, 1, dt, seed, eps, theta0)
-    th_f, sp_f, _ = res[FACT]
-    th_m, sp_m, _ = res[MAT]
-    assert np.array_equal(sp_f, sp_d) and np.array_equal(sp_m, sp_d)
-    assert rel_err(th_f - theta0, th_d - theta0) < 1e-3
-    assert rel_err(th_m - theta0, th_d - theta0) < 1e-3
-
-
-def test_rbm_mixed_full_size_chain64_rbm():
-    """The chain64_rbm configuration the benchmark times (N = 64, M = 128, P = 8384, N_s = 2048,
-    T path of size 4096, weights N(0, 0.01^2), shift 1e-4 as in the workload): one trajectory step of
-    the mixed path (factorised T) against the FP64 path on the same draws, on two trajectories:
-    identical chains, parameter change within 1e-3, moments within 1e-5."""
-    w = synth.WORKLOADS["chain64_rbm"]
-    c = RbmCase(w.n, w.n_hidden, h=w.h, kappa=w.kappa, gamma=w.gamma, alpha=w.alpha)
+@pytest.mark.parametrize("workload,ns,T", [("chain64_rbm", 2048, 1), ("square16_rbm", 128, 2)])
+def test_rbm_mixed_workload_shape_matches_oracle(workload, ns, T):
+    """The RBM workloads' models and ansatz shapes with the workloads' shift 1e-4 and initial
+    weights N(0, 0.01^2): chain64_rbm (N = 64, M = 128, P = 8384) at ns = 2048, the smallest
+    sample count of its mix (T path of size 4096), and square16_rbm (16 x 16 lattice, N = M = 256,
+    P = 66048) at ns = 128.  One midpoint step of the mixed path (factorised T) against the
+    oracle on the same draws: identical chains, parameter change within 1e-4."""
+    w = synth.WORKLOADS[workload]
+    import paper_2506_23928_gb300 as pkg
+    c = RbmCase.__new__(RbmCase)
+    c.J = couplings(w.extent, w.J, w.alpha)
+    c.n, c.m = w.n, w.n_hidden
+    c.kappa, c.gamma = np.full(c.n, w.kappa), np.full(c.n, w.gamma)
+    c.omodel = OModel(J=c.J, h=w.h, kappa=c.kappa, gamma=c.gamma)
+    c.oans = RBM(c.n, c.m)
+    c.model = pkg.Model(c.J, w.h, c.kappa, c.gamma)
+    c.ans = pkg.Ansatz(c.model, kind=abi.OTVMC_RBM, n_hidden=c.m)
+    c.P, c.nops, c.W = c.ans.P, c.model.nops, (c.n + 63) // 64
     check(abi.otvmc_ansatz_set_rbm_t_build(c.ans.handle, FACT))
-    T, ns, seed = 2, 2048, 7
-    g = synth.rng(11)
-    theta0 = np.zeros(c.P, complex)
-    theta0[c.n + c.m:] = g.normal(0, 0.01, c.n * c.m) + 1j * g.normal(0, 0.01, c.n * c.m)
-    th_m, sp_m, mo_m = _run(c, MIXED, T, ns, 1, w.dt, seed, w.eps, theta0)
-    th_f, sp_f, mo_f = _run(c, FP64, T, ns, 1, w.dt, seed, w.eps, theta0)
-    assert np.array_equal(sp_m, sp_f)
-    e = rel_err(th_m - theta0, th_f - theta0)
-    assert e < 1e-3, e
-    assert rel_err(mo_m, mo_f) < 1e-5
+    seed = 7
+    theta0 = _workload_theta0(c, 11)
+    th_m, sp_m, _ = _run(c, MIXED, T, ns, 1, w.dt, seed, w.eps, theta0)
+    oth, osig = _oracle_step(c, T, ns, w.dt, seed, w.eps, theta0)
+    assert np.array_equal(sp_m, osig)
+    e = rel_err(th_m - theta0, oth - theta0)
+    assert e < 1e-4, e
