@@ -197,15 +197,21 @@ cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16
                               cudaStream_t s);
 // RBM T path of the mixed path without materialised O (k_rbm_factored.cu)
 size_t rbm_factored_bytes(const otvmc_ansatz* a, int ntraj, int ns);
-// FP64 corrections of the push-through solve of the mixed RBM path (k_rbm_factored.cu)
+// Corrections of the mixed RBM solve against the exact operator (k_rbm_factored.cu)
 constexpr int RBM_PUSH_REFINE = 2;
+size_t rbm_tanh_obar_bytes(const otvmc_ansatz* a, int ntraj);
+cudaError_t launch_rbm_tanh_obar(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int T, int ns,
+                                 double2* Td, float2* Tf, unsigned long long* fmax, double2* obar, void* ws,
+                                 cudaStream_t s);
 size_t rbm_refine_bytes(const otvmc_ansatz* a, int ntraj, int ns);
 cudaError_t launch_rbm_refine_push(const otvmc_ansatz* a, int T, int ns, double eps, int iters,
-                                   const uint64_t* spins, const double2* Td, const double2* obar, const double2* rhs,
-                                   double2* z, void* chol, void* ws, double2* delta, cudaStream_t s);
+                                   const uint64_t* spins, const double2* Td, const unsigned long long* fmax,
+                                   const double2* obar, const double2* rhs, double2* z, void* chol, void* ws,
+                                   double2* delta, cudaStream_t s);
 cudaError_t launch_rbm_refine_S(const otvmc_ansatz* a, int T, int ns, double eps, int iters, const uint64_t* spins,
-                                const double2* Td, const double2* obar, const double2* vemb, double2* xe, void* chol,
-                                void* ws, double2* delta, cudaStream_t s);
+                                const double2* Td, const unsigned long long* fmax, const double2* obar,
+                                const double2* vemb, double2* xe, void* chol, void* ws, double2* delta,
+                                cudaStream_t s);
 cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
                                             const double2* v, const double* vinfo, int T, int ns, double eps,
                                             void* ws, double2* delta, int* status, cudaStream_t s);

@@ -829,7 +829,8 @@ size_t rbm_mixed_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
     const size_t mx = P > (size_t)ns ? P : (size_t)ns;
     return rup(T * M * ns * 16) + rup(T * P * 16) + rup(T * rows * 3 * kp * 2) + rup(T * rows * rows * 4) +
            rup(T * rows * 8) + 2 * rup(T * 2 * mx * 16) + rbm_refine_bytes(a, ntraj, ns) +
-           (tpath ? 0 : rup(T * 2 * P * 16)) + chol_ws_bytes(ntraj, (int)rows, OTVMC_PREC_MIXED) + 1024;
+           (tpath ? 0 : rup(T * 2 * P * 16)) + rup(T * 8) + rbm_tanh_obar_bytes(a, ntraj) +
+           chol_ws_bytes(ntraj, (int)rows, OTVMC_PREC_MIXED) + 1024;
 }
 
 cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16_t* Xs, float* G, int* status,
@@ -864,16 +865,18 @@ cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* t
     double2* sol = (double2*)take((size_t)T * 2 * mx * 16);
     void* rws = take(rbm_refine_bytes(a, T, ns));
     double2* xe = tpath ? nullptr : (double2*)take((size_t)T * 2 * P * 16);
+    unsigned long long* fmax = (unsigned long long*)take((size_t)T * 8);
+    void* tws = take(rbm_tanh_obar_bytes(a, T));
     void* chol = q;
+    cudaError_t e = launch_rbm_tanh_obar(a, theta, spins, T, ns, Th, nullptr, fmax, obar, tws, s);
+    if (e != cudaSuccess) return e;
     {
         ProfScope prof_(OTVMC_K_OBUILD, s);
-        rbm_tanh_kernel<<<dim3((ns + 255) / 256, M, T), 256, 0, s>>>(n, M, W, P, ns, theta, spins, Th);
-        rbm_obar_kernel<<<dim3((P + 7) / 8, T), 256, 0, s>>>(n, M, W, P, ns, spins, Th, obar);
         rbm_Xsplit_kernel<<<dim3(1024, T), 256, 0, s>>>(n, M, W, P, ns, tpath ? 0 : 1, kp, spins, Th, obar, Xs);
         rbm_vtilde_kernel<<<dim3((2 * ns + 255) / 256, T), 256, 0, s>>>(ns, v, vinfo, rhs);
-        count_launch(4);
+        count_launch(2);
     }
-    cudaError_t e = cudaMemsetAsync(zero, 0, (size_t)T * rows * 8, s);
+    e = cudaMemsetAsync(zero, 0, (size_t)T * rows * 8, s);
     if (e != cudaSuccess) return e;
     e = launch_gram_split(T, rows, K, kp, Xs, Gs, status, s);
     if (e != cudaSuccess) return e;
@@ -887,14 +890,16 @@ cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* t
         e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, sol, xe, nullptr, chol, 0,
                               status, s);
         if (e != cudaSuccess) return e;
-        return launch_rbm_refine_S(a, T, ns, eps, RBM_PUSH_REFINE, spins, Th, obar, rhs, xe, chol, rws, delta, s);
+        return launch_rbm_refine_S(a, T, ns, eps, RBM_PUSH_REFINE, spins, Th, fmax, obar, rhs, xe, chol, rws, delta,
+                                   s);
     }
     // (T~ + eps I) y = v~, T~ = Gs / ns, then corrections against the FP64 operator (through the
     // factorisation of O with the FP64 tanh gamma and obar) and delta = O_c^+ y / ns in FP64
     e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, rhs, sol, nullptr, chol, 0, status,
                           s);
     if (e != cudaSuccess) return e;
-    return launch_rbm_refine_push(a, T, ns, eps, RBM_PUSH_REFINE, spins, Th, obar, rhs, sol, chol, rws, delta, s);
+    return launch_rbm_refine_push(a, T, ns, eps, RBM_PUSH_REFINE, spins, Th, fmax, obar, rhs, sol, chol, rws, delta,
+                                  s);
 }
 
 }  // namespace otvmc
