@@ -198,7 +198,10 @@ cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16
 // RBM T path of the mixed path without materialised O (k_rbm_factored.cu)
 size_t rbm_factored_bytes(const otvmc_ansatz* a, int ntraj, int ns);
 // Corrections of the mixed RBM solve against the exact operator (k_rbm_factored.cu)
-constexpr int RBM_PUSH_REFINE = 2;
+// number of corrections: one after the factorised T (FP32 entries from exact integer and short
+// FP32 sums), two after the materialised split-BF16 product (FP32 sums over K = 2P)
+constexpr int RBM_REFINE_FACTORED = 1;
+constexpr int RBM_REFINE_MATERIALISED = 2;
 size_t rbm_tanh_obar_bytes(const otvmc_ansatz* a, int ntraj);
 cudaError_t launch_rbm_tanh_obar(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int T, int ns,
                                  double2* Td, float2* Tf, unsigned long long* fmax, double2* obar, void* ws,

@@ -890,16 +890,16 @@ cudaError_t launch_rbm_build_solve_mixed(const otvmc_ansatz* a, const double2* t
         e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, sol, xe, nullptr, chol, 0,
                               status, s);
         if (e != cudaSuccess) return e;
-        return launch_rbm_refine_S(a, T, ns, eps, RBM_PUSH_REFINE, spins, Th, fmax, obar, rhs, xe, chol, rws, delta,
-                                   s);
+        return launch_rbm_refine_S(a, T, ns, eps, RBM_REFINE_MATERIALISED, spins, Th, fmax, obar, rhs, xe, chol, rws,
+                                   delta, s);
     }
     // (T~ + eps I) y = v~, T~ = Gs / ns, then corrections against the FP64 operator (through the
     // factorisation of O with the FP64 tanh gamma and obar) and delta = O_c^+ y / ns in FP64
     e = launch_chol_solve(T, rows, ns, OTVMC_PREC_MIXED, eps, nullptr, Gs, zero, rhs, sol, nullptr, chol, 0, status,
                           s);
     if (e != cudaSuccess) return e;
-    return launch_rbm_refine_push(a, T, ns, eps, RBM_PUSH_REFINE, spins, Th, fmax, obar, rhs, sol, chol, rws, delta,
-                                  s);
+    return launch_rbm_refine_push(a, T, ns, eps, RBM_REFINE_MATERIALISED, spins, Th, fmax, obar, rhs, sol, chol, rws,
+                                  delta, s);
 }
 
 }  // namespace otvmc

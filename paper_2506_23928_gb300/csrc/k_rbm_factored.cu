@@ -773,7 +773,7 @@ size_t rbm_factored_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
 
 // Build + solve of one evaluation on the T path (P > ns) of the mixed RBM path, factored:
 // t in FP64 (and its FP32 rounding), obar, u', the embedded T_c in FP32, the tensor-core
-// Cholesky of size 2 ns, then RBM_PUSH_REFINE corrections against the exact operator and delta
+// Cholesky of size 2 ns, then RBM_REFINE_FACTORED corrections against the exact operator and delta
 // from the exact column sums of the solution.
 cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins,
                                             const double2* v, const double* vinfo, int T, int ns, double eps,
@@ -819,8 +819,8 @@ cudaError_t launch_rbm_build_solve_factored(const otvmc_ansatz* a, const double2
     e = launch_chol_solve(T, 2 * ns, ns, OTVMC_PREC_MIXED, eps, nullptr, G, zero, rhs, sol, nullptr, chol, 0, status,
                           s);
     if (e != cudaSuccess) return e;
-    return launch_rbm_refine_push(a, T, ns, eps, RBM_PUSH_REFINE, spins, Td, fmax, obar, rhs, sol, chol, rws, delta,
-                                  s);
+    return launch_rbm_refine_push(a, T, ns, eps, RBM_REFINE_FACTORED, spins, Td, fmax, obar, rhs, sol, chol, rws,
+                                  delta, s);
 }
 
 }  // namespace otvmc
