@@ -10,7 +10,7 @@ paper, each citing the equation or section it follows:
   lindblad      exact density matrix, Eq. 1 (RK4; dense Liouvillian for expm checks)
   sse           exact-state trajectories of Eq. 2 (Ito) and Eq. 4-5 (Stratonovich, App. C)
   fossfeig      closed form of App. D (h = 0, periodic chain)
-  ansatz        Jastrow (Eq. 12) and RBM (Eq. 11): log psi, O_k, flip ratios
+  ansatz        Jastrow (Eq. 12), its tied variants LJPHd / LJH, RBM (Eq. 11): log psi, O_k, flip ratios
   tvmc          local estimators, S / F / N^n / D (after Eq. 8), shift and SNR solves,
                 Metropolis sampling, the predictor-corrector step of App. C
   observables   M, C and Wineland xi^2 (LITF paragraph) from local estimators

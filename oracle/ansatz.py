@@ -1,4 +1,5 @@
-"""Variational wavefunctions of the otVMC method: long-range Jastrow (Eq. 12) and RBM (Eq. 11).
+"""Variational wavefunctions of the otVMC method: long-range Jastrow (Eq. 12), its partially
+inhomogeneous variants LJPHd / LJH (paragraph after Eq. 12) and RBM (Eq. 11).
 
 Test infrastructure (oracle side).  sig is an integer array (Ns, N) of sigma_j in {-1, +1}
 (eigenvalues of sz_j, LITF paragraph); theta is a complex vector (P,).
@@ -7,6 +8,9 @@ Parameter layouts (interface with the CUDA library, shared as a convention only)
 * Jastrow, P = N(N+1)/2: theta = [a_0 .. a_{N-1}, eta_jk for j < k in row-major order
   (0,1), (0,2), .., (0,N-1), (1,2), .., (N-2,N-1)].
   log psi = sum_i a_i sigma_i + sum_{j<k} eta_jk sigma_j sigma_k       (Eq. 12)
+* LJPHd / LJH (tied Jastrow): theta = [a_0 .. a_{N-1}, one eta per group of pairs], the
+  groups from lj_groups: the pairs at distance <= d one by one in row-major order, then the
+  pairs of each larger distance together, in increasing distance.  P = N + number of groups.
 * RBM with M hidden units, P = N + M + N M: theta = [a (N), b (M), W (N x M row-major)].
   log psi = sum_i a_i sigma_i + sum_m log(2 cosh gamma_m),
   gamma_m = b_m + sum_i W_im sigma_i                                    (Eq. 11)
@@ -64,6 +68,81 @@ class Jastrow:
         return lr[:, :, None] + lr[:, None, :] + 4.0 * s[:, :, None] * s[:, None, :] * eta[None]
 
 
+def lj_groups(n, d, pbc=False):
+    """Parameter groups of the partially inhomogeneous long-range Jastrow LJPHd (Eq. 12 and the
+    paragraph after it): eta_jk is free for every pair at distance D <= d and shared by all
+    pairs at the same distance D > d.  D = |j - k| for an open chain, or the nearest-image
+    distance min(|j - k|, N - |j - k|) for a periodic one (pbc).  d = 0 is the homogeneous LJH,
+    d >= the largest distance the fully inhomogeneous LJNH (the full Jastrow).
+
+    Returns a list of groups, each a list of pairs (j, k) with j < k: first one group per free
+    pair in row-major order, then one group per shared distance in increasing order.
+    """
+    def dist(j, k):
+        D = k - j
+        return min(D, n - D) if pbc else D
+    pairs = [(j, k) for j in range(n) for k in range(j + 1, n)]
+    groups = [[p] for p in pairs if dist(*p) <= d]
+    for D in sorted({dist(*p) for p in pairs if dist(*p) > d}):
+        groups.append([p for p in pairs if dist(*p) == D])
+    return groups
+
+
+class TiedJastrow:
+    """Long-range Jastrow (Eq. 12) whose two-body parameters are shared within groups of pairs.
+
+    theta = [a_0 .. a_{N-1}, eta_g for each group g]; log psi = sum_i a_i sigma_i +
+    sum_g eta_g sum_{(j,k) in g} sigma_j sigma_k, so O_{eta_g} = sum_{(j,k) in g} sigma_j sigma_k
+    and the flip ratios are those of the full Jastrow with eta_jk = eta_g(j,k).
+    """
+    kind = "jastrow"
+
+    def __init__(self, n, groups):
+        self.n = n
+        self.groups = [list(g) for g in groups]
+        self.P = n + len(self.groups)
+        self.gidx = np.full((n, n), -1, dtype=np.int64)
+        for g, grp in enumerate(self.groups):
+            for j, k in grp:
+                self.gidx[j, k] = self.gidx[k, j] = g
+
+    def split(self, theta):
+        """(a, eta) with eta the full symmetric N x N matrix of the expanded pair parameters."""
+        n = self.n
+        a = theta[:n]
+        eta = np.zeros((n, n), dtype=complex)
+        off = self.gidx >= 0
+        eta[off] = theta[n + self.gidx[off]]
+        return a, eta
+
+    def logpsi(self, theta, sig):
+        a, eta = self.split(theta)
+        s = sig.astype(np.float64)
+        return s @ a + 0.5 * np.einsum("xj,jk,xk->x", s, eta, s)
+
+    def O(self, theta, sig):
+        s = sig.astype(np.float64)
+        cols = [s[:, [j for j, _ in g]] * s[:, [k for _, k in g]] for g in self.groups]
+        two = np.stack([c.sum(axis=1) for c in cols], axis=1) if cols else np.zeros((s.shape[0], 0))
+        return np.concatenate([s, two], axis=1).astype(complex)
+
+    def log_flip_ratios(self, theta, sig):
+        a, eta = self.split(theta)
+        s = sig.astype(np.float64)
+        return -2.0 * s * (a[None, :] + s @ eta.T)
+
+    def log_pair_flip_ratios(self, theta, sig):
+        a, eta = self.split(theta)
+        s = sig.astype(np.float64)
+        lr = self.log_flip_ratios(theta, sig)
+        return lr[:, :, None] + lr[:, None, :] + 4.0 * s[:, :, None] * s[:, None, :] * eta[None]
+
+
+def lj_ansatz(n, d, pbc=False):
+    """LJPHd on N sites (LJH for d = 0)."""
+    return TiedJastrow(n, lj_groups(n, d, pbc))
+
+
 class RBM:
     kind = "rbm"
 
@@ -109,5 +188,7 @@ class RBM:
         return da[:, :, None] + da[:, None, :] + log2cosh(g2).sum(axis=3) - lc0[:, None, None]
 
 
-def make_ansatz(kind, n, m=0):
+def make_ansatz(kind, n, m=0, d=0, pbc=False):
+    if kind == "lj":
+        return lj_ansatz(n, d, pbc)
     return Jastrow(n) if kind == "jastrow" else RBM(n, m)
