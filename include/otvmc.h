@@ -76,7 +76,7 @@ typedef enum otvmc_status {
     OTVMC_ERR_WORKSPACE = 9    /* work_bytes smaller than otvmc_workspace_bytes */
 } otvmc_status;
 
-enum { OTVMC_JASTROW = 0, OTVMC_RBM = 1 };
+enum { OTVMC_JASTROW = 0, OTVMC_RBM = 1, OTVMC_LJ = 2 };
 enum { OTVMC_PREC_FP64 = 0, OTVMC_PREC_MIXED = 1 };
 enum { OTVMC_REG_SHIFT = 0, OTVMC_REG_SNR = 1 };
 enum { OTVMC_HEUN = 0, OTVMC_MIDPOINT = 1 };
@@ -132,6 +132,23 @@ OTVMC_API otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, i
                                  otvmc_ansatz** out);
 OTVMC_API void otvmc_ansatz_destroy(otvmc_ansatz* ansatz);
 OTVMC_API int64_t otvmc_ansatz_nparams(const otvmc_ansatz* ansatz);
+
+/* Partially inhomogeneous long-range Jastrow LJPHd (Eq. 12 and the paragraph after it): the
+ * two-body parameters eta_jk are free for every pair at distance D <= d and shared by all
+ * pairs at the same distance D > d; the biases a_i stay free.  D = |j - k| (pbc = 0) or the
+ * nearest-image distance min(|j - k|, N - |j - k|) (pbc = 1, for a periodic chain).  d = 0 is
+ * the homogeneous LJH; d at least the largest distance gives the full Jastrow (LJNH) with the
+ * OTVMC_JASTROW layout.  theta = [a (N), one eta per group]: first the pairs at distance <= d
+ * one by one in row-major order (j < k), then one parameter per distance D > d in increasing
+ * D.  P = N + number of groups: 2N - 1 - d + N d - d(d+1)/2 for an open chain; N + N d +
+ * floor(N/2) - d for a periodic one with d < N/2 (the paper prints 2N - 1 - d + N d / 2, which
+ * agrees with the open-chain count at d = 0 and d = N - 1 only).
+ * Kind OTVMC_LJ.  Sampling, local estimators and observables run the Jastrow kernels on the
+ * expanded pair parameters (held in the workspace); build_S_F gives S in FP64 (S_d required,
+ * from exact integer counts of the tied log-derivatives O_g = sum over the group of s_j s_k)
+ * and D, obar folded from the exact pair sums, for either precision; solve_step then factors
+ * S in FP64 (G_d unused); otvmc_solve_snr takes it for P <= 96.  N <= 200. */
+OTVMC_API otvmc_status otvmc_ansatz_create_lj(const otvmc_model* model, int d, int pbc, otvmc_ansatz** out);
 
 /* How the MIXED path of run_trajectories forms T = O_c O_c^+ / ns of an RBM on the T path
  * (P > ns; the push-through solve of the otVMC procedure).

@@ -41,11 +41,15 @@ class Model:
 
 
 class Ansatz:
-    """otvmc_ansatz handle: Jastrow (Eq. 12) or RBM with n_hidden hidden units (Eq. 11)."""
+    """otvmc_ansatz handle: Jastrow (Eq. 12), RBM with n_hidden hidden units (Eq. 11), or the tied
+    Jastrow LJPHd (kind OTVMC_LJ, tie distance d, nearest-image distances when pbc)."""
 
-    def __init__(self, model, kind=abi.OTVMC_JASTROW, n_hidden=0):
+    def __init__(self, model, kind=abi.OTVMC_JASTROW, n_hidden=0, d=0, pbc=False):
         out = ctypes.c_void_p()
-        check(abi.otvmc_ansatz_create(model.handle, kind, n_hidden, out))
+        if kind == abi.OTVMC_LJ:
+            check(abi.otvmc_ansatz_create_lj(model.handle, d, int(pbc), out))
+        else:
+            check(abi.otvmc_ansatz_create(model.handle, kind, n_hidden, out))
         self.handle = out.value
         self.model = model
         self.n = model.n

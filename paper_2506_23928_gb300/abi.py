@@ -20,7 +20,7 @@ OTVMC_ERR_NONFINITE = 6
 OTVMC_ERR_RANGE = 7
 OTVMC_ERR_UNSUPPORTED = 8
 OTVMC_ERR_WORKSPACE = 9
-OTVMC_JASTROW, OTVMC_RBM = 0, 1
+OTVMC_JASTROW, OTVMC_RBM, OTVMC_LJ = 0, 1, 2
 OTVMC_PREC_FP64, OTVMC_PREC_MIXED = 0, 1
 OTVMC_REG_SHIFT, OTVMC_REG_SNR = 0, 1
 OTVMC_HEUN, OTVMC_MIDPOINT = 0, 1
@@ -53,6 +53,7 @@ SIGNATURES = {
     "otvmc_model_destroy": (None, [P]),
     "otvmc_model_nops": (c_int, [P]),
     "otvmc_ansatz_create": (c_int, [P, c_int, c_int, P]),
+    "otvmc_ansatz_create_lj": (c_int, [P, c_int, c_int, P]),
     "otvmc_ansatz_destroy": (None, [P]),
     "otvmc_ansatz_nparams": (c_int64, [P]),
     "otvmc_ansatz_set_rbm_t_build": (c_int, [P, c_int]),
@@ -156,6 +157,10 @@ def otvmc_model_nops(model):
 
 def otvmc_ansatz_create(model, kind, n_hidden, out):
     return _call("otvmc_ansatz_create", model, kind, n_hidden, ctypes.addressof(out))
+
+
+def otvmc_ansatz_create_lj(model, d, pbc, out):
+    return _call("otvmc_ansatz_create_lj", model, d, pbc, ctypes.addressof(out))
 
 
 def otvmc_ansatz_destroy(ansatz):

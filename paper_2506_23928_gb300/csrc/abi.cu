@@ -371,8 +371,68 @@ void otvmc_ansatz_destroy(otvmc_ansatz* a) {
     if (!a) return;
     cudaFree(a->pairs_d);
     cudaFree(a->tiles_d);
+    cudaFree(a->grp_off_d);
+    cudaFree(a->grp_pair_d);
+    cudaFree(a->pair_grp_d);
+    otvmc_ansatz_destroy(a->full);
     delete a;
 }
+
+otvmc_status otvmc_ansatz_create_lj(const otvmc_model* model, int d, int pbc, otvmc_ansatz** out) {
+    if (!model || !out || d < 0 || (pbc != 0 && pbc != 1)) return fail(OTVMC_ERR_INVALID, "create_lj: bad arguments");
+    otvmc_ansatz* full = nullptr;
+    otvmc_status st = otvmc_ansatz_create(model, OTVMC_JASTROW, 0, &full);
+    if (st) return st;
+    const int n = model->n;
+    auto dist = [&](int j, int k) { return pbc ? std::min(k - j, n - (k - j)) : k - j; };
+    auto pidx = [&](int j, int k) { return j * n - j * (j + 1) / 2 + (k - j - 1); };
+    // groups: each pair at distance <= d on its own (row-major), then one group per larger distance
+    std::vector<int> off{0}, gpair, pgrp((size_t)n * (n - 1) / 2, -1);
+    for (int j = 0; j < n; ++j)
+        for (int k = j + 1; k < n; ++k)
+            if (dist(j, k) <= d) {
+                pgrp[pidx(j, k)] = (int)off.size() - 1;
+                gpair.push_back(pidx(j, k));
+                off.push_back((int)gpair.size());
+            }
+    for (int D = d + 1; D < n; ++D) {
+        const size_t before = gpair.size();
+        for (int j = 0; j < n; ++j)
+            for (int k = j + 1; k < n; ++k)
+                if (dist(j, k) == D) {
+                    pgrp[pidx(j, k)] = (int)off.size() - 1;
+                    gpair.push_back(pidx(j, k));
+                }
+        if (gpair.size() > before) off.push_back((int)gpair.size());
+    }
+    auto* a = new otvmc_ansatz();
+    a->model = model;
+    a->kind = OTVMC_LJ;
+    a->n = n;
+    a->full = full;
+    a->lj_d = d;
+    a->lj_pbc = pbc;
+    a->ngroups = (int)off.size() - 1;
+    a->P = (int64_t)n + a->ngroups;
+    bool ok = cudaMalloc(&a->grp_off_d, sizeof(int) * off.size()) == cudaSuccess &&
+              cudaMemcpy(a->grp_off_d, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && !gpair.empty())
+        ok = cudaMalloc(&a->grp_pair_d, sizeof(int) * gpair.size()) == cudaSuccess &&
+             cudaMemcpy(a->grp_pair_d, gpair.data(), sizeof(int) * gpair.size(), cudaMemcpyHostToDevice) ==
+                 cudaSuccess &&
+             cudaMalloc(&a->pair_grp_d, sizeof(int) * pgrp.size()) == cudaSuccess &&
+             cudaMemcpy(a->pair_grp_d, pgrp.data(), sizeof(int) * pgrp.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        otvmc_ansatz_destroy(a);
+        return fail(OTVMC_ERR_OOM, "device allocation for the ansatz failed");
+    }
+    *out = a;
+    return OTVMC_OK;
+}
+
+// The ansatz whose kernels run the sampling, estimators and observables: the full Jastrow of a
+// tied Jastrow (on the expanded parameters), else the ansatz itself.
+static const otvmc_ansatz* eval_ansatz(const otvmc_ansatz* a) { return a->kind == OTVMC_LJ ? a->full : a; }
 
 int64_t otvmc_ansatz_nparams(const otvmc_ansatz* a) { return a ? a->P : 0; }
 
@@ -395,6 +455,16 @@ size_t otvmc_workspace_bytes(const otvmc_ansatz* a, int ntraj, int ns, int preci
         const size_t solve = 256 + rbm_solve_bytes(ntraj, (int)a->P) + 1024;
         if (est > m) m = est;
         if (build > m) m = build;
+        if (solve > m) m = solve;
+        return m + 256;
+    }
+    if (a->kind == OTVMC_LJ) {
+        // expanded parameters, then the full Jastrow's evaluation buffers and the tied build, or
+        // the FP64 solve
+        const size_t thf = (size_t)ntraj * a->full->P * 16 + 256;
+        size_t m = thf + eval_bufs_bytes(a->full, ntraj, ns) + (size_t)ntraj * (a->model->nops + 1) * 8 +
+                   lj_build_bytes(a, ntraj, ns) + (size_t)ntraj * a->P * 8 + 2048;
+        const size_t solve = 256 + chol_ws_bytes(ntraj, (int)a->P, OTVMC_PREC_FP64);
         if (solve > m) m = solve;
         return m + 256;
     }
@@ -458,7 +528,15 @@ otvmc_status otvmc_sample(const otvmc_ansatz* a, const double* theta_d, int ntra
            "sample launch");
         return OTVMC_OK;
     }
-    CK(launch_sample_jastrow(a, (const double2*)theta_d, ntraj, traj0, ns, n_sweep, seed, eval_index, spins_d,
+    const double2* th = (const double2*)theta_d;
+    if (a->kind == OTVMC_LJ) {
+        Carver c(work_d, work_bytes);
+        double2* thf = c.take<double2>((size_t)ntraj * a->full->P);
+        if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+        CK(launch_lj_expand(a, ntraj, th, thf, (cudaStream_t)stream), "expand launch");
+        th = thf;
+    }
+    CK(launch_sample_jastrow(eval_ansatz(a), th, ntraj, traj0, ns, n_sweep, seed, eval_index, spins_d,
                              (unsigned long long*)accepted_d, (int*)work_d, (cudaStream_t)stream),
        "sample launch");
     return OTVMC_OK;
@@ -491,11 +569,17 @@ otvmc_status otvmc_local_estimators(const otvmc_ansatz* a, const double* theta_d
         return fail(OTVMC_ERR_INVALID, "unknown precision");
     if ((st = rbm_precision(a, precision))) return st;
     Carver c(work_d, work_bytes);
-    EvalBufs b = carve_eval_bufs(c, a, ntraj, ns);
+    double2* thf = a->kind == OTVMC_LJ ? c.take<double2>((size_t)ntraj * a->full->P) : nullptr;
+    EvalBufs b = carve_eval_bufs(c, eval_ansatz(a), ntraj, ns);
     double* lpl = lpl_d ? lpl_d : c.take<double>((size_t)ntraj * (a->model->nops + 1));
     if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
-    return run_estimators(a, (const double2*)theta_d, spins_d, ntraj, ns, dW_d, dt, precision == OTVMC_PREC_MIXED, b,
-                          lpl, (double2*)Eeff_d, (double2*)v_d, (int*)work_d, (cudaStream_t)stream);
+    const double2* th = (const double2*)theta_d;
+    if (thf) {
+        CK(launch_lj_expand(a, ntraj, th, thf, (cudaStream_t)stream), "expand launch");
+        th = thf;
+    }
+    return run_estimators(eval_ansatz(a), th, spins_d, ntraj, ns, dW_d, dt, precision == OTVMC_PREC_MIXED, b, lpl,
+                          (double2*)Eeff_d, (double2*)v_d, (int*)work_d, (cudaStream_t)stream);
 }
 
 // D (and obar) from v; S or G by precision.
@@ -548,6 +632,22 @@ otvmc_status otvmc_build_S_F(const otvmc_ansatz* a, const double* theta_d, const
            "rbm build launch");
         return OTVMC_OK;
     }
+    if (a->kind == OTVMC_LJ) {
+        if (precision != OTVMC_PREC_FP64 && precision != OTVMC_PREC_MIXED)
+            return fail(OTVMC_ERR_INVALID, "unknown precision");
+        if (!S_d) return fail(OTVMC_ERR_INVALID, "tied Jastrow build needs S_d (FP64 at either precision)");
+        Carver c(work_d, work_bytes);
+        c.take<double2>((size_t)ntraj * a->full->P);  // same layout as the other stages
+        EvalBufs b = carve_eval_bufs(c, a->full, ntraj, ns);
+        char* ws = c.take<char>(lj_build_bytes(a, ntraj, ns));
+        double* obar = obar_d ? obar_d : c.take<double>((size_t)ntraj * a->P);
+        if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+        cudaStream_t s = (cudaStream_t)stream;
+        CK(launch_vpart(ntraj, ns, (const double2*)v_d, b, s), "vpart launch");
+        CK(launch_vquant(ntraj, ns, (const double2*)v_d, b, s), "vquant launch");
+        CK(launch_lj_build(a, spins_d, ntraj, ns, b, ws, S_d, obar, (double2*)D_d, s), "tied build launch");
+        return OTVMC_OK;
+    }
     if (precision == OTVMC_PREC_FP64 && !S_d) return fail(OTVMC_ERR_INVALID, "FP64 build needs S_d");
     if (precision == OTVMC_PREC_MIXED) {
         if (!G_d) return fail(OTVMC_ERR_INVALID, "mixed build needs G_d");
@@ -585,6 +685,11 @@ otvmc_status otvmc_solve_step(const otvmc_ansatz* a, int ntraj, int ns, int prec
            "rbm solve launch");
         return OTVMC_OK;
     }
+    if (a->kind == OTVMC_LJ) {
+        // S of the tied parameters is built in FP64 at either precision: FP64 Cholesky
+        if (!S_d) return fail(OTVMC_ERR_INVALID, "tied Jastrow solve needs S_d");
+        precision = OTVMC_PREC_FP64;
+    }
     if (precision == OTVMC_PREC_FP64 && !S_d) return fail(OTVMC_ERR_INVALID, "FP64 solve needs S_d");
     if (precision == OTVMC_PREC_MIXED && (!G_d || !obar_d))
         return fail(OTVMC_ERR_INVALID, "mixed solve needs G_d and obar_d");
@@ -602,7 +707,7 @@ otvmc_status otvmc_solve_snr(const otvmc_ansatz* a, int ntraj, int ns, const dou
                              void* stream) {
     otvmc_status st = check_batch(a, ntraj, ns);
     if (st) return st;
-    if (a->kind != OTVMC_JASTROW) return fail(OTVMC_ERR_UNSUPPORTED, "solve_snr: only the Jastrow ansatz is built");
+    if (a->kind == OTVMC_RBM) return fail(OTVMC_ERR_UNSUPPORTED, "solve_snr: built for the Jastrow ansaetze");
     if (a->P > SNR_PMAX)
         return fail(OTVMC_ERR_UNSUPPORTED, "solve_snr: built for P <= " + std::to_string(SNR_PMAX));
     if (!S_d || !obar_d || !spins_d || !v_d || !D_d || !delta_d || !work_d || !(snr_thresh >= 0.0) ||
@@ -635,22 +740,28 @@ otvmc_status otvmc_observables(const otvmc_ansatz* a, const double* theta_d, con
     if (st) return st;
     if (!theta_d || !spins_d || !moments_d || !work_d) return fail(OTVMC_ERR_INVALID, "observables: bad arguments");
     Carver c(work_d, work_bytes);
-    EvalBufs b = carve_eval_bufs(c, a, ntraj, ns);
+    double2* thf = a->kind == OTVMC_LJ ? c.take<double2>((size_t)ntraj * a->full->P) : nullptr;
+    const otvmc_ansatz* e = eval_ansatz(a);
+    EvalBufs b = carve_eval_bufs(c, e, ntraj, ns);
     double* lpl = c.take<double>((size_t)ntraj * (a->model->nops + 1));
     if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     const bool fp32 = precision == OTVMC_PREC_MIXED;
     if ((st = rbm_precision(a, precision))) return st;
-    st = run_estimators(a, (const double2*)theta_d, spins_d, ntraj, ns, nullptr, 0.0, fp32, b, lpl, nullptr, nullptr,
-                        (int*)work_d, s);
+    const double2* th = (const double2*)theta_d;
+    if (thf) {
+        CK(launch_lj_expand(a, ntraj, th, thf, s), "expand launch");
+        th = thf;
+    }
+    st = run_estimators(e, th, spins_d, ntraj, ns, nullptr, 0.0, fp32, b, lpl, nullptr, nullptr, (int*)work_d, s);
     if (st) return st;
     if (a->kind == OTVMC_RBM) {
-        CK(launch_obs_rbm(a, (const double2*)theta_d, spins_d, ntraj, ns, fp32, b, s), "observables launch");
+        CK(launch_obs_rbm(a, th, spins_d, ntraj, ns, fp32, b, s), "observables launch");
         CK(launch_obs_final(a->n, ns, ntraj, b, moments_d, s), "observables launch");
         return OTVMC_OK;
     }
-    CK(launch_obs_prep(a, (const double2*)theta_d, ntraj, fp32, b, s), "obs prep launch");
-    CK(launch_observables(a, spins_d, ntraj, ns, fp32, b, moments_d, s), "observables launch");
+    CK(launch_obs_prep(e, th, ntraj, fp32, b, s), "obs prep launch");
+    CK(launch_observables(e, spins_d, ntraj, ns, fp32, b, moments_d, s), "observables launch");
     return OTVMC_OK;
 }
 
@@ -736,6 +847,7 @@ struct RunBufs {
     double* lcr;
     float4* tab;   // RBM flip table of the FP32 sampler
     void* rbm;     // RBM build scratch
+    double2* thf;  // tied Jastrow: the expanded parameters of the full Jastrow
     EvalBufs eb;
 };
 
@@ -743,7 +855,8 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
     const int T = d->ntraj, ns = d->ns;
     const size_t P = (size_t)a->P;
     RunBufs r;
-    r.eb = carve_eval_bufs(c, a, T, ns);
+    r.thf = a->kind == OTVMC_LJ ? c.take<double2>((size_t)T * a->full->P) : nullptr;
+    r.eb = carve_eval_bufs(c, a->kind == OTVMC_LJ ? a->full : a, T, ns);
     r.theta_c = c.take<double2>(T * P);
     r.d0 = c.take<double2>(T * P);
     r.d1 = c.take<double2>(T * P);
@@ -771,6 +884,14 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
             r.rbm = c.take<char>(rbm_build_bytes(a, T, ns));
             r.chol = c.take<char>(chol_ws_bytes(T, 2 * (int)(P <= (size_t)ns ? P : (size_t)ns), OTVMC_PREC_FP64));
         }
+        return r;
+    }
+    if (a->kind == OTVMC_LJ) {
+        // S of the tied parameters in FP64 from exact integer counts, FP64 Cholesky
+        r.S = c.take<double>(T * P * P);
+        r.G = nullptr;
+        r.obuf = c.take<char>(lj_build_bytes(a, T, ns));
+        r.chol = c.take<char>(chol_ws_bytes(T, (int)P, OTVMC_PREC_FP64));
         return r;
     }
     if (d->precision == OTVMC_PREC_FP64) {
@@ -801,7 +922,7 @@ static otvmc_status check_run(const otvmc_ansatz* a, const otvmc_run_desc* d) {
     if ((st = rbm_precision(a, d->precision))) return st;
     if (a->kind == OTVMC_RBM && d->reg != OTVMC_REG_SHIFT)
         return fail(OTVMC_ERR_UNSUPPORTED, "the SNR regulariser is built for the Jastrow ansatz");
-    if (d->reg == OTVMC_REG_SNR && a->kind == OTVMC_JASTROW && (a->P > SNR_PMAX || !(d->snr_thresh >= 0.0)))
+    if (d->reg == OTVMC_REG_SNR && a->kind != OTVMC_RBM && (a->P > SNR_PMAX || !(d->snr_thresh >= 0.0)))
         return fail(OTVMC_ERR_UNSUPPORTED, "SNR regulariser: built for P <= " + std::to_string(SNR_PMAX) +
                                                " (one CTA per trajectory) and snr_thresh >= 0");
     return OTVMC_OK;
@@ -913,24 +1034,36 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
                "rbm build/solve launch");
         return OTVMC_OK;
     }
-    CK(launch_sample_jastrow(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, nullptr, status, s),
+    // the tied Jastrow samples, estimates and measures through the full Jastrow's kernels
+    const otvmc_ansatz* e = eval_ansatz(a);
+    const double2* th = theta;
+    if (a->kind == OTVMC_LJ) {
+        CK(launch_lj_expand(a, T, theta, r.thf, s), "expand launch");
+        th = r.thf;
+    }
+    CK(launch_sample_jastrow(e, th, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, nullptr, status, s),
        "sample launch");
-    otvmc_status st = run_estimators(a, theta, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s);
+    otvmc_status st = run_estimators(e, th, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s);
     if (st) return st;
     if (moments_row) {
-        CK(launch_obs_prep(a, theta, T, fp32, r.eb, s), "obs prep launch");
-        CK(launch_observables(a, spins, T, ns, fp32, r.eb, moments_row, s), "observables launch");
+        CK(launch_obs_prep(e, th, T, fp32, r.eb, s), "obs prep launch");
+        CK(launch_observables(e, spins, T, ns, fp32, r.eb, moments_row, s), "observables launch");
     }
-    st = run_build(a, spins, r.v, T, ns, d->precision, true, r.eb, r.obuf, r.S, r.G, r.obar, r.D, status, s);
-    if (st) return st;
+    if (a->kind == OTVMC_LJ) {
+        CK(launch_vquant(T, ns, r.v, r.eb, s), "vquant launch");
+        CK(launch_lj_build(a, spins, T, ns, r.eb, r.obuf, r.S, r.obar, r.D, s), "tied build launch");
+    } else {
+        st = run_build(a, spins, r.v, T, ns, d->precision, true, r.eb, r.obuf, r.S, r.G, r.obar, r.D, status, s);
+        if (st) return st;
+    }
     if (d->reg == OTVMC_REG_SNR) {
         CK(launch_snr_solve(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr, status,
                             s),
            "snr solve launch");
         return OTVMC_OK;
     }
-    CK(launch_chol_solve(T, (int)a->P, ns, d->precision, d->eps, r.S, r.G, r.obar, r.D, delta, nullptr, r.chol, 1,
-                         status, s),
+    CK(launch_chol_solve(T, (int)a->P, ns, a->kind == OTVMC_LJ ? OTVMC_PREC_FP64 : d->precision, d->eps, r.S, r.G,
+                         r.obar, r.D, delta, nullptr, r.chol, 1, status, s),
        "solve launch");
     return OTVMC_OK;
 }
@@ -967,21 +1100,26 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
             CK(sample_rbm_any(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, r.gam, r.lcr, r.tab, nullptr,
                                  s),
                "sample launch");
-        else
-            CK(launch_sample_jastrow(a, theta, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, nullptr, status,
-                                     s),
+        const otvmc_ansatz* e = eval_ansatz(a);
+        const double2* th = theta;
+        if (a->kind == OTVMC_LJ) {
+            CK(launch_lj_expand(a, T, theta, r.thf, s), "expand launch");
+            th = r.thf;
+        }
+        if (!rbm)
+            CK(launch_sample_jastrow(e, th, T, d->traj0, d->ns, d->n_sweep, d->seed, ev, spins_d, nullptr, status, s),
                "sample launch");
         const bool fp32 = d->precision == OTVMC_PREC_MIXED;
-        otvmc_status st = run_estimators(a, theta, spins_d, T, d->ns, nullptr, 0.0, fp32, r.eb, r.lpl, nullptr,
-                                         nullptr, status, s);
+        otvmc_status st = run_estimators(e, th, spins_d, T, d->ns, nullptr, 0.0, fp32, r.eb, r.lpl, nullptr, nullptr,
+                                         status, s);
         if (st) return st;
         double* mrow = moments_d + (size_t)row * mstride * OTVMC_MOMENTS;
         if (rbm) {
             CK(launch_obs_rbm(a, theta, spins_d, T, d->ns, fp32, r.eb, s), "observables launch");
             CK(launch_obs_final(a->n, d->ns, T, r.eb, mrow, s), "observables launch");
         } else {
-            CK(launch_obs_prep(a, theta, T, fp32, r.eb, s), "obs prep launch");
-            CK(launch_observables(a, spins_d, T, d->ns, fp32, r.eb, mrow, s), "observables launch");
+            CK(launch_obs_prep(e, th, T, fp32, r.eb, s), "obs prep launch");
+            CK(launch_observables(e, spins_d, T, d->ns, fp32, r.eb, mrow, s), "observables launch");
         }
     }
     return OTVMC_OK;

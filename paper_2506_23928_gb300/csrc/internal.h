@@ -33,6 +33,14 @@ struct otvmc_ansatz {
     int2* tiles_d = nullptr; // upper-triangle tiles of the tensor-core Gram kernel
     int ntiles = 0;
     int rbm_t_build = 0;     // OTVMC_RBM_T_FACTORED or OTVMC_RBM_T_MATERIALISED
+    // Tied Jastrow (OTVMC_LJ): the full Jastrow of the same model, on which sampling, local
+    // estimators, observables and the pair-level sums run with the expanded parameters, and the
+    // groups of pairs that share a parameter (pairs by their full-Jastrow pair index).
+    otvmc_ansatz* full = nullptr;
+    int lj_d = 0, lj_pbc = 0, ngroups = 0;
+    int* grp_off_d = nullptr;   // [ngroups + 1]
+    int* grp_pair_d = nullptr;  // [N(N-1)/2], grouped
+    int* pair_grp_d = nullptr;  // [N(N-1)/2] group of each pair
 };
 
 namespace otvmc {
@@ -228,6 +236,13 @@ inline size_t rbm_tab_bytes(const otvmc_ansatz* a, int ntraj) {
 inline size_t rbm_sample_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
     return (size_t)ntraj * a->m * ns * (16 + 8) + rbm_tab_bytes(a, ntraj) + 1024;
 }
+
+// tied Jastrow (k_lj.cu)
+cudaError_t launch_lj_expand(const otvmc_ansatz* a, int ntraj, const double2* theta, double2* theta_full,
+                             cudaStream_t s);
+size_t lj_build_bytes(const otvmc_ansatz* a, int ntraj, int ns);
+cudaError_t launch_lj_build(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const EvalBufs& b,
+                            void* ws, double* S, double* obar, double2* D, cudaStream_t s);
 
 // SNR-filtered eigen pseudo-inverse (one CTA per trajectory, P <= SNR_PMAX)
 constexpr int SNR_PMAX = 96;

@@ -30,16 +30,28 @@ __device__ __forceinline__ void rr_pair(int m, int r, int k, int& p, int& q) {
     }
 }
 
-// Jastrow O_k(x) - obar_k: k < n single sigma_j, else the pair (j, l) of pair index k - n.
-__device__ __forceinline__ double oc_val(const uint64_t* w, const int* pairs, int n, int k, const double* ob) {
+// Jastrow O_k(x) - obar_k: k < n single sigma_j, else the pair (j, l) of pair index k - n, or
+// (tied Jastrow, grp_off given) the sum of sigma_j sigma_l over the pairs of group k - n.
+__device__ __forceinline__ double oc_val(const uint64_t* w, const int* pairs, const int* grp_off,
+                                         const int* grp_pair, int n, int k, const double* ob) {
     if (k < n) return (double)spin_of(w, k) - ob[k];
-    const int j = pairs[2 * (k - n)], l = pairs[2 * (k - n) + 1];
-    return (double)(spin_of(w, j) * spin_of(w, l)) - ob[k];
+    if (grp_off == nullptr) {
+        const int j = pairs[2 * (k - n)], l = pairs[2 * (k - n) + 1];
+        return (double)(spin_of(w, j) * spin_of(w, l)) - ob[k];
+    }
+    int sum = 0;
+    for (int e = grp_off[k - n]; e < grp_off[k - n + 1]; ++e) {
+        const int p = grp_pair[e];
+        sum += spin_of(w, pairs[2 * p]) * spin_of(w, pairs[2 * p + 1]);
+    }
+    return (double)sum - ob[k];
 }
 
 __global__ void __launch_bounds__(SNR_THREADS) snr_solve_kernel(int n, int W, int P, int ns,
                                                                 const uint64_t* __restrict__ spins,
                                                                 const int* __restrict__ pairs,
+                                                                const int* __restrict__ grp_off,
+                                                                const int* __restrict__ grp_pair,
                                                                 const double* __restrict__ S,
                                                                 const double* __restrict__ obar,
                                                                 const double2* __restrict__ v,
@@ -196,7 +208,7 @@ __global__ void __launch_bounds__(SNR_THREADS) snr_solve_kernel(int n, int W, in
             for (int x = g; x < ns; x += G) {
                 const uint64_t* w = sp + (size_t)x * W;
                 double y = 0.0;
-                for (int i = 0; i < P; ++i) y += oc_val(w, pairs, n, i, ob) * V[i * LDA + k];
+                for (int i = 0; i < P; ++i) y += oc_val(w, pairs, grp_off, grp_pair, n, i, ob) * V[i * LDA + k];
                 const double2 vc = make_double2(vt[x].x - vbar.x, vt[x].y - vbar.y);
                 const double2 qv = make_double2(y * vc.x, y * vc.y);
                 if (pass == 0) {
@@ -264,8 +276,10 @@ cudaError_t launch_snr_solve(const otvmc_ansatz* a, int ntraj, int ns, const uin
     const size_t smem = snr_smem_bytes(P);
     cudaError_t e = cudaFuncSetAttribute(snr_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    snr_solve_kernel<<<ntraj, SNR_THREADS, smem, s>>>(n, W, P, ns, spins, a->pairs_d, S, obar, v, D, thr, eps_svd,
-                                                      delta, lam, status);
+    const bool tied = a->kind == OTVMC_LJ;
+    snr_solve_kernel<<<ntraj, SNR_THREADS, smem, s>>>(n, W, P, ns, spins, tied ? a->full->pairs_d : a->pairs_d,
+                                                      tied ? a->grp_off_d : nullptr, tied ? a->grp_pair_d : nullptr,
+                                                      S, obar, v, D, thr, eps_svd, delta, lam, status);
     count_launch();
     return cudaGetLastError();
 }
