@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-rbm-path", action="store_true")
     ap.add_argument("--no-rbm-workloads", action="store_true")
     ap.add_argument("--no-jastrow-workloads", action="store_true")
+    ap.add_argument("--no-equal-error", action="store_true")
     return ap.parse_args()
 
 
@@ -127,8 +128,11 @@ def workload(args):
 def build_model(w):
     import numpy as np
     import paper_2506_23928_gb300 as pkg
+    from paper_2506_23928_gb300 import abi
     J = pkg.lattice_couplings(w.extent, w.J, w.alpha, w.kac, w.pbc)
     model = pkg.Model(J, w.h, np.full(w.n, w.kappa), np.full(w.n, w.gamma))
+    if w.ansatz == "lj":
+        return model, pkg.Ansatz(model, kind=abi.OTVMC_LJ, d=w.lj_d, pbc=w.pbc)
     return model, pkg.Ansatz(model)
 
 
@@ -306,7 +310,7 @@ def jastrow_workload(name, stream, precision, steps=3, warmup=2):
     import synth
     from paper_2506_23928_gb300 import abi, waves as wv
     from paper_2506_23928_gb300.abi import check
-    w = synth.WORKLOADS[name]
+    w = synth.WORKLOADS[name] if name in synth.WORKLOADS else synth.PAPER_WORKLOADS[name]
     model, ans = build_model(w)
     P, T, Wd = ans.P, w.ntraj, (w.n + 63) // 64
     seed = 20261204
@@ -343,7 +347,74 @@ def jastrow_workload(name, stream, precision, steps=3, warmup=2):
             "ms_per_step_min": min(per), "ms_per_step_max": max(per), "steps": steps, "warmup": warmup,
             "precision": "mixed" if precision == abi.OTVMC_PREC_MIXED else "fp64",
             "config": {"workload": name, "N": w.n, "P": P, "ns": w.ns, "ntraj": T, "dt": w.dt, "scheme": w.scheme,
-                       "eps": w.eps, "waves": [list(x) for x in plan], "workspace_bytes": nb}}
+                       "eps": w.eps, "ansatz": "LJPH%d" % w.lj_d if w.ansatz == "lj" else "Jastrow",
+                       "waves": [list(x) for x in plan], "workspace_bytes": nb}}
+
+
+GOLDEN_CHAIN8 = os.path.join(ROOT, "tests", "golden", "chain8_lindblad.txt")
+
+
+def equal_error_chain8(stream, T=256):
+    """Throughput at a measured observable error: the 8-spin workload (h = 1, decay 0.1, Heun,
+    dt = 0.01) to t = 1 with T trajectories, (a) on the plain FP64 Jastrow path run one
+    trajectory per call, (b) on the mixed batched RBM path (16 hidden units, weights drawn
+    N(0, 0.05^2), shift 1e-3) in one batch.  Each ensemble's magnetisation at t = 0.1 .. 1 is
+    compared with the exact Lindblad values stored in tests/golden/chain8_lindblad.txt; the
+    error is the largest |M - M_exact| over those times (standard error beside it)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2506_23928_gb300 as pkg
+    from paper_2506_23928_gb300 import abi
+    from paper_2506_23928_gb300.abi import check
+    exact = np.loadtxt(GOLDEN_CHAIN8)
+    w = synth.WORKLOADS["chain8_jastrow"]
+    steps, every, seed = 100, 10, 11
+    model, jas = build_model(w)
+    M_h = 16
+    rbm = pkg.Ansatz(model, kind=abi.OTVMC_RBM, n_hidden=M_h)
+
+    def run(ans, P, th0, per_call, precision, eps):
+        nm = None
+        moms, ms = [], 0.0
+        for t0 in range(0, T, per_call):
+            c = min(per_call, T - t0)
+            desc = abi.RunDesc(ntraj=c, traj0=t0, ns=w.ns, n_steps=steps, step0=0, n_sweep=w.n_sweep, dt=w.dt,
+                               scheme=abi.OTVMC_HEUN, precision=precision, reg=abi.OTVMC_REG_SHIFT, eps=eps,
+                               snr_thresh=4.0, seed=seed, measure_every=every, measure_final=1, use_graph=0)
+            nm = abi.otvmc_run_n_meas(desc)
+            theta = torch.from_numpy(np.tile(th0, (c, 1)).view(np.float64).copy()).cuda().reshape(c, P, 2)
+            spins = torch.zeros((c, w.ns, 1), dtype=torch.int64, device="cuda")
+            check(abi.otvmc_init_chains(ans.handle, c, t0, w.ns, seed, spins, stream))
+            nb = abi.otvmc_run_workspace_bytes(ans.handle, desc)
+            work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+            mom = torch.zeros((nm, c, 9), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            check(abi.otvmc_run_trajectories(ans.handle, desc, theta, spins, mom, work, nb, stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            moms.append(mom.cpu().numpy())
+        mom = np.concatenate(moms, axis=1)
+        m = mom[1:, :, :3]                                   # t = 0.1 .. 1.0
+        M = m.mean(axis=1)
+        se = m.std(axis=1, ddof=1) / np.sqrt(T)
+        err = np.abs(M - exact[1:, 1:4])
+        return {"value": T * steps / (ms / 1000.0), "unit": METRIC, "max_abs_dM": float(err.max()),
+                "mean_abs_dM_t06_t1": float(err[5:].max(axis=1).mean()), "standard_error_max": float(se.max()),
+                "ntraj": T, "trajectories_per_call": per_call}
+
+    g = synth.rng(17)
+    th_r = np.zeros(rbm.P, complex)
+    th_r[w.n + M_h:] = g.normal(0, 0.05, w.n * M_h) + 1j * g.normal(0, 0.05, w.n * M_h)
+    j = run(jas, jas.P, np.zeros(jas.P, complex), 1, abi.OTVMC_PREC_FP64, w.eps)
+    r = run(rbm, rbm.P, th_r, T, abi.OTVMC_PREC_MIXED, 1e-3)
+    return {"workload": "chain8_jastrow (N = 8, h = 1, kappa = 0.1, Heun, dt = 0.01, to t = 1)",
+            "jastrow_fp64_per_trajectory": j, "rbm_mixed_batched": r,
+            "rbm_error_not_larger": r["max_abs_dM"] <= j["max_abs_dM"],
+            "speedup_at_no_larger_error": r["value"] / j["value"]}
 
 
 def cpu_baseline(w, steps=1):
@@ -598,7 +669,13 @@ def main():
         jw = {"chain8_jastrow": jastrow_workload("chain8_jastrow", stream, abi.OTVMC_PREC_FP64, steps=20, warmup=3),
               "chain8_jastrow_mixed": jastrow_workload("chain8_jastrow", stream, abi.OTVMC_PREC_MIXED, steps=20,
                                                        warmup=3),
-              "square10_jastrow": jastrow_workload("square10_jastrow", stream, abi.OTVMC_PREC_MIXED)}
+              "square10_jastrow": jastrow_workload("square10_jastrow", stream, abi.OTVMC_PREC_MIXED),
+              "ring100_ljph1": jastrow_workload("ring100_ljph1", stream, abi.OTVMC_PREC_MIXED),
+              "ring160_ljph1": jastrow_workload("ring160_ljph1", stream, abi.OTVMC_PREC_MIXED)}
+
+    eq = None
+    if not args.no_equal_error and world == 1:
+        eq = equal_error_chain8(stream)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -619,7 +696,7 @@ def main():
             "kernel_timing": f"CUDA events per launch over {prof_steps} more step(s) after the timed region, "
                              "solver trajectory groups serialised (launch durations not shared)",
             "stage_ms_per_step": stage_ms, "cpu_baseline": cpu, "fp64_path": fp64, "rbm_mixed_path": rbm,
-            "rbm_workloads": rbm_full, "jastrow_workloads": jw,
+            "rbm_workloads": rbm_full, "jastrow_workloads": jw, "equal_error": eq,
             "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)

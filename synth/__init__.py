@@ -27,6 +27,7 @@ class Workload:
     n_sweep: int = 2         # Metropolis sweeps (N proposals each) per evaluation
     pbc: bool = False
     kac: bool = False
+    lj_d: int = 0            # tie distance of the "lj" ansatz (LJPHd; 0 = LJH)
 
     @property
     def n(self):
@@ -49,6 +50,15 @@ WORKLOADS = {
                             8192, 128, 0.005, 200, "midpoint"),
     "square16_rbm": Workload("square16_rbm", (16, 16), 1.0, 1.5, 1.0, 0.1, 0.0, "rbm", 256,
                              4096, 64, 0.005, 200, "midpoint"),
+}
+
+# The paper's large-N setups with the tied ansatz LJPH1 (periodic ring, alpha = 1 with the Kac
+# factor, the LITF sign: couplings -J/(K r), field -h), 400 trajectories to t = 0.8.
+PAPER_WORKLOADS = {
+    "ring100_ljph1": Workload("ring100_ljph1", (100,), -1.0, 1.0, -1.07, 0.27, 0.0, "lj", 0,
+                              4096, 400, 0.005, 160, "midpoint", pbc=True, kac=True, lj_d=1),
+    "ring160_ljph1": Workload("ring160_ljph1", (160,), -1.0, 1.0, 0.0, 0.1, 0.0, "lj", 0,
+                              4096, 400, 0.005, 160, "midpoint", pbc=True, kac=True, lj_d=1),
 }
 
 

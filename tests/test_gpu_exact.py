@@ -186,3 +186,50 @@ def test_paper_fig1_setup_matches_closed_form():
         assert np.all(np.abs(M - Mf) <= 3 * dM + 1e-3), (t, M, Mf, dM)
         xi, xif = squeezing(M, C, n), squeezing(Mf, Cf, n)
         assert abs(xi - xif) < 0.05 * xif, (t, xi, xif)
+
+
+def test_paper_fig2_setup_ljph1_matches_closed_form():
+    """The setup of the paper's N = 160 study (Fig. 2): periodic ring of 160 spins, alpha = 1
+    with the Kac factor, the LITF sign, h = 0, kappa = 0.1, the tied ansatz LJPH1 (P = 399);
+    256 trajectories of 2048 samples, dt = 0.005, midpoint, shift 1e-4, to t = 0.7, where App. D's
+    xi^2 reaches its minimum (0.215).  At t <= 0.4: M within 3 standard errors (+1e-3) and xi^2
+    within 2 %; up to the minimum: M within 0.01 and xi^2 within 8 % (LJPH1 departs slightly
+    from the exact state as the correlations grow, as the paper reports for this ansatz)."""
+    import paper_2506_23928_gb300 as pkg
+    from oracle.observables import squeezing
+    n, kappa = 160, 0.1
+    Jd = fossfeig.ring_couplings(n, 1.0, 1.0, kac=True)
+    Jij = np.array([[0.0 if i == j else -Jd[(i - j) % n] for j in range(n)] for i in range(n)])
+    model = pkg.Model(Jij, 0.0, np.full(n, kappa), np.zeros(n))
+    ans = pkg.Ansatz(model, kind=abi.OTVMC_LJ, d=1, pbc=True)
+    assert ans.P == 399
+    T, ns, steps, every, dt = 256, 2048, 140, 20, 0.005
+    desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=abi.OTVMC_MIDPOINT,
+                       precision=MIXED, reg=abi.OTVMC_REG_SHIFT, eps=1e-4, snr_thresh=4.0, seed=3,
+                       measure_every=every, measure_final=1, use_graph=0)
+    nm = abi.otvmc_run_n_meas(desc)
+    theta = torch.zeros((T, ans.P, 2), dtype=torch.float64, device="cuda")
+    spins = torch.zeros((T, ns, 3), dtype=torch.int64, device="cuda")
+    check(abi.otvmc_init_chains(ans.handle, T, 0, ns, 3, spins))
+    nb = abi.otvmc_run_workspace_bytes(ans.handle, desc)
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    mom = torch.zeros((nm, T, 9), dtype=torch.float64, device="cuda")
+    check(abi.otvmc_run_trajectories(ans.handle, desc, theta, spins, mom, work, nb))
+    check(abi.otvmc_check(work))
+    mom = mom.cpu().numpy()
+    flip = np.array([1, -1, 1])
+    for i in range(1, nm):
+        t = min(i * every, steps) * dt
+        Mf, Cf = fossfeig.fossfeig(Jd, kappa, t)
+        Mf, Cf = Mf * flip, Cf * np.outer(flip, flip)
+        q = np.zeros((T, 3, 3))
+        for (a, b), col in zip([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)], range(3, 9)):
+            q[:, a, b] = q[:, b, a] = mom[i, :, col]
+        M, C, dM = ensemble(mom[i, :, :3], q)
+        xi, xif = squeezing(M, C, n), squeezing(Mf, Cf, n)
+        if t <= 0.4 + 1e-9:
+            assert np.all(np.abs(M - Mf) <= 3 * dM + 1e-3), (t, M, Mf, dM)
+            assert abs(xi - xif) < 0.02 * xif, (t, xi, xif)
+        else:
+            assert np.abs(M - Mf).max() < 0.01, (t, M, Mf)
+            assert abs(xi - xif) < 0.08 * xif, (t, xi, xif)
