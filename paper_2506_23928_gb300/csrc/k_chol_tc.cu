@@ -4,16 +4,20 @@
 //
 // Left-looking blocked Cholesky, 128-wide block columns jb = 0, 128, ...:
 //   update  (tcgen05)  C[i, jb:jb+128] = A[i, jb:jb+128] - sum_{k<jb} L[i,k] L[jb+c,k], i >= jb.
-//           L is kept as three BF16 pieces (L = h + m + l to ~2^-24 relative); the six
-//           products h.h + h.m + m.h + h.l + m.m + l.h accumulate in FP32 in TMEM, which
-//           gives FP32-level accuracy.  One CTA = 128 rows x 128 columns of one trajectory;
-//           32-column k slices (64-byte swizzle) in a 2-stage ring, two CTAs per SM.
+//           L is kept as two FP16 pieces (L = h + m to 22 significant bits; the entries of L
+//           are bounded by the square roots of the matrix's diagonal, at most 1 + eps for the
+//           Jastrow S, far inside FP16's range); the three products h.h + h.m + m.h accumulate
+//           in FP32 in TMEM (the dropped m.m is below 2^-22 of the product).  One CTA = 128 rows x 128 columns of
+//           one trajectory; 32-column k slices (64-byte swizzle) in a 3-stage ring, two CTAs
+//           per SM.
 //   diag    (SIMT)     factor the 128 x 128 diagonal block and invert its factor in one pass of
 //           right-looking elimination over register-held 8 x 8 tiles;
 //   panel   (tcgen05)  the rows below, X = C L_dd^-T, with C (written by the update kernel as
-//           BF16 pieces) and L_dd^-1 (written by the diagonal kernel as BF16 pieces) through the
-//           same six piece products over K = 128, one 128-row tile per CTA; diag and panel
-//           write L in FP32 (for the triangular solves) and as BF16 pieces (for later updates).
+//           FP16 pieces) and L_dd^-1 (written by the diagonal kernel as FP16 pieces) through the
+//           same three piece products over K = 128, one 128-row tile per CTA; diag and panel
+//           write L in FP32 (for the triangular solves) and as FP16 pieces (for later updates).
+//   The factor is accurate to a few 2^-22 of |S|; the refinement below, whose residual is exact,
+//   brings the solution to the accuracy of the FP64 solve.
 //   The forward substitution L y = D rides along: diag applies L_dd^-1 to its block of the
 //   right-hand side, the panel kernel subtracts the block's contribution from the rows below.
 // solve     (SIMT)     backward substitution x = L^-T y by blocks through the stored inverses,
@@ -22,7 +26,7 @@
 //           many CTAs, and one more forward and backward substitution for the correction.
 // A trajectory whose pivot is not positive is marked and solved again by the single-CTA
 // solver, which raises the shift (x100, at most three times).
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdio>
 #include <map>
@@ -35,12 +39,14 @@
 namespace otvmc {
 namespace chol {
 
+using piece_t = __half;                   // operand pieces of the tensor-core products
 constexpr int NB = 128;                  // block column width
-constexpr int BK = 32;                   // k extent of one TMA box (bf16: 64 bytes, 64-byte swizzle)
-constexpr int NPC = 3;                   // bf16 pieces of L
+constexpr int BK = 32;                   // k extent of one operand box (fp16: 64 bytes, 64-byte swizzle)
+constexpr int NPC = 2;                   // fp16 pieces of L (h + m: 22 significant bits)
+constexpr int NPROD = 3;                 // piece products kept: h.h, h.m, m.h
 constexpr int BOX = 128 * BK * 2;        // one 128-row box: 8 KB
-constexpr int STAGE = 2 * NPC * BOX;     // A pieces + B pieces: 48 KB
-constexpr int STAGES = 2;                // about 97 KB of shared memory: two CTAs per SM
+constexpr int STAGE = 2 * NPC * BOX;     // A pieces + B pieces: 32 KB
+constexpr int STAGES = 3;                // about 97 KB of shared memory: two CTAs per SM
 constexpr int SMEM_U = STAGES * STAGE + 1024 + 256;
 constexpr uint32_t TCOLS = 128;
 
@@ -51,8 +57,8 @@ __device__ __forceinline__ float a_orig(const float* Gt, const double* ob, int P
     return i == j ? v + eps : v;
 }
 
-// ------------------------------------------------------------------ BF16 piece layout
-// BF16 pieces of L are stored tiled: for piece p of trajectory t, the 128-row tile i / 128
+// ------------------------------------------------------------------ piece layout
+// FP16 pieces of L are stored tiled: for piece p of trajectory t, the 128-row tile i / 128
 // and the 32-column chunk k / 32 form one contiguous 8 KB block [i % 128][k % 32] laid out
 // exactly as the update kernel's shared-memory operand box: rows of 64 bytes with the
 // 64-byte swizzle (16-byte unit u of row r stored at unit u ^ ((r / 2) mod 4)), so that one
@@ -67,39 +73,37 @@ struct LbLayout {
     }
 };
 
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+__device__ __forceinline__ uint32_t pack_h2(piece_t lo, piece_t hi) {
+    return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+}
+// x = h + m with h = fp16(x), m = fp16(x - h): 22 significant bits for |x| in the normal range
+// of m, an absolute error below 2^-25 for smaller |x| (subnormal m); |x| < 65504.
+__device__ __forceinline__ void split2(float x, piece_t& h, piece_t& m) {
+    h = __float2half_rn(x);
+    m = __float2half_rn(x - __half2float(h));
 }
 
-// The three BF16 pieces of eight consecutive entries (a 16-byte unit of each piece's plane).
-__device__ __forceinline__ void store_P8(__nv_bfloat16* Bt, size_t pl, size_t idx, const float (&v)[8]) {
-    uint32_t h[4], m[4], l[4];
+// The two FP16 pieces of eight consecutive entries (a 16-byte unit of each piece's plane).
+__device__ __forceinline__ void store_P8(piece_t* Bt, size_t pl, size_t idx, const float (&v)[8]) {
+    uint32_t h[4], m[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        __nv_bfloat16 hp[2], mp[2], lp[2];
+        piece_t hp[2], mp[2];
 #pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            const float x = v[2 * u + w];
-            hp[w] = __float2bfloat16_rn(x);
-            const float r1 = x - __bfloat162float(hp[w]);
-            mp[w] = __float2bfloat16_rn(r1);
-            lp[w] = __float2bfloat16_rn(r1 - __bfloat162float(mp[w]));
-        }
-        h[u] = pack_bf16x2(hp[0], hp[1]);
-        m[u] = pack_bf16x2(mp[0], mp[1]);
-        l[u] = pack_bf16x2(lp[0], lp[1]);
+        for (int w = 0; w < 2; ++w) split2(v[2 * u + w], hp[w], mp[w]);
+        h[u] = pack_h2(hp[0], hp[1]);
+        m[u] = pack_h2(mp[0], mp[1]);
     }
     *reinterpret_cast<uint4*>(Bt + idx) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(Bt + pl + idx) = make_uint4(m[0], m[1], m[2], m[3]);
-    *reinterpret_cast<uint4*>(Bt + 2 * pl + idx) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // ------------------------------------------------------------------------- update (tcgen05)
-__global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16* __restrict__ Lb, size_t plane,
+__global__ void __launch_bounds__(192, 2) chol_update_kernel(const piece_t* __restrict__ Lb, size_t plane,
                                                              int KC, int t0, int P, int ns, int jb, float eps,
                                                              const float* __restrict__ G,
                                                              const double* __restrict__ obar, float* __restrict__ Pn,
-                                                             __nv_bfloat16* __restrict__ Cb, size_t planeC,
+                                                             piece_t* __restrict__ Cb, size_t planeC,
                                                              const int* __restrict__ fail, int* status) {
     using namespace tc;
     const int t = t0 + blockIdx.y;
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
                 // k slice kb = chunk kb of the row tiles i0 / 128 (A) and jb / 128 (B): each an
                 // 8 KB contiguous image of the swizzled shared-memory box
                 for (int p = 0; p < NPC; ++p) {
-                    const __nv_bfloat16* pl = Lb + (size_t)(t * NPC + p) * plane;
+                    const piece_t* pl = Lb + (size_t)(t * NPC + p) * plane;
                     bulk_load(st + p * BOX, pl + ((size_t)(i0 >> 7) * KC + kb) * (BOX / 2), BOX, &full[s]);
                     bulk_load(st + (NPC + p) * BOX, pl + ((size_t)(jb >> 7) * KC + kb) * (BOX / 2), BOX, &full[s]);
                 }
@@ -161,10 +165,10 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // piece products kept: (h,h) (h,m) (m,h) (h,l) (m,m) (l,h)
-            const int pa[6] = {0, 0, 1, 0, 1, 2};
-            const int pb[6] = {0, 1, 0, 2, 1, 0};
-            constexpr uint32_t ID = idesc_bf16(128, NB);
+            // piece products kept: (h,h) (h,m) (m,h)
+            const int pa[NPROD] = {0, 0, 1};
+            const int pb[NPROD] = {0, 1, 0};
+            constexpr uint32_t ID = idesc_f16(128, NB);
             for (int kb = 0; kb < nk; ++kb) {
                 const int s = kb % STAGES;
                 const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
 #pragma unroll
                 for (int k = 0; k < BK / 16; ++k)
 #pragma unroll
-                    for (int q = 0; q < 6; ++q)
+                    for (int q = 0; q < NPROD; ++q)
                         umma(tmem, smem_desc_sw64(st + pa[q] * BOX + k * 32),
                              smem_desc_sw64(st + (NPC + pb[q]) * BOX + k * 32), ID, (kb > 0 || k > 0 || q > 0) ? 1u : 0u);
                 umma_commit(&empty[s]);
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
     } else {
         // epilogue: C = A - acc.  The diagonal tile (blockIdx.x = 0) goes to PnT[t][c][i]
         // (FP32, transposed, so that the lanes of a warp store consecutive addresses) for the
-        // diagonal-block kernel; the tiles below go out as three BF16 pieces in the operand-box
+        // diagonal-block kernel; the tiles below go out as two FP16 pieces in the operand-box
         // layout of the panel kernel (one 16-byte unit of each piece per 8 columns of a row).
         const int q = warp & 3;
         const float* Gt = G + (size_t)t * P * P;
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
                 } else {
                     // rows below the diagonal block: every column j = jb + c0 + u < i
                     const LbLayout layC{(P + NB - 1) / NB, NB / BK};
-                    __nv_bfloat16* Cbt = Cb + (size_t)t * NPC * planeC;
+                    piece_t* Cbt = Cb + (size_t)t * NPC * planeC;
 #pragma unroll
                     for (int u8 = 0; u8 < 4; ++u8) {
                         float c8[8];
@@ -257,29 +261,22 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const __nv_bfloat16
 }
 
 // Eight consecutive entries L[i][k0 .. k0+8) (k0 a multiple of 8): FP32 copy for the
-// triangular solves and the three BF16 pieces h + m + l for the tensor-core updates.
+// triangular solves and the two FP16 pieces h + m for the tensor-core updates.
 // Only the first nv entries are in the matrix.
-__device__ __forceinline__ void store_L8(float* Lft, __nv_bfloat16* Lbt, const LbLayout& lay, int LD, int i, int k0,
+__device__ __forceinline__ void store_L8(float* Lft, piece_t* Lbt, const LbLayout& lay, int LD, int i, int k0,
                                          const float (&v)[8], int nv) {
-    __nv_bfloat16 hp[8], mp[8], lp[8];
+    piece_t hp[8], mp[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        hp[u] = __float2bfloat16_rn(v[u]);
-        const float r1 = v[u] - __bfloat162float(hp[u]);
-        mp[u] = __float2bfloat16_rn(r1);
-        lp[u] = __float2bfloat16_rn(r1 - __bfloat162float(mp[u]));
-    }
+    for (int u = 0; u < 8; ++u) split2(v[u], hp[u], mp[u]);
     const size_t idx = lay.at(i, k0), pl = lay.plane();
     float* dst = Lft + (size_t)i * LD + k0;
     if (nv >= 8) {
         reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
         reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
-        *reinterpret_cast<uint4*>(Lbt + idx) = make_uint4(pack_bf16x2(hp[0], hp[1]), pack_bf16x2(hp[2], hp[3]),
-                                                          pack_bf16x2(hp[4], hp[5]), pack_bf16x2(hp[6], hp[7]));
-        *reinterpret_cast<uint4*>(Lbt + pl + idx) = make_uint4(pack_bf16x2(mp[0], mp[1]), pack_bf16x2(mp[2], mp[3]),
-                                                               pack_bf16x2(mp[4], mp[5]), pack_bf16x2(mp[6], mp[7]));
-        *reinterpret_cast<uint4*>(Lbt + 2 * pl + idx) = make_uint4(
-            pack_bf16x2(lp[0], lp[1]), pack_bf16x2(lp[2], lp[3]), pack_bf16x2(lp[4], lp[5]), pack_bf16x2(lp[6], lp[7]));
+        *reinterpret_cast<uint4*>(Lbt + idx) = make_uint4(pack_h2(hp[0], hp[1]), pack_h2(hp[2], hp[3]),
+                                                          pack_h2(hp[4], hp[5]), pack_h2(hp[6], hp[7]));
+        *reinterpret_cast<uint4*>(Lbt + pl + idx) = make_uint4(pack_h2(mp[0], mp[1]), pack_h2(mp[2], mp[3]),
+                                                               pack_h2(mp[4], mp[5]), pack_h2(mp[6], mp[7]));
     } else {
 #pragma unroll
         for (int u = 0; u < 8; ++u)
@@ -287,7 +284,6 @@ __device__ __forceinline__ void store_L8(float* Lft, __nv_bfloat16* Lbt, const L
                 dst[u] = v[u];
                 Lbt[idx + u] = hp[u];
                 Lbt[pl + idx + u] = mp[u];
-                Lbt[2 * pl + idx + u] = lp[u];
             }
     }
 }
@@ -509,9 +505,9 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
                                                                     const double* __restrict__ obar,
                                                                     const double2* __restrict__ D,
                                                                     const float* __restrict__ Pn, float* __restrict__ Lf,
-                                                                    __nv_bfloat16* __restrict__ Lb,
+                                                                    piece_t* __restrict__ Lb,
                                                                     float* __restrict__ Dinv,
-                                                                    __nv_bfloat16* __restrict__ Db,
+                                                                    piece_t* __restrict__ Db,
                                                                     float* __restrict__ yv, int* __restrict__ fail) {
     const int t = t0 + blockIdx.x;
     if (fail[t]) return;
@@ -630,10 +626,10 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     }
     // X12 = 0
     __syncthreads();
-    // outputs: L (FP32 and BF16 pieces), X (padded rows / columns zero), y_b = X rhs
+    // outputs: L (FP32 and FP16 pieces), X (padded rows / columns zero), y_b = X rhs
     const LbLayout lay{(P + NB - 1) / NB, LD / 32};
     float* Lft = Lf + (size_t)t * P * LD;
-    __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
+    piece_t* Lbt = Lb + (size_t)t * NPC * lay.plane();
     for (int e = tid; e < NB * (NB / 8); e += blockDim.x) {
         const int i = e >> 4, c8 = e & 15;
         if (i >= nb || c8 * 8 > i) continue;
@@ -655,10 +651,10 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         *reinterpret_cast<float4*>(Dv + (size_t)i * NB + 4 * c4) = v;
     }
     {
-        // L_dd^-1 as three BF16 pieces in the operand-box layout of the panel kernel
+        // L_dd^-1 as two FP16 pieces in the operand-box layout of the panel kernel
         const LbLayout layD{1, NB / BK};
         const size_t pl = layD.plane();
-        __nv_bfloat16* Dbt = Db + (size_t)t * NPC * pl;
+        piece_t* Dbt = Db + (size_t)t * NPC * pl;
         for (int e = tid; e < NB * (NB / 8); e += blockDim.x) {
             const int i = e >> 4, c8 = e & 15;
             float v[8];
@@ -689,18 +685,18 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
 
 // ---------------------------------------------------------------------------------- panel
 // Rows below the diagonal block, X = C L_dd^-T, on the tensor cores: one CTA = 128 rows of one
-// trajectory, A = the rows of C (three BF16 pieces written by the update kernel, or for the
-// first block column by chol_cb0_kernel from the Gram counts), B = L_dd^-1 (three pieces
-// written by the diagonal kernel), the six piece products of the update kernel over K = 128
+// trajectory, A = the rows of C (two FP16 pieces written by the update kernel, or for the
+// first block column by chol_cb0_kernel from the Gram counts), B = L_dd^-1 (two pieces
+// written by the diagonal kernel), the three piece products of the update kernel over K = 128
 // (four 32-column slices), FP32 accumulators in TMEM.  The epilogue (one row per thread)
 // writes L (FP32 + pieces) and subtracts the row's component along the block from the
 // forward-substitution vector, y_i -= X[i, :] . y_b.
 
 // C of the first block column for the rows below it: (S + eps I)_ic = G[c][i]/ns - obar_i obar_c
-// (i >= 128 > c), as BF16 pieces.  Thread: row r = tid % 128 of the tile, column groups
+// (i >= 128 > c), as FP16 pieces.  Thread: row r = tid % 128 of the tile, column groups
 // tid / 128 + 2 g (g < 8) of eight columns; rows beyond P are written as zeros.
 __global__ void __launch_bounds__(256) chol_cb0_kernel(int t0, int P, int ns, const float* __restrict__ G,
-                                                       const double* __restrict__ obar, __nv_bfloat16* __restrict__ Cb,
+                                                       const double* __restrict__ obar, piece_t* __restrict__ Cb,
                                                        size_t planeC, const int* __restrict__ fail) {
     const int t = t0 + blockIdx.y;
     if (fail[t]) return;
@@ -708,7 +704,7 @@ __global__ void __launch_bounds__(256) chol_cb0_kernel(int t0, int P, int ns, co
     const float* Gt = G + (size_t)t * P * P;
     const double* ob = obar + (size_t)t * P;
     const LbLayout layC{(P + NB - 1) / NB, NB / BK};
-    __nv_bfloat16* Cbt = Cb + (size_t)t * NPC * planeC;
+    piece_t* Cbt = Cb + (size_t)t * NPC * planeC;
     const float inv_ns = 1.0f / (float)ns;
     const float obi = i < P ? (float)ob[i] : 0.f;
 #pragma unroll 1
@@ -723,10 +719,10 @@ __global__ void __launch_bounds__(256) chol_cb0_kernel(int t0, int P, int ns, co
     }
 }
 
-__global__ void __launch_bounds__(192, 2) chol_panel_kernel(const __nv_bfloat16* __restrict__ Cb, size_t planeC,
-                                                            const __nv_bfloat16* __restrict__ Db, int t0, int P,
+__global__ void __launch_bounds__(192, 2) chol_panel_kernel(const piece_t* __restrict__ Cb, size_t planeC,
+                                                            const piece_t* __restrict__ Db, int t0, int P,
                                                             int LD, int jb, float* __restrict__ Lf,
-                                                            __nv_bfloat16* __restrict__ Lb, float* __restrict__ yv,
+                                                            piece_t* __restrict__ Lb, float* __restrict__ yv,
                                                             const int* __restrict__ fail, int* status) {
     using namespace tc;
     const int t = t0 + blockIdx.y;
@@ -776,8 +772,8 @@ __global__ void __launch_bounds__(192, 2) chol_panel_kernel(const __nv_bfloat16*
                 uint8_t* sb = smem + st * STAGE;
                 mbar_expect_tx(&full[st], STAGE);
                 for (int p = 0; p < NPC; ++p) {
-                    const __nv_bfloat16* pa = Cb + (size_t)(t * NPC + p) * planeC;
-                    const __nv_bfloat16* pb = Db + (size_t)(t * NPC + p) * planeD;
+                    const piece_t* pa = Cb + (size_t)(t * NPC + p) * planeC;
+                    const piece_t* pb = Db + (size_t)(t * NPC + p) * planeD;
                     bulk_load(sb + p * BOX, pa + ((size_t)(i0 >> 7) * nk + kb) * (BOX / 2), BOX, &full[st]);
                     bulk_load(sb + (NPC + p) * BOX, pb + (size_t)kb * (BOX / 2), BOX, &full[st]);
                 }
@@ -788,9 +784,9 @@ __global__ void __launch_bounds__(192, 2) chol_panel_kernel(const __nv_bfloat16*
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const int pa[6] = {0, 0, 1, 0, 1, 2};
-            const int pb[6] = {0, 1, 0, 2, 1, 0};
-            constexpr uint32_t ID = idesc_bf16(128, NB);
+            const int pa[NPROD] = {0, 0, 1};
+            const int pb[NPROD] = {0, 1, 0};
+            constexpr uint32_t ID = idesc_f16(128, NB);
             for (int kb = 0; kb < nk; ++kb) {
                 const int st = kb % STAGES;
                 const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
@@ -803,7 +799,7 @@ __global__ void __launch_bounds__(192, 2) chol_panel_kernel(const __nv_bfloat16*
 #pragma unroll
                 for (int k = 0; k < BK / 16; ++k)
 #pragma unroll
-                    for (int q = 0; q < 6; ++q)
+                    for (int q = 0; q < NPROD; ++q)
                         umma(tmem, smem_desc_sw64(sa + pa[q] * BOX + k * 32),
                              smem_desc_sw64(sa + (NPC + pb[q]) * BOX + k * 32), ID, (kb > 0 || k > 0 || q > 0) ? 1u : 0u);
                 umma_commit(&empty[st]);
@@ -830,7 +826,7 @@ __global__ void __launch_bounds__(192, 2) chol_panel_kernel(const __nv_bfloat16*
             const int i = i0 + q * 32 + lane;
             const LbLayout lay{(P + NB - 1) / NB, LD / 32};
             float* Lft = Lf + (size_t)t * P * LD;
-            __nv_bfloat16* Lbt = Lb + (size_t)t * NPC * lay.plane();
+            piece_t* Lbt = Lb + (size_t)t * NPC * lay.plane();
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll 1
             for (int c0 = 0; c0 < NB; c0 += 32) {
@@ -1324,8 +1320,8 @@ size_t chol_tc_ws_bytes(int ntraj, int P) {
     add((size_t)ntraj * 4 * P * 8);          // x (and the fallback's residual)
     add((size_t)ntraj * 2 * P * 4);          // forward-substitution vector
     add((size_t)ntraj * nblk * nblk * 2 * NB * 8);  // residual slots
-    add((size_t)ntraj * NPC * nblk * NB * NB * 2);  // C of the panel rows, BF16 pieces
-    add((size_t)ntraj * NPC * NB * NB * 2);         // L_dd^-1, BF16 pieces
+    add((size_t)ntraj * NPC * nblk * NB * NB * 2);  // C of the panel rows, FP16 pieces
+    add((size_t)ntraj * NPC * NB * NB * 2);         // L_dd^-1, FP16 pieces
     return b + 256;
 }
 
@@ -1353,7 +1349,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
         return (void*)r;
     };
     const int NT = (P + NB - 1) / NB;
-    __nv_bfloat16* Lb = (__nv_bfloat16*)take((size_t)ntraj * NPC * NT * 128 * LD * 2);
+    piece_t* Lb = (piece_t*)take((size_t)ntraj * NPC * NT * 128 * LD * 2);
     float* Lf = (float*)take((size_t)ntraj * P * LD * 4);
     float* Pn = (float*)take((size_t)ntraj * P * NB * 4);
     float* Dv = (float*)take((size_t)ntraj * nblk * NB * NB * 4);
@@ -1363,8 +1359,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     float* yv = (float*)take((size_t)ntraj * 2 * P * 4);
     double* part = (double*)take((size_t)ntraj * nblk * nblk * 2 * NB * 8);
     const size_t planeC = LbLayout{NT, NB / BK}.plane();
-    __nv_bfloat16* Cb = (__nv_bfloat16*)take((size_t)ntraj * NPC * planeC * 2);
-    __nv_bfloat16* Db = (__nv_bfloat16*)take((size_t)ntraj * NPC * NB * NB * 2);
+    piece_t* Cb = (piece_t*)take((size_t)ntraj * NPC * planeC * 2);
+    piece_t* Db = (piece_t*)take((size_t)ntraj * NPC * NB * NB * 2);
 
     const LbLayout lay{NT, LD / 32};
     const size_t plane = lay.plane();
