@@ -17,7 +17,10 @@
 //           same three piece products over K = 128, one 128-row tile per CTA; diag and panel
 //           write L in FP32 (for the triangular solves) and as FP16 pieces (for later updates).
 //   The factor is accurate to a few 2^-22 of |S|; the refinement below, whose residual is exact,
-//   brings the solution to the accuracy of the FP64 solve.
+//   brings the solution to the accuracy of the FP64 solve.  Every trajectory's system is
+//   factored divided by a power of two s >= max_i (S + eps I)_ii (chol_scale_kernel), which
+//   changes no rounding and bounds the entries of L by 1, inside FP16's range for any S; a
+//   block inverse beyond FP16's range (a near-singular S) sends the trajectory to the fallback.
 //   The forward substitution L y = D rides along: diag applies L_dd^-1 to its block of the
 //   right-hand side, the panel kernel subtracts the block's contribution from the rows below.
 // solve     (SIMT)     backward substitution x = L^-T y by blocks through the stored inverses,
@@ -101,6 +104,7 @@ __device__ __forceinline__ void store_P8(piece_t* Bt, size_t pl, size_t idx, con
 // ------------------------------------------------------------------------- update (tcgen05)
 __global__ void __launch_bounds__(192, 2) chol_update_kernel(const piece_t* __restrict__ Lb, size_t plane,
                                                              int KC, int t0, int P, int ns, int jb, float eps,
+                                                             const float* __restrict__ inv_s,
                                                              const float* __restrict__ G,
                                                              const double* __restrict__ obar, float* __restrict__ Pn,
                                                              piece_t* __restrict__ Cb, size_t planeC,
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const piece_t* __re
         if (ok) {
             const int i = i0 + q * 32 + lane;
             const int ii = i < P ? i : P - 1;
-            const float inv_ns = 1.0f / (float)ns;
+            const float inv_ns = 1.0f / (float)ns, sc = inv_s[t];
             const float obi = (float)ob[ii];
             float* pcol = Pn + (size_t)t * NB * P + ii;
 #pragma unroll 1
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const piece_t* __re
                         if (j < P && j <= i) {
                             float a = g[u] * inv_ns - obi * obj_s[c0 + u];
                             if (i == j) a += eps;
-                            pcol[(size_t)(c0 + u) * P] = a - __uint_as_float(v[u]);
+                            pcol[(size_t)(c0 + u) * P] = a * sc - __uint_as_float(v[u]);
                         }
                     }
                 } else {
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(192, 2) chol_update_kernel(const piece_t* __re
 #pragma unroll
                         for (int w = 0; w < 8; ++w) {
                             const int u = 8 * u8 + w;
-                            c8[w] = g[u] * inv_ns - obi * obj_s[c0 + u] - __uint_as_float(v[u]);
+                            c8[w] = (g[u] * inv_ns - obi * obj_s[c0 + u]) * sc - __uint_as_float(v[u]);
                         }
                         store_P8(Cbt, planeC, layC.at(i, c0 + 8 * u8), c8);
                     }
@@ -501,6 +505,7 @@ __device__ __forceinline__ void gemm64_nn(const float* A, int lda, const float* 
 }
 
 __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, int LD, int ns, int jb, float eps,
+                                                                    const float* __restrict__ inv_s,
                                                                     const float* __restrict__ G,
                                                                     const double* __restrict__ obar,
                                                                     const double2* __restrict__ D,
@@ -528,17 +533,18 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     const int nb = min(NB, P - jb);
     float* yt = yv + (size_t)t * 2 * P;
     const double2* Dt = D + (size_t)t * P;
+    const float sc = inv_s[t];
     if (tid < 2 * NB) {
         const int h = tid >> 7, i = tid & (NB - 1);
         float v = 0.f;
-        if (i < nb) v = jb == 0 ? (float)(h ? Dt[i].y : Dt[i].x) : yt[h * P + jb + i];
+        if (i < nb) v = jb == 0 ? (float)(h ? Dt[i].y : Dt[i].x) * sc : yt[h * P + jb + i];
         rhs[h * NB + i] = v;
     }
     if (jb == 0)
         for (int k = NB + tid; k < P; k += blockDim.x) {
             const double2 d = Dt[k];
-            yt[k] = (float)d.x;
-            yt[P + k] = (float)d.y;
+            yt[k] = (float)d.x * sc;
+            yt[P + k] = (float)d.y * sc;
         }
     // the lower block (with the diagonal), identity padding beyond nb; lanes along rows i.
     // Loads are issued in batches of 16 per thread before any of them is used.
@@ -569,6 +575,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
                     if (jb == 0) {
                         x = x * inv_ns - obs[i] * obs[c];
                         if (i == c) x += eps;
+                        x *= sc;
                     }
                 }
                 A[i * DSD + c] = x;
@@ -626,6 +633,24 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     }
     // X12 = 0
     __syncthreads();
+    {
+        // the inverse's pieces must fit FP16 (|x| < 65504); a larger inverse (a near-singular
+        // block) sends the trajectory to the fallback solver, as a failed pivot does
+        __shared__ int big;
+        if (tid == 0) big = 0;
+        __syncthreads();
+        bool b = false;
+        for (int e = tid; e < NB * NB; e += blockDim.x) {
+            const float x = xat(e >> 7, e & (NB - 1));
+            b |= !(fabsf(x) < 16384.f);
+        }
+        if (b) big = 1;
+        __syncthreads();
+        if (big) {
+            if (tid == 0) fail[t] = 1;
+            return;
+        }
+    }
     // outputs: L (FP32 and FP16 pieces), X (padded rows / columns zero), y_b = X rhs
     const LbLayout lay{(P + NB - 1) / NB, LD / 32};
     float* Lft = Lf + (size_t)t * P * LD;
@@ -695,7 +720,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
 // C of the first block column for the rows below it: (S + eps I)_ic = G[c][i]/ns - obar_i obar_c
 // (i >= 128 > c), as FP16 pieces.  Thread: row r = tid % 128 of the tile, column groups
 // tid / 128 + 2 g (g < 8) of eight columns; rows beyond P are written as zeros.
-__global__ void __launch_bounds__(256) chol_cb0_kernel(int t0, int P, int ns, const float* __restrict__ G,
+__global__ void __launch_bounds__(256) chol_cb0_kernel(int t0, int P, int ns, const float* __restrict__ inv_s,
+                                                       const float* __restrict__ G,
                                                        const double* __restrict__ obar, piece_t* __restrict__ Cb,
                                                        size_t planeC, const int* __restrict__ fail) {
     const int t = t0 + blockIdx.y;
@@ -705,7 +731,7 @@ __global__ void __launch_bounds__(256) chol_cb0_kernel(int t0, int P, int ns, co
     const double* ob = obar + (size_t)t * P;
     const LbLayout layC{(P + NB - 1) / NB, NB / BK};
     piece_t* Cbt = Cb + (size_t)t * NPC * planeC;
-    const float inv_ns = 1.0f / (float)ns;
+    const float inv_ns = 1.0f / (float)ns, sc = inv_s[t];
     const float obi = i < P ? (float)ob[i] : 0.f;
 #pragma unroll 1
     for (int g = 0; g < 8; ++g) {
@@ -714,7 +740,7 @@ __global__ void __launch_bounds__(256) chol_cb0_kernel(int t0, int P, int ns, co
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = i < P ? Gt[(size_t)(c0 + u) * P + i] : 0.f;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = i < P ? v[u] * inv_ns - obi * (float)ob[c0 + u] : 0.f;
+        for (int u = 0; u < 8; ++u) v[u] = i < P ? (v[u] * inv_ns - obi * (float)ob[c0 + u]) * sc : 0.f;
         store_P8(Cbt, planeC, layC.at(i, c0), v);
     }
 }
@@ -1172,10 +1198,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
                                                                     const double* __restrict__ part,
                                                                     double* __restrict__ xw, double2* __restrict__ delta,
                                                                     double* __restrict__ shift_used,
-                                                                    const int* __restrict__ fail) {
+                                                                    const int* __restrict__ fail,
+                                                                    const float* __restrict__ inv_s) {
     const int t = t0 + blockIdx.x;
     if (fail[t]) return;
     const int nblk = (P + NB - 1) / NB, PY = nblk * NB;
+    const double sc = (double)inv_s[t];  // the factor is of (S + eps I) / s: right-hand sides / s
     extern __shared__ __align__(16) float wsm[];
     float* y = wsm;              // [2][PY]
     float* red = y + 2 * PY;              // [SW_WARPS][NB][2]
@@ -1189,8 +1217,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
     for (int k = P + tid; k < PY; k += blockDim.x) y[k] = y[PY + k] = 0.f;
     if (mode == 2) {
         for (int k = tid; k < P; k += blockDim.x) {
-            y[k] = (float)Dt[k].x;
-            y[PY + k] = (float)Dt[k].y;
+            y[k] = (float)(Dt[k].x * sc);
+            y[PY + k] = (float)(Dt[k].y * sc);
         }
         __syncthreads();
         sweep_forward(P, PY, LD, Lt, Dv, y, tb);
@@ -1244,8 +1272,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
             }
             const double r0 = Dt[k].x - (s0 * inv_ns - ob[k] * ox0 + eps * xt[k]);
             const double r1 = Dt[k].y - (s1 * inv_ns - ob[k] * ox1 + eps * xt[P + k]);
-            y[k] = (float)r0;
-            y[PY + k] = (float)r1;
+            y[k] = (float)(r0 * sc);
+            y[PY + k] = (float)(r1 * sc);
         }
         __syncthreads();
         sweep_forward(P, PY, LD, Lt, Dv, y, tb);
@@ -1265,6 +1293,33 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
         }
     }
     if (last && tid == 0 && shift_used) shift_used[t] = eps;
+}
+
+// inv_s[t] = 2^-k with 2^(k-1) < max_i (S + eps I)_ii <= 2^k (1 if that maximum is not a positive
+// finite number): the factored system is (S + eps I) / s, whose factor has entries at most 1.
+__global__ void chol_scale_kernel(int P, int ns, double eps, const float* __restrict__ G,
+                                  const double* __restrict__ obar, float* __restrict__ inv_s) {
+    const int t = blockIdx.x, tid = threadIdx.x;
+    __shared__ double red[256];
+    const float* Gt = G + (size_t)t * P * P;
+    const double* ob = obar + (size_t)t * P;
+    double mx = 0.0;
+    for (int i = tid; i < P; i += 256) mx = fmax(mx, (double)Gt[(size_t)i * P + i] / ns - ob[i] * ob[i] + eps);
+    red[tid] = mx;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (tid < h) red[tid] = fmax(red[tid], red[tid + h]);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        float v = 1.f;
+        if (red[0] > 0.0 && red[0] < 1e30) {
+            int k;
+            const double f = frexp(red[0], &k);  // red = f 2^k, f in [1/2, 1)
+            v = (float)ldexp(1.0, f == 0.5 ? 1 - k : -k);
+        }
+        inv_s[t] = v;
+    }
 }
 
 inline int ldim(int P) { return ((P + 63) / 64) * 64; }
@@ -1322,6 +1377,7 @@ size_t chol_tc_ws_bytes(int ntraj, int P) {
     add((size_t)ntraj * nblk * nblk * 2 * NB * 8);  // residual slots
     add((size_t)ntraj * NPC * nblk * NB * NB * 2);  // C of the panel rows, FP16 pieces
     add((size_t)ntraj * NPC * NB * NB * 2);         // L_dd^-1, FP16 pieces
+    add((size_t)ntraj * 4);                         // 1 / s per trajectory
     return b + 256;
 }
 
@@ -1361,12 +1417,18 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     const size_t planeC = LbLayout{NT, NB / BK}.plane();
     piece_t* Cb = (piece_t*)take((size_t)ntraj * NPC * planeC * 2);
     piece_t* Db = (piece_t*)take((size_t)ntraj * NPC * NB * NB * 2);
+    float* inv_s = (float*)take((size_t)ntraj * 4);
 
     const LbLayout lay{NT, LD / 32};
     const size_t plane = lay.plane();
 
     cudaError_t e = cudaMemsetAsync(fail, 0, (size_t)ntraj * 4, s);
     if (e != cudaSuccess) return chol_fail(e, "memset");
+    {
+        ProfScope pd(OTVMC_K_CHOLD, s);
+        chol_scale_kernel<<<ntraj, 256, 0, s>>>(P, ns, eps, G, obar, inv_s);
+        count_launch();
+    }
     e = cudaFuncSetAttribute(chol_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DIAG_SMEM);
     if (e != cudaSuccess) return chol_fail(e, "diag attribute");
     e = cudaFuncSetAttribute(chol_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_U);
@@ -1398,13 +1460,13 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
             if (jb > 0) {
                 ProfScope pu(OTVMC_K_CHOLU, gsm);
                 dim3 grid((P - jb + 127) / 128, nt);
-                chol_update_kernel<<<grid, 192, SMEM_U, gsm>>>(Lb, plane, LD / 32, ta, P, ns, jb, feps, G, obar, Pn,
+                chol_update_kernel<<<grid, 192, SMEM_U, gsm>>>(Lb, plane, LD / 32, ta, P, ns, jb, feps, inv_s, G, obar, Pn,
                                                                Cb, planeC, fail, status);
                 count_launch();
             }
             {
                 ProfScope pd(OTVMC_K_CHOLD, gsm);
-                chol_diag_kernel<<<nt, DIAG_THREADS, DIAG_SMEM, gsm>>>(ta, P, LD, ns, jb, feps, G, obar, D, Pn, Lf, Lb, Dv,
+                chol_diag_kernel<<<nt, DIAG_THREADS, DIAG_SMEM, gsm>>>(ta, P, LD, ns, jb, feps, inv_s, G, obar, D, Pn, Lf, Lb, Dv,
                                                                        Db, yv, fail);
                 count_launch();
             }
@@ -1413,7 +1475,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
                 ProfScope pp(OTVMC_K_CHOLP, gsm);
                 dim3 grid((nrows + NB - 1) / NB, nt);
                 if (jb == 0) {
-                    chol_cb0_kernel<<<grid, 256, 0, gsm>>>(ta, P, ns, G, obar, Cb, planeC, fail);
+                    chol_cb0_kernel<<<grid, 256, 0, gsm>>>(ta, P, ns, inv_s, G, obar, Cb, planeC, fail);
                     count_launch();
                 }
                 chol_panel_kernel<<<grid, 192, SMEM_U, gsm>>>(Cb, planeC, Db, ta, P, LD, jb, Lf, Lb, yv, fail, status);
@@ -1423,7 +1485,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
         {
             ProfScope ps(OTVMC_K_SOLVE, gsm);
             chol_sweep_kernel<<<nt, SWEEP_THREADS, wsmem, gsm>>>(ta, P, LD, ns, eps, 0, refine_iters <= 0 ? 1 : 0, obar,
-                                                                  D, Lf, Dv, yv, part, x, delta, shift_used, fail);
+                                                                  D, Lf, Dv, yv, part, x, delta, shift_used, fail, inv_s);
             count_launch();
         }
         for (int it = 0; it < refine_iters; ++it) {
@@ -1435,7 +1497,7 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
             }
             ProfScope ps(OTVMC_K_SOLVE, gsm);
             chol_sweep_kernel<<<nt, SWEEP_THREADS, wsmem, gsm>>>(ta, P, LD, ns, eps, 1, it == refine_iters - 1 ? 1 : 0,
-                                                                  obar, D, Lf, Dv, yv, part, x, delta, shift_used, fail);
+                                                                  obar, D, Lf, Dv, yv, part, x, delta, shift_used, fail, inv_s);
             count_launch();
         }
         if (forked) {
@@ -1469,13 +1531,20 @@ cudaError_t launch_chol_tc_resolve(int ntraj, int P, void* ws, const double2* r,
     take((size_t)ntraj * P * NB * 4);
     float* Dv = (float*)take((size_t)ntraj * nblk * NB * NB * 4);
     int* fail = (int*)take((size_t)ntraj * 4);
+    take((size_t)ntraj * 2 * P * 4);                       // fallback y
+    take((size_t)ntraj * 4 * P * 8);                       // x
+    take((size_t)ntraj * 2 * P * 4);                       // forward-substitution vector
+    take((size_t)ntraj * nblk * nblk * 2 * NB * 8);        // residual slots
+    take((size_t)ntraj * NPC * LbLayout{NT, NB / BK}.plane() * 2);  // C pieces
+    take((size_t)ntraj * NPC * NB * NB * 2);               // L_dd^-1 pieces
+    const float* inv_s = (const float*)take((size_t)ntraj * 4);
     const int PY = (int)nblk * NB;
     const int wsmem = (2 * PY + SW_WARPS * NB * 2 + 2 * NB) * (int)sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(chol_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
     if (e != cudaSuccess) return chol_fail(e, "sweep attribute");
     ProfScope ps(OTVMC_K_SOLVE, s);
     chol_sweep_kernel<<<ntraj, SWEEP_THREADS, wsmem, s>>>(0, P, LD, 0, 0.0, 2, 0, nullptr, r, Lf, Dv, nullptr, nullptr,
-                                                           nullptr, x, nullptr, fail);
+                                                           nullptr, x, nullptr, fail, inv_s);
     count_launch();
     return cudaGetLastError();
 }
