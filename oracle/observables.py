@@ -74,6 +74,21 @@ def ensemble(m_traj, q_traj):
     return M, C, dM
 
 
+def ensemble_weighted(m_traj, q_traj, Q):
+    """Eq. 3 for the linear SSE (App. B): the normalised moments of each trajectory weighted by
+    its norm Q_j, M = (1/N_T) sum_j Q_j m_j, <q> likewise, C = <q> - M M^T; standard errors of M
+    from the weighted samples Q_j m_j."""
+    m_traj = np.asarray(m_traj)
+    q_traj = np.asarray(q_traj)
+    Q = np.asarray(Q, dtype=np.float64)
+    nt = m_traj.shape[0]
+    mw = Q[:, None] * m_traj
+    M = mw.mean(axis=0)
+    C = (Q[:, None, None] * q_traj).mean(axis=0) - np.outer(M, M)
+    dM = mw.std(axis=0, ddof=1) / np.sqrt(nt) if nt > 1 else np.zeros(3)
+    return M, C, dM
+
+
 def squeezing(M, C, n):
     """xi^2 = N lambda_min(C restricted to the plane perpendicular to M) / |M|^2."""
     M = np.asarray(M, dtype=np.float64)

@@ -1,4 +1,5 @@
-"""Exact-state quantum trajectories of the nonlinear stochastic Schroedinger equation.
+"""Exact-state quantum trajectories of the nonlinear and the linear stochastic Schroedinger
+equation.
 
 Test infrastructure (oracle side).  State vectors psi in C^(2^N), small N only.
 
@@ -12,6 +13,9 @@ Test infrastructure (oracle side).  State vectors psi in C^(2^N), small N only.
     H_eff = H - i/2 sum_n (L^+L - 2<L+L^+> L + L^2 + <L+L^+>^2 - 1/2 <L^2 + 2 L^+L + L^+2>).
 Expectations <.> are taken in the normalised state (Eq. 2 preserves the norm; the
 discrete schemes only to O(dt)).  Trajectory averages follow Eq. 3.
+* Linear SSE (App. B): Ito form dpsi = [(-iH - 1/2 sum L^+L) dt + sum L dW] psi, Stratonovich
+  form dpsi = [-i H_lin dt + sum L o dW] psi with H_lin = H - i/2 sum (L^+L + L^2).  The state
+  is not normalised; Eq. 3 holds with unnormalised expectations <psi|A|psi>.
 """
 import numpy as np
 
@@ -66,5 +70,35 @@ def step_strat(psi, H, Ls, dt, dW, scheme="heun"):
         return psi + 0.5 * (incr0 + incr1)
     if scheme == "midpoint":
         a1, b1 = strat_drift_diffusion(0.5 * (psi + pred), H, Ls)
+        return psi + a1 * dt + sum(bn * w for bn, w in zip(b1, dW))
+    raise ValueError(scheme)
+
+
+def lin_strat_drift_diffusion(psi, H, Ls):
+    """A(psi) = -i H_lin psi, B_n(psi) = L_n psi (linear SSE, App. B)."""
+    Hpsi = H @ psi
+    diff = []
+    for L in Ls:
+        Lpsi = L @ psi
+        Hpsi = Hpsi - 0.5j * (L.conj().T @ Lpsi + L @ Lpsi)
+        diff.append(Lpsi)
+    return -1j * Hpsi, diff
+
+
+def step_lin_ito_em(psi, H, Ls, dt, dW):
+    drift = -1j * (H @ psi) - 0.5 * sum(L.conj().T @ (L @ psi) for L in Ls)
+    return psi + drift * dt + sum((L @ psi) * w for L, w in zip(Ls, dW))
+
+
+def step_lin_strat(psi, H, Ls, dt, dW, scheme="heun"):
+    """One predictor-corrector step (App. C) of the linear Stratonovich SSE."""
+    a0, b0 = lin_strat_drift_diffusion(psi, H, Ls)
+    incr0 = a0 * dt + sum(bn * w for bn, w in zip(b0, dW))
+    pred = psi + incr0
+    if scheme == "heun":
+        a1, b1 = lin_strat_drift_diffusion(pred, H, Ls)
+        return psi + 0.5 * (incr0 + a1 * dt + sum(bn * w for bn, w in zip(b1, dW)))
+    if scheme == "midpoint":
+        a1, b1 = lin_strat_drift_diffusion(0.5 * (psi + pred), H, Ls)
         return psi + a1 * dt + sum(bn * w for bn, w in zip(b1, dW))
     raise ValueError(scheme)

@@ -70,6 +70,11 @@ def effective_energy(terms, lpl):
     return terms["EH"] - 0.5j * bracket.sum(axis=1)
 
 
+def effective_energy_linear(terms):
+    """E_eff^lin(x) = <x|H_lin|psi>/psi(x), H_lin = H - i/2 sum_n (L^+L + L^2) (linear SSE, App. B)."""
+    return terms["EH"] - 0.5j * (terms["LdL"] + terms["L2"]).sum(axis=1)
+
+
 def expectation(w, X):
     """sum_x w(x) X(x, ...) with weights summing to one (MC: 1/Ns; exact: |psi|^2/Z)."""
     return np.tensordot(w, X, axes=(0, 0))
@@ -81,16 +86,17 @@ def covariance(w, A, B):
     return Ac.T @ (w[:, None] * B) - np.outer(expectation(w, Ac), expectation(w, B))
 
 
-def evaluate(model, ans, theta, sig, w, dW, dt, with_S=True):
+def evaluate(model, ans, theta, sig, w, dW, dt, with_S=True, linear=False):
     """S, F, N^n and D at theta from configurations sig with weights w.
 
     D = -i F dt + sum_n N^n dW_n (otVMC procedure paragraph, hbar = 1).  with_S=False skips
     the P x P matrix S (S is None then), for parameter counts where only the push-through
-    solve below is affordable.
+    solve below is affordable.  linear=True takes the linear SSE's local effective energy
+    E_eff^lin in place of E_eff (App. B), so that F is F^lin.
     """
     terms = local_terms(model, ans, theta, sig)
     lpl = expectation(w, terms["LpLd"]).real
-    E = effective_energy(terms, lpl)
+    E = effective_energy_linear(terms) if linear else effective_energy(terms, lpl)
     O = ans.O(theta, sig)
     S = covariance(w, O, O) if with_S else None
     F = covariance(w, O, E[:, None])[:, 0]
@@ -169,6 +175,14 @@ def solve_snr(S, D, O, v, w, snr_thresh=4.0, eps_svd=1e-12):
         f_svd = 1.0 / (1.0 + (eps_svd * lam_max / np.maximum(lam, 1e-300)) ** 6)
         inv = np.where(lam > 0, f_snr * f_svd / np.maximum(lam, 1e-300), 0.0)
     return V @ (inv * rho)
+
+
+def log_norm_increment(ev, w, dW, dt):
+    """Increment of ln Q over one step of the linear SSE (normalisation SDE of App. B, dQ =
+    Q (2 Im<E_eff^lin> dt + 2 sum_n Re<B^n> o dW_n), Stratonovich, so d ln Q is the bracket)."""
+    Emean = expectation(w, ev["E"])
+    Bmean = expectation(w, ev["terms"]["B"])
+    return 2.0 * Emean.imag * dt + 2.0 * float(np.dot(Bmean.real, np.asarray(dW, dtype=np.float64)))
 
 
 def local_v(ev, dW, dt):
