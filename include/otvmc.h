@@ -360,6 +360,26 @@ OTVMC_API otvmc_status otvmc_run_trajectories(const otvmc_ansatz* ansatz, const 
                                     double* theta_d, uint64_t* spins_d, double* moments_d,
                                     void* work_d, size_t work_bytes, void* stream);
 
+/* The linear stochastic Schroedinger equation (App. B) instead of the nonlinear one: the same
+ * otVMC equations with E_eff replaced by E_eff^lin = <x|H - i/2 sum_n (L_n^+ L_n + L_n^2)|psi>/psi(x)
+ * (so F^lin = F - i sum_n <L_n + L_n^+> N^n), and for every trajectory the normalisation Q of
+ * its unnormalised state, d ln Q = 2 Im<E_eff^lin> dt + 2 sum_n Re<B^n> o dW_n (the
+ * normalisation SDE, read in Stratonovich form for ln Q), integrated by the run's scheme
+ * alongside theta.  lnQ_d [ntraj] (in/out, 0 for a normalised start) holds ln Q; lnQ_rows_d
+ * (optional) [n_meas][ntraj] receives ln Q at each measured row.  Ensemble averages of the
+ * linear SSE weight each trajectory's (normalised) moments by Q = exp(ln Q):
+ * otvmc_ensemble_weighted.  Everything else as otvmc_run_trajectories.  Synchronises. */
+OTVMC_API otvmc_status otvmc_run_trajectories_linear(const otvmc_ansatz* ansatz, const otvmc_run_desc* desc,
+                                                     double* theta_d, uint64_t* spins_d, double* moments_d,
+                                                     double* lnQ_d, double* lnQ_rows_d, void* work_d,
+                                                     size_t work_bytes, void* stream);
+
+/* Host: the trajectory average of the linear SSE (App. B, the weighted form of Eq. 3):
+ * M = (1/N_T) sum_j w_j m_j and <q> likewise, with weights w_h[ntraj] = Q_j; then C, xi2 and dM
+ * as otvmc_ensemble (dM the standard error of the weighted samples w_j m_j). */
+OTVMC_API otvmc_status otvmc_ensemble_weighted(const double* moments_h, const double* w_h, int ntraj, int n_sites,
+                                               double* M_h, double* C_h, double* xi2_h, double* dM_h);
+
 /* Same with host buffers (pinned or pageable): copies theta_h / spins_h in, runs, copies
  * theta_h / spins_h / moments_h back; device copies live in work_d, which must hold
  * otvmc_run_host_workspace_bytes(...).  Synchronises. */

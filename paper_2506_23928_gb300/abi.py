@@ -74,6 +74,8 @@ SIGNATURES = {
     "otvmc_run_workspace_bytes": (c_size_t, [P, P]),
     "otvmc_run_n_meas": (c_int, [P]),
     "otvmc_run_trajectories": (c_int, [P, P, P, P, P, P, c_size_t, P]),
+    "otvmc_run_trajectories_linear": (c_int, [P, P, P, P, P, P, P, P, c_size_t, P]),
+    "otvmc_ensemble_weighted": (c_int, [P, P, c_int, c_int, P, P, P, P]),
     "otvmc_run_host_workspace_bytes": (c_size_t, [P, P]),
     "otvmc_run_trajectories_host": (c_int, [P, P, P, P, P, P, c_size_t, P]),
     "otvmc_profile_enable": (None, [c_int]),
@@ -253,6 +255,17 @@ def otvmc_run_n_meas(desc):
 def otvmc_run_trajectories(ansatz, desc, theta_d, spins_d, moments_d, work_d, work_bytes, stream=None):
     return _call("otvmc_run_trajectories", ansatz, ctypes.addressof(desc), ptr(theta_d), ptr(spins_d),
                  ptr(moments_d), ptr(work_d), work_bytes, stream_ptr(stream))
+
+
+def otvmc_run_trajectories_linear(ansatz, desc, theta_d, spins_d, moments_d, lnQ_d, lnQ_rows_d, work_d, work_bytes,
+                                  stream=None):
+    return _call("otvmc_run_trajectories_linear", ansatz, ctypes.addressof(desc), ptr(theta_d), ptr(spins_d),
+                 ptr(moments_d), ptr(lnQ_d), ptr(lnQ_rows_d), ptr(work_d), work_bytes, stream_ptr(stream))
+
+
+def otvmc_ensemble_weighted(moments_h, w_h, ntraj, n_sites, M_h, C_h, xi2_h, dM_h):
+    return _call("otvmc_ensemble_weighted", ptr(moments_h), ptr(w_h), ntraj, n_sites, ptr(M_h), ptr(C_h), ptr(xi2_h),
+                 ptr(dM_h))
 
 
 def otvmc_run_host_workspace_bytes(ansatz, desc):

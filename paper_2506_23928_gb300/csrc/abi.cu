@@ -543,9 +543,12 @@ otvmc_status otvmc_sample(const otvmc_ansatz* a, const double* theta_d, int ntra
 }
 
 // est1 + site means + est2 on carved buffers; lpl may be internal.
+// lpl_e (optional): the <L + L^+> that E_eff takes, in place of the estimated ones (zeros give the
+// linear SSE's E_eff^lin = E_H - i/2 sum_n [(L^+L)_loc + (L^2)_loc]).
 static otvmc_status run_estimators(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int T, int ns,
                                    const double* dW, double dt, bool fp32, const EvalBufs& b, double* lpl,
-                                   double2* Eeff, double2* v, int* status, cudaStream_t s) {
+                                   double2* Eeff, double2* v, int* status, cudaStream_t s,
+                                   const double* lpl_e = nullptr) {
     if (a->kind == OTVMC_RBM) {
         if (fp32) CK(launch_est_rbm_mixed(a, theta, spins, T, ns, b, s), "est rbm launch");
         else CK(launch_est_rbm(a, theta, spins, T, ns, b, s), "est rbm launch");
@@ -554,7 +557,7 @@ static otvmc_status run_estimators(const otvmc_ansatz* a, const double2* theta, 
         CK(launch_est1_jastrow(a, spins, T, ns, fp32, b, status, s), "est1 launch");
     }
     CK(launch_site_means(a, T, ns, b, lpl, s), "site means launch");
-    if (v) CK(launch_est2(a, spins, T, ns, fp32, dW, dt, lpl, b, Eeff, v, s), "est2 launch");
+    if (v) CK(launch_est2(a, spins, T, ns, fp32, dW, dt, lpl_e ? lpl_e : lpl, b, Eeff, v, s), "est2 launch");
     return OTVMC_OK;
 }
 
@@ -848,7 +851,15 @@ struct RunBufs {
     float4* tab;   // RBM flip table of the FP32 sampler
     void* rbm;     // RBM build scratch
     double2* thf;  // tied Jastrow: the expanded parameters of the full Jastrow
+    double* lpl0;  // linear SSE: zeros in place of <L + L^+> in E_eff
+    double* gq;    // linear SSE: the predictor's increment of ln Q
     EvalBufs eb;
+};
+
+// Linear SSE (App. B): ln Q per trajectory (in/out) and its values at the measured rows.
+struct LinState {
+    double* lnQ;
+    double* rows;
 };
 
 static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc* d) {
@@ -862,6 +873,8 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
     r.d1 = c.take<double2>(T * P);
     r.dW = c.take<double>((size_t)T * (a->model->nops + 1));
     r.lpl = c.take<double>((size_t)T * (a->model->nops + 1));
+    r.lpl0 = c.take<double>((size_t)T * (a->model->nops + 1));
+    r.gq = c.take<double>((size_t)T);
     r.Eeff = c.take<double2>((size_t)T * ns);
     r.v = c.take<double2>((size_t)T * ns);
     r.obar = c.take<double>(T * P);
@@ -1011,20 +1024,23 @@ size_t otvmc_run_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d)
 // One evaluation at theta (eval index ev): sample, estimators, [observables], S/D, solve.
 static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, const RunBufs& r, const double2* theta,
                              uint64_t* spins, int64_t ev, double* moments_row, double2* delta, int* status,
-                             cudaStream_t s) {
+                             cudaStream_t s, const LinState* lin) {
     const int T = d->ntraj, ns = d->ns;
     const bool fp32 = d->precision == OTVMC_PREC_MIXED;
+    const double* lpl_e = lin ? r.lpl0 : nullptr;
+    const int stage = (int)(ev & 1);
     if (a->kind == OTVMC_RBM) {
         CK(sample_rbm_any(a, theta, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, r.gam, r.lcr, r.tab, nullptr, s),
            "sample launch");
         otvmc_status st =
-            run_estimators(a, theta, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s);
+            run_estimators(a, theta, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s, lpl_e);
         if (st) return st;
         if (moments_row) {
             CK(launch_obs_rbm(a, theta, spins, T, ns, fp32, r.eb, s), "observables launch");
             CK(launch_obs_final(a->n, ns, T, r.eb, moments_row, s), "observables launch");
         }
         CK(launch_vquant(T, ns, r.v, r.eb, s), "vquant launch");
+        if (lin) CK(launch_lnq(T, d->scheme, stage, r.eb.vinfo, r.gq, lin->lnQ, s), "lnq launch");
         if (fp32)
             CK(launch_rbm_build_solve_mixed(a, theta, spins, r.v, r.eb.vinfo, T, ns, d->eps, r.rbm, delta, status, s),
                "rbm build/solve launch");
@@ -1043,7 +1059,8 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     }
     CK(launch_sample_jastrow(e, th, T, d->traj0, ns, d->n_sweep, d->seed, ev, spins, nullptr, status, s),
        "sample launch");
-    otvmc_status st = run_estimators(e, th, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s);
+    otvmc_status st =
+        run_estimators(e, th, spins, T, ns, r.dW, d->dt, fp32, r.eb, r.lpl, r.Eeff, r.v, status, s, lpl_e);
     if (st) return st;
     if (moments_row) {
         CK(launch_obs_prep(e, th, T, fp32, r.eb, s), "obs prep launch");
@@ -1056,6 +1073,7 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
         st = run_build(a, spins, r.v, T, ns, d->precision, true, r.eb, r.obuf, r.S, r.G, r.obar, r.D, status, s);
         if (st) return st;
     }
+    if (lin) CK(launch_lnq(T, d->scheme, stage, r.eb.vinfo, r.gq, lin->lnQ, s), "lnq launch");
     if (d->reg == OTVMC_REG_SNR) {
         CK(launch_snr_solve(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr, status,
                             s),
@@ -1072,10 +1090,18 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
 // this batch's come first in moments_d.
 static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d, uint64_t* spins_d,
                               double* moments_d, int mstride, void* work_d, size_t work_bytes, int* status,
-                              cudaStream_t s) {
+                              cudaStream_t s, const LinState* lin) {
     Carver c(work_d, work_bytes);
     RunBufs r = carve_run(c, a, d);
     if (!c.ok()) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    if (lin)
+        CK(cudaMemsetAsync(r.lpl0, 0, sizeof(double) * (size_t)d->ntraj * (a->model->nops + 1), s), "memset");
+    // ln Q at a measured row (the value at the time of that row's samples)
+    auto lnq_row = [&](int row) -> cudaError_t {
+        if (!lin || !lin->rows) return cudaSuccess;
+        return cudaMemcpyAsync(lin->rows + (size_t)row * mstride, lin->lnQ, sizeof(double) * d->ntraj,
+                               cudaMemcpyDeviceToDevice, s);
+    };
     const int T = d->ntraj;
     const int64_t P = a->P;
     double2* theta = (double2*)theta_d;
@@ -1084,12 +1110,14 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
         const int64_t step = d->step0 + i;
         CK(launch_noise(a->model, T, d->traj0, d->seed, step, d->dt, r.dW, s), "noise launch");
         double* mrow = nullptr;
-        if (d->measure_every > 0 && i % d->measure_every == 0 && moments_d)
+        if (d->measure_every > 0 && i % d->measure_every == 0 && moments_d) {
+            CK(lnq_row(row), "lnq row copy");
             mrow = moments_d + (size_t)(row++) * mstride * OTVMC_MOMENTS;
-        otvmc_status st = run_eval(a, d, r, theta, spins_d, 2 * step, mrow, r.d0, status, s);
+        }
+        otvmc_status st = run_eval(a, d, r, theta, spins_d, 2 * step, mrow, r.d0, status, s, lin);
         if (st) return st;
         CK(launch_sde(T, P, d->scheme, 0, theta, r.d0, nullptr, r.theta_c, nullptr, status, s), "sde launch");
-        st = run_eval(a, d, r, r.theta_c, spins_d, 2 * step + 1, nullptr, r.d1, status, s);
+        st = run_eval(a, d, r, r.theta_c, spins_d, 2 * step + 1, nullptr, r.d1, status, s, lin);
         if (st) return st;
         CK(launch_sde(T, P, d->scheme, 1, theta, r.d0, r.d1, theta, nullptr, status, s), "sde launch");
     }
@@ -1113,6 +1141,7 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
         otvmc_status st = run_estimators(e, th, spins_d, T, d->ns, nullptr, 0.0, fp32, r.eb, r.lpl, nullptr, nullptr,
                                          status, s);
         if (st) return st;
+        CK(lnq_row(row), "lnq row copy");
         double* mrow = moments_d + (size_t)row * mstride * OTVMC_MOMENTS;
         if (rbm) {
             CK(launch_obs_rbm(a, theta, spins_d, T, d->ns, fp32, r.eb, s), "observables launch");
@@ -1127,10 +1156,11 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
 
 // The batch as sub-batches on forked streams (one after another on s under serial profiling).
 static otvmc_status run_pipelined(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d, uint64_t* spins_d,
-                                  double* moments_d, void* work_d, size_t work_bytes, cudaStream_t s) {
+                                  double* moments_d, void* work_d, size_t work_bytes, cudaStream_t s,
+                                  const LinState* lin = nullptr) {
     int* status = (int*)work_d;
     const int np = run_pipes(a, d);
-    if (np == 1) return run_steps(a, d, theta_d, spins_d, moments_d, d->ntraj, work_d, work_bytes, status, s);
+    if (np == 1) return run_steps(a, d, theta_d, spins_d, moments_d, d->ntraj, work_d, work_bytes, status, s, lin);
     const bool forked = !profiling_serial();
     PipeStreams& ps = pipe_streams(s);
     if (forked) CK(cudaEventRecord(ps.fork, s), "pipeline fork");
@@ -1144,9 +1174,11 @@ static otvmc_status run_pipelined(const otvmc_ansatz* a, const otvmc_run_desc* d
         if (need > left) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
         cudaStream_t sp = forked ? ps.s[p] : s;
         if (forked) CK(cudaStreamWaitEvent(sp, ps.fork, 0), "pipeline fork");
+        LinState lp{};
+        if (lin) lp = LinState{lin->lnQ + first, lin->rows ? lin->rows + first : nullptr};
         otvmc_status st = run_steps(a, &q, theta_d + (size_t)first * a->P * 2, spins_d + (size_t)first * d->ns * W,
                                     moments_d ? moments_d + (size_t)first * OTVMC_MOMENTS : nullptr, d->ntraj, w, need,
-                                    status, sp);
+                                    status, sp, lin ? &lp : nullptr);
         if (forked) {
             // joined also after an error, so that the caller's stream stays ordered after it
             CK(cudaEventRecord(ps.join[p], sp), "pipeline join");
@@ -1170,6 +1202,29 @@ otvmc_status otvmc_run_trajectories(const otvmc_ansatz* a, const otvmc_run_desc*
     st = run_pipelined(a, d, theta_d, spins_d, moments_d, work_d, work_bytes, s);
     if (st) return st;
     return otvmc_check(work_d, stream);
+}
+
+otvmc_status otvmc_run_trajectories_linear(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d,
+                                           uint64_t* spins_d, double* moments_d, double* lnQ_d, double* lnQ_rows_d,
+                                           void* work_d, size_t work_bytes, void* stream) {
+    otvmc_status st = check_run(a, d);
+    if (st) return st;
+    if (!theta_d || !spins_d || !work_d || !lnQ_d) return fail(OTVMC_ERR_INVALID, "run_linear: null buffer");
+    if (otvmc_run_n_meas(d) > 0 && !moments_d) return fail(OTVMC_ERR_INVALID, "run_linear: moments_d needed");
+    cudaStream_t s = (cudaStream_t)stream;
+    const LinState lin{lnQ_d, moments_d ? lnQ_rows_d : nullptr};
+    st = run_pipelined(a, d, theta_d, spins_d, moments_d, work_d, work_bytes, s, &lin);
+    if (st) return st;
+    return otvmc_check(work_d, stream);
+}
+
+otvmc_status otvmc_ensemble_weighted(const double* mom, const double* w, int ntraj, int n_sites, double* M_h,
+                                     double* C_h, double* xi2_h, double* dM_h) {
+    if (!mom || !w || ntraj < 1 || n_sites < 1) return fail(OTVMC_ERR_INVALID, "ensemble_weighted: bad arguments");
+    std::vector<double> wm((size_t)ntraj * OTVMC_MOMENTS);
+    for (int t = 0; t < ntraj; ++t)
+        for (int k = 0; k < OTVMC_MOMENTS; ++k) wm[(size_t)t * OTVMC_MOMENTS + k] = w[t] * mom[(size_t)t * OTVMC_MOMENTS + k];
+    return otvmc_ensemble(wm.data(), ntraj, n_sites, M_h, C_h, xi2_h, dM_h);
 }
 
 size_t otvmc_run_host_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d) {

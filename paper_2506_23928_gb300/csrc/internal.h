@@ -260,6 +260,9 @@ cudaError_t gram_set_wait_limit(unsigned long long ns);
 cudaError_t chol_set_wait_limit(unsigned long long ns);
 // x += (L L^T)^-1 r with the factor left in ws by the last mixed (tensor-core) solve of this size
 cudaError_t launch_chol_tc_resolve(int ntraj, int P, void* ws, const double2* r, double2* x, cudaStream_t s);
+// linear SSE: ln Q of every trajectory from the mean of v^lin (k_misc.cu)
+cudaError_t launch_lnq(int ntraj, int scheme, int stage, const double* vinfo, double* g0, double* lnQ,
+                       cudaStream_t s);
 cudaError_t launch_sde(int ntraj, int64_t P, int scheme, int stage, const double2* theta, const double2* d0,
                        const double2* d1, double2* out, int* failed, int* status, cudaStream_t s);
 cudaError_t launch_obs_prep(const otvmc_ansatz* a, const double2* theta, int ntraj, bool fp32,

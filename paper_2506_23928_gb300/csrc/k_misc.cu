@@ -125,4 +125,29 @@ cudaError_t launch_sde(int ntraj, int64_t P, int scheme, int stage, const double
     return cudaGetLastError();
 }
 
+// Normalisation of the linear SSE (App. B): d ln Q = 2 Im<E_eff^lin> dt + 2 sum_n Re<B^n> o dW_n,
+// which over one step is twice the real part of the sample mean of v^lin = -i dt E_eff^lin +
+// sum_n dW_n B^n (vinfo[4 t] after the v reduction).  Stage 0 keeps the predictor's increment;
+// stage 1 advances ln Q by the scheme of the parameters: the trapezoidal mean of the two
+// increments (Heun) or the corrector's increment (midpoint).
+__global__ void lnq_kernel(int ntraj, int scheme, int stage, const double* __restrict__ vinfo,
+                           double* __restrict__ g0, double* __restrict__ lnQ) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntraj) return;
+    const double g = 2.0 * vinfo[4 * t];
+    if (stage == 0) {
+        g0[t] = g;
+    } else {
+        lnQ[t] += scheme == OTVMC_HEUN ? 0.5 * (g0[t] + g) : g;
+    }
+}
+
+cudaError_t launch_lnq(int ntraj, int scheme, int stage, const double* vinfo, double* g0, double* lnQ,
+                       cudaStream_t s) {
+    ProfScope prof_(OTVMC_K_SDE, s);
+    lnq_kernel<<<(ntraj + 127) / 128, 128, 0, s>>>(ntraj, scheme, stage, vinfo, g0, lnQ);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace otvmc

@@ -82,6 +82,27 @@ def test_ensemble_helper_matches_oracle(lib):
     assert abs(xi2[0] - squeezing(M0, C0, n)) < 1e-12
 
 
+def test_weighted_ensemble_helper_matches_oracle(lib):
+    """The linear SSE's average (each trajectory's moments weighted by its norm Q_j, App. B)."""
+    from oracle.observables import ensemble_weighted
+    g = np.random.default_rng(5)
+    nt, n = 30, 10
+    m = g.normal(0, 0.1, (nt, 3)) + np.array([0.6, 0.2, -0.3])
+    q = np.zeros((nt, 3, 3))
+    for t in range(nt):
+        A = g.normal(0, 0.05, (3, 3))
+        q[t] = A @ A.T + np.outer(m[t], m[t])
+    Q = np.exp(g.normal(0, 0.3, nt))
+    mom = np.concatenate([m, q[:, [0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]]], axis=1)
+    M, C, xi2, dM = np.zeros(3), np.zeros(9), np.zeros(1), np.zeros(3)
+    abi.check(abi.otvmc_ensemble_weighted(np.ascontiguousarray(mom), Q, nt, n, M, C, xi2, dM))
+    M0, C0, dM0 = ensemble_weighted(m, q, Q)
+    assert np.allclose(M, M0, atol=1e-14)
+    assert np.allclose(C.reshape(3, 3), C0, atol=1e-14)
+    assert np.allclose(dM, dM0, atol=1e-14)
+    assert abs(xi2[0] - squeezing(M0, C0, n)) < 1e-12
+
+
 def test_bad_arguments_are_rejected_without_a_gpu(lib):
     out = np.zeros(4)
     st = abi.otvmc_lattice_couplings(3, [2, 2, 1], 1.0, 1.0, 0, 0, out)
