@@ -150,10 +150,17 @@ def test_rbm_gains_over_jastrow_at_later_times():
 def test_paper_fig1_setup_matches_closed_form():
     """The setup of the paper's N = 10 benchmark (LITF paragraph, Fig. 1): periodic ring,
     alpha = 1 with the Kac factor, the LITF sign of Eq. 10 (J_ij = -J_d), kappa = 0.5, h = 0,
-    400 trajectories, midpoint; full Jastrow ansatz with 4096 samples, dt = 0.005, shift 1e-3.
-    Against App. D's closed form (its y components flipped for the LITF sign): M within 3
-    standard errors (+1e-3) at t = 0.1, 0.2, 0.3, and the squeezing parameter xi^2 (which falls
-    from 1 to about 0.58 over this time) within 5 %."""
+    400 trajectories, midpoint; full Jastrow ansatz with 4096 samples, dt = 0.005, shift 1e-3,
+    to t = 0.8 (the paper's T_max).  Two references:
+      - the oracle's enumeration otVMC of the same ansatz, shift, dt and Wiener increments, with
+        exact expectations over all 2^10 configurations (tests/golden/fig1_enumeration.txt):
+        M within 3 standard errors and xi^2 within 2 % at every t -- the GPU's sampled run adds
+        nothing beyond sampling noise;
+      - App. D's closed form (y components flipped for the LITF sign): M_x and M_z within 3
+        standard errors (+1e-3) throughout, M_y up to t = 0.4, and xi^2 within 7 %.  Beyond
+        t = 0.4 M_y drifts from App. D (5 standard errors at t = 0.8) in the enumeration run as
+        well, also with shift 1e-4 and dt = 0.0025: the variational error of the Jastrow ansatz."""
+    import os
     import paper_2506_23928_gb300 as pkg
     from oracle.observables import squeezing
     n, alpha, kappa = 10, 1.0, 0.5
@@ -161,7 +168,7 @@ def test_paper_fig1_setup_matches_closed_form():
     Jij = np.array([[0.0 if i == j else -Jd[(i - j) % n] for j in range(n)] for i in range(n)])
     model = pkg.Model(Jij, 0.0, np.full(n, kappa), np.zeros(n))
     ans = pkg.Ansatz(model)
-    T, ns, steps, every, dt = 400, 4096, 60, 20, 0.005
+    T, ns, steps, every, dt = 400, 4096, 160, 20, 0.005
     desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=abi.OTVMC_MIDPOINT,
                        precision=MIXED, reg=abi.OTVMC_REG_SHIFT, eps=1e-3, snr_thresh=4.0, seed=3,
                        measure_every=every, measure_final=1, use_graph=0)
@@ -174,6 +181,7 @@ def test_paper_fig1_setup_matches_closed_form():
     mom = torch.zeros((nm, T, 9), dtype=torch.float64, device="cuda")
     check(abi.otvmc_run_trajectories(ans.handle, desc, theta, spins, mom, work, nb))
     mom = mom.cpu().numpy()
+    enum = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fig1_enumeration.txt"))
     flip = np.array([1, -1, 1])
     for i in range(1, nm):
         t = min(i * every, steps) * dt
@@ -183,9 +191,14 @@ def test_paper_fig1_setup_matches_closed_form():
         for (a, b), col in zip([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)], range(3, 9)):
             q[:, a, b] = q[:, b, a] = mom[i, :, col]
         M, C, dM = ensemble(mom[i, :, :3], q)
-        assert np.all(np.abs(M - Mf) <= 3 * dM + 1e-3), (t, M, Mf, dM)
         xi, xif = squeezing(M, C, n), squeezing(Mf, Cf, n)
-        assert abs(xi - xif) < 0.05 * xif, (t, xi, xif)
+        er = enum[i]
+        assert abs(er[0] - t) < 1e-12
+        assert np.all(np.abs(M - er[1:4]) <= 3 * dM), (t, M, er[1:4], dM)
+        assert abs(xi - er[4]) < 0.02 * er[4], (t, xi, er[4])
+        comps = [0, 1, 2] if t <= 0.4 + 1e-9 else [0, 2]
+        assert np.all(np.abs(M - Mf)[comps] <= 3 * dM[comps] + 1e-3), (t, M, Mf, dM)
+        assert abs(xi - xif) < 0.07 * xif, (t, xi, xif)
 
 
 def test_paper_fig2_setup_ljph1_matches_closed_form():
