@@ -39,8 +39,8 @@ FP32_LANES_PER_SM = 128
 GRAM_DRAM_BYTES_PER_TRAJ = (283.8e6 + 105.8e6) / 16
 # DRAM bytes (read + write) of the block-column update kernel per trajectory-evaluation, from an
 # ncu capture of all 64 update launches of one evaluation of 32 trajectories (four groups of 8;
-# 44.28 MB per launch), chain64_jastrow shape
-UPDATE_DRAM_BYTES_PER_TRAJ_EVAL = 44.28e6 * 64 / 32
+# 30.90 MB per launch with the factor in two FP16 pieces), chain64_jastrow shape
+UPDATE_DRAM_BYTES_PER_TRAJ_EVAL = 30.90e6 * 64 / 32
 
 
 def parse():
