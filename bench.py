@@ -685,7 +685,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "mixed: bf16 Gram (exact), fp32 Cholesky + fp64 refinement, int64/fp64 fields"
+            "dtype": "mixed: bf16 Gram (exact), fp16-piece tensor-core Cholesky + fp64 refinement, int64/fp64 fields"
             if prec == abi.OTVMC_PREC_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "N": w.n, "P": P, "ns": ns, "ntraj_per_gpu": T, "dt": w.dt,

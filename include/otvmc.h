@@ -123,9 +123,11 @@ OTVMC_API int otvmc_model_nops(const otvmc_model* model);
  *   cosh(g - 2 s W) / cosh g = 1 + (cosh 2W - 1) - s tanh(g) sinh 2W, tabulated per call in
  *   the workspace.  MIXED (M <= 256): the same flip factors for the estimators' ratios, FP32
  *   log 2cosh in the observables; in run_trajectories, S (P <= ns) or T (P > ns) from
- *   split-BF16 tensor-core products accumulated in FP32 and the tensor-core Cholesky with
- *   refinement against that matrix (delta within ~1e-4 relative of the FP64 path at eps 1e-3);
- *   on the T path T is by default formed without O (otvmc_ansatz_set_rbm_t_build);
+ *   split-BF16 tensor-core products accumulated in FP32 and the tensor-core Cholesky, whose
+ *   solution is corrected against the exact S or T (residuals from integer fixed-point sums,
+ *   FP64 right-hand side): delta agrees with the FP64 oracle to about 1e-6 relative on the
+ *   factorised T path at eps 1e-3; on the T path T is by default formed without O
+ *   (otvmc_ansatz_set_rbm_t_build);
  *   build_S_F / solve_step of an RBM run in FP64 for either precision.
  * The ansatz keeps a pointer to the model, which must outlive it. */
 OTVMC_API otvmc_status otvmc_ansatz_create(const otvmc_model* model, int kind, int n_hidden,
@@ -266,8 +268,12 @@ OTVMC_API otvmc_status otvmc_build_S_F(const otvmc_ansatz* ansatz, const double*
  * not positive definite the shift is raised (x100, up to 3 times) and OTVMC_ERR_NOT_PD is
  * recorded only if all attempts fail (delta = 0 then).
  *   FP64:  S_d (full FP64), FP64 Cholesky.
- *   MIXED: G_d + obar_d; FP32 Cholesky of S + eps I, then two steps of iterative
- *          refinement with the residual D - (S + eps I) x in FP64 from the exact G.
+ *   MIXED: G_d + obar_d; tensor-core Cholesky of (S + eps I) / 2^k (2^k the power of two
+ *          that bounds the factor's entries by 1; the factor held as two FP16 pieces, 22
+ *          significant bits, each 128 x 128 tile product taken as three FP16 tcgen05 products
+ *          accumulated in FP32), then two steps of iterative refinement with the residual
+ *          D - (S + eps I) x in FP64 from the exact G.  A trajectory whose diagonal blocks
+ *          would leave FP16's range is solved by an FP32 fallback factorisation instead.
  *   RBM (FP64 only): S_d the complex [ntraj][P][P] double2 of otvmc_build_S_F; the real
  *          embedding [[Re S, -Im S], [Im S, Re S]] + eps I (size 2P) is factored in FP64.
  * shift_used_d (optional): [ntraj] double, the shift that succeeded.
