@@ -265,7 +265,8 @@ OTVMC_API otvmc_status otvmc_build_S_F(const otvmc_ansatz* ansatz, const double*
 /* ----------------------------------------------------------------- A7: regularised solve
  * delta = (S + eps I)^{-1} D by Cholesky (diagonal shift; the SNR filter of the otVMC
  * procedure paragraph needs the samples and is otvmc_solve_snr).  If S + eps I is
- * not positive definite the shift is raised (x100, up to 3 times) and OTVMC_ERR_NOT_PD is
+ * not positive definite in the working precision (a pivot not above zero, or a solution that
+ * is not finite) the shift is raised (x100, up to 3 times) and OTVMC_ERR_NOT_PD is
  * recorded only if all attempts fail (delta = 0 then).
  *   FP64:  S_d (full FP64), FP64 Cholesky.
  *   MIXED: G_d + obar_d; tensor-core Cholesky of (S + eps I) / 2^k (2^k the power of two
@@ -273,7 +274,8 @@ OTVMC_API otvmc_status otvmc_build_S_F(const otvmc_ansatz* ansatz, const double*
  *          significant bits, each 128 x 128 tile product taken as three FP16 tcgen05 products
  *          accumulated in FP32), then two steps of iterative refinement with the residual
  *          D - (S + eps I) x in FP64 from the exact G.  A trajectory whose diagonal blocks
- *          would leave FP16's range is solved by an FP32 fallback factorisation instead.
+ *          would leave FP16's range, or whose solution is not finite, is solved by an FP32
+ *          fallback factorisation (with the shift retries above) instead.
  *   RBM (FP64 only): S_d the complex [ntraj][P][P] double2 of otvmc_build_S_F; the real
  *          embedding [[Re S, -Im S], [Im S, Re S]] + eps I (size 2P) is factored in FP64.
  * shift_used_d (optional): [ntraj] double, the shift that succeeded.

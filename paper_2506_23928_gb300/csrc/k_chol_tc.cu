@@ -332,176 +332,219 @@ __device__ __forceinline__ int reduce8_index(int lane) {
 
 // ----------------------------------------------------------------------- diagonal block
 // Cholesky factor L_dd of the 128 x 128 diagonal block of block column jb and its inverse
-// X = L_dd^-1, one CTA per trajectory, by 2 x 2 blocks of 64:
-//     L11 X11 <- factor64(A11);  L21 = A21 X11^T;  A22 -= L21 L21^T;  L22 X22 <- factor64(A22);
-//     X21 = -X22 (L21 X11)
-// (the block form of the factor and of the inverse of a lower-triangular matrix).  factor64
-// is one pass of right-looking elimination over register-held 4 x 4 tiles: threads 0..135
-// own the lower tiles of A (becoming L), threads 136..271 those of X (starting at I); step m
-// publishes column m of A and row m of X through shared memory and every tile applies
-//     A[i][j] -= A[i][m] A[j][m] / A[m][m]  (i, j > m),   X[i][j] -= A[i][m] X[m][j] / A[m][m]  (i > m),
-// with L[i][m] = A[i][m] / sqrt(A[m][m]) and X[m][j] = X[m][j] / sqrt(A[m][m]).  The four 64^3
-// products run as register-tiled SIMT GEMMs on float4 shared-memory operands.  The forward
-// substitution of the solve is fused in: the block's right-hand sides (D for the first block,
-// else the running residual that the TRSM kernels of earlier block columns left behind) are
-// multiplied by X here.  Rows and columns beyond nb are padded with the identity.
-constexpr int DIAG_THREADS = 288;
+// X = L_dd^-1, one CTA of eight warps per trajectory, by 4 x 4 tiles of 32 (right-looking):
+//   for k = 0..3:
+//     L_kk, X_kk <- factor32(A_kk)                      (one warp, registers, shared broadcasts)
+//     L_ik = A_ik X_kk^T (i > k);   X_kj = X_kk W_kj (j < k)
+//     A_ij -= L_ik L_jk^T (k < j <= i);   W_ij -= L_ik X_kj (i > k, j <= k)
+// W starts as the identity, so that X is the block forward substitution of L X = I.  The tile
+// products are warp-level SIMT GEMMs on float4 shared-memory operands.  Warp 0 updates A_k+1,k+1
+// first and factors it at once, while the other warps finish the remaining updates of step k.
+// The forward substitution of the solve is fused in: the block's right-hand sides (D for the
+// first block, else the running residual that the panel kernels of earlier block columns left
+// behind) are multiplied by X here.  Rows and columns beyond nb are padded with the identity.
+constexpr int DIAG_THREADS = 256;
 constexpr int HB = 64;                      // half block
-constexpr int T4 = HB / 4;                  // 16 tile rows of a half block
-constexpr int NTRI4 = T4 * (T4 + 1) / 2;    // 136 lower 4 x 4 tiles
+constexpr int TB = 32;                      // tile of the block algorithm
 constexpr int DSD = NB + 4;                 // shared row of the 128-wide block (16-byte aligned)
 constexpr int DSX = HB + 4;                 // shared row of a 64-wide quarter of the inverse
 // The inverse is kept as its three nonzero 64 x 64 quarters X11, X21, X22 (X12 = 0), so that the
 // kernel's ~119 KB of shared memory leaves room for an update-kernel CTA on the same SM.
-constexpr int DIAG_SMEM = (NB * DSD + 3 * HB * DSX + 4 * HB + 2 * NB) * (int)sizeof(float) + 16;
+constexpr int DIAG_SMEM = (NB * DSD + 3 * HB * DSX + 2 * NB) * (int)sizeof(float) + 16;
 
-__device__ __forceinline__ void tri_index(int q, int& bi, int& bj) {
-    int b = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-    while ((b + 1) * (b + 2) / 2 <= q) ++b;
-    while (b * (b + 1) / 2 > q) --b;
-    bi = b;
-    bj = q - b * (b + 1) / 2;
-}
-
-// Factor the 64 x 64 lower block at A (row stride lda) in place into L and write its inverse
-// into X (row stride ldx; lower, zeros above the diagonal).  Returns false (uniformly) on a bad pivot.
-__device__ bool factor64(float* A, int lda, float* X, int ldx, float* cbuf, float* rbuf) {
-    const int tid = threadIdx.x;
-    const bool isA = tid < NTRI4, isX = tid >= NTRI4 && tid < 2 * NTRI4;
-    int bi = 0, bj = 0;
-    if (isA || isX) tri_index(isA ? tid : tid - NTRI4, bi, bj);
-    float a[4][4];
-    if (isA) {
+// Factor the 32 x 32 tile at A (row stride lda; lower triangle read) into L (written in place,
+// zeros above the diagonal) and write X = L^-1 to X (row stride ldx, zeros above the diagonal).
+// One warp: lane i holds row i of both.  Step m: the pivot is broadcast, lanes i >= m scale
+// their entry of column m, lane m scales its row of X; column m of L and row m of X go to the
+// scratch (scr: 128 floats, two buffers alternating by step), and every lane i > m subtracts
+// L_im times them, reading the scratch four entries at a time.
+// Returns false (uniformly over the warp) on a pivot that is not finite or not above dmin.
+__device__ bool factor32(float* A, int lda, float* X, int ldx, float* scr, float dmin) {
+    const int lane = threadIdx.x & 31;
+    float a[TB], x[TB];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+    for (int q = 0; q < TB / 4; ++q) {
+        const float4 v = ld4(A + lane * lda + 4 * q);
+        a[4 * q] = v.x;
+        a[4 * q + 1] = v.y;
+        a[4 * q + 2] = v.z;
+        a[4 * q + 3] = v.w;
+    }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) a[r][c] = A[(bi * 4 + r) * lda + bj * 4 + c];
-    } else {
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) a[r][c] = (bi == bj && r == c) ? 1.f : 0.f;
+    for (int j = 0; j < TB; ++j) {
+        if (j > lane) a[j] = 0.f;
+        x[j] = j == lane ? 1.f : 0.f;
     }
     bool ok = true;
-#pragma unroll 1
-    for (int bm = 0; bm < T4; ++bm) {
 #pragma unroll
-        for (int mm = 0; mm < 4; ++mm) {
-            const int m = bm * 4 + mm;
-            float* cb = cbuf + (mm & 1) * HB;
-            float* rb = rbuf + (mm & 1) * HB;
-            if (isA && bj == bm) {
+    for (int m = 0; m < TB; ++m) {
+        float* col = scr + (m & 1) * 2 * TB;
+        float* xrow = col + TB;
+        const float d = __shfl_sync(0xffffffffu, a[m], m);
+        ok = ok && d > dmin && isfinite(d);
+        // a few ulps suffice here: the factor is refined against the exact matrix later
+        const float isd = rsqrtf(ok ? d : 1.f);
+        const float l = lane >= m ? a[m] * isd : 0.f;
+        a[m] = l;
+        col[lane] = l;
+        if (lane == m) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) cb[bi * 4 + r] = a[r][mm];
-            }
-            if (isX && bi == bm) {
+            for (int j = 0; j <= m; ++j) x[j] *= isd;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) rb[bj * 4 + c] = a[mm][c];
-            }
-            __syncthreads();
-            const float d = cb[m];
-            ok = ok && d > 0.f && isfinite(d);
-            const float dd = ok ? d : 1.f;
-            // a few ulps suffice here: the factor is refined against the exact matrix later
-            const float isd = rsqrtf(dd), id = isd * isd;
-            if (isA && bj >= bm) {
-                float li[4], lj[4];
+            for (int q = 0; q <= m / 4; ++q)
+                *reinterpret_cast<float4*>(xrow + 4 * q) = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        }
+        __syncwarp();
+        const float lu = lane > m ? l : 0.f;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) li[r] = bi * 4 + r > m ? cb[bi * 4 + r] * id : 0.f;
+        for (int q = (m + 1) / 4; q < TB / 4; ++q) {
+            const float4 c = ld4(col + 4 * q);
+            if (4 * q + 0 > m) a[4 * q + 0] = fmaf(-lu, c.x, a[4 * q + 0]);
+            if (4 * q + 1 > m) a[4 * q + 1] = fmaf(-lu, c.y, a[4 * q + 1]);
+            if (4 * q + 2 > m) a[4 * q + 2] = fmaf(-lu, c.z, a[4 * q + 2]);
+            if (4 * q + 3 > m) a[4 * q + 3] = fmaf(-lu, c.w, a[4 * q + 3]);
+        }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) lj[c] = bj * 4 + c > m ? cb[bj * 4 + c] : 0.f;
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) a[r][c] = fmaf(-li[r], lj[c], a[r][c]);
-                if (bj == bm) {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-                        if (bi * 4 + r >= m) a[r][mm] = cb[bi * 4 + r] * isd;
-                }
-            }
-            if (isX && bi >= bm && bj <= bm) {
-                float li[4], xm[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) li[r] = bi * 4 + r > m ? cb[bi * 4 + r] * id : 0.f;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) xm[c] = rb[bj * 4 + c];
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) a[r][c] = fmaf(-li[r], xm[c], a[r][c]);
-                if (bi == bm) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) a[mm][c] = xm[c] * isd;
-                }
-            }
+        for (int q = 0; q <= m / 4; ++q) {
+            const float4 r = ld4(xrow + 4 * q);
+            if (4 * q + 0 <= m) x[4 * q + 0] = fmaf(-lu, r.x, x[4 * q + 0]);
+            if (4 * q + 1 <= m) x[4 * q + 1] = fmaf(-lu, r.y, x[4 * q + 1]);
+            if (4 * q + 2 <= m) x[4 * q + 2] = fmaf(-lu, r.z, x[4 * q + 2]);
+            if (4 * q + 3 <= m) x[4 * q + 3] = fmaf(-lu, r.w, x[4 * q + 3]);
         }
     }
-    __syncthreads();
-    if (isA || isX) {
-        float* dst = isA ? A : X;
-        const int ld = isA ? lda : ldx;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) dst[(bi * 4 + r) * ld + bj * 4 + c] = (bi == bj && c > r) ? 0.f : a[r][c];
-            if (bi != bj) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) dst[(bj * 4 + r) * ld + bi * 4 + c] = 0.f;  // upper tile
-            }
-        }
+    for (int q = 0; q < TB / 4; ++q) {
+        float4 v, w;
+        v.x = 4 * q + 0 <= lane ? a[4 * q + 0] : 0.f;
+        v.y = 4 * q + 1 <= lane ? a[4 * q + 1] : 0.f;
+        v.z = 4 * q + 2 <= lane ? a[4 * q + 2] : 0.f;
+        v.w = 4 * q + 3 <= lane ? a[4 * q + 3] : 0.f;
+        w.x = x[4 * q];
+        w.y = x[4 * q + 1];
+        w.z = x[4 * q + 2];
+        w.w = x[4 * q + 3];
+        *reinterpret_cast<float4*>(A + lane * lda + 4 * q) = v;
+        *reinterpret_cast<float4*>(X + lane * ldx + 4 * q) = w;
     }
-    __syncthreads();
+    __syncwarp();
     return ok;
 }
 
-// 64 x 64 x 64 products on shared-memory operands (row strides lda, ldb), threads 0..255; thread
-// (ti, tj) = (tid / 16, tid % 16).
-// NT: out[i][j] = sum_k A[i][k] B[j][k]; rows ti + 16 a, columns tj + 16 b.
-__device__ __forceinline__ void gemm64_nt(const float* A, int lda, const float* B, int ldb, float (&acc)[4][4]) {
-    const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+// 32 x 32 x 32 tile products of one warp on shared-memory operands (row strides lda, ldb
+// multiples of 4 and = 4 mod 32: conflict-free float4 rows).  Lane (g, c) = (lane / 4, lane % 4)
+// owns rows g + 8 a (a < 4).
+// NT: acc[a][b] = sum_m A[g + 8a][m] B[c + 4b][m]   (columns c + 4 b)
+__device__ __forceinline__ void tile_nt(const float* A, int lda, const float* B, int ldb, float (&acc)[4][8]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < HB; k += 4) {
-        float4 av[4], bv[4];
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
+    for (int m = 0; m < TB; m += 4) {
+        float4 av[4], bv[8];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (ti + 16 * a) * lda + k);
+        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (g + 8 * a) * lda + m);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = ld4(B + (tj + 16 * b) * ldb + k);
+        for (int b = 0; b < 8; ++b) bv[b] = ld4(B + (c + 4 * b) * ldb + m);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = dot4(av[a], bv[b], acc[a][b]);
+            for (int b = 0; b < 8; ++b) acc[a][b] = dot4(av[a], bv[b], acc[a][b]);
     }
 }
-// NN: out[i][j] = sum_k A[i][k] B[k][j]; rows ti + 16 a, columns 4 tj .. 4 tj + 3.
-__device__ __forceinline__ void gemm64_nn(const float* A, int lda, const float* B, int ldb, float (&acc)[4][4]) {
-    const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+// NN: acc[a][b] = sum_m A[g + 8a][m] B[m][8c + b]   (columns 8 c + b)
+__device__ __forceinline__ void tile_nn(const float* A, int lda, const float* B, int ldb, float (&acc)[4][8]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
 #pragma unroll 2
-    for (int k = 0; k < HB; k += 4) {
+    for (int m = 0; m < TB; m += 4) {
         float4 av[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (ti + 16 * a) * lda + k);
+        for (int a = 0; a < 4; ++a) av[a] = ld4(A + (g + 8 * a) * lda + m);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const float4 bv = ld4(B + (k + kk) * ldb + 4 * tj);
+        for (int mm = 0; mm < 4; ++mm) {
+            const float4 b0 = ld4(B + (m + mm) * ldb + 8 * c), b1 = ld4(B + (m + mm) * ldb + 8 * c + 4);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const float x = kk == 0 ? av[a].x : kk == 1 ? av[a].y : kk == 2 ? av[a].z : av[a].w;
-                acc[a][0] = fmaf(x, bv.x, acc[a][0]);
-                acc[a][1] = fmaf(x, bv.y, acc[a][1]);
-                acc[a][2] = fmaf(x, bv.z, acc[a][2]);
-                acc[a][3] = fmaf(x, bv.w, acc[a][3]);
+                const float s = mm == 0 ? av[a].x : mm == 1 ? av[a].y : mm == 2 ? av[a].z : av[a].w;
+                acc[a][0] = fmaf(s, b0.x, acc[a][0]);
+                acc[a][1] = fmaf(s, b0.y, acc[a][1]);
+                acc[a][2] = fmaf(s, b0.z, acc[a][2]);
+                acc[a][3] = fmaf(s, b0.w, acc[a][3]);
+                acc[a][4] = fmaf(s, b1.x, acc[a][4]);
+                acc[a][5] = fmaf(s, b1.y, acc[a][5]);
+                acc[a][6] = fmaf(s, b1.z, acc[a][6]);
+                acc[a][7] = fmaf(s, b1.w, acc[a][7]);
             }
         }
     }
+}
+// C = sgn * acc (set) or C -= acc (sub), in the column layout of tile_nt (nt) or tile_nn.
+template <bool NT>
+__device__ __forceinline__ void tile_store(float* C, int ldc, const float (&acc)[4][8], bool sub) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            float& dst = C[(g + 8 * a) * ldc + (NT ? c + 4 * b : 8 * c + b)];
+            dst = sub ? dst - acc[a][b] : acc[a][b];
+        }
+}
+
+struct DiagTiles {
+    float* A;
+    float* X11;
+    float* X21;
+    float* X22;
+    // tile (i, j) of the block (i >= j) and of the inverse / identity remainder W
+    __device__ float* a(int i, int j) const { return A + i * TB * DSD + j * TB; }
+    __device__ float* x(int i, int j) const {
+        if (i < 2) return X11 + i * TB * DSX + j * TB;
+        return (j < 2 ? X21 + j * TB : X22 + (j - 2) * TB) + (i - 2) * TB * DSX;
+    }
+};
+
+// Phase "panel" of step k: job q < 3 - k is L_ik = A_ik X_kk^T with i = k + 1 + q; the others
+// X_kj = X_kk W_kj with j = q - (3 - k).  In place: each job owns its output tile.
+__device__ void diag_panel_job(const DiagTiles& T, int k, int q) {
+    float acc[4][8];
+    if (q < 3 - k) {
+        float* Aik = T.a(k + 1 + q, k);
+        tile_nt(Aik, DSD, T.x(k, k), DSX, acc);
+        __syncwarp();
+        tile_store<true>(Aik, DSD, acc, false);
+    } else {
+        float* Wkj = T.x(k, q - (3 - k));
+        tile_nn(T.x(k, k), DSX, Wkj, DSX, acc);
+        __syncwarp();
+        tile_store<false>(Wkj, DSX, acc, false);
+    }
+    __syncwarp();
+}
+// Phase "update" of step k: the (3-k)(4-k)/2 tiles A_ij -= L_ik L_jk^T (k < j <= i) and the
+// (3-k)(k+1) tiles W_ij -= L_ik X_kj (i > k, j <= k), numbered A tiles first, row by row.
+__device__ int diag_update_jobs(int k) { return (3 - k) * (4 - k) / 2 + (3 - k) * (k + 1); }
+__device__ void diag_update_job(const DiagTiles& T, int k, int q) {
+    float acc[4][8];
+    const int nA = (3 - k) * (4 - k) / 2;
+    if (q < nA) {
+        int i = k + 1, r = q;
+        while (r > i - k - 1) { r -= i - k; ++i; }
+        const int j = k + 1 + r;
+        tile_nt(T.a(i, k), DSD, T.a(j, k), DSD, acc);
+        tile_store<true>(T.a(i, j), DSD, acc, true);
+    } else {
+        const int r = q - nA, i = k + 1 + r / (k + 1), j = r % (k + 1);
+        tile_nn(T.a(i, k), DSD, T.x(k, j), DSX, acc);
+        tile_store<false>(T.x(i, j), DSX, acc, true);
+    }
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, int LD, int ns, int jb, float eps,
@@ -517,23 +560,30 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     const int t = t0 + blockIdx.x;
     if (fail[t]) return;
     extern __shared__ __align__(16) float dsm[];
-    float* A = dsm;                 // [NB][DSD] the block, becoming L (lower); upper-right quarter scratch
+    float* A = dsm;                 // [NB][DSD] the block, becoming L (lower)
     float* X11 = A + NB * DSD;      // [HB][DSX] quarters of the inverse (lower)
     float* X21 = X11 + HB * DSX;    // [HB][DSX]
     float* X22 = X21 + HB * DSX;    // [HB][DSX]
-    float* cbuf = X22 + HB * DSX;   // [2][HB]
+    float* rhs = X22 + HB * DSX;    // [2][NB]
+    __shared__ int pivots_ok;
+    __shared__ __align__(16) float fscr[4 * TB];  // factor32's broadcast buffers
+    const DiagTiles T{A, X11, X21, X22};
     // entry (i, c) of the inverse (zero above the diagonal and in the upper-right quarter)
     auto xat = [&](int i, int c) -> float {
-        if (i < HB) return c < HB ? X11[i * DSX + c] : 0.f;
+        if (c > i) return 0.f;
+        if (i < HB) return X11[i * DSX + c];
         return c < HB ? X21[(i - HB) * DSX + c] : X22[(i - HB) * DSX + c - HB];
     };
-    float* rbuf = cbuf + 2 * HB;    // [2][HB]
-    float* rhs = rbuf + 2 * HB;     // [2][NB]
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int nb = min(NB, P - jb);
     float* yt = yv + (size_t)t * 2 * P;
     const double2* Dt = D + (size_t)t * P;
     const float sc = inv_s[t];
+    // Every pivot of the Cholesky factor of (S + eps I) / s is at least eps / s (a pivot is a
+    // diagonal entry of a Schur complement, bounded below by the smallest eigenvalue).  A pivot
+    // below half of that means that rounding in this precision has overtaken the shift: the
+    // trajectory goes to the fallback solver, which raises the shift.
+    const float dmin = 0.5f * eps * sc;
     if (tid < 2 * NB) {
         const int h = tid >> 7, i = tid & (NB - 1);
         float v = 0.f;
@@ -561,14 +611,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
             for (int q = 0; q < 16; ++q) {
                 const int e = base + tid + DIAG_THREADS * q, c = e >> 7, i = e & (NB - 1);
                 float x = 0.f;
-                if (e < NB * NB && i < nb && c < nb && c <= i)
+                if (i < nb && c < nb && c <= i)
                     x = jb == 0 ? Gt[(size_t)c * P + i] : Pn[((size_t)t * NB + c) * P + jb + i];
                 v[q] = x;
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int e = base + tid + DIAG_THREADS * q, c = e >> 7, i = e & (NB - 1);
-                if (e >= NB * NB) continue;
                 float x = i == c ? 1.f : 0.f;
                 if (i < nb && c < nb && c <= i) {
                     x = v[q];
@@ -583,73 +632,38 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         }
     }
     __syncthreads();
-    // L11, X11
-    bool ok = factor64(A, DSD, X11, DSX, cbuf, rbuf);
-    float acc[4][4];
-    const int ti = tid >> 4, tj = tid & 15;
-    if (ok) {
-        // L21 = A21 X11^T (in place, after all reads)
-        if (tid < 256) gemm64_nt(A + HB * DSD, DSD, X11, DSX, acc);
-        __syncthreads();
-        if (tid < 256) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) A[(HB + ti + 16 * a) * DSD + tj + 16 * b] = acc[a][b];
+    // W: zero below the diagonal tiles (the diagonal tiles are written by factor32)
+    if (warp == 0) {
+        const bool ok = factor32(T.a(0, 0), DSD, T.x(0, 0), DSX, fscr, dmin);
+        if (tid == 0) pivots_ok = ok;
+    } else {
+        for (int e = tid - 32; e < 6 * TB * TB / 4; e += DIAG_THREADS - 32) {
+            const int q = e / (TB * TB / 4), r = (e >> 3) & (TB - 1), c4 = e & 7;
+            const int i = q == 0 ? 1 : q < 3 ? 2 : 3;
+            const int j = q == 0 ? 0 : q == 1 ? 0 : q == 2 ? 1 : q == 3 ? 0 : q == 4 ? 1 : 2;
+            *reinterpret_cast<float4*>(T.x(i, j) + r * DSX + 4 * c4) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __syncthreads();
-        // A22 -= L21 L21^T
-        if (tid < 256) {
-            gemm64_nt(A + HB * DSD, DSD, A + HB * DSD, DSD, acc);
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) A[(HB + ti + 16 * a) * DSD + HB + tj + 16 * b] -= acc[a][b];
-        }
-        __syncthreads();
-        // L22, X22
-        ok = factor64(A + HB * DSD + HB, DSD, X22, DSX, cbuf, rbuf);
-    }
-    if (!ok) {  // uniform: every thread saw the same pivots
-        if (tid == 0) fail[t] = 1;
-        return;
-    }
-    // T = L21 X11 into the unused upper-right quarter of A, then X21 = -X22 T
-    float* Tm = A + HB;
-    if (tid < 256) {
-        gemm64_nn(A + HB * DSD, DSD, X11, DSX, acc);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) Tm[(ti + 16 * a) * DSD + 4 * tj + b] = acc[a][b];
     }
     __syncthreads();
-    if (tid < 256) {
-        gemm64_nn(X22, DSX, Tm, DSD, acc);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) X21[(ti + 16 * a) * DSX + 4 * tj + b] = -acc[a][b];
-    }
-    // X12 = 0
-    __syncthreads();
-    {
-        // the inverse's pieces must fit FP16 (|x| < 65504); a larger inverse (a near-singular
-        // block) sends the trajectory to the fallback solver, as a failed pivot does
-        __shared__ int big;
-        if (tid == 0) big = 0;
-        __syncthreads();
-        bool b = false;
-        for (int e = tid; e < NB * NB; e += blockDim.x) {
-            const float x = xat(e >> 7, e & (NB - 1));
-            b |= !(fabsf(x) < 16384.f);
-        }
-        if (b) big = 1;
-        __syncthreads();
-        if (big) {
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        if (!pivots_ok) {  // uniform: read after a barrier
             if (tid == 0) fail[t] = 1;
             return;
         }
+        if (warp < 3) diag_panel_job(T, k, warp);
+        __syncthreads();
+        if (k == 3) break;
+        // warp 0: the next diagonal tile's update (job 0), then its factor; the others the rest
+        const int nj = diag_update_jobs(k);
+        if (warp == 0) {
+            diag_update_job(T, k, 0);
+            const bool ok = factor32(T.a(k + 1, k + 1), DSD, T.x(k + 1, k + 1), DSX, fscr, dmin);
+            if (tid == 0) pivots_ok = ok;
+        } else {
+            for (int q = warp; q < nj; q += DIAG_THREADS / 32 - 1) diag_update_job(T, k, q);
+        }
+        __syncthreads();
     }
     // outputs: L (FP32 and FP16 pieces), X (padded rows / columns zero), y_b = X rhs
     const LbLayout lay{(P + NB - 1) / NB, LD / 32};
@@ -664,32 +678,30 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         for (int u = 0; u < 8; ++u) v[u] = c8 * 8 + u <= i ? A[i * DSD + c8 * 8 + u] : 0.f;
         store_L8(Lft, Lbt, lay, LD, jb + i, jb + c8 * 8, v, nv);
     }
+    // L_dd^-1 in FP32 and as two FP16 pieces in the operand-box layout of the panel kernel.  The
+    // pieces must fit FP16 (|x| < 65504): a larger inverse (a near-singular block) sends the
+    // trajectory to the fallback solver, as a failed pivot does.
     float* Dv = Dinv + ((size_t)t * ((P + NB - 1) / NB) + jb / NB) * NB * NB;
-    for (int e = tid; e < NB * (NB / 4); e += blockDim.x) {
-        const int i = e >> 5, c4 = e & 31;
-        float4 v = make_float4(xat(i, 4 * c4), xat(i, 4 * c4 + 1), xat(i, 4 * c4 + 2), xat(i, 4 * c4 + 3));
-        if (i >= nb) v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (4 * c4 + 0 >= nb) v.x = 0.f;
-        if (4 * c4 + 1 >= nb) v.y = 0.f;
-        if (4 * c4 + 2 >= nb) v.z = 0.f;
-        if (4 * c4 + 3 >= nb) v.w = 0.f;
-        *reinterpret_cast<float4*>(Dv + (size_t)i * NB + 4 * c4) = v;
-    }
-    {
-        // L_dd^-1 as two FP16 pieces in the operand-box layout of the panel kernel
-        const LbLayout layD{1, NB / BK};
-        const size_t pl = layD.plane();
-        piece_t* Dbt = Db + (size_t)t * NPC * pl;
-        for (int e = tid; e < NB * (NB / 8); e += blockDim.x) {
-            const int i = e >> 4, c8 = e & 15;
-            float v[8];
+    const LbLayout layD{1, NB / BK};
+    const size_t pl = layD.plane();
+    piece_t* Dbt = Db + (size_t)t * NPC * pl;
+    int big = 0;
+    for (int e = tid; e < NB * (NB / 8); e += blockDim.x) {
+        const int i = e >> 4, c8 = e & 15;
+        float v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = 8 * c8 + u;
-                v[u] = (i < nb && c < nb) ? xat(i, c) : 0.f;
-            }
-            store_P8(Dbt, pl, layD.at(i, 8 * c8), v);
+        for (int u = 0; u < 8; ++u) {
+            const int c = 8 * c8 + u;
+            v[u] = (i < nb && c < nb) ? xat(i, c) : 0.f;
+            big |= !(fabsf(v[u]) < 16384.f);
         }
+        *reinterpret_cast<float4*>(Dv + (size_t)i * NB + 8 * c8) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(Dv + (size_t)i * NB + 8 * c8 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        store_P8(Dbt, pl, layD.at(i, 8 * c8), v);
+    }
+    if (__syncthreads_or(big)) {
+        if (tid == 0) fail[t] = 1;
+        return;
     }
     if (tid < 2 * NB) {
         const int h = tid >> 7, i = tid & (NB - 1);
@@ -1189,6 +1201,13 @@ __device__ void sweep_backward(int P, int PY, int LD, const float* Lt, const flo
 //   mode 2: the right-hand side D is a residual formed by the caller; dx = L^-T L^-1 D is added
 //           to delta (in place, FP64), with the factor left by an earlier call.
 // The last pass writes delta (and the shift used), the others keep x in xw (FP64).
+// true (for this thread's entries) if both right-hand sides of y are finite
+__device__ __forceinline__ bool sweep_finite(int P, int PY, const float* y) {
+    bool ok = true;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) ok = ok && isfinite(y[k]) && isfinite(y[PY + k]);
+    return ok;
+}
+
 __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P, int LD, int ns, double eps, int mode,
                                                                     int last, const double* __restrict__ obar,
                                                                     const double2* __restrict__ D,
@@ -1198,7 +1217,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
                                                                     const double* __restrict__ part,
                                                                     double* __restrict__ xw, double2* __restrict__ delta,
                                                                     double* __restrict__ shift_used,
-                                                                    const int* __restrict__ fail,
+                                                                    int* __restrict__ fail,
                                                                     const float* __restrict__ inv_s) {
     const int t = t0 + blockIdx.x;
     if (fail[t]) return;
@@ -1223,6 +1242,9 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
         __syncthreads();
         sweep_forward(P, PY, LD, Lt, Dv, y, tb);
         sweep_backward(P, PY, LD, Lt, Dv, y, tb, red);
+        // a correction that is not finite (an FP32 factor of a system too ill-conditioned for
+        // it) is not applied: x keeps its value
+        if (__syncthreads_or(!sweep_finite(P, PY, y))) return;
         double2* dt = delta + (size_t)t * P;
         for (int k = tid; k < P; k += blockDim.x) {
             const double2 o = dt[k];
@@ -1279,6 +1301,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS) chol_sweep_kernel(int t0, int P
         sweep_forward(P, PY, LD, Lt, Dv, y, tb);
     }
     sweep_backward(P, PY, LD, Lt, Dv, y, tb, red);
+    // a solution that is not finite (an FP32 factor of a system too ill-conditioned for it, with
+    // no pivot below zero) sends the trajectory to the fallback solver, which runs after the sweeps
+    if (__syncthreads_or(!sweep_finite(P, PY, y))) {
+        if (tid == 0) fail[t] = 1;
+        return;
+    }
     for (int k = tid; k < P; k += blockDim.x) {
         double vr = (double)y[k], vi = (double)y[PY + k];
         if (mode == 1) {
@@ -1381,10 +1409,13 @@ size_t chol_tc_ws_bytes(int ntraj, int P) {
     return b + 256;
 }
 
-// Fallback: the single-CTA solver of k_solve.cu restricted to the marked trajectories.
+// Fallback: the single-CTA solver of k_solve.cu restricted to the marked trajectories; its
+// factor of trajectory t goes to L + t * lstride (here the trajectory's own region of Lf, so
+// that the factors of the other trajectories, which later corrections reuse, stay intact).
 cudaError_t launch_chol_solve_masked(int ntraj, int P, int ns, double eps, const float* G, const double* obar,
-                                     const double2* D, double2* delta, double* shift_used, float* L, float* y,
-                                     double* x, int refine_iters, const int* only, int* status, cudaStream_t s);
+                                     const double2* D, double2* delta, double* shift_used, float* L, size_t lstride,
+                                     float* y, double* x, int refine_iters, const int* only, int* status,
+                                     cudaStream_t s);
 
 static cudaError_t chol_fail(cudaError_t e, const char* what) {
     if (e != cudaSuccess) set_error(std::string("cholesky: ") + what + ": " + cudaGetErrorString(e));
@@ -1508,8 +1539,8 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
     e = cudaGetLastError();
     if (e != cudaSuccess) return chol_fail(e, "kernel launch");
     // trajectories whose pivot failed: robust solver with shift retries (exits at once for the others)
-    return launch_chol_solve_masked(ntraj, P, ns, eps, G, obar, D, delta, shift_used, Lf, yf, x, refine_iters, fail,
-                                    status, s);
+    return launch_chol_solve_masked(ntraj, P, ns, eps, G, obar, D, delta, shift_used, Lf, (size_t)P * LD, yf, x,
+                                    refine_iters, fail, status, s);
 }
 
 // One more correction with the factor that the last launch_chol_tc on this workspace left:

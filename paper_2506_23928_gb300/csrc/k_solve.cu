@@ -11,8 +11,10 @@
 // precision MIXED: S = G / ns - obar obar^T from the exact Gram counts; FP32 factor and
 // solves, then `refine` steps of iterative refinement x += solve(D - (S + eps I) x) with the
 // residual formed in FP64 from G and obar.
-// A non-positive or non-finite pivot restarts the factorization with eps * 100 (at most
-// three restarts); if all fail delta = 0 and OTVMC_ERR_NOT_PD is recorded.
+// A pivot below eps / 2 (every pivot of the factor of S + eps I is at least eps: a smaller one
+// means rounding in this precision has overtaken the shift), a pivot that is not finite, or a
+// solution that is not finite restarts the factorization with eps * 100 (at most three
+// restarts); if all fail delta = 0 and OTVMC_ERR_NOT_PD is recorded.
 #include "common.cuh"
 
 namespace otvmc {
@@ -108,7 +110,9 @@ __device__ bool factor(int P, int ns, double eps, const double* S, const float* 
         if (warp == 0) {
             for (int p = 0; p < nb; ++p) {
                 const T d = sm.Dg[p][p];
-                const bool bad = !(d > (T)0) || !isfinite((double)d);
+                // every pivot of the factor of S + eps I is at least eps; one below eps / 2
+                // means rounding has overtaken the shift (the caller raises it)
+                const bool bad = !(d > (T)(0.5 * eps)) || !isfinite((double)d);
                 if (bad) {
                     if (lane == 0) fail = 1;
                     break;
@@ -240,15 +244,16 @@ __global__ void __launch_bounds__(256, 1) chol_solve_kernel(int P, int ns, doubl
                                                             const double* __restrict__ obar,
                                                             const double2* __restrict__ D, double2* __restrict__ delta,
                                                             double* __restrict__ shift_used, T* __restrict__ Lws,
-                                                            T* __restrict__ yws, double* __restrict__ xws,
-                                                            const int* __restrict__ only, int* status) {
+                                                            size_t lstride, T* __restrict__ yws,
+                                                            double* __restrict__ xws, const int* __restrict__ only,
+                                                            int* status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     SolveSmem<T>& sm = *reinterpret_cast<SolveSmem<T>*>(smraw);
     __shared__ double red[2][8];
     const int t = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (only != nullptr && only[t] == 0) return;
     const size_t PP = (size_t)P * P;
-    T* L = Lws + (size_t)t * PP;
+    T* L = Lws + (size_t)t * lstride;  // lstride >= P * P elements per trajectory
     const double* St = GRAM ? nullptr : S + (size_t)t * PP;
     const float* Gt = GRAM ? G + (size_t)t * PP : nullptr;
     const double* ob = GRAM ? obar + (size_t)t * P : nullptr;
@@ -265,6 +270,20 @@ __global__ void __launch_bounds__(256, 1) chol_solve_kernel(int P, int ns, doubl
     for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
         ok = factor<T, GRAM>(P, ns, eps, St, Gt, ob, L, sm);
         __syncthreads();
+        if (ok) {
+            for (int k = tid; k < P; k += blockDim.x) {
+                yr[k] = (T)Dt[k].x;
+                yi[k] = (T)Dt[k].y;
+            }
+            __syncthreads();
+            tri_solve<T>(P, L, yr, yi);
+            __syncthreads();
+            // a solution that is not finite (a factor too ill-conditioned for this precision,
+            // with no pivot below zero) counts as a failed attempt
+            bool fin = true;
+            for (int k = tid; k < P; k += blockDim.x) fin = fin && isfinite(yr[k]) && isfinite(yi[k]);
+            ok = !__syncthreads_or(!fin);
+        }
         if (!ok) eps *= 100.0;
     }
     if (!ok) {
@@ -275,12 +294,6 @@ __global__ void __launch_bounds__(256, 1) chol_solve_kernel(int P, int ns, doubl
         }
         return;
     }
-    for (int k = tid; k < P; k += blockDim.x) {
-        yr[k] = (T)Dt[k].x;
-        yi[k] = (T)Dt[k].y;
-    }
-    __syncthreads();
-    tri_solve<T>(P, L, yr, yi);
     for (int k = tid; k < P; k += blockDim.x) {
         xr[k] = (double)yr[k];
         xi[k] = (double)yi[k];
@@ -363,12 +376,13 @@ size_t chol_ws_bytes(int ntraj, int P, int precision) {
 }
 
 cudaError_t launch_chol_solve_masked(int ntraj, int P, int ns, double eps, const float* G, const double* obar,
-                                     const double2* D, double2* delta, double* shift_used, float* L, float* y,
-                                     double* x, int refine_iters, const int* only, int* status, cudaStream_t s) {
+                                     const double2* D, double2* delta, double* shift_used, float* L, size_t lstride,
+                                     float* y, double* x, int refine_iters, const int* only, int* status,
+                                     cudaStream_t s) {
     const int smem = (int)sizeof(SolveSmem<float>);
     cudaFuncSetAttribute(chol_solve_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     chol_solve_kernel<float, true><<<ntraj, 256, smem, s>>>(P, ns, eps, refine_iters, nullptr, G, obar, D, delta,
-                                                            shift_used, L, y, x, only, status);
+                                                            shift_used, L, lstride, y, x, only, status);
     count_launch();
     return cudaGetLastError();
 }
@@ -391,7 +405,8 @@ cudaError_t launch_chol_solve(int ntraj, int P, int ns, int precision, double ep
     const int smem = (int)sizeof(SolveSmem<double>);
     cudaFuncSetAttribute(chol_solve_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     chol_solve_kernel<double, false><<<ntraj, 256, smem, s>>>(P, ns, eps, 0, S, G, obar, D, delta, shift_used,
-                                                              (double*)L, (double*)y, x, nullptr, status);
+                                                              (double*)L, (size_t)P * P, (double*)y, x, nullptr,
+                                                              status);
     count_launch();
     return cudaGetLastError();
 }

