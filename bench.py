@@ -227,8 +227,9 @@ def rbm_path(stream, fp64_value, peaks_):
 def rbm_workload(name, stream, fp64_value, steps=3, warmup=2):
     """A whole RBM workload at its full size on the mixed path (T formed from the factorised
     kernel): chain64_rbm = 128 trajectories whose sample counts go round-robin over
-    2048 / 4096 / 8192 (one batch per sample count, the batches run one after another in a
-    step); square16_rbm = 64 trajectories at 4096 samples.  Hidden weights N(0, 0.01) in real
+    2048 / 4096 / 8192, timed as one batch per sample count run one after another
+    (`sequential`) and as one grouped call that runs the three concurrently (`grouped`, the
+    line's value when it fits in memory); square16_rbm = 64 trajectories at 4096 samples.  Hidden weights N(0, 0.01) in real
     and imaginary part, a = b = 0; observables off (the RBM's pair terms cost N^2 M per sample).
     Each step is every trajectory of the workload advanced once."""
     import numpy as np
@@ -288,14 +289,49 @@ def rbm_workload(name, stream, fp64_value, steps=3, warmup=2):
     torch.cuda.synchronize()
     stage = {c: v[0] for c, v in abi.profile_summary().items()}
     abi.otvmc_profile_enable(0)
-    del work, batches
+    del work
     torch.cuda.empty_cache()
-    value = w.ntraj * steps / (total_ms / 1000.0)
-    return {"value": value, "unit": METRIC, "ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup,
+    seq_value = w.ntraj * steps / (total_ms / 1000.0)
+    grouped = None
+    if len(ns_mix) > 1:
+        # the same step as one grouped call: the sample counts' batches concurrently on forked
+        # streams (the largest N_s at the highest stream priority), each in its own workspace
+        s0 = warmup + steps + 1
+        descs = lambda i: [desc(k, s0 + i) for k in range(len(ns_mix))]
+        nbg = abi.otvmc_run_grouped_workspace_bytes(ans.handle, descs(0))
+        free, _ = torch.cuda.mem_get_info()
+        if nbg and nbg < free - (4 << 30):
+            workg = torch.zeros(nbg, dtype=torch.uint8, device="cuda")
+            gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for i in range(warmup + steps):
+                if i >= warmup:
+                    gev[i - warmup][0].record(stream)
+                check(abi.otvmc_run_trajectories_grouped(ans.handle, descs(i), [b[0] for b in batches],
+                                                         [b[1] for b in batches], [None] * len(ns_mix), workg, nbg,
+                                                         stream))
+                if i >= warmup:
+                    gev[i - warmup][1].record(stream)
+                torch.cuda.synchronize()
+            gms = sum(a.elapsed_time(b) for a, b in gev) / steps
+            grouped = {"value": w.ntraj / (gms / 1000.0), "ms_per_step": gms, "workspace_bytes": nbg,
+                       "call": "otvmc_run_trajectories_grouped, one group per N_s"}
+            del workg
+        else:
+            grouped = {"unavailable": f"grouped workspace {nbg} bytes exceeds the free memory {free}"}
+        torch.cuda.empty_cache()
+    del batches
+    torch.cuda.empty_cache()
+    value = grouped["value"] if grouped and "value" in grouped else seq_value
+    return {"value": value, "unit": METRIC,
+            "ms_per_step": (grouped["ms_per_step"] if grouped and "value" in grouped else total_ms / steps),
+            "steps": steps, "warmup": warmup,
             "precision": "mixed (FP32 ratios; T factorised; tensor-core Cholesky + refinement)",
             "config": {"workload": name, "N": w.n, "M": M, "P": P, "ntraj": w.ntraj, "ns": list(ns_mix),
-                       "solve": "T path (2 ns)", "observables": "off", "workspace_bytes": nb},
-            "per_ns": per_ns, "stage_ms_per_step": stage,
+                       "solve": "T path (2 ns)", "observables": "off", "workspace_bytes": nb,
+                       "launch": "one grouped call per step" if grouped and "value" in grouped
+                       else "one batch per sample count, one after another"},
+            "sequential": {"value": seq_value, "ms_per_step": total_ms / steps, "per_ns": per_ns},
+            "grouped": grouped, "stage_ms_per_step": stage,
             "vs_fp64_jastrow_path": (value / fp64_value) if fp64_value else None}
 
 

@@ -368,6 +368,23 @@ OTVMC_API otvmc_status otvmc_run_trajectories(const otvmc_ansatz* ansatz, const 
                                     double* theta_d, uint64_t* spins_d, double* moments_d,
                                     void* work_d, size_t work_bytes, void* stream);
 
+/* Grouped run: ngroups (1 .. OTVMC_MAX_GROUPS) batches of trajectories of one ansatz, each with its
+ * own descriptor (sample count, trajectory range, steps, precision may differ: e.g. one ensemble
+ * spread over several N_s), run concurrently in one call, each group on its own stream forked
+ * from `stream` and joined back into it.  Group g reads and writes theta_d[g], spins_d[g] and
+ * moments_d[g] (moments_d itself may be NULL when no group measures) exactly as
+ * otvmc_run_trajectories with descs[g] would: its results are bit-identical to that call.  The
+ * group with the largest ns runs at the highest stream priority.  work_d holds each group's run
+ * workspace in turn (otvmc_run_grouped_workspace_bytes, 0 for invalid arguments).  Synchronises;
+ * returns the first error of any group. */
+enum { OTVMC_MAX_GROUPS = 8 };
+OTVMC_API size_t otvmc_run_grouped_workspace_bytes(const otvmc_ansatz* ansatz, const otvmc_run_desc* descs,
+                                                   int ngroups);
+OTVMC_API otvmc_status otvmc_run_trajectories_grouped(const otvmc_ansatz* ansatz, const otvmc_run_desc* descs,
+                                                      int ngroups, double* const* theta_d,
+                                                      uint64_t* const* spins_d, double* const* moments_d,
+                                                      void* work_d, size_t work_bytes, void* stream);
+
 /* The linear stochastic Schroedinger equation (App. B) instead of the nonlinear one: the same
  * otVMC equations with E_eff replaced by E_eff^lin = <x|H - i/2 sum_n (L_n^+ L_n + L_n^2)|psi>/psi(x)
  * (so F^lin = F - i sum_n <L_n + L_n^+> N^n), and for every trajectory the normalisation Q of

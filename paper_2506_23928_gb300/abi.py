@@ -27,6 +27,7 @@ OTVMC_HEUN, OTVMC_MIDPOINT = 0, 1
 OTVMC_RBM_T_FACTORED, OTVMC_RBM_T_MATERIALISED = 0, 1
 OTVMC_PROFILE_OFF, OTVMC_PROFILE_ON, OTVMC_PROFILE_SERIAL = 0, 1, 2
 OTVMC_MOMENTS = 9
+OTVMC_MAX_GROUPS = 8
 KERNEL_CLASSES = ["sample", "prep", "est1", "est2", "reduce", "obs", "D", "obuild", "gram", "syrk", "solve", "sde",
                   "noise", "chol_update", "chol_trsm", "chol_diag", "chol_resid"]
 
@@ -75,6 +76,8 @@ SIGNATURES = {
     "otvmc_run_n_meas": (c_int, [P]),
     "otvmc_run_trajectories": (c_int, [P, P, P, P, P, P, c_size_t, P]),
     "otvmc_run_trajectories_linear": (c_int, [P, P, P, P, P, P, P, P, c_size_t, P]),
+    "otvmc_run_grouped_workspace_bytes": (c_size_t, [P, P, c_int]),
+    "otvmc_run_trajectories_grouped": (c_int, [P, P, c_int, P, P, P, P, c_size_t, P]),
     "otvmc_ensemble_weighted": (c_int, [P, P, c_int, c_int, P, P, P, P]),
     "otvmc_run_host_workspace_bytes": (c_size_t, [P, P]),
     "otvmc_run_trajectories_host": (c_int, [P, P, P, P, P, P, c_size_t, P]),
@@ -255,6 +258,29 @@ def otvmc_run_n_meas(desc):
 def otvmc_run_trajectories(ansatz, desc, theta_d, spins_d, moments_d, work_d, work_bytes, stream=None):
     return _call("otvmc_run_trajectories", ansatz, ctypes.addressof(desc), ptr(theta_d), ptr(spins_d),
                  ptr(moments_d), ptr(work_d), work_bytes, stream_ptr(stream))
+
+
+def _desc_array(descs):
+    arr = (RunDesc * len(descs))()
+    for i, d in enumerate(descs):
+        arr[i] = d
+    return arr
+
+
+def otvmc_run_grouped_workspace_bytes(ansatz, descs):
+    arr = _desc_array(descs)
+    return _call("otvmc_run_grouped_workspace_bytes", ansatz, ctypes.addressof(arr), len(descs))
+
+
+def otvmc_run_trajectories_grouped(ansatz, descs, thetas, spins, moments, work_d, work_bytes, stream=None):
+    """descs, thetas, spins, moments: one entry per group (moments entries may be None)."""
+    n = len(descs)
+    arr = _desc_array(descs)
+    th = (ctypes.c_void_p * n)(*[ptr(x) for x in thetas])
+    sp = (ctypes.c_void_p * n)(*[ptr(x) for x in spins])
+    mo = (ctypes.c_void_p * n)(*[ptr(x) for x in moments])
+    return _call("otvmc_run_trajectories_grouped", ansatz, ctypes.addressof(arr), n, ctypes.addressof(th),
+                 ctypes.addressof(sp), ctypes.addressof(mo), ptr(work_d), work_bytes, stream_ptr(stream))
 
 
 def otvmc_run_trajectories_linear(ansatz, desc, theta_d, spins_d, moments_d, lnQ_d, lnQ_rows_d, work_d, work_bytes,

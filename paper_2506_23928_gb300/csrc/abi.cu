@@ -1204,6 +1204,105 @@ otvmc_status otvmc_run_trajectories(const otvmc_ansatz* a, const otvmc_run_desc*
     return otvmc_check(work_d, stream);
 }
 
+// Grouped runs: up to OTVMC_MAX_GROUPS batches of one ansatz with their own descriptors, each on
+// its own forked stream (one set per (device, calling stream)).  Streams take priorities by the
+// groups' sample counts: the group with the most samples per trajectory, whose step is the
+// longest chain of dependent launches, gets the highest priority, so that the others' launches
+// fill the GPU around it rather than delay it.
+struct GroupRunStreams {
+    cudaStream_t s[OTVMC_MAX_GROUPS];
+    cudaEvent_t fork;
+    cudaEvent_t join[OTVMC_MAX_GROUPS];
+};
+static GroupRunStreams& group_run_streams(cudaStream_t caller) {
+    static std::mutex mu;
+    static std::map<std::pair<int, uintptr_t>, GroupRunStreams> sets;
+    std::lock_guard<std::mutex> lk(mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto key = std::make_pair(dev, (uintptr_t)caller);
+    auto it = sets.find(key);
+    if (it != sets.end()) return it->second;
+    GroupRunStreams& g = sets[key];
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    for (int i = 0; i < OTVMC_MAX_GROUPS; ++i) {
+        // rank i (0 = most samples) gets priority greatest + i, clamped to the range
+        const int pr = std::min(least, greatest + i);
+        cudaStreamCreateWithPriority(&g.s[i], cudaStreamNonBlocking, pr);
+        cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming);
+    }
+    cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
+    return g;
+}
+
+static size_t group_slice(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t otvmc_run_grouped_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* descs, int ngroups) {
+    if (!a || !descs || ngroups < 1 || ngroups > OTVMC_MAX_GROUPS) return 0;
+    size_t total = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        const size_t b = otvmc_run_workspace_bytes(a, &descs[g]);
+        if (!b) return 0;
+        total += group_slice(b);
+    }
+    return total;
+}
+
+otvmc_status otvmc_run_trajectories_grouped(const otvmc_ansatz* a, const otvmc_run_desc* descs, int ngroups,
+                                            double* const* theta_d, uint64_t* const* spins_d,
+                                            double* const* moments_d, void* work_d, size_t work_bytes,
+                                            void* stream) {
+    if (!a || !descs || !theta_d || !spins_d || !work_d || ngroups < 1 || ngroups > OTVMC_MAX_GROUPS)
+        return fail(OTVMC_ERR_INVALID, "run_grouped: bad arguments");
+    size_t off[OTVMC_MAX_GROUPS], need[OTVMC_MAX_GROUPS], total = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        otvmc_status st = check_run(a, &descs[g]);
+        if (st) return st;
+        if (!theta_d[g] || !spins_d[g]) return fail(OTVMC_ERR_INVALID, "run_grouped: null buffer");
+        if (otvmc_run_n_meas(&descs[g]) > 0 && (!moments_d || !moments_d[g]))
+            return fail(OTVMC_ERR_INVALID, "run_grouped: moments_d needed");
+        need[g] = otvmc_run_workspace_bytes(a, &descs[g]);
+        off[g] = total;
+        total += group_slice(need[g]);
+    }
+    if (total > work_bytes) return fail(OTVMC_ERR_WORKSPACE, "run_grouped: workspace too small");
+    // rank of each group by sample count (ties by position): rank 0 runs at the highest priority
+    int rank[OTVMC_MAX_GROUPS];
+    for (int g = 0; g < ngroups; ++g) {
+        rank[g] = 0;
+        for (int h = 0; h < ngroups; ++h)
+            if (descs[h].ns > descs[g].ns || (descs[h].ns == descs[g].ns && h < g)) ++rank[g];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool forked = ngroups > 1 && !profiling_serial();
+    GroupRunStreams& gs = group_run_streams(s);
+    if (forked) CK(cudaEventRecord(gs.fork, s), "grouped fork");
+    otvmc_status first_err = OTVMC_OK;
+    // launched in rank order: the longest group's first launches go out first
+    for (int r = 0; r < ngroups; ++r) {
+        int g = 0;
+        while (rank[g] != r) ++g;
+        char* w = (char*)work_d + off[g];
+        cudaStream_t sg = forked ? gs.s[r] : s;
+        if (forked) CK(cudaStreamWaitEvent(sg, gs.fork, 0), "grouped fork");
+        otvmc_status st = run_pipelined(a, &descs[g], theta_d[g], spins_d[g], moments_d ? moments_d[g] : nullptr, w,
+                                        need[g], sg);
+        if (forked) {
+            CK(cudaEventRecord(gs.join[r], sg), "grouped join");
+            CK(cudaStreamWaitEvent(s, gs.join[r], 0), "grouped join");
+        }
+        if (st && !first_err) first_err = st;
+    }
+    if (first_err) return first_err;
+    // every group's device status lives at the head of its own workspace slice
+    for (int g = 0; g < ngroups; ++g) {
+        otvmc_status st = otvmc_check((char*)work_d + off[g], stream);
+        if (st && !first_err) first_err = st;
+    }
+    return first_err;
+}
+
 otvmc_status otvmc_run_trajectories_linear(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d,
                                            uint64_t* spins_d, double* moments_d, double* lnQ_d, double* lnQ_rows_d,
                                            void* work_d, size_t work_bytes, void* stream) {

@@ -359,7 +359,7 @@ constexpr int DIAG_SMEM = (NB * DSD + 3 * HB * DSX + 2 * NB) * (int)sizeof(float
 // scratch (scr: 128 floats, two buffers alternating by step), and every lane i > m subtracts
 // L_im times them, reading the scratch four entries at a time.
 // Returns false (uniformly over the warp) on a pivot that is not finite or not above dmin.
-__device__ bool factor32(float* A, int lda, float* X, int ldx, float* scr, float dmin) {
+__device__ __noinline__ bool factor32(float* A, int lda, float* X, int ldx, float* scr, float dmin) {
     const int lane = threadIdx.x & 31;
     float a[TB], x[TB];
 #pragma unroll
