@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-rbm-workloads", action="store_true")
     ap.add_argument("--no-jastrow-workloads", action="store_true")
     ap.add_argument("--no-equal-error", action="store_true")
+    ap.add_argument("--snr-full-size", action="store_true",
+                    help="also time the SNR regulariser at P = 2080 on 8 trajectories (about two minutes)")
     return ap.parse_args()
 
 
@@ -136,12 +138,12 @@ def build_model(w):
     return model, pkg.Ansatz(model)
 
 
-def run_desc(w, ntraj, traj0, step0, n_steps, precision, seed):
+def run_desc(w, ntraj, traj0, step0, n_steps, precision, seed, reg=None):
     from paper_2506_23928_gb300 import abi
     return abi.RunDesc(ntraj=ntraj, traj0=traj0, ns=w.ns, n_steps=n_steps, step0=step0, n_sweep=w.n_sweep, dt=w.dt,
                        scheme=abi.OTVMC_HEUN if w.scheme == "heun" else abi.OTVMC_MIDPOINT, precision=precision,
-                       reg=abi.OTVMC_REG_SHIFT, eps=w.eps, snr_thresh=4.0, seed=seed, measure_every=1,
-                       measure_final=0, use_graph=0)
+                       reg=abi.OTVMC_REG_SHIFT if reg is None else reg, eps=w.eps, snr_thresh=4.0, seed=seed,
+                       measure_every=1, measure_final=0, use_graph=0)
 
 
 def rbm_path(stream, fp64_value, peaks_):
@@ -335,12 +337,13 @@ def rbm_workload(name, stream, fp64_value, steps=3, warmup=2):
             "vs_fp64_jastrow_path": (value / fp64_value) if fp64_value else None}
 
 
-def jastrow_workload(name, stream, precision, steps=3, warmup=2):
+def jastrow_workload(name, stream, precision, steps=3, warmup=2, reg=None, ntraj=None):
     """A whole Jastrow workload at its full size: every trajectory advanced by one trajectory
     step per step (observables of the predictor samples included, as in the headline step), in
     waves of contiguous trajectory ids by device-memory footprint when the batch's workspace
     exceeds the free memory (one workspace of the largest wave, reused; the waves run one after
-    another).  CUDA events around each step."""
+    another).  CUDA events around each step.  reg: the regulariser (diagonal shift by default,
+    or the SNR filter); ntraj: fewer trajectories than the workload's, for a costly variant."""
     import numpy as np
     import torch
     import synth
@@ -348,11 +351,11 @@ def jastrow_workload(name, stream, precision, steps=3, warmup=2):
     from paper_2506_23928_gb300.abi import check
     w = synth.WORKLOADS[name] if name in synth.WORKLOADS else synth.PAPER_WORKLOADS[name]
     model, ans = build_model(w)
-    P, T, Wd = ans.P, w.ntraj, (w.n + 63) // 64
+    P, T, Wd = ans.P, (ntraj or w.ntraj), (w.n + 63) // 64
     seed = 20261204
 
     def desc(o, c, step0):
-        return run_desc(w, c, o, step0, 1, precision, seed)
+        return run_desc(w, c, o, step0, 1, precision, seed, reg)
     torch.cuda.empty_cache()
     free = torch.cuda.mem_get_info()[0]
     state = T * (P * 16 + w.ns * Wd * 8 + 9 * 8)
@@ -384,6 +387,7 @@ def jastrow_workload(name, stream, precision, steps=3, warmup=2):
             "precision": "mixed" if precision == abi.OTVMC_PREC_MIXED else "fp64",
             "config": {"workload": name, "N": w.n, "P": P, "ns": w.ns, "ntraj": T, "dt": w.dt, "scheme": w.scheme,
                        "eps": w.eps, "ansatz": "LJPH%d" % w.lj_d if w.ansatz == "lj" else "Jastrow",
+                       "regulariser": "snr (threshold 4)" if reg == abi.OTVMC_REG_SNR else "diagonal shift",
                        "waves": [list(x) for x in plan], "workspace_bytes": nb}}
 
 
@@ -724,7 +728,16 @@ def main():
                                                        warmup=3),
               "square10_jastrow": jastrow_workload("square10_jastrow", stream, abi.OTVMC_PREC_MIXED),
               "ring100_ljph1": jastrow_workload("ring100_ljph1", stream, abi.OTVMC_PREC_MIXED),
-              "ring160_ljph1": jastrow_workload("ring160_ljph1", stream, abi.OTVMC_PREC_MIXED)}
+              "ring160_ljph1": jastrow_workload("ring160_ljph1", stream, abi.OTVMC_PREC_MIXED),
+              # the paper's own regulariser (the SNR filter, threshold 4) on its Fig. 3 / Fig. 2 setups
+              "ring100_ljph1_snr": jastrow_workload("ring100_ljph1", stream, abi.OTVMC_PREC_MIXED, steps=2, warmup=1,
+                                                    reg=abi.OTVMC_REG_SNR),
+              "ring160_ljph1_snr": jastrow_workload("ring160_ljph1", stream, abi.OTVMC_PREC_MIXED, steps=2, warmup=1,
+                                                    reg=abi.OTVMC_REG_SNR)}
+        if args.snr_full_size:
+            # the SNR filter at the benchmark's P = 2080 (O(P^3) FP64 per trajectory): 8 trajectories
+            jw["chain64_jastrow_snr"] = jastrow_workload("chain64_jastrow", stream, abi.OTVMC_PREC_MIXED, steps=1,
+                                                         warmup=0, reg=abi.OTVMC_REG_SNR, ntraj=8)
 
     eq = None
     if not args.no_equal_error and world == 1:

@@ -149,7 +149,7 @@ OTVMC_API int64_t otvmc_ansatz_nparams(const otvmc_ansatz* ansatz);
  * expanded pair parameters (held in the workspace); build_S_F gives S in FP64 (S_d required,
  * from exact integer counts of the tied log-derivatives O_g = sum over the group of s_j s_k)
  * and D, obar folded from the exact pair sums, for either precision; solve_step then factors
- * S in FP64 (G_d unused); otvmc_solve_snr takes it for P <= 96.  N <= 200. */
+ * S in FP64 (G_d unused); otvmc_solve_snr takes it as well.  N <= 200. */
 OTVMC_API otvmc_status otvmc_ansatz_create_lj(const otvmc_model* model, int d, int pbc, otvmc_ansatz** out);
 
 /* How the MIXED path of run_trajectories forms T = O_c O_c^+ / ns of an RBM on the T path
@@ -293,12 +293,20 @@ OTVMC_API otvmc_status otvmc_solve_step(const otvmc_ansatz* ansatz, int ntraj, i
  *   SNR_k = |rho_k| / sqrt(Var_x Q_k / ns),
  *   f_k = 1 / (1 + (snr_thresh / SNR_k)^6) * 1 / (1 + (eps_svd lambda_max / lambda_k)^6),
  *   delta = V diag(f_k / lambda_k) rho, eigenvalues lambda_k <= 0 dropped.
- * Jastrow ansatz, P <= 96: one CTA per trajectory does a cyclic Jacobi eigen-decomposition
- * in FP64 in shared memory (else OTVMC_ERR_UNSUPPORTED).  Inputs: S_d [ntraj][P][P] full
- * FP64 S (otvmc_build_S_F), obar_d [ntraj][P], spins_d [ntraj][ns][W], v_d [ntraj][ns]
- * double2 (otvmc_local_estimators), D_d [ntraj][P] double2.  Outputs: delta_d [ntraj][P]
+ * Jastrow and tied Jastrow ansaetze, one CTA per trajectory, FP64 throughout.  P <= 96: a
+ * cyclic Jacobi eigen-decomposition in shared memory.  Larger P (up to what the shared memory
+ * of one CTA holds for the tridiagonal and a chunk of samples, about 3000): Householder
+ * tridiagonalisation of a copy of S in the workspace, the eigenvectors formed explicitly and
+ * refined by the implicit QL iteration (shift from the leading 2 x 2 block), then one pass over
+ * the samples; this costs O(P^3) FP64 work per trajectory for the decomposition and
+ * O(ns P^2) for the pass.  Inputs: S_d [ntraj][P][P] full FP64 S (otvmc_build_S_F), obar_d
+ * [ntraj][P], spins_d [ntraj][ns][W], v_d [ntraj][ns] double2 (otvmc_local_estimators), D_d
+ * [ntraj][P] double2.  work_bytes >= otvmc_snr_workspace_bytes(ansatz, ntraj) (256 bytes of
+ * status for P <= 96, plus 2 P^2 doubles per trajectory beyond).  Outputs: delta_d [ntraj][P]
  * double2; lambda_d (optional) [ntraj][P] eigenvalues, unordered.  A decomposition that has
- * not converged after 40 sweeps records OTVMC_ERR_NONFINITE in the status word. */
+ * not converged (40 Jacobi sweeps, or 60 QL iterations for one eigenvalue) records
+ * OTVMC_ERR_NONFINITE in the status word (delta = 0 for the QL case). */
+OTVMC_API size_t otvmc_snr_workspace_bytes(const otvmc_ansatz* ansatz, int ntraj);
 OTVMC_API otvmc_status otvmc_solve_snr(const otvmc_ansatz* ansatz, int ntraj, int ns, const double* S_d,
                                        const double* obar_d, const uint64_t* spins_d, const double* v_d,
                                        const double* D_d, double snr_thresh, double eps_svd, double* delta_d,
@@ -352,7 +360,7 @@ typedef struct otvmc_run_desc {
     double dt;
     int scheme;          /* OTVMC_HEUN or OTVMC_MIDPOINT */
     int precision;       /* OTVMC_PREC_FP64 or OTVMC_PREC_MIXED */
-    int reg;             /* OTVMC_REG_SHIFT, or OTVMC_REG_SNR (P <= 96, eps_svd = 1e-12) */
+    int reg;             /* OTVMC_REG_SHIFT, or OTVMC_REG_SNR (Jastrow ansaetze, eps_svd = 1e-12) */
     double eps;          /* diagonal shift */
     double snr_thresh;
     uint64_t seed;

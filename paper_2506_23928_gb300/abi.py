@@ -69,6 +69,7 @@ SIGNATURES = {
     "otvmc_solve_step": (c_int, [P, c_int, c_int, c_int, c_int, c_double, c_double, P, P, P, P, P, P, P, c_size_t,
                                  P]),
     "otvmc_solve_snr": (c_int, [P, c_int, c_int, P, P, P, P, P, c_double, c_double, P, P, P, c_size_t, P]),
+    "otvmc_snr_workspace_bytes": (c_size_t, [P, c_int]),
     "otvmc_sde_combine": (c_int, [c_int, c_int64, c_int, c_int, P, P, P, P, P, P, c_size_t, P]),
     "otvmc_observables": (c_int, [P, P, P, c_int, c_int, c_int, P, P, c_size_t, P]),
     "otvmc_ensemble": (c_int, [P, c_int, c_int, P, P, P, P]),
@@ -265,6 +266,10 @@ def _desc_array(descs):
     for i, d in enumerate(descs):
         arr[i] = d
     return arr
+
+
+def otvmc_snr_workspace_bytes(ansatz, ntraj):
+    return _call("otvmc_snr_workspace_bytes", ansatz, ntraj)
 
 
 def otvmc_run_grouped_workspace_bytes(ansatz, descs):

@@ -711,16 +711,27 @@ otvmc_status otvmc_solve_snr(const otvmc_ansatz* a, int ntraj, int ns, const dou
     otvmc_status st = check_batch(a, ntraj, ns);
     if (st) return st;
     if (a->kind == OTVMC_RBM) return fail(OTVMC_ERR_UNSUPPORTED, "solve_snr: built for the Jastrow ansaetze");
-    if (a->P > SNR_PMAX)
-        return fail(OTVMC_ERR_UNSUPPORTED, "solve_snr: built for P <= " + std::to_string(SNR_PMAX));
+    if (!snr_big_fits((int)a->P))
+        return fail(OTVMC_ERR_UNSUPPORTED, "solve_snr: P beyond the shared memory of one CTA");
     if (!S_d || !obar_d || !spins_d || !v_d || !D_d || !delta_d || !work_d || !(snr_thresh >= 0.0) ||
         !(eps_svd >= 0.0))
         return fail(OTVMC_ERR_INVALID, "solve_snr: bad arguments");
-    if (work_bytes < 256) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
-    CK(launch_snr_solve(a, ntraj, ns, spins_d, S_d, obar_d, (const double2*)v_d, (const double2*)D_d, snr_thresh,
-                        eps_svd, (double2*)delta_d, lambda_d, (int*)work_d, (cudaStream_t)stream),
-       "snr solve launch");
+    if (work_bytes < otvmc_snr_workspace_bytes(a, ntraj)) return fail(OTVMC_ERR_WORKSPACE, "workspace too small");
+    if (a->P > SNR_PMAX)
+        CK(launch_snr_big(a, ntraj, ns, spins_d, S_d, obar_d, (const double2*)v_d, (const double2*)D_d, snr_thresh,
+                          eps_svd, (double2*)delta_d, lambda_d, (char*)work_d + 256, (int*)work_d,
+                          (cudaStream_t)stream),
+           "snr solve launch");
+    else
+        CK(launch_snr_solve(a, ntraj, ns, spins_d, S_d, obar_d, (const double2*)v_d, (const double2*)D_d, snr_thresh,
+                            eps_svd, (double2*)delta_d, lambda_d, (int*)work_d, (cudaStream_t)stream),
+           "snr solve launch");
     return OTVMC_OK;
+}
+
+size_t otvmc_snr_workspace_bytes(const otvmc_ansatz* a, int ntraj) {
+    if (!a || ntraj < 1) return 0;
+    return a->P > SNR_PMAX ? 256 + snr_big_ws_bytes(ntraj, (int)a->P) : 256;
 }
 
 otvmc_status otvmc_sde_combine(int ntraj, int64_t P, int scheme, int stage, const double* theta_d,
@@ -850,6 +861,7 @@ struct RunBufs {
     double* lcr;
     float4* tab;   // RBM flip table of the FP32 sampler
     void* rbm;     // RBM build scratch
+    void* snr;     // SNR filter beyond the shared-memory size: the eigen-decomposition's matrices
     double2* thf;  // tied Jastrow: the expanded parameters of the full Jastrow
     double* lpl0;  // linear SSE: zeros in place of <L + L^+> in E_eff
     double* gq;    // linear SSE: the predictor's increment of ln Q
@@ -883,6 +895,7 @@ static RunBufs carve_run(Carver& c, const otvmc_ansatz* a, const otvmc_run_desc*
     r.lcr = nullptr;
     r.tab = nullptr;
     r.rbm = nullptr;
+    r.snr = (d->reg == OTVMC_REG_SNR && a->P > SNR_PMAX) ? c.take<char>(snr_big_ws_bytes(T, (int)P)) : nullptr;
     if (a->kind == OTVMC_RBM) {
         r.S = nullptr;
         r.G = nullptr;
@@ -935,9 +948,9 @@ static otvmc_status check_run(const otvmc_ansatz* a, const otvmc_run_desc* d) {
     if ((st = rbm_precision(a, d->precision))) return st;
     if (a->kind == OTVMC_RBM && d->reg != OTVMC_REG_SHIFT)
         return fail(OTVMC_ERR_UNSUPPORTED, "the SNR regulariser is built for the Jastrow ansatz");
-    if (d->reg == OTVMC_REG_SNR && a->kind != OTVMC_RBM && (a->P > SNR_PMAX || !(d->snr_thresh >= 0.0)))
-        return fail(OTVMC_ERR_UNSUPPORTED, "SNR regulariser: built for P <= " + std::to_string(SNR_PMAX) +
-                                               " (one CTA per trajectory) and snr_thresh >= 0");
+    if (d->reg == OTVMC_REG_SNR && a->kind != OTVMC_RBM && (!snr_big_fits((int)a->P) || !(d->snr_thresh >= 0.0)))
+        return fail(OTVMC_ERR_UNSUPPORTED, "SNR regulariser: needs snr_thresh >= 0 and P within the shared "
+                                           "memory of one CTA");
     return OTVMC_OK;
 }
 
@@ -1075,9 +1088,14 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     }
     if (lin) CK(launch_lnq(T, d->scheme, stage, r.eb.vinfo, r.gq, lin->lnQ, s), "lnq launch");
     if (d->reg == OTVMC_REG_SNR) {
-        CK(launch_snr_solve(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr, status,
-                            s),
-           "snr solve launch");
+        if (a->P > SNR_PMAX)
+            CK(launch_snr_big(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr,
+                              r.snr, status, s),
+               "snr solve launch");
+        else
+            CK(launch_snr_solve(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr,
+                                status, s),
+               "snr solve launch");
         return OTVMC_OK;
     }
     CK(launch_chol_solve(T, (int)a->P, ns, a->kind == OTVMC_LJ ? OTVMC_PREC_FP64 : d->precision, d->eps, r.S, r.G,

@@ -248,6 +248,12 @@ cudaError_t launch_lj_build(const otvmc_ansatz* a, const uint64_t* spins, int nt
 constexpr int SNR_PMAX = 96;
 constexpr double SNR_EPS_SVD = 1e-12;
 size_t snr_smem_bytes(int P);
+// the same filter for larger P: Householder tridiagonalisation, implicit QL, sample pass (k_snr_big.cu)
+size_t snr_big_ws_bytes(int ntraj, int P);
+bool snr_big_fits(int P);
+cudaError_t launch_snr_big(const otvmc_ansatz* a, int ntraj, int ns, const uint64_t* spins, const double* S,
+                           const double* obar, const double2* v, const double2* D, double thr, double eps_svd,
+                           double2* delta, double* lam, void* ws, int* status, cudaStream_t s);
 cudaError_t launch_snr_solve(const otvmc_ansatz* a, int ntraj, int ns, const uint64_t* spins, const double* S,
                              const double* obar, const double2* v, const double2* D, double thr, double eps_svd,
                              double2* delta, double* lam, int* status, cudaStream_t s);

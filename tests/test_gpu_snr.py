@@ -42,17 +42,22 @@ def _build(c, precision, T, ns, v, sp):
 
 
 @pytest.mark.parametrize("precision", [FP64, MIXED])
-@pytest.mark.parametrize("n,ns,thr", [(8, 1024, 4.0), (6, 304, 4.0), (9, 512, 40.0), (5, 200, 1e-9)])
+@pytest.mark.parametrize("n,ns,thr", [(8, 1024, 4.0), (6, 304, 4.0), (9, 512, 40.0), (5, 200, 1e-9),
+                                      (14, 512, 4.0), (24, 1024, 4.0), (31, 2048, 40.0), (20, 400, 1e-9),
+                                      (32, 1024, 4.0)])
 def test_solve_snr_matches_oracle(precision, n, ns, thr):
     """Odd and even P (Jacobi with and without the dummy index), a threshold that filters
-    many modes, and a vanishing one (the plain pseudo-inverse)."""
+    many modes, and a vanishing one (the plain pseudo-inverse); P = 105, 300, 496, 210 and 528
+    take the tridiagonal path (Householder, implicit QL, one pass over the samples)."""
     c = Case((n,), h=0.8, kappa=0.1, gamma=0.05)
     T, dt = 3, 0.01
     evs, v, sp, w = _evaluate(c, T, ns, 61, 0.2, dt)
     S, ob, D, v_d = _build(c, precision, T, ns, v, sp)
     delta = torch.zeros((T, c.P, 2), dtype=torch.float64, device="cuda")
     lam = torch.zeros((T, c.P), dtype=torch.float64, device="cuda")
-    work, nb = c.work(T, ns, precision)
+    nb = abi.otvmc_snr_workspace_bytes(c.ans.handle, T)
+    assert nb == (256 if c.P <= 96 else 256 + 2 * T * c.P * c.P * 8 + 256)
+    work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     check(abi.otvmc_solve_snr(c.ans.handle, T, ns, S, ob, sp, v_d, D, thr, 1e-12, delta, lam, work, nb))
     check(abi.otvmc_check(work))
     got = from_dev_complex(delta)[..., 0]
@@ -63,20 +68,30 @@ def test_solve_snr_matches_oracle(precision, n, ns, thr):
         assert rel_err(np.sort(lam[t].cpu().numpy()), np.linalg.eigvalsh(ev["S"].real)) < 1e-12
 
 
-def test_solve_snr_rejects_large_P_and_other_ansatz():
-    c = Case((14,), kappa=0.1)  # P = 105 > 96
+def test_solve_snr_rejects_what_it_does_not_hold():
+    """P beyond the shared memory of one CTA (N = 80: P = 3240), a workspace without room for
+    the decomposition, and the RBM."""
+    import paper_2506_23928_gb300 as pkg
     T, ns = 1, 64
     z = torch.zeros(8, dtype=torch.float64, device="cuda")
-    work, nb = c.work(T, ns, FP64)
-    st = abi.otvmc_solve_snr(c.ans.handle, T, ns, z, z, z, z, z, 4.0, 1e-12, z, None, work, nb)
-    assert st == abi.OTVMC_ERR_UNSUPPORTED
+    big = Case((80,), kappa=0.1)
+    work = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    assert abi.otvmc_solve_snr(big.ans.handle, T, ns, z, z, z, z, z, 4.0, 1e-12, z, None, work, 256) == \
+        abi.OTVMC_ERR_UNSUPPORTED
+    c = Case((14,), kappa=0.1)  # P = 105: needs 2 P^2 doubles of workspace per trajectory
+    assert abi.otvmc_solve_snr(c.ans.handle, T, ns, z, z, z, z, z, 4.0, 1e-12, z, None, work, 256) == \
+        abi.OTVMC_ERR_WORKSPACE
+    rbm = pkg.Ansatz(c.model, kind=abi.OTVMC_RBM, n_hidden=4)
+    assert abi.otvmc_solve_snr(rbm.handle, T, ns, z, z, z, z, z, 4.0, 1e-12, z, None, work, 256) == \
+        abi.OTVMC_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("scheme", [abi.OTVMC_HEUN, abi.OTVMC_MIDPOINT])
-def test_run_snr_matches_oracle(scheme):
+@pytest.mark.parametrize("scheme,n", [(abi.OTVMC_HEUN, 8), (abi.OTVMC_MIDPOINT, 8), (abi.OTVMC_MIDPOINT, 16)])
+def test_run_snr_matches_oracle(scheme, n):
     """Whole trajectories with the SNR regulariser (FP64): bit-identical chains and parameters
-    that agree to 1e-9 with the oracle's MC otVMC driven by the same draws."""
-    c = Case((8,), alpha=1.5, h=1.0, kappa=0.1)
+    that agree to 1e-9 with the oracle's MC otVMC driven by the same draws (P = 36 on the
+    Jacobi path, P = 136 on the tridiagonal one)."""
+    c = Case((n,), alpha=1.5, h=1.0, kappa=0.1)
     T, ns, steps, dt, seed = 2, 256, 3, 0.01, 91
     desc = abi.RunDesc(ntraj=T, traj0=0, ns=ns, n_steps=steps, step0=0, n_sweep=2, dt=dt, scheme=scheme,
                        precision=FP64, reg=abi.OTVMC_REG_SNR, eps=1e-4, snr_thresh=4.0, seed=seed,
@@ -97,7 +112,7 @@ def test_run_snr_matches_oracle(scheme):
 
 
 def test_run_snr_rejects_large_P():
-    c = Case((16,), kappa=0.1)  # P = 136
+    c = Case((80,), kappa=0.1)  # P = 3240
     desc = abi.RunDesc(ntraj=1, traj0=0, ns=64, n_steps=1, step0=0, n_sweep=1, dt=0.01, scheme=abi.OTVMC_HEUN,
                        precision=FP64, reg=abi.OTVMC_REG_SNR, eps=1e-4, snr_thresh=4.0, seed=1,
                        measure_every=0, measure_final=0, use_graph=0)
