@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-rbm-workloads", action="store_true")
     ap.add_argument("--no-jastrow-workloads", action="store_true")
     ap.add_argument("--no-equal-error", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shape")
     ap.add_argument("--snr-full-size", action="store_true",
                     help="also time the SNR regulariser at P = 2080 on 8 trajectories (about two minutes)")
     return ap.parse_args()
@@ -541,7 +542,8 @@ def main():
     d1 = run_desc(w, T, traj0, 0, 1, prec, seed)
     nb = abi.otvmc_run_workspace_bytes(ans.handle, d1)
     nbh = abi.otvmc_run_host_workspace_bytes(ans.handle, d1)
-    work = torch.zeros(max(nb, nbh), dtype=torch.uint8, device="cuda")
+    nbt = abi.otvmc_autotune_workspace_bytes(ans.handle, d1)
+    work = torch.zeros(max(nb, nbh, nbt), dtype=torch.uint8, device="cuda")
     mom = torch.zeros((1, T, 9), dtype=torch.float64, device="cuda")
 
     def step(i):
@@ -551,6 +553,14 @@ def main():
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
+    # launch shape (sub-batches, solver groups) picked by the library's autotuner on this batch,
+    # from a copy of the warmed-up state; no result depends on it
+    launch_shape = {"source": "built-in"}
+    if not args.no_autotune:
+        st, pipes, groups, tms = abi.otvmc_autotune_run(ans.handle, d1, theta, spins, work, max(nb, nbh, nbt), stream)
+        check(st)
+        launch_shape = {"source": "otvmc_autotune_run", "sub_batches": pipes,
+                        "solver_groups": groups if groups else "built-in rule", "tuning_step_ms": tms}
 
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
@@ -761,7 +771,7 @@ def main():
             "roofline": rl, "roofline_by_kernel": roof, "dominant_kernel": dominant,
             "kernel_timing": f"CUDA events per launch over {prof_steps} more step(s) after the timed region, "
                              "solver trajectory groups serialised (launch durations not shared)",
-            "stage_ms_per_step": stage_ms, "cpu_baseline": cpu, "fp64_path": fp64, "rbm_mixed_path": rbm,
+            "stage_ms_per_step": stage_ms, "launch_shape": launch_shape, "cpu_baseline": cpu, "fp64_path": fp64, "rbm_mixed_path": rbm,
             "rbm_workloads": rbm_full, "jastrow_workloads": jw, "equal_error": eq,
             "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}

@@ -393,6 +393,26 @@ OTVMC_API otvmc_status otvmc_run_trajectories_grouped(const otvmc_ansatz* ansatz
                                                       uint64_t* const* spins_d, double* const* moments_d,
                                                       void* work_d, size_t work_bytes, void* stream);
 
+/* Launch-shape autotuner.  A run's launches can be issued as 1, 2 or 4 sub-batches on forked
+ * streams (each of at least 8 trajectories), and the mixed tensor-core solver's launches as 1, 2
+ * or 4 trajectory groups on forked streams inside each; none of this changes any result.
+ * otvmc_autotune_run times one step of every candidate shape for this batch (the fastest of three
+ * repetitions, from copies of theta_d and spins_d, which are left untouched; with measurements
+ * when desc measures),
+ * records the fastest for the batch shape (ansatz kind and sizes, ns, ntraj, precision,
+ * regulariser), and later runs of that shape in this process use it.  Without a record the
+ * built-in shape applies (2 sub-batches for a Jastrow batch of 32 trajectories or more, else 1;
+ * the solver's own group rule).  otvmc_run_workspace_bytes already covers every shape.
+ * work_bytes >= otvmc_autotune_workspace_bytes (the run's workspace plus copies of the state).
+ * Outputs (optional): the chosen sub-batch count, group count (0: the solver's rule) and the
+ * step time in ms.  Synchronises.  otvmc_autotune_clear forgets every record. */
+OTVMC_API size_t otvmc_autotune_workspace_bytes(const otvmc_ansatz* ansatz, const otvmc_run_desc* desc);
+OTVMC_API otvmc_status otvmc_autotune_run(const otvmc_ansatz* ansatz, const otvmc_run_desc* desc,
+                                          const double* theta_d, const uint64_t* spins_d, void* work_d,
+                                          size_t work_bytes, void* stream, int* pipes_out, int* groups_out,
+                                          double* ms_out);
+OTVMC_API void otvmc_autotune_clear(void);
+
 /* The linear stochastic Schroedinger equation (App. B) instead of the nonlinear one: the same
  * otVMC equations with E_eff replaced by E_eff^lin = <x|H - i/2 sum_n (L_n^+ L_n + L_n^2)|psi>/psi(x)
  * (so F^lin = F - i sum_n <L_n + L_n^+> N^n), and for every trajectory the normalisation Q of

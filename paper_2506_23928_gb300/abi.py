@@ -78,6 +78,9 @@ SIGNATURES = {
     "otvmc_run_trajectories": (c_int, [P, P, P, P, P, P, c_size_t, P]),
     "otvmc_run_trajectories_linear": (c_int, [P, P, P, P, P, P, P, P, c_size_t, P]),
     "otvmc_run_grouped_workspace_bytes": (c_size_t, [P, P, c_int]),
+    "otvmc_autotune_workspace_bytes": (c_size_t, [P, P]),
+    "otvmc_autotune_run": (c_int, [P, P, P, P, P, c_size_t, P, P, P, P]),
+    "otvmc_autotune_clear": (None, []),
     "otvmc_run_trajectories_grouped": (c_int, [P, P, c_int, P, P, P, P, c_size_t, P]),
     "otvmc_ensemble_weighted": (c_int, [P, P, c_int, c_int, P, P, P, P]),
     "otvmc_run_host_workspace_bytes": (c_size_t, [P, P]),
@@ -266,6 +269,23 @@ def _desc_array(descs):
     for i, d in enumerate(descs):
         arr[i] = d
     return arr
+
+
+def otvmc_autotune_workspace_bytes(ansatz, desc):
+    return _call("otvmc_autotune_workspace_bytes", ansatz, ctypes.addressof(desc))
+
+
+def otvmc_autotune_run(ansatz, desc, theta_d, spins_d, work_d, work_bytes, stream=None):
+    """Returns (status, sub-batches, solver groups, ms per step) of the recorded shape."""
+    pipes, groups, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    st = _call("otvmc_autotune_run", ansatz, ctypes.addressof(desc), ptr(theta_d), ptr(spins_d), ptr(work_d),
+               work_bytes, stream_ptr(stream), ctypes.addressof(pipes), ctypes.addressof(groups),
+               ctypes.addressof(ms))
+    return st, pipes.value, groups.value, ms.value
+
+
+def otvmc_autotune_clear():
+    _call("otvmc_autotune_clear")
 
 
 def otvmc_snr_workspace_bytes(ansatz, ntraj):

@@ -974,11 +974,49 @@ int otvmc_run_n_meas(const otvmc_run_desc* d) {
 // status word at its head.
 constexpr int RUN_PIPES = 2;
 constexpr int RUN_PIPE_MIN = 32;
+constexpr int RUN_MAX_PIPES = 4;      // the most sub-batches a launch-shape setting may ask for
+constexpr int RUN_PIPE_MIN_SIZE = 8;  // ... each of at least this many trajectories
 
-// (Jastrow only: with the RBM's T path the solve of size 2 ns dominates, and sub-batches
-// whose solves compete measured slower.)
-static int run_pipes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
-    return a->kind == OTVMC_JASTROW && d->ntraj >= RUN_PIPE_MIN ? RUN_PIPES : 1;
+// Launch shape of a run: sub-batches on forked streams, and trajectory groups of the mixed
+// solver inside each (0: the solver's own rule).  Neither changes any result (trajectories are
+// independent and every draw is keyed by the global trajectory id).  otvmc_autotune_run times
+// the candidates on a batch and records the fastest per batch shape; runs of that shape use it.
+struct LaunchShape {
+    int pipes;
+    int groups;
+};
+struct TuneKey {
+    int kind, n, m, P, ns, ntraj, precision, reg;
+    bool operator<(const TuneKey& o) const {
+        const int a[8] = {kind, n, m, P, ns, ntraj, precision, reg};
+        const int b[8] = {o.kind, o.n, o.m, o.P, o.ns, o.ntraj, o.precision, o.reg};
+        for (int i = 0; i < 8; ++i)
+            if (a[i] != b[i]) return a[i] < b[i];
+        return false;
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, LaunchShape> g_tune;
+static TuneKey tune_key(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    return TuneKey{a->kind, a->n, a->m, (int)a->P, d->ns, d->ntraj, d->precision, d->reg};
+}
+
+// (Jastrow only by default: with the RBM's T path the solve of size 2 ns dominates, and
+// sub-batches whose solves compete measured slower.)
+static LaunchShape default_shape(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    return LaunchShape{a->kind == OTVMC_JASTROW && d->ntraj >= RUN_PIPE_MIN ? RUN_PIPES : 1, 0};
+}
+static LaunchShape run_shape(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(a, d));
+    return it != g_tune.end() ? it->second : default_shape(a, d);
+}
+// sub-batch counts a run of this batch may use (the workspace is sized for the largest need)
+static int pipe_candidates(const otvmc_run_desc* d, int* out) {
+    int n = 0;
+    for (int np = 1; np <= RUN_MAX_PIPES; np *= 2)
+        if (np == 1 || d->ntraj >= np * RUN_PIPE_MIN_SIZE) out[n++] = np;
+    return n;
 }
 
 // Sub-batch p of np: its descriptor and the offset of its first trajectory in the batch.
@@ -999,9 +1037,9 @@ static size_t pipe_bytes(const otvmc_ansatz* a, const otvmc_run_desc* q) {
 }
 
 struct PipeStreams {
-    cudaStream_t s[RUN_PIPES];
+    cudaStream_t s[RUN_MAX_PIPES];
     cudaEvent_t fork;
-    cudaEvent_t join[RUN_PIPES];
+    cudaEvent_t join[RUN_MAX_PIPES];
 };
 // One set per (device, calling stream), created on first use.
 static PipeStreams& pipe_streams(cudaStream_t caller) {
@@ -1014,7 +1052,7 @@ static PipeStreams& pipe_streams(cudaStream_t caller) {
     auto it = sets.find(key);
     if (it != sets.end()) return it->second;
     PipeStreams& g = sets[key];
-    for (int i = 0; i < RUN_PIPES; ++i) {
+    for (int i = 0; i < RUN_MAX_PIPES; ++i) {
         cudaStreamCreateWithFlags(&g.s[i], cudaStreamNonBlocking);
         cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming);
     }
@@ -1022,9 +1060,7 @@ static PipeStreams& pipe_streams(cudaStream_t caller) {
     return g;
 }
 
-size_t otvmc_run_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
-    if (check_run(a, d)) return 0;
-    const int np = run_pipes(a, d);
+static size_t run_bytes_pipes(const otvmc_ansatz* a, const otvmc_run_desc* d, int np) {
     size_t total = 0;
     for (int p = 0; p < np; ++p) {
         int first = 0;
@@ -1032,6 +1068,17 @@ size_t otvmc_run_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d)
         total += pipe_bytes(a, &q);
     }
     return total + 256;
+}
+
+// The largest need over the launch shapes a run of this batch may take (a shape recorded by
+// the autotuner later must fit a workspace sized now).
+size_t otvmc_run_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    if (check_run(a, d)) return 0;
+    int cand[4];
+    const int nc = pipe_candidates(d, cand);
+    size_t best = 0;
+    for (int i = 0; i < nc; ++i) best = std::max(best, run_bytes_pipes(a, d, cand[i]));
+    return best;
 }
 
 // One evaluation at theta (eval index ev): sample, estimators, [observables], S/D, solve.
@@ -1173,11 +1220,19 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
 }
 
 // The batch as sub-batches on forked streams (one after another on s under serial profiling).
-static otvmc_status run_pipelined(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d, uint64_t* spins_d,
-                                  double* moments_d, void* work_d, size_t work_bytes, cudaStream_t s,
-                                  const LinState* lin = nullptr) {
+// Restores the issuing thread's solver-group setting when a run's launches have been issued.
+struct GroupSetting {
+    int old;
+    explicit GroupSetting(int g) : old(chol_set_groups(g)) {}
+    ~GroupSetting() { chol_set_groups(old); }
+};
+
+static otvmc_status run_pipelined_shape(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d,
+                                        uint64_t* spins_d, double* moments_d, void* work_d, size_t work_bytes,
+                                        cudaStream_t s, const LinState* lin, LaunchShape shape) {
     int* status = (int*)work_d;
-    const int np = run_pipes(a, d);
+    const int np = shape.pipes;
+    const GroupSetting gs_(shape.groups);
     if (np == 1) return run_steps(a, d, theta_d, spins_d, moments_d, d->ntraj, work_d, work_bytes, status, s, lin);
     const bool forked = !profiling_serial();
     PipeStreams& ps = pipe_streams(s);
@@ -1207,6 +1262,12 @@ static otvmc_status run_pipelined(const otvmc_ansatz* a, const otvmc_run_desc* d
         left -= need;
     }
     return OTVMC_OK;
+}
+
+static otvmc_status run_pipelined(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d, uint64_t* spins_d,
+                                  double* moments_d, void* work_d, size_t work_bytes, cudaStream_t s,
+                                  const LinState* lin = nullptr) {
+    return run_pipelined_shape(a, d, theta_d, spins_d, moments_d, work_d, work_bytes, s, lin, run_shape(a, d));
 }
 
 otvmc_status otvmc_run_trajectories(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d,
@@ -1319,6 +1380,91 @@ otvmc_status otvmc_run_trajectories_grouped(const otvmc_ansatz* a, const otvmc_r
         if (st && !first_err) first_err = st;
     }
     return first_err;
+}
+
+// ------------------------------------------------------------------ launch-shape autotuner
+// the tuning step: one step with the caller's measurement setting
+static otvmc_run_desc tune_desc(const otvmc_run_desc* d) {
+    otvmc_run_desc q = *d;
+    q.n_steps = 1;
+    q.measure_every = d->measure_every > 0 ? 1 : 0;
+    return q;
+}
+static size_t tune_state_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    const size_t T = (size_t)d->ntraj;
+    const otvmc_run_desc q = tune_desc(d);
+    return ((T * a->P * 16 + 255) & ~(size_t)255) + ((T * d->ns * ((a->n + 63) / 64) * 8 + 255) & ~(size_t)255) +
+           (((size_t)otvmc_run_n_meas(&q) * T * OTVMC_MOMENTS * 8 + 255) & ~(size_t)255);
+}
+
+size_t otvmc_autotune_workspace_bytes(const otvmc_ansatz* a, const otvmc_run_desc* d) {
+    const size_t b = otvmc_run_workspace_bytes(a, d);
+    return b ? ((b + 255) & ~(size_t)255) + tune_state_bytes(a, d) : 0;
+}
+
+otvmc_status otvmc_autotune_run(const otvmc_ansatz* a, const otvmc_run_desc* d, const double* theta_d,
+                                const uint64_t* spins_d, void* work_d, size_t work_bytes, void* stream,
+                                int* pipes_out, int* groups_out, double* ms_out) {
+    otvmc_status st = check_run(a, d);
+    if (st) return st;
+    if (!theta_d || !spins_d || !work_d) return fail(OTVMC_ERR_INVALID, "autotune: null buffer");
+    const size_t need = otvmc_autotune_workspace_bytes(a, d);
+    if (work_bytes < need) return fail(OTVMC_ERR_WORKSPACE, "autotune: workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    // one step with the caller's measurement setting, from copies of the caller's state (left
+    // untouched)
+    const otvmc_run_desc q = tune_desc(d);
+    const size_t rb = (otvmc_run_workspace_bytes(a, d) + 255) & ~(size_t)255;
+    const size_t T = (size_t)d->ntraj, W = (size_t)((a->n + 63) / 64);
+    double* th = (double*)((char*)work_d + rb);
+    uint64_t* sp = (uint64_t*)((char*)th + ((T * a->P * 16 + 255) & ~(size_t)255));
+    double* mo = (double*)((char*)sp + ((T * d->ns * W * 8 + 255) & ~(size_t)255));
+    int cand[4];
+    const int nc = pipe_candidates(d, cand);
+    const bool grouped = a->kind != OTVMC_LJ && d->precision == OTVMC_PREC_MIXED;  // the tensor-core solver
+    const int gcand[4] = {0, 1, 2, CHOL_MAX_GROUPS};
+    const int ngc = grouped ? 4 : 1;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "autotune event");
+    CK(cudaEventCreate(&e1), "autotune event");
+    LaunchShape best{1, 0};
+    float best_ms = INFINITY;
+    for (int i = 0; i < nc && !st; ++i)
+        for (int j = 0; j < ngc && !st; ++j) {
+            const LaunchShape sh{cand[i], gcand[j]};
+            float ms = INFINITY;
+            for (int rep = 0; rep < 3 && !st; ++rep) {  // the fastest of three (the first may be cold)
+                cudaMemcpyAsync(th, theta_d, T * a->P * 16, cudaMemcpyDeviceToDevice, s);
+                cudaMemcpyAsync(sp, spins_d, T * d->ns * W * 8, cudaMemcpyDeviceToDevice, s);
+                cudaEventRecord(e0, s);
+                st = run_pipelined_shape(a, &q, th, sp, otvmc_run_n_meas(&q) ? mo : nullptr, work_d, rb, s, nullptr,
+                                         sh);
+                cudaEventRecord(e1, s);
+                if (!st) st = otvmc_check(work_d, stream);
+                float m = 0.f;
+                if (!st && cudaEventElapsedTime(&m, e0, e1) == cudaSuccess) ms = std::min(ms, m);
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = sh;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tune_key(a, d)] = best;
+    }
+    if (pipes_out) *pipes_out = best.pipes;
+    if (groups_out) *groups_out = best.groups;
+    if (ms_out) *ms_out = best_ms;
+    return OTVMC_OK;
+}
+
+void otvmc_autotune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
 }
 
 otvmc_status otvmc_run_trajectories_linear(const otvmc_ansatz* a, const otvmc_run_desc* d, double* theta_d,

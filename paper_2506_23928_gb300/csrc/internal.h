@@ -264,6 +264,10 @@ size_t chol_ws_bytes(int ntraj, int P, int precision);
 // bound of the pipeline waits of the tensor-core kernels of one translation unit (current device)
 cudaError_t gram_set_wait_limit(unsigned long long ns);
 cudaError_t chol_set_wait_limit(unsigned long long ns);
+// number of trajectory groups of the mixed solver's launches issued by this host thread from now
+// on (0: the built-in rule); returns the previous setting
+int chol_set_groups(int groups);
+constexpr int CHOL_MAX_GROUPS = 4;
 // x += (L L^T)^-1 r with the factor left in ws by the last mixed (tensor-core) solve of this size
 cudaError_t launch_chol_tc_resolve(int ntraj, int P, void* ws, const double2* r, double2* x, cudaStream_t s);
 // linear SSE: ln Q of every trajectory from the mean of v^lin (k_misc.cu)

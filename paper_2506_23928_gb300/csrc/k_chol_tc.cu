@@ -1355,7 +1355,11 @@ inline int ldim(int P) { return ((P + 63) / 64) * 64; }
 constexpr int CHOL_GROUPS = 4;
 // Trajectory groups of one call: groups of 64 once the call has 128 trajectories or more
 // (each launch then fills the GPU by itself), else CHOL_GROUPS groups from 16 trajectories.
+// A run's launch-shape setting (set around a run's launches on the issuing host thread) may fix
+// the number of groups instead: 1 .. CHOL_GROUPS, at most one group per trajectory.
+thread_local int t_chol_groups = 0;
 inline int chol_groups(int ntraj) {
+    if (t_chol_groups > 0) return t_chol_groups < ntraj ? t_chol_groups : ntraj;
     if (ntraj < 16) return 1;
     if (ntraj >= 128) return ntraj / 64 < CHOL_GROUPS ? ntraj / 64 : CHOL_GROUPS;
     return CHOL_GROUPS;
@@ -1546,6 +1550,12 @@ cudaError_t launch_chol_tc(int ntraj, int P, int ns, double eps, const float* G,
 // One more correction with the factor that the last launch_chol_tc on this workspace left:
 // x += (L L^T)^-1 r for every trajectory whose pivots did not fail (the others were solved by
 // the fallback with a raised shift and keep x).  r, x: [ntraj][P] double2 (two right-hand sides).
+int chol_set_groups(int groups) {
+    const int old = chol::t_chol_groups;
+    chol::t_chol_groups = groups < 0 ? 0 : (groups > chol::CHOL_GROUPS ? chol::CHOL_GROUPS : groups);
+    return old;
+}
+
 cudaError_t launch_chol_tc_resolve(int ntraj, int P, void* ws, const double2* r, double2* x, cudaStream_t s) {
     using namespace chol;
     const int LD = ldim(P);
