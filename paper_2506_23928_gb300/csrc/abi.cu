@@ -1137,7 +1137,8 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     if (d->reg == OTVMC_REG_SNR) {
         if (a->P > SNR_PMAX)
             CK(launch_snr_big(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr,
-                              r.snr, status, s),
+                              r.snr, status, s, d->precision == OTVMC_PREC_MIXED,
+                              a->kind == OTVMC_LJ ? lj_built_O(a, T, r.obuf) : nullptr),
                "snr solve launch");
         else
             CK(launch_snr_solve(a, T, ns, spins, r.S, r.obar, r.v, r.D, d->snr_thresh, SNR_EPS_SVD, delta, nullptr,

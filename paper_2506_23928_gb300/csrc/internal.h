@@ -240,6 +240,8 @@ inline size_t rbm_sample_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
 // tied Jastrow (k_lj.cu)
 cudaError_t launch_lj_expand(const otvmc_ansatz* a, int ntraj, const double2* theta, double2* theta_full,
                              cudaStream_t s);
+// the tied log-derivatives O [ntraj][P][ns] int16 that launch_lj_build left in its workspace
+const int16_t* lj_built_O(const otvmc_ansatz* a, int ntraj, const void* ws);
 size_t lj_build_bytes(const otvmc_ansatz* a, int ntraj, int ns);
 cudaError_t launch_lj_build(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const EvalBufs& b,
                             void* ws, double* S, double* obar, double2* D, cudaStream_t s);
@@ -253,7 +255,8 @@ size_t snr_big_ws_bytes(int ntraj, int P);
 bool snr_big_fits(int P);
 cudaError_t launch_snr_big(const otvmc_ansatz* a, int ntraj, int ns, const uint64_t* spins, const double* S,
                            const double* obar, const double2* v, const double2* D, double thr, double eps_svd,
-                           double2* delta, double* lam, void* ws, int* status, cudaStream_t s);
+                           double2* delta, double* lam, void* ws, int* status, cudaStream_t s,
+                           bool fp32_pass = false, const int16_t* Oint = nullptr);
 cudaError_t launch_snr_solve(const otvmc_ansatz* a, int ntraj, int ns, const uint64_t* spins, const double* S,
                              const double* obar, const double2* v, const double2* D, double thr, double eps_svd,
                              double2* delta, double* lam, int* status, cudaStream_t s);

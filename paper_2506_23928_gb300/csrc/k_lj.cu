@@ -186,6 +186,12 @@ size_t lj_build_bytes(const otvmc_ansatz* a, int ntraj, int ns) {
     return rup(T * Pf * 8) + rup(T * Pf * 16) + rup(T * P * ns * 2) + rup(T * P * P * 8) + 256;
 }
 
+const int16_t* lj_built_O(const otvmc_ansatz* a, int ntraj, const void* ws) {
+    using lj::rup;
+    const size_t T = (size_t)ntraj, Pf = (size_t)a->full->P;
+    return (const int16_t*)((const char*)ws + rup(T * Pf * 8) + rup(T * Pf * 16));
+}
+
 // S (full FP64), obar and D of the tied parameters from the samples and the quantised v in b
 // (vpart / vquant already run on b): D and obar of the full Jastrow by the exact integer sums,
 // folded over the groups; S from the exact integer Gram matrix of the tied O.

@@ -25,23 +25,8 @@ namespace otvmc {
 constexpr int SNRB_THREADS = 256;
 constexpr int SNRB_WARPS = SNRB_THREADS / 32;
 constexpr int SNRB_MAX_ITER = 60;        // QL iterations per eigenvalue before giving up
-constexpr int SNRB_SMEM_BUDGET = 220 * 1024;
-
-// O_k(x) - obar_k of a Jastrow (pairs) or tied Jastrow (groups of pairs) ansatz
-__device__ __forceinline__ double ocb_val(const uint64_t* w, const int* pairs, const int* grp_off,
-                                          const int* grp_pair, int n, int k, const double* ob) {
-    if (k < n) return (double)spin_of(w, k) - ob[k];
-    if (grp_off == nullptr) {
-        const int j = pairs[2 * (k - n)], l = pairs[2 * (k - n) + 1];
-        return (double)(spin_of(w, j) * spin_of(w, l)) - ob[k];
-    }
-    int sum = 0;
-    for (int e = grp_off[k - n]; e < grp_off[k - n + 1]; ++e) {
-        const int p = grp_pair[e];
-        sum += spin_of(w, pairs[2 * p]) * spin_of(w, pairs[2 * p + 1]);
-    }
-    return (double)sum - ob[k];
-}
+constexpr int SNRB_SMEM_BUDGET = 216 * 1024;  // + the signs of a chunk of samples
+constexpr int SNRB_SGN_BYTES = 16 * 200;          // 16 samples x N <= 200 sites
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -68,12 +53,94 @@ __host__ __device__ inline int snrb_chunk(int P) {
     return c > 16 ? 16 : c;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// One pass over the samples in chunks of CH held in shared memory (och): per eigenvector k
+// (row k of V), the sums over x of Q_k(x) = y_k(x) v_c(x), y_k(x) = sum_i V_ki O_c,i(x), and of
+// |Q_k(x)|^2, added to qs[k] and q2[k].  One warp per k; y in T, Q and the sums in FP64.
+template <typename T>
+__device__ void snrb_sample_pass(int n, int W, int P, int ns, const uint64_t* sp, const int* pairs,
+                                 const int* grp_off, const int* grp_pair, const int16_t* Oint, const double* ob,
+                                 const T* V, T* och, signed char* sgn, int CH, const double2* vt, double vbx,
+                                 double vby, double2* qs, double* q2) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int x0 = 0; x0 < ns; x0 += CH) {
+        const int nc = min(CH, ns - x0);
+        if (Oint != nullptr) {
+            // the log-derivatives already built as integers ([P][ns] of this trajectory)
+            for (int q = tid; q < nc * P; q += blockDim.x) {
+                const int i = q / nc, c = q % nc;
+                och[(size_t)c * P + i] = (T)((double)Oint[(size_t)i * ns + x0 + c] - ob[i]);
+            }
+        } else {
+            // the chunk's spins as signs in shared memory, then O - obar from them
+            for (int q = tid; q < nc * n; q += blockDim.x) {
+                const int c = q / n, j = q % n;
+                sgn[c * n + j] = (signed char)spin_of(sp + (size_t)(x0 + c) * W, j);
+            }
+            __syncthreads();
+            for (int q = tid; q < nc * P; q += blockDim.x) {
+                const int c = q / P, i = q % P;
+                const signed char* sg = sgn + c * n;
+                int o;
+                if (i < n) {
+                    o = sg[i];
+                } else if (grp_off == nullptr) {
+                    o = sg[pairs[2 * (i - n)]] * sg[pairs[2 * (i - n) + 1]];
+                } else {
+                    o = 0;
+                    for (int e = grp_off[i - n]; e < grp_off[i - n + 1]; ++e) {
+                        const int pp = grp_pair[e];
+                        o += sg[pairs[2 * pp]] * sg[pairs[2 * pp + 1]];
+                    }
+                }
+                och[(size_t)c * P + i] = (T)((double)o - ob[i]);
+            }
+        }
+        __syncthreads();
+        for (int k = warp; k < P; k += SNRB_WARPS) {
+            const T* Vk = V + (size_t)k * P;
+            T y[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) y[c] = (T)0;
+            for (int i = lane; i < P; i += 32) {
+                const T vk = Vk[i];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    if (c < nc) y[c] += vk * och[(size_t)c * P + i];
+            }
+            double ax = 0.0, ay = 0.0, a2 = 0.0;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                if (c >= nc) break;
+                const double yc = (double)warp_sum_t(y[c]);
+                const double vx = vt[x0 + c].x - vbx, vy = vt[x0 + c].y - vby;
+                const double qx = yc * vx, qy = yc * vy;
+                ax += qx;
+                ay += qy;
+                a2 += qx * qx + qy * qy;
+            }
+            if (lane == 0) {
+                qs[k].x += ax;
+                qs[k].y += ay;
+                q2[k] += a2;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(SNRB_THREADS, 1) snr_big_kernel(
     int n, int W, int P, int ns, const uint64_t* __restrict__ spins, const int* __restrict__ pairs,
     const int* __restrict__ grp_off, const int* __restrict__ grp_pair, const double* __restrict__ S,
     const double* __restrict__ obar, const double2* __restrict__ v, const double2* __restrict__ D, double thr,
     double eps_svd, double* __restrict__ Aws, double* __restrict__ Xws, double2* __restrict__ delta,
-    double* __restrict__ lam_out, int* status) {
+    double* __restrict__ lam_out, int* status, int fp32_pass, const int16_t* __restrict__ Oint) {
     const int t = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     extern __shared__ __align__(16) double sm[];
     double* d = sm;            // [P] diagonal, then the eigenvalues
@@ -85,6 +152,7 @@ __global__ void __launch_bounds__(SNRB_THREADS, 1) snr_big_kernel(
     double* ss = cs + P;       // [P] rotation sines
     double* red = ss + P;      // [32] (+1 for odd P: och stays 16-byte aligned)
     double* och = red + 32 + (P & 1);  // [CH][P] centred O of a chunk of samples
+    signed char* sgn = reinterpret_cast<signed char*>(och + (size_t)snrb_chunk(P) * P);  // [CH][N] spins
     __shared__ int ql_l, ql_m, ql_lo, ql_done, ql_fail;
     const size_t PP = (size_t)P * P;
     double* A = Aws + (size_t)t * PP;
@@ -226,7 +294,8 @@ __global__ void __launch_bounds__(SNRB_THREADS, 1) snr_big_kernel(
                 for (; i >= l; --i) {
                     double f = s * e[i];
                     const double b = c * e[i];
-                    r = hypot(f, g);
+                    r = sqrt(f * f + g * g);
+                    if (!(r > 1e-150)) r = hypot(f, g);  // squares below the normal range
                     e[i + 1] = r;
                     if (r == 0.0) {  // deflation inside the sweep
                         d[i + 1] -= p;
@@ -234,8 +303,9 @@ __global__ void __launch_bounds__(SNRB_THREADS, 1) snr_big_kernel(
                         underflow = true;
                         break;
                     }
-                    s = f / r;
-                    c = g / r;
+                    const double ir = 1.0 / r;
+                    s = f * ir;
+                    c = g * ir;
                     g = d[i + 1] - p;
                     r = (d[i] - g) * s + 2.0 * c * b;
                     p = s * r;
@@ -265,11 +335,21 @@ __global__ void __launch_bounds__(SNRB_THREADS, 1) snr_big_kernel(
             for (int col = tid; col < P; col += blockDim.x) {
                 if (m - 1 < lo) break;
                 double zi1 = X[(size_t)m * P + col];  // row i + 1 for i = m - 1
-                for (int i = m - 1; i >= lo; --i) {
-                    const double zi = X[(size_t)i * P + col];
-                    const double c = cs[i], s = ss[i];
-                    X[(size_t)(i + 1) * P + col] = s * zi + c * zi1;
-                    zi1 = c * zi - s * zi1;
+                // rows are loaded eight at a time ahead of the rotations that use them (each
+                // row is stored only after it has been loaded)
+                for (int i = m - 1; i >= lo; i -= 8) {
+                    const int nb = min(8, i - lo + 1);
+                    double z[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (u < nb) z[u] = X[(size_t)(i - u) * P + col];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (u < nb) {
+                            const double c = cs[i - u], s = ss[i - u];
+                            X[(size_t)(i - u + 1) * P + col] = s * z[u] + c * zi1;
+                            zi1 = c * z[u] - s * zi1;
+                        }
                 }
                 X[(size_t)lo * P + col] = zi1;
             }
@@ -317,42 +397,18 @@ __global__ void __launch_bounds__(SNRB_THREADS, 1) snr_big_kernel(
     const int CH = snrb_chunk(P);
     const uint64_t* sp = spins + (size_t)t * ns * W;
     const double* ob = obar + (size_t)t * P;
-    for (int x0 = 0; x0 < ns; x0 += CH) {
-        const int nc = min(CH, ns - x0);
-        for (int q = tid; q < nc * P; q += blockDim.x) {
-            const int c = q / P, i = q % P;
-            och[(size_t)c * P + i] = ocb_val(sp + (size_t)(x0 + c) * W, pairs, grp_off, grp_pair, n, i, ob);
-        }
+    const int16_t* Ot = Oint != nullptr ? Oint + (size_t)t * P * ns : nullptr;
+    if (fp32_pass) {
+        // y in FP32 from an FP32 copy of the eigenvectors (in A's place, no longer needed):
+        // the variances only set the filter, to a relative accuracy of about 1e-6
+        float* Xf = reinterpret_cast<float*>(A);
+        for (size_t i = tid; i < PP; i += blockDim.x) Xf[i] = (float)X[i];
         __syncthreads();
-        for (int k = warp; k < P; k += SNRB_WARPS) {
-            const double* Xk = X + (size_t)k * P;
-            double y[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) y[c] = 0.0;
-            for (int i = lane; i < P; i += 32) {
-                const double xk = Xk[i];
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c < nc) y[c] += xk * och[(size_t)c * P + i];
-            }
-            double ax = 0.0, ay = 0.0, a2 = 0.0;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                if (c >= nc) break;
-                const double yc = warp_sum(y[c]);
-                const double vx = vt[x0 + c].x - vbx, vy = vt[x0 + c].y - vby;
-                const double qx = yc * vx, qy = yc * vy;
-                ax += qx;
-                ay += qy;
-                a2 += qx * qx + qy * qy;
-            }
-            if (lane == 0) {
-                qs[k].x += ax;
-                qs[k].y += ay;
-                q2[k] += a2;
-            }
-        }
-        __syncthreads();
+        snrb_sample_pass<float>(n, W, P, ns, sp, pairs, grp_off, grp_pair, Ot, ob, Xf, reinterpret_cast<float*>(och),
+                                sgn, CH, vt, vbx, vby, qs, q2);
+    } else {
+        snrb_sample_pass<double>(n, W, P, ns, sp, pairs, grp_off, grp_pair, Ot, ob, X, och, sgn, CH, vt, vbx, vby, qs,
+                                 q2);
     }
 
     // ---- (5) filter and back-projection: delta_i = sum_k V_ik c_k, c_k = f_k rho_k / lambda_k
@@ -390,7 +446,9 @@ __global__ void __launch_bounds__(SNRB_THREADS, 1) snr_big_kernel(
     }
 }
 
-size_t snr_big_smem_bytes(int P) { return (size_t)(7 * P + 32 + (P & 1) + snrb_chunk(P) * P) * sizeof(double); }
+size_t snr_big_smem_bytes(int P) {
+    return (size_t)(7 * P + 32 + (P & 1) + snrb_chunk(P) * P) * sizeof(double) + SNRB_SGN_BYTES;
+}
 
 size_t snr_big_ws_bytes(int ntraj, int P) { return (size_t)ntraj * 2 * (size_t)P * P * sizeof(double) + 256; }
 
@@ -398,7 +456,8 @@ bool snr_big_fits(int P) { return snrb_chunk(P) >= 2; }
 
 cudaError_t launch_snr_big(const otvmc_ansatz* a, int ntraj, int ns, const uint64_t* spins, const double* S,
                            const double* obar, const double2* v, const double2* D, double thr, double eps_svd,
-                           double2* delta, double* lam, void* ws, int* status, cudaStream_t s) {
+                           double2* delta, double* lam, void* ws, int* status, cudaStream_t s, bool fp32_pass,
+                           const int16_t* Oint) {
     ProfScope prof_(OTVMC_K_SOLVE, s);
     const int P = (int)a->P, n = a->n, W = (n + 63) / 64;
     const size_t smem = snr_big_smem_bytes(P);
@@ -409,7 +468,8 @@ cudaError_t launch_snr_big(const otvmc_ansatz* a, int ntraj, int ns, const uint6
     const bool tied = a->kind == OTVMC_LJ;
     snr_big_kernel<<<ntraj, SNRB_THREADS, smem, s>>>(n, W, P, ns, spins, tied ? a->full->pairs_d : a->pairs_d,
                                                      tied ? a->grp_off_d : nullptr, tied ? a->grp_pair_d : nullptr,
-                                                     S, obar, v, D, thr, eps_svd, Aws, Xws, delta, lam, status);
+                                                     S, obar, v, D, thr, eps_svd, Aws, Xws, delta, lam, status,
+                                                     fp32_pass ? 1 : 0, Oint);
     count_launch();
     return cudaGetLastError();
 }
