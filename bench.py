@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-equal-error", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shape")
     ap.add_argument("--snr-full-size", action="store_true",
-                    help="also time the SNR regulariser at P = 2080 on 8 trajectories (about two minutes)")
+                    help="time the SNR regulariser at P = 2080 on 8 trajectories instead of 2")
     return ap.parse_args()
 
 
@@ -744,10 +744,11 @@ def main():
                                                     reg=abi.OTVMC_REG_SNR),
               "ring160_ljph1_snr": jastrow_workload("ring160_ljph1", stream, abi.OTVMC_PREC_MIXED, steps=2, warmup=1,
                                                     reg=abi.OTVMC_REG_SNR)}
-        if args.snr_full_size:
-            # the SNR filter at the benchmark's P = 2080 (O(P^3) FP64 per trajectory): 8 trajectories
-            jw["chain64_jastrow_snr"] = jastrow_workload("chain64_jastrow", stream, abi.OTVMC_PREC_MIXED, steps=1,
-                                                         warmup=0, reg=abi.OTVMC_REG_SNR, ntraj=8)
+        # the SNR filter at the benchmark's P = 2080 (O(P^3) FP64 per trajectory, one CTA each): 2
+        # trajectories by default (about a minute), 8 with --snr-full-size
+        jw["chain64_jastrow_snr"] = jastrow_workload("chain64_jastrow", stream, abi.OTVMC_PREC_MIXED, steps=1,
+                                                     warmup=0, reg=abi.OTVMC_REG_SNR,
+                                                     ntraj=8 if args.snr_full_size else 2)
 
     eq = None
     if not args.no_equal_error and world == 1:
