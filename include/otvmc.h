@@ -348,7 +348,9 @@ OTVMC_API otvmc_status otvmc_ensemble(const double* moments_h, int ntraj, int n_
  * [ntraj][ns][W] are the state (in/out; start chains with otvmc_init_chains).
  * moments_d (may be NULL when measure_every = 0): [n_meas][ntraj][9] with one row per
  * measured step (steps i with i % measure_every == 0, from the predictor samples at
- * theta_i) plus, if measure_final, one row at the final time.  Synchronises and returns
+ * theta_i) plus, if measure_final, one row at the final time.  With OTVMC_REG_SNR the solve is
+ * otvmc_solve_snr's filter; on the mixed path its pass over the samples (beyond P = 96) projects
+ * in FP32 (the variances that set the filter to about 1e-6 relative).  Synchronises and returns
  * the device status at the end.  work_bytes >= otvmc_run_workspace_bytes(...). */
 typedef struct otvmc_run_desc {
     int ntraj;
