@@ -568,12 +568,6 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     __shared__ int pivots_ok;
     __shared__ __align__(16) float fscr[4 * TB];  // factor32's broadcast buffers
     const DiagTiles T{A, X11, X21, X22};
-    // entry (i, c) of the inverse (zero above the diagonal and in the upper-right quarter)
-    auto xat = [&](int i, int c) -> float {
-        if (c > i) return 0.f;
-        if (i < HB) return X11[i * DSX + c];
-        return c < HB ? X21[(i - HB) * DSX + c] : X22[(i - HB) * DSX + c - HB];
-    };
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nb = min(NB, P - jb);
     float* yt = yv + (size_t)t * 2 * P;
@@ -597,7 +591,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
             yt[P + k] = (float)d.y * sc;
         }
     // the lower block (with the diagonal), identity padding beyond nb; lanes along rows i.
-    // Loads are issued in batches of 16 per thread before any of them is used.
+    // Loads are issued in batches of 32 per thread before any of them is used.
     {
         const float* Gt = G + (size_t)t * P * P;
         const float inv_ns = 1.0f / (float)ns;
@@ -605,10 +599,10 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         if (jb == 0 && tid < NB) obs[tid] = tid < nb ? (float)obar[(size_t)t * P + tid] : 0.f;
         __syncthreads();
 #pragma unroll 1
-        for (int base = 0; base < NB * NB; base += 16 * DIAG_THREADS) {
-            float v[16];
+        for (int base = 0; base < NB * NB; base += 32 * DIAG_THREADS) {
+            float v[32];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < 32; ++q) {
                 const int e = base + tid + DIAG_THREADS * q, c = e >> 7, i = e & (NB - 1);
                 float x = 0.f;
                 if (i < nb && c < nb && c <= i)
@@ -616,7 +610,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
                 v[q] = x;
             }
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < 32; ++q) {
                 const int e = base + tid + DIAG_THREADS * q, c = e >> 7, i = e & (NB - 1);
                 float x = i == c ? 1.f : 0.f;
                 if (i < nb && c < nb && c <= i) {
@@ -673,9 +667,11 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
         const int i = e >> 4, c8 = e & 15;
         if (i >= nb || c8 * 8 > i) continue;
         const int nv = nb - c8 * 8;
-        float v[8];
+        const float4 q0 = ld4(A + i * DSD + c8 * 8), q1 = ld4(A + i * DSD + c8 * 8 + 4);
+        float v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = c8 * 8 + u <= i ? A[i * DSD + c8 * 8 + u] : 0.f;
+        for (int u = 0; u < 8; ++u)
+            if (c8 * 8 + u > i) v[u] = 0.f;
         store_L8(Lft, Lbt, lay, LD, jb + i, jb + c8 * 8, v, nv);
     }
     // L_dd^-1 in FP32 and as two FP16 pieces in the operand-box layout of the panel kernel.  The
@@ -688,11 +684,19 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(int t0, int P, 
     int big = 0;
     for (int e = tid; e < NB * (NB / 8); e += blockDim.x) {
         const int i = e >> 4, c8 = e & 15;
-        float v[8];
+        // the eight entries from the quarter that holds them (X12 = 0)
+        const float* src = i < HB ? (c8 < HB / 8 ? X11 + i * DSX + 8 * c8 : nullptr)
+                                  : (c8 < HB / 8 ? X21 + (i - HB) * DSX + 8 * c8 : X22 + (i - HB) * DSX + 8 * c8 - HB);
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+        if (src) {
+            q0 = ld4(src);
+            q1 = ld4(src + 4);
+        }
+        float v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int c = 8 * c8 + u;
-            v[u] = (i < nb && c < nb) ? xat(i, c) : 0.f;
+            if (!(i < nb && c < nb && c <= i)) v[u] = 0.f;
             big |= !(fabsf(v[u]) < 16384.f);
         }
         *reinterpret_cast<float4*>(Dv + (size_t)i * NB + 8 * c8) = make_float4(v[0], v[1], v[2], v[3]);
