@@ -209,6 +209,37 @@ def test_metropolis_samples_psi_squared():
     assert acc.mean() > 0
 
 
+def test_metropolis_samples_rbm_psi_squared():
+    """The RBM branch of the proposal ratios (log 2cosh differences of the hidden angles):
+    chains of a complex RBM (4 sites, 3 hidden units) visit the 16 configurations with the
+    frequencies |psi|^2 / Z computed by enumeration."""
+    n, m = 4, 3
+    ans = RBM(n, m)
+    th = _theta(ans, 29, 0.4)
+    sig0 = philox.initial_spins(7, 0, 4000, n)
+    sig, acc = tvmc.metropolis(ans, th, sig0, 7, 0, 0, n_sweep=30)
+    idx = ((sig > 0).astype(int) << np.arange(n)).sum(axis=1)
+    counts = np.bincount(idx, minlength=2 ** n)
+    p = tvmc.exact_weights(ans, th, tvmc.all_configs(n))
+    assert p.max() / p.min() > 1.5  # not the uniform distribution
+    chi2 = scipy.stats.chisquare(counts, p * counts.sum())
+    assert chi2.pvalue > 1e-3
+    assert acc.mean() > 0
+
+
+def test_ensemble_moments_and_standard_error_closed_form():
+    """Eq. 3 averages on hand-made trajectories: M the mean, C = <q> - M M^T, and dM the sample
+    standard deviation (ddof 1) over sqrt(N_T); for q = m m^T (product states) C is the
+    population covariance of the m's."""
+    m = np.array([[1.0, 0.0, 0.5], [-1.0, 0.0, 0.5], [1.0, 0.0, -0.5], [-1.0, 0.0, -0.5]])
+    q = np.einsum("ta,tb->tab", m, m)
+    M, C, dM = ensemble(m, q)
+    assert np.allclose(M, 0.0)
+    assert np.allclose(dM, [np.sqrt(4.0 / 3.0) / 2.0, 0.0, np.sqrt(1.0 / 3.0) / 2.0])
+    assert np.allclose(C, np.cov(m.T, bias=True))
+    assert np.allclose(np.diag(C), [1.0, 0.0, 0.25])
+
+
 def test_metropolis_chain_is_deterministic_and_counter_based():
     ans = Jastrow(6)
     th = _theta(ans, 2, 0.2)
