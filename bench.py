@@ -714,10 +714,30 @@ def main():
             torch.cuda.synchronize()
             per.append(e0.elapsed_time(e1))
         med = statistics.median(per)
+        # FP64 roofline of this path: its dominant work, per evaluation, is the S build
+        # (ns P (P + 1) multiply-adds) and the Cholesky (P^3 / 3), against the FP64 rate that a
+        # library DGEMM (cuBLAS through torch, 8192^3) reaches on this GPU
+        fl = 2 * (2.0 * ns * P * (P + 1) / 2 + P ** 3 / 3.0)   # flops per trajectory-step
+        a64 = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+        b64 = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+        torch.matmul(a64, b64)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(3):
+            torch.matmul(a64, b64)
+        g1.record()
+        torch.cuda.synchronize()
+        dgemm = 3 * 2.0 * 8192 ** 3 / (g0.elapsed_time(g1) / 1000.0) / 1e12
+        del a64, b64
+        ach = fl * Tf / (med / 1000.0) / 1e12
         fp64 = {"value": Tf / (med / 1000.0), "unit": METRIC, "ms_per_step_median": med,
                 "ms_per_step_min": min(per), "ms_per_step_max": max(per), "steps": n_fp64, "warmup": 1,
                 "sample": f"{Tf} trajectories x {n_fp64} steps (CUDA events, median) after 1 warm-up step, "
-                          "same workload, FP64 O / S / Cholesky"}
+                          "same workload, FP64 O / S / Cholesky",
+                "roofline": {"bound": "fp64", "achieved": ach, "peak": dgemm, "unit": "TFLOP/s", "frac": ach / dgemm,
+                             "peak_kind": "cuBLAS DGEMM 8192^3 through torch, measured in this run",
+                             "work": "S build ns P(P+1) + Cholesky P^3/3 multiply-adds per evaluation"}}
         del wf
 
     rbm = None
