@@ -147,7 +147,7 @@ def run_desc(w, ntraj, traj0, step0, n_steps, precision, seed, reg=None):
                        measure_every=1, measure_final=0, use_graph=0)
 
 
-def rbm_path(stream, fp64_value, peaks_):
+def rbm_path(stream, fp64_value, peaks_, autotune=True):
     """The mixed batched RBM path on the chain64_rbm shape (N = 64, M = 128 hidden units,
     P = 8384 > ns: the T path), on a reduced batch that fits beside the main run: 16
     trajectories at ns = 2048 (the smallest of the workload's sample counts), hidden weights
@@ -176,15 +176,23 @@ def rbm_path(stream, fp64_value, peaks_):
                            scheme=abi.OTVMC_MIDPOINT, precision=abi.OTVMC_PREC_MIXED, reg=abi.OTVMC_REG_SHIFT,
                            eps=w.eps, snr_thresh=4.0, seed=seed, measure_every=0, measure_final=0, use_graph=0)
 
-    def measure(mode):
+    shape = {}
+
+    def measure(mode, tune):
         check(abi.otvmc_ansatz_set_rbm_t_build(ans.handle, mode))
         theta = torch.from_numpy(th0.view(np.float64).copy()).cuda().reshape(T, P, 2)
         spins = torch.zeros((T, ns, 1), dtype=torch.int64, device="cuda")
         check(abi.otvmc_init_chains(ans.handle, T, 0, ns, seed, spins, stream))
         nb = abi.otvmc_run_workspace_bytes(ans.handle, desc(0))
-        work = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+        nbt = abi.otvmc_autotune_workspace_bytes(ans.handle, desc(0)) if tune else 0
+        work = torch.zeros(max(nb, nbt), dtype=torch.uint8, device="cuda")
         check(abi.otvmc_run_trajectories(ans.handle, desc(0), theta, spins, None, work, nb, stream))
         torch.cuda.synchronize()
+        if tune:
+            st, pipes, groups, tms = abi.otvmc_autotune_run(ans.handle, desc(0), theta, spins, work, nbt, stream)
+            check(st)
+            shape.update({"source": "otvmc_autotune_run", "sub_batches": pipes,
+                          "solver_groups": groups if groups else "built-in rule", "tuning_step_ms": tms})
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(steps):
@@ -201,8 +209,9 @@ def rbm_path(stream, fp64_value, peaks_):
         del work
         return value, {k: v[0] for k, v in prof.items()}, nb
 
-    v_f, st_f, nb_f = measure(abi.OTVMC_RBM_T_FACTORED)
-    v_m, st_m, nb_m = measure(abi.OTVMC_RBM_T_MATERIALISED)
+    v_f, st_f, nb_f = measure(abi.OTVMC_RBM_T_FACTORED, autotune)
+    abi.otvmc_autotune_clear()
+    v_m, st_m, nb_m = measure(abi.OTVMC_RBM_T_MATERIALISED, False)
     check(abi.otvmc_ansatz_set_rbm_t_build(ans.handle, abi.OTVMC_RBM_T_FACTORED))
     rows, K = 2 * ns, 2 * P
     # BF16 product flops of the split T-GEMM: six piece products of the upper triangle of the
@@ -220,6 +229,7 @@ def rbm_path(stream, fp64_value, peaks_):
             "config": {"workload": w.name, "N": w.n, "M": M, "P": P, "ns": ns, "ntraj": T,
                        "solve": "T path (2 ns)", "steps_timed": steps, "observables": "off",
                        "workspace_bytes": nb_f},
+            "launch_shape": shape or None,
             "stage_ms_per_step": st_f,
             "vs_fp64_jastrow_path": (v_f / fp64_value) if fp64_value else None,
             "materialised_T": {"value": v_m, "unit": METRIC, "workspace_bytes": nb_m, "stage_ms_per_step": st_m,
@@ -742,7 +752,7 @@ def main():
 
     rbm = None
     if not args.no_rbm_path and world == 1:
-        rbm = rbm_path(stream, fp64["value"] if fp64 else None, pk)
+        rbm = rbm_path(stream, fp64["value"] if fp64 else None, pk, not args.no_autotune)
 
     rbm_full = None
     if not args.no_rbm_workloads and world == 1:
