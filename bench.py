@@ -30,10 +30,12 @@ METRIC = "trajectory-steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of the Gram kernel per trajectory-evaluation, from an ncu capture of
-# one launch of 16 trajectories (O with its 17 extra rows: 283.8 MB read, 105.8 MB written),
-# chain64_jastrow shape
-GRAM_DRAM_BYTES_PER_TRAJ = (283.8e6 + 105.8e6) / 16
+# DRAM bytes (read + write) of the Gram kernel per trajectory-evaluation, from an ncu capture
+# (None: not yet captured for the E4M3 operand)
+GRAM_DRAM_BYTES_PER_TRAJ = None
+# nominal dense FP8 / BF16 tensor rate (4.5 / 2.25 PFLOP/s): the FP8 peak is the measured BF16
+# peak times this
+FP8_PER_BF16 = 2.0
 # DRAM bytes (read + write) of the block-column update kernel per trajectory-evaluation, from an
 # ncu capture of all 64 update launches of one evaluation of 32 trajectories (four groups of 8;
 # 30.90 MB per launch with the factor in two FP16 pieces), chain64_jastrow shape
@@ -647,8 +649,8 @@ def main():
     jbs = list(range(0, P, NBK))
     # algorithmic work per trajectory-evaluation of each kernel class
     work = {
-        # useful tensor flops of G = O^T O (upper triangle incl. diagonal)
-        "gram": ("tensor", 2.0 * ns * P * (P + 1) / 2),
+        # useful tensor flops of G = O^T O (upper triangle incl. diagonal), E4M3 operands
+        "gram": ("tensor_fp8", 2.0 * ns * P * (P + 1) / 2),
         # bytes of the Cholesky block-column updates C = A - L L^T: the two FP16 pieces of
         # L[i >= jb, k < jb] read once, the Gram counts of the block column read (FP32) and C
         # written below the diagonal tile (two FP16 pieces).  Its arithmetic intensity, 2 x 128
@@ -672,7 +674,11 @@ def main():
             continue
         ms, cnt = prof[cls]
         total = per_eval * T * evals
-        if bound == "tensor":
+        if bound == "tensor_fp8":
+            bound = "tensor"
+            ach, peak, unit = total / (ms / 1000.0) / 1e12, FP8_PER_BF16 * pk["bf16_tflops_sustained"], "TFLOP/s"
+            kind = f"fp8 = 2 x bf16 sustained ({pk_kind}; nominal dense ratio 4.5 / 2.25)"
+        elif bound == "tensor":
             ach, peak, unit = total / (ms / 1000.0) / 1e12, pk["bf16_tflops_sustained"], "TFLOP/s"
             kind = f"bf16 sustained, {pk_kind}"
         elif bound == "alu":
@@ -792,7 +798,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "mixed: bf16 Gram (exact), fp16-piece tensor-core Cholesky + fp64 refinement, int64/fp64 fields"
+            "dtype": "mixed: e4m3 Gram (exact), fp16-piece tensor-core Cholesky + fp64 refinement, int64/fp64 fields"
             if prec == abi.OTVMC_PREC_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "N": w.n, "P": P, "ns": ns, "ntraj_per_gpu": T, "dt": w.dt,

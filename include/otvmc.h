@@ -244,8 +244,8 @@ OTVMC_API otvmc_status otvmc_local_estimators_noalloc(const otvmc_ansatz* ansatz
  * symmetric.
  *   FP64:  S_d [ntraj][P][P] double (full symmetric) from FP64 centred O.
  *   MIXED: G_d [ntraj][P][P] float, the uncentred Gram counts sum_x O_xi O_xj for j >= i
- *          (row-major upper triangle; lower part unspecified), from a BF16 tcgen05 GEMM
- *          (exact: O = +-1, FP32 accumulation exact below 2^24 samples); obar_d [ntraj][P]
+ *          (row-major upper triangle; lower part unspecified), from an FP8 (E4M3) tcgen05
+ *          GEMM (exact: O = +-1, FP32 accumulation exact below 2^24 samples); obar_d [ntraj][P]
  *          double column means; S = G / ns - obar obar^T exactly.  S_d, if not NULL, is
  *          also filled (full FP64).
  * RBM (FP64 only; theta_d required): O is complex (O_a = s, O_b = tanh gamma, O_W = s tanh
@@ -462,7 +462,7 @@ enum {
     OTVMC_K_REDUCE = 4,  /* site means, v reductions and quantisation */
     OTVMC_K_OBS = 5,     /* observables */
     OTVMC_K_D = 6,       /* D = Cov(O^*, v) and column means */
-    OTVMC_K_OBUILD = 7,  /* O in BF16 / FP64 */
+    OTVMC_K_OBUILD = 7,  /* O in E4M3 / FP64 */
     OTVMC_K_GRAM = 8,    /* Gram G = O^T O (tensor cores); the RBM T of the mixed T path */
     OTVMC_K_SYRK = 9,    /* FP64 S (plain path) */
     OTVMC_K_SOLVE = 10,  /* Cholesky solve (FP64 path) / triangular substitutions and refinement */

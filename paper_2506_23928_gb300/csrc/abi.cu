@@ -129,7 +129,7 @@ EvalBufs carve_est_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
 
 static size_t obuf_bytes(const otvmc_ansatz* a, int T, int ns, int precision) {
     if (precision == OTVMC_PREC_FP64) return (size_t)T * a->P * ns * 8 + 256;
-    return (size_t)T * (a->P + D_XROWS) * ns * 2 + 256;  // BF16 O and its extra rows
+    return (size_t)T * (a->P + D_XROWS) * o_pitch(ns) + 256;  // E4M3 O and its extra rows
 }
 
 static bool valid_ansatz(const otvmc_ansatz* a) { return a != nullptr && a->model != nullptr && a->P > 0; }
@@ -603,10 +603,10 @@ static otvmc_status run_build(const otvmc_ansatz* a, const uint64_t* spins, cons
         // sums stay exact in FP32; else by the integer sums
         const bool dx = b.dx != nullptr && ns <= D_XROWS_MAX_NS;
         if (!dx) CK(launch_D_fixed_jastrow(a, spins, T, ns, b, obar, D, s), "D launch");
-        uint16_t* Ot = (uint16_t*)obuf;
-        CK(launch_obuild_bf16_jastrow(a, spins, T, ns, dx ? b.qv : nullptr, Ot, s), "obuild bf16 launch");
-        CK(launch_gram_tc(T, P, dx ? P + D_XROWS : P, ns, Ot, a->tiles_d, a->ntiles, G, dx ? b.dx : nullptr, status,
-                          s),
+        uint8_t* Ot = (uint8_t*)obuf;
+        CK(launch_obuild_f8_jastrow(a, spins, T, ns, dx ? b.qv : nullptr, Ot, s), "obuild launch");
+        CK(launch_gram_tc(T, P, dx ? P + D_XROWS : P, ns, o_pitch(ns), Ot, a->tiles_d, a->ntiles, G,
+                          dx ? b.dx : nullptr, status, s),
            "gram launch");
         if (dx) CK(launch_D_from_gram(a, T, ns, b, obar, D, s), "D launch");
         if (S) CK(launch_expand_S(T, P, ns, G, obar, S, s), "expand launch");

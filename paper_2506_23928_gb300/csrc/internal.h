@@ -119,11 +119,11 @@ struct EvalBufs {
     float4* rtab;        // RBM only: the mixed kernels' FP32 tables (rbm_tab_bytes)
 };
 
-// Extra rows of the BF16 operand O on the mixed Jastrow path: the quantised centred v as
-// eight balanced base-256 digits of its real part and eight of its imaginary part, then a row
-// of ones; the Gram kernel's tiles reach these columns, so the same tensor-core pass yields
-// sum_x O_k(x) q(x) and sum_x O_k(x), exactly while 128 ns < 2^24.
-constexpr int D_XROWS = 17;
+// Extra rows of the E4M3 operand O on the mixed Jastrow path: the quantised centred v as
+// sixteen balanced base-16 digits (in [-8, 7], exact in E4M3) of its real part and sixteen of
+// its imaginary part, then a row of ones; the Gram kernel's tiles reach these columns, so the
+// same tensor-core pass yields sum_x O_k(x) q(x) and sum_x O_k(x), exactly while 8 ns < 2^24.
+constexpr int D_XROWS = 33;
 constexpr int D_XROWS_MAX_NS = 1 << 17;
 
 size_t eval_bufs_bytes(const otvmc_ansatz* a, int ntraj, int ns);
@@ -153,9 +153,11 @@ cudaError_t launch_vpart(int ntraj, int ns, const double2* v, const EvalBufs& b,
 cudaError_t launch_vquant(int ntraj, int ns, const double2* v, const EvalBufs& b, cudaStream_t s);
 cudaError_t launch_D_fixed_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
                                    const EvalBufs& b, double* obar, double2* D, cudaStream_t s);
-// Ot [ntraj][rows][ns]: rows = P, or P + D_XROWS with the extra rows from qv when qv is given
-cudaError_t launch_obuild_bf16_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
-                                       const long long* qv, uint16_t* Ot, cudaStream_t s);
+// Ot [ntraj][rows][o_pitch(ns)] E4M3 codes, samples from ns to the pitch zero: rows = P, or
+// P + D_XROWS with the extra rows from qv when qv is given
+constexpr int o_pitch(int ns) { return (ns + 15) / 16 * 16; }
+cudaError_t launch_obuild_f8_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
+                                     const long long* qv, uint8_t* Ot, cudaStream_t s);
 cudaError_t launch_obuild_f64_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
                                       const double* obar, double* Oc, cudaStream_t s);
 cudaError_t launch_syrk_f64(int ntraj, int P, int ns, const double* Oc, double* S, cudaStream_t s);
@@ -163,10 +165,11 @@ cudaError_t launch_gemv_D_f64(int ntraj, int P, int ns, const double* Oc, const 
                               double2* D, cudaStream_t s);
 std::vector<int2> gram_tiles(int P);
 std::vector<int2> gram_tiles_x(int P, int PC);
-// G (P x P, upper) from Ot [ntraj][rows][ns]; with X, also X[t][k][c] = sum_x O_k O_{P+c} for
-// k < P, c < rows - P (the extra rows; the tile list must reach column rows - 1).
-cudaError_t launch_gram_tc(int ntraj, int P, int rows, int ns, const uint16_t* Ot, const int2* tiles, int ntiles,
-                           float* G, float* X, int* status, cudaStream_t s);
+// G (P x P, upper) from the E4M3 operand Ot [ntraj][rows][pitch] (pitch a multiple of 16, the
+// samples from ns on zero); with X, also X[t][k][c] = sum_x O_k O_{P+c} for k < P,
+// c < rows - P (the extra rows; the tile list must reach column rows - 1).
+cudaError_t launch_gram_tc(int ntraj, int P, int rows, int ns, int pitch, const uint8_t* Ot, const int2* tiles,
+                           int ntiles, float* G, float* X, int* status, cudaStream_t s);
 cudaError_t launch_D_from_gram(const otvmc_ansatz* a, int ntraj, int ns, const EvalBufs& b, double* obar, double2* D,
                                cudaStream_t s);
 cudaError_t launch_expand_S(int ntraj, int P, int ns, const float* G, const double* obar, double* S,

@@ -2,8 +2,6 @@
 // Jastrow ansatz (definitions after Eq. 8: S = <O^* O> - <O^*><O>, F and N^n likewise;
 // D = -i F dt + sum_n N^n dW_n = Cov(O^*, v) with v = -i dt E_eff + sum_n dW_n B^n).
 // Jastrow log-derivatives are real: O_{a_j} = sigma_j, O_{eta_jk} = sigma_j sigma_k (Eq. 12).
-#include <cuda_bf16.h>
-
 #include "common.cuh"
 
 namespace otvmc {
@@ -107,10 +105,10 @@ __global__ void __launch_bounds__(256) D_final_kernel(int P, int ns, const long 
     D[(size_t)t * P + k] = make_double2(dr, di);
 }
 
-// D and obar from the Gram kernel's side output X[t][k][17] (the sums of O_k against the
-// extra rows): sum_x O_k q = sum_p X[p] 256^p for the real (p < 8) and imaginary (8 <= p < 16)
-// digits, in wrapping 64-bit arithmetic (the true sum fits in 64 bits), and c_k = X[16] =
-// sum_x O_k; then the formula of D_final_kernel with 2 a_r - Q_r = sum_x O_k q_r.
+// D and obar from the Gram kernel's side output X[t][k][33] (the sums of O_k against the
+// extra rows): sum_x O_k q = sum_p X[p] 16^p for the real (p < 16) and imaginary
+// (16 <= p < 32) digits, in wrapping 64-bit arithmetic (the true sum fits in 64 bits), and
+// c_k = X[32] = sum_x O_k; then the formula of D_final_kernel with 2 a_r - Q_r = sum_x O_k q_r.
 __global__ void __launch_bounds__(256) D_from_gram_kernel(int P, int ns, const float* __restrict__ X,
                                                           const double* __restrict__ vinfo,
                                                           const long long* __restrict__ qsum, double* __restrict__ obar,
@@ -121,11 +119,11 @@ __global__ void __launch_bounds__(256) D_from_gram_kernel(int P, int ns, const f
     const float* x = X + ((size_t)t * P + k) * D_XROWS;
     unsigned long long sr = 0ull, si = 0ull;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        sr += (unsigned long long)(long long)x[p] << (8 * p);
-        si += (unsigned long long)(long long)x[8 + p] << (8 * p);
+    for (int p = 0; p < 16; ++p) {
+        sr += (unsigned long long)(long long)x[p] << (4 * p);
+        si += (unsigned long long)(long long)x[16 + p] << (4 * p);
     }
-    const long long c = (long long)x[16];
+    const long long c = (long long)x[32];
     const long long Qr = qsum[2 * t], Qi = qsum[2 * t + 1];
     const double inv = vinfo[4 * t + 2] / ns;
     const double dr = ((double)(long long)sr - (double)c * (double)Qr / ns) * inv;
@@ -159,37 +157,45 @@ cudaError_t launch_D_fixed_jastrow(const otvmc_ansatz* a, const uint64_t* spins,
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ O in BF16 (K-major)
-// Ot[t][k][x] = O_xk as bf16 (+1 = 0x3F80, -1 = 0xBF80), rows k contiguous over samples x,
-// the operand layout of the tensor-core Gram kernel.  One thread = eight consecutive
-// samples: it first transposes their spins into one byte per site (bit s = sigma_j of
-// sample s is +1), then writes each parameter's eight values as one 16-byte store, so a
-// warp writes 512 contiguous bytes per parameter.
-constexpr int OB_SPT = 8;
+// ------------------------------------------------------------------ O in E4M3 (K-major)
+// Ot[t][k][x] = O_xk as an E4M3 code (+1 = 0x38, -1 = 0xB8), rows k contiguous over the samples
+// x with a pitch of o_pitch(ns) bytes (the samples from ns on hold 0), the operand layout of the
+// tensor-core Gram kernel.  One thread = sixteen consecutive samples: it first transposes their
+// spins into a 16-bit mask per site (bit s set: sigma_j of sample s is +1), then writes each
+// parameter's sixteen codes as one 16-byte store, so a warp writes 512 contiguous bytes per
+// parameter.  The parameters are split over gridDim.z blocks (each rebuilds the masks), so
+// that small batches still fill the GPU.
+constexpr int OB_SPT = 16;
+constexpr int OB_THREADS = 128;
 
-__device__ __forceinline__ uint4 bf16_pm1x8(uint32_t e) {
-    // bit s of e set -> +1 (0x3F80), clear -> -1 (0xBF80); sample 2q in the low half of word q
+// Sixteen codes from a 16-bit mask: byte s is 0x38 (+1) if bit s is set, else 0xB8 (-1).  The
+// multiply spreads the four bits of a nibble to bits 0, 8, 16, 24 (the shifted copies do not
+// overlap, so no carries).
+__device__ __forceinline__ uint4 e4m3_pm1x16(uint32_t e) {
     uint32_t w[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        w[q] = 0xBF80BF80u ^ ((e << (15 - 2 * q)) & 0x8000u) ^ ((e << (30 - 2 * q)) & 0x80000000u);
+    for (int q = 0; q < 4; ++q) w[q] = 0xB8B8B8B8u ^ ((((e >> (4 * q)) & 0xFu) * 0x00204081u & 0x01010101u) << 7);
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-__device__ __forceinline__ uint32_t bf16_int_pair(int lo, int hi) {
-    // two small integers (|d| <= 128, exact in BF16) packed as BF16 bits
-    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)lo)) |
-           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)hi)) << 16);
+// E4M3 code of an integer |d| <= 8, from the format's definition: sign bit, exponent biased by
+// 7 (bits 3..6), three fraction bits; d = 2^e (1 + f / 8).
+__device__ __forceinline__ uint32_t e4m3_small_int(int d) {
+    if (d == 0) return 0u;
+    const uint32_t sg = d < 0 ? 0x80u : 0u;
+    const int a = d < 0 ? -d : d;
+    const int e = 31 - __clz(a);
+    return sg | ((uint32_t)(e + 7) << 3) | (uint32_t)((a << (3 - e)) - 8);
 }
 
-__global__ void __launch_bounds__(256) obuild_bf16_jastrow_kernel(int n, int W, int P, int rows, int ns,
-                                                                  const uint64_t* __restrict__ spins,
-                                                                  const int* __restrict__ pairs,
-                                                                  const long long* __restrict__ qv,
-                                                                  uint16_t* __restrict__ Ot) {
-    extern __shared__ uint8_t msk[];  // [n][256]: site masks of each thread's samples
+__global__ void __launch_bounds__(OB_THREADS) obuild_f8_jastrow_kernel(int n, int W, int P, int rows, int ns,
+                                                                       int pitch, const uint64_t* __restrict__ spins,
+                                                                       const int* __restrict__ pairs,
+                                                                       const long long* __restrict__ qv,
+                                                                       uint8_t* __restrict__ Ot) {
+    extern __shared__ uint16_t msk[];  // [n][OB_THREADS]: site masks of each thread's samples
     const int t = blockIdx.y, tid = threadIdx.x;
-    const int x0 = (blockIdx.x * blockDim.x + tid) * OB_SPT;
+    const int x0 = (blockIdx.x * OB_THREADS + tid) * OB_SPT;
     for (int w = 0; w < W; ++w) {
         uint64_t wd[OB_SPT];
 #pragma unroll
@@ -199,72 +205,77 @@ __global__ void __launch_bounds__(256) obuild_bf16_jastrow_kernel(int n, int W, 
             uint32_t m = 0;
 #pragma unroll
             for (int q = 0; q < OB_SPT; ++q) m |= (uint32_t)((wd[q] >> b) & 1ull) << q;
-            msk[(64 * w + b) * blockDim.x + tid] = (uint8_t)m;
+            msk[(64 * w + b) * OB_THREADS + tid] = (uint16_t)m;
         }
     }
     __syncthreads();
-    if (x0 >= ns) return;
-    uint16_t* base = Ot + (size_t)t * rows * ns + x0;
-    const bool vec = (ns % OB_SPT) == 0;  // rows start on 16-byte boundaries and hold whole groups
-    for (int k = 0; k < P; ++k) {
+    if (x0 >= pitch) return;  // x0 < pitch = o_pitch(ns) implies x0 < ns
+    // byte masks of the valid samples (all ones except in the last group of a ragged ns)
+    const int nv = min(OB_SPT, ns - x0);
+    uint32_t vm[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = min(4, max(0, nv - 4 * q));
+        vm[q] = c >= 4 ? 0xFFFFFFFFu : ((1u << (8 * c)) - 1u);
+    }
+    uint8_t* base = Ot + (size_t)t * rows * pitch + x0;
+    const int k0 = (int)(((long long)P * blockIdx.z) / gridDim.z);
+    const int k1 = (int)(((long long)P * (blockIdx.z + 1)) / gridDim.z);
+    for (int k = k0; k < k1; ++k) {
         uint32_t e;
         if (k < n) {
-            e = msk[k * blockDim.x + tid];
+            e = msk[k * OB_THREADS + tid];
         } else {
             const int j = __ldg(pairs + 2 * (k - n)), l = __ldg(pairs + 2 * (k - n) + 1);
-            e = ~(uint32_t)(msk[j * blockDim.x + tid] ^ msk[l * blockDim.x + tid]) & 0xFFu;
+            e = ~(uint32_t)(msk[j * OB_THREADS + tid] ^ msk[l * OB_THREADS + tid]) & 0xFFFFu;
         }
-        const uint4 v = bf16_pm1x8(e);
-        uint16_t* dst = base + (size_t)k * ns;
-        if (vec) {
-            *reinterpret_cast<uint4*>(dst) = v;
-        } else {
-            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int q = 0; q < OB_SPT; ++q)
-                if (x0 + q < ns) dst[q] = (uint16_t)(wv[q >> 1] >> (16 * (q & 1)));
-        }
+        const uint4 v = e4m3_pm1x16(e);
+        *reinterpret_cast<uint4*>(base + (size_t)k * pitch) = make_uint4(v.x & vm[0], v.y & vm[1], v.z & vm[2],
+                                                                         v.w & vm[3]);
     }
-    if (qv == nullptr) return;
-    // extra rows P .. P + 16: the balanced base-256 digits d_p in [-128, 127] of q (real part,
-    // then imaginary part; q = sum_p d_p 256^p), then ones (ns is a multiple of 8 here)
+    if (qv == nullptr || blockIdx.z != gridDim.z - 1) return;
+    // extra rows P .. P + 32: the balanced base-16 digits d_p in [-8, 7] of q (real part, then
+    // imaginary part; q = sum_p d_p 16^p), then ones; 0 for the samples from ns on
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
         long long r[OB_SPT];
 #pragma unroll
         for (int q = 0; q < OB_SPT; ++q) r[q] = (x0 + q < ns) ? qv[((size_t)t * ns + x0 + q) * 2 + h] : 0ll;
 #pragma unroll 1
-        for (int p = 0; p < 8; ++p) {
-            int d[OB_SPT];
+        for (int p = 0; p < 16; ++p) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int q = 0; q < OB_SPT; ++q) {
-                d[q] = (int)((r[q] & 0xFF) ^ 0x80) - 0x80;
-                r[q] = (r[q] - d[q]) >> 8;  // exact: r - d is a multiple of 256
+                const int d = (int)((r[q] & 0xF) ^ 0x8) - 0x8;
+                r[q] = (r[q] - d) >> 4;  // exact: r - d is a multiple of 16
+                w[q >> 2] |= e4m3_small_int(d) << (8 * (q & 3));
             }
-            *reinterpret_cast<uint4*>(base + (size_t)(P + 8 * h + p) * ns) =
-                make_uint4(bf16_int_pair(d[0], d[1]), bf16_int_pair(d[2], d[3]), bf16_int_pair(d[4], d[5]),
-                           bf16_int_pair(d[6], d[7]));
+            *reinterpret_cast<uint4*>(base + (size_t)(P + 16 * h + p) * pitch) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
-    *reinterpret_cast<uint4*>(base + (size_t)(P + 16) * ns) = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u,
-                                                                          0x3F803F80u);
+    *reinterpret_cast<uint4*>(base + (size_t)(P + 32) * pitch) =
+        make_uint4(0x38383838u & vm[0], 0x38383838u & vm[1], 0x38383838u & vm[2], 0x38383838u & vm[3]);
 }
 
-cudaError_t launch_obuild_bf16_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
-                                       const long long* qv, uint16_t* Ot, cudaStream_t s) {
+cudaError_t launch_obuild_f8_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns,
+                                     const long long* qv, uint8_t* Ot, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_OBUILD, s);
     const int n = a->n, W = (n + 63) / 64, P = (int)a->P;
-    if (qv != nullptr && ns % OB_SPT != 0) return cudaErrorInvalidValue;
+    const int pitch = o_pitch(ns);
     const int rows = qv != nullptr ? P + D_XROWS : P;
-    const int per_block = 256 * OB_SPT;
-    dim3 grid((ns + per_block - 1) / per_block, ntraj);
-    const size_t smem = (size_t)n * 256;
+    const int per_block = OB_THREADS * OB_SPT;
+    const int gx = (pitch + per_block - 1) / per_block;
+    // parameter ranges: about eight blocks per SM over the batch, each range >= 64 parameters
+    int kz = (8 * 152 + gx * ntraj - 1) / (gx * ntraj);
+    kz = max(1, min(kz, P / 64));
+    dim3 grid(gx, ntraj, kz);
+    const size_t smem = (size_t)n * OB_THREADS * sizeof(uint16_t);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(obuild_bf16_jastrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(obuild_f8_jastrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    obuild_bf16_jastrow_kernel<<<grid, 256, smem, s>>>(n, W, P, rows, ns, spins, a->pairs_d, qv, Ot);
+    obuild_f8_jastrow_kernel<<<grid, OB_THREADS, smem, s>>>(n, W, P, rows, ns, pitch, spins, a->pairs_d, qv, Ot);
     count_launch();
     return cudaGetLastError();
 }

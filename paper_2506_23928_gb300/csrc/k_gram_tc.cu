@@ -2,15 +2,17 @@
 // (tcgen05, sm_103a): the contraction behind the quantum geometric tensor
 // S = <O^* O> - <O^*><O> (definitions after Eq. 8), S = G / ns - obar obar^T.
 //
-// For the Jastrow ansatz O = +-1 is exact in BF16 and FP32 accumulation of up to 2^24
-// samples is exact, so G (and with the FP64 centring, S) is exact.
+// For the Jastrow ansatz O = +-1 is exact in E4M3, the operands are FP8 (kind::f8f6f4, twice
+// the BF16 rate, half the bytes) and FP32 accumulation of integer sums below 2^24 is exact, so
+// G (and with the FP64 centring, S) is exact.  The same kernel in BF16 forms the Gram of the
+// three-piece split operands of the RBM path.
 //
 // One CTA computes one 128 x 256 tile of the upper triangle of G for one trajectory:
-//   warp 0      TMA producer: three 128-row boxes (A rows i, B rows j, j+128) of 64 samples
+//   warp 0      TMA producer: three 128-row boxes (A rows i, B rows j, j+128) of 128 bytes
 //               per stage into a 2-stage ring, 128-byte swizzled, completing on mbarriers (two
 //               CTAs per SM, so that one CTA's epilogue overlaps the other's MMAs);
 //   warp 1      allocates 256 TMEM columns; one lane issues tcgen05.mma (M=128, N=256,
-//               K=16, BF16 in, FP32 accumulate in TMEM) and commits each stage back;
+//               K = 32 E4M3 or 16 BF16, FP32 accumulate in TMEM) and commits each stage back;
 //   warps 2..5  epilogue: tcgen05.ld of their 32 TMEM lanes, FP32 stores of the j >= i part;
 //               operand rows from P on (the digits of the quantised v and a row of ones, on the
 //               mixed Jastrow path) give the columns of a side output X instead.
@@ -55,6 +57,9 @@ __device__ __forceinline__ int2 tile_of(int q, int P) {
     return make_int2(MT, NT);
 }
 
+// F8: operands in E4M3 (kind::f8f6f4, 128 samples per 128-byte stage row, K = 32 per MMA);
+// else BF16 (kind::f16, 64 samples per row, K = 16).  The stage layout in bytes is the same.
+template <bool F8>
 __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int P, int ns,
                                                           int kpad, int npairs, const int2* __restrict__ tiles,
                                                           float* __restrict__ G, float* __restrict__ X, int nx,
@@ -73,7 +78,8 @@ __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__
     const int t = blockIdx.y;
     const int2 tl = tiles ? tiles[blockIdx.x] : tile_of(blockIdx.x, P);
     const int i0 = tl.x * BM, j0 = tl.y * BN;
-    const int nks = (ns + BK - 1) / BK;  // k slices of one piece
+    constexpr int BKE = F8 ? 2 * BK : BK;  // samples per stage
+    const int nks = (ns + BKE - 1) / BKE;  // k slices of one piece
     const int nk = nks * npairs;
 
     if (threadIdx.x == 0) {
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__
                 }
                 mbar_expect_tx(&full[s], STAGE_BYTES);
                 const int pr = kb / nks, kk = kb - pr * nks;
-                const int ka = c_pair_a[pr] * kpad + kk * BK, kbx = c_pair_b[pr] * kpad + kk * BK;
+                const int ka = c_pair_a[pr] * kpad + kk * BKE, kbx = c_pair_b[pr] * kpad + kk * BKE;
                 tma_load_3d(sA + s * A_BYTES, &tmap, &full[s], ka, i0, t);
                 tma_load_3d(sB + s * B_BYTES, &tmap, &full[s], kbx, j0, t);
                 tma_load_3d(sB + s * B_BYTES + BOX_BYTES, &tmap, &full[s], kbx, j0 + 128, t);
@@ -129,8 +135,14 @@ __global__ void __launch_bounds__(192, 2) gram_tc_kernel(const __grid_constant__
                 fence_after();
                 const uint32_t a0 = su32(sA + s * A_BYTES), b0 = su32(sB + s * B_BYTES);
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k)
-                    umma(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc_bf16(BM, BN), (kb > 0 || k > 0) ? 1u : 0u);
+                for (int k = 0; k < BK / 16; ++k) {  // 32 bytes of each row per instruction
+                    if (F8)
+                        umma_f8(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc_e4m3(BM, BN),
+                                (kb > 0 || k > 0) ? 1u : 0u);
+                    else
+                        umma(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc_bf16(BM, BN),
+                             (kb > 0 || k > 0) ? 1u : 0u);
+                }
                 umma_commit(&empty[s]);
             }
             umma_commit(done);
@@ -208,26 +220,27 @@ std::vector<int2> gram_tiles_x(int P, int PC) {
     return v;
 }
 
-cudaError_t launch_gram_tc(int ntraj, int P, int rows, int ns, const uint16_t* Ot, const int2* tiles, int ntiles,
-                           float* G, float* X, int* status, cudaStream_t s) {
+cudaError_t launch_gram_tc(int ntraj, int P, int rows, int ns, int pitch, const uint8_t* Ot, const int2* tiles,
+                           int ntiles, float* G, float* X, int* status, cudaStream_t s) {
     ProfScope prof_(OTVMC_K_GRAM, s);
-    if (rows < P || (X != nullptr && rows == P)) return cudaErrorInvalidValue;
+    if (rows < P || (X != nullptr && rows == P) || pitch < ns || pitch % 16 != 0) return cudaErrorInvalidValue;
     auto encode = tc::get_encode();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)ns, (cuuint64_t)rows, (cuuint64_t)ntraj};
-    const cuuint64_t strides[2] = {(cuuint64_t)ns * 2, (cuuint64_t)rows * ns * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)tc::BK, 128u, 1u};
+    const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)rows, (cuuint64_t)ntraj};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)rows * pitch};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * tc::BK), 128u, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Ot, dims, strides, box, estr,
+    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void*)Ot, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(tc::gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tc::gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid(ntiles, ntraj);
-    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, P, ns, ns, 1, tiles, G, X, X ? rows - P : 0, status);
+    tc::gram_tc_kernel<true><<<grid, 192, tc::SMEM_BYTES, s>>>(map, P, pitch, pitch, 1, tiles, G, X,
+                                                                X ? rows - P : 0, status);
     count_launch();
     return cudaGetLastError();
 }
@@ -250,12 +263,12 @@ cudaError_t launch_gram_split(int ntraj, int rows, int K, int kpad, const uint16
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(tc::gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tc::gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int ntiles = (int)gram_tiles(rows).size();
     dim3 grid(ntiles, ntraj);
-    tc::gram_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(map, rows, kpad, kpad, 6, nullptr, G, nullptr, 0, status);
+    tc::gram_tc_kernel<false><<<grid, 192, tc::SMEM_BYTES, s>>>(map, rows, kpad, kpad, 6, nullptr, G, nullptr, 0, status);
     count_launch();
     return cudaGetLastError();
 }

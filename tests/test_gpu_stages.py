@@ -148,7 +148,7 @@ def test_build_S_F_many_tiles(precision):
 @pytest.mark.parametrize("n,ns", [(22, 136), (22, 4096), (64, 4096)])
 def test_D_from_gram_pass(n, ns):
     """On the mixed path D and obar come out of the Gram kernel: the quantised centred v enters as
-    extra rows of O (balanced base-256 digits, exact in BF16, digit sums exact in FP32) and a row
+    extra rows of O (balanced base-16 digits, exact in E4M3, digit sums exact in FP32) and a row
     of ones.  P = 253 needs one more column tile for those rows, P = 2080 has room in its last
     tile.  obar equals the FP64 path's (exact counts) bit for bit, D agrees with the FP64 path's
     GEMV to rounding (a digit lost or misplaced would show at 1e-10 or above), and G stays the
@@ -166,6 +166,34 @@ def test_D_from_gram_pass(n, ns):
         assert rel_err(D_m[t], D_f[t]) < 1e-13
     O = np.concatenate([sig[0].astype(np.float64), np.stack([sig[0][:, j] * sig[0][:, k] for j in range(n)
                                                              for k in range(j + 1, n)], axis=1)], axis=1)
+    iu = np.triu_indices(c.P)
+    assert np.array_equal(G.cpu().numpy()[0][iu], (O.T @ O)[iu])
+
+
+@pytest.mark.parametrize("ns", [1 << 17, 131064])
+def test_gram_accumulation_at_the_largest_sums(ns):
+    """The FP8 Gram pass at its largest sums: ns = 2^17 samples (the most that take D from the
+    Gram pass) and a ragged count just below it.  Site 0 follows the sign of v and site 1 is up
+    in three samples of four, so the digit sums of q against O_0 approach 8 ns = 2^20 and the
+    counts G_00 = ns, G_01 ~ ns / 2 stay large while the products added to them are +-1: a
+    tensor-core accumulation narrower than FP32 would drop units here.  G must equal the
+    exact integer Gram and D the FP64 path's to rounding."""
+    n = 6
+    c = Case((n,), h=0.7, kappa=0.1, gamma=0.05)
+    g = synth.rng(51)
+    re = np.where(g.random(ns) < 0.5, -1.0, 1.0) * (1.0 + 0.01 * g.random(ns))
+    v = (re + 1j * 0.5 * re)[None, :]
+    sig = synth.random_spins(52, 1, ns, n)
+    sig[0, :, 0] = np.where(re > 0, 1, -1)
+    sig[0, :, 1] = np.where(g.random(ns) < 0.75, 1, -1)
+    sp = torch.from_numpy(synth.pack_spins(sig).view(np.int64)).cuda()
+    _, G, ob_m, D_m = _build(c, MIXED, 1, ns, v, sp, want_S=False)
+    _, _, ob_f, D_f = _build(c, FP64, 1, ns, v, sp)
+    assert torch.equal(ob_m, ob_f)
+    assert rel_err(from_dev_complex(D_m)[0, :, 0], from_dev_complex(D_f)[0, :, 0]) < 1e-13
+    s0 = sig[0].astype(np.float64)
+    O = np.concatenate([s0, np.stack([s0[:, j] * s0[:, k] for j in range(n) for k in range(j + 1, n)], axis=1)],
+                       axis=1)
     iu = np.triu_indices(c.P)
     assert np.array_equal(G.cpu().numpy()[0][iu], (O.T @ O)[iu])
 
