@@ -86,7 +86,7 @@ EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.base_re = c.take<long long>((size_t)T * n);
     b.base_im = c.take<long long>((size_t)T * n);
     b.r = c.take<double2>((size_t)T * ns * n);
-    b.EH = c.take<double2>((size_t)T * ns);
+    b.EH = c.take<double2>((size_t)T * ns * (a->kind == OTVMC_JASTROW ? est_tc_nq(n) : 1));
     b.part_r = c.take<double2>((size_t)T * nblk * n);
     b.part_sr = c.take<double2>((size_t)T * nblk * n);
     b.part_s = c.take<double>((size_t)T * nblk * n);
@@ -103,6 +103,7 @@ EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.part_obs = c.take<double>((size_t)T * (nblk > (size_t)obs_blocks(n, ns) ? nblk : obs_blocks(n, ns)) * 9);
     b.dsum = c.take<long long>((size_t)T * a->P * 3);
     b.dx = a->kind == OTVMC_JASTROW ? c.take<float>((size_t)T * a->P * D_XROWS) : nullptr;
+    b.etc = (a->kind == OTVMC_JASTROW && n <= ETC_MAX_N) ? c.take<char>(est_tc_bytes(T, n)) : nullptr;
     return b;
 }
 
@@ -115,7 +116,7 @@ EvalBufs carve_est_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.base_re = c.take<long long>((size_t)T * n);
     b.base_im = c.take<long long>((size_t)T * n);
     b.r = c.take<double2>((size_t)T * ns * n);
-    b.EH = c.take<double2>((size_t)T * ns);
+    b.EH = c.take<double2>((size_t)T * ns * (a->kind == OTVMC_JASTROW ? est_tc_nq(n) : 1));
     b.part_r = c.take<double2>((size_t)T * nblk * n);
     b.part_sr = c.take<double2>((size_t)T * nblk * n);
     b.part_s = c.take<double>((size_t)T * nblk * n);
@@ -124,6 +125,7 @@ EvalBufs carve_est_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.mean_s = c.take<double>((size_t)T * n);
     b.part_v = c.take<double2>((size_t)T * vblk);
     b.part_vmax = c.take<double>((size_t)T * vblk);
+    b.etc = (a->kind == OTVMC_JASTROW && n <= ETC_MAX_N) ? c.take<char>(est_tc_bytes(T, n)) : nullptr;
     return b;
 }
 
@@ -196,6 +198,7 @@ otvmc_status otvmc_debug_set_wait_limit(uint64_t ns) {
     const unsigned long long v = ns == 0 ? 2000000000ull : (unsigned long long)ns;
     CK(gram_set_wait_limit(v), "set wait limit (Gram kernel)");
     CK(chol_set_wait_limit(v), "set wait limit (Cholesky kernels)");
+    CK(est_tc_set_wait_limit(v), "set wait limit (estimator kernels)");
     return OTVMC_OK;
 }
 
@@ -556,7 +559,7 @@ static otvmc_status run_estimators(const otvmc_ansatz* a, const double2* theta, 
         CK(launch_jastrow_prep(a, theta, T, b, status, s), "prep launch");
         CK(launch_est1_jastrow(a, spins, T, ns, fp32, b, status, s), "est1 launch");
     }
-    CK(launch_site_means(a, T, ns, b, lpl, s), "site means launch");
+    CK(launch_site_means(a, T, ns, fp32, b, lpl, s), "site means launch");
     if (v) CK(launch_est2(a, spins, T, ns, fp32, dW, dt, lpl_e ? lpl_e : lpl, b, Eeff, v, s), "est2 launch");
     return OTVMC_OK;
 }

@@ -90,6 +90,12 @@ inline int obs_blocks(int n, int ns) {
     const int sb = (256 / est_threads_per_sample(n)) * obs_samples_per_thread();
     return (ns + sb - 1) / sb;
 }
+// Tensor-core local estimators (Jastrow, mixed path, N <= ETC_MAX_N): CTAs of ETC_SITES sites
+// by ETC_TILES tiles of 128 samples; E_H in one partial per site block, the per-site sums in
+// one partial per CTA along the samples.
+constexpr int ETC_SITES = 16, ETC_TILES = 4, ETC_MAX_N = 128;
+inline int est_tc_chunks(int ns) { return (ns + 128 * ETC_TILES - 1) / (128 * ETC_TILES); }
+inline int est_tc_nq(int n) { return n <= ETC_MAX_N ? (n + ETC_SITES - 1) / ETC_SITES : 1; }
 constexpr int VRED_BLOCK = 256;  // samples per block of the v reduction
 inline int v_blocks(int ns) { return (ns + VRED_BLOCK - 1) / VRED_BLOCK; }
 
@@ -117,7 +123,10 @@ struct EvalBufs {
     long long* dsum;     // [T][P][3] exact sums behind D and obar
     float* dx;           // Jastrow only: [T][P][D_XROWS] sums of O_k against the extra rows of O
     float4* rtab;        // RBM only: the mixed kernels' FP32 tables (rbm_tab_bytes)
+    char* etc;           // Jastrow, N <= ETC_MAX_N: operand images of the tensor-core estimators
 };
+// EH is [T][ns][est_tc_nq(n)] for the Jastrow ansatz (partials per site block on the
+// tensor-core path, the first entry alone otherwise), [T][ns] for the others.
 
 // Extra rows of the E4M3 operand O on the mixed Jastrow path: the quantised centred v as
 // sixteen balanced base-16 digits (in [-8, 7], exact in E4M3) of its real part and sixteen of
@@ -144,7 +153,7 @@ cudaError_t launch_jastrow_prep(const otvmc_ansatz* a, const double2* theta, int
                                 int* status, cudaStream_t s);
 cudaError_t launch_est1_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
                                 const EvalBufs& b, int* status, cudaStream_t s);
-cudaError_t launch_site_means(const otvmc_ansatz* a, int ntraj, int ns, const EvalBufs& b, double* lpl,
+cudaError_t launch_site_means(const otvmc_ansatz* a, int ntraj, int ns, bool fp32, const EvalBufs& b, double* lpl,
                               cudaStream_t s);
 cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
                         const double* dW, double dt, const double* lpl, const EvalBufs& b, double2* Eeff, double2* v,
@@ -269,6 +278,15 @@ cudaError_t launch_chol_solve(int ntraj, int P, int ns, int precision, double ep
 size_t chol_ws_bytes(int ntraj, int P, int precision);
 // bound of the pipeline waits of the tensor-core kernels of one translation unit (current device)
 cudaError_t gram_set_wait_limit(unsigned long long ns);
+cudaError_t est_tc_set_wait_limit(unsigned long long ns);
+// Tensor-core local estimators (k_est_tc.cu): bytes of b.etc, and the launch (prep + fields,
+// ratios, E_H partials, per-site sums) in place of the SIMT est1 kernel.
+size_t est_tc_bytes(int ntraj, int n);
+cudaError_t launch_est_tc(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const EvalBufs& b,
+                          int* status, cudaStream_t s);
+inline bool est_tc_ok(const otvmc_ansatz* a, bool fp32) {
+    return fp32 && a->kind == OTVMC_JASTROW && a->n <= ETC_MAX_N;
+}
 cudaError_t chol_set_wait_limit(unsigned long long ns);
 // number of trajectory groups of the mixed solver's launches issued by this host thread from now
 // on (0: the built-in rule); returns the previous setting

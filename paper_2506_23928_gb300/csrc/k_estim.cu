@@ -281,6 +281,7 @@ static size_t est1_smem(int n, int W) {
 
 cudaError_t launch_est1_jastrow(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
                                 const EvalBufs& b, int* status, cudaStream_t s) {
+    if (est_tc_ok(a, fp32)) return launch_est_tc(a, spins, ntraj, ns, b, status, s);
     ProfScope prof_(OTVMC_K_EST1, s);
     (void)status;
     const int n = a->n, W = (n + 63) / 64;
@@ -335,11 +336,14 @@ __global__ void site_means_kernel(int n, int nblk, int ns, int nops, const doubl
     }
 }
 
-cudaError_t launch_site_means(const otvmc_ansatz* a, int ntraj, int ns, const EvalBufs& b, double* lpl,
+cudaError_t launch_site_means(const otvmc_ansatz* a, int ntraj, int ns, bool fp32, const EvalBufs& b, double* lpl,
                               cudaStream_t s) {
     ProfScope prof_(OTVMC_K_REDUCE, s);
     const otvmc_model* m = a->model;
-    site_means_kernel<<<ntraj, 256, 0, s>>>(a->n, est_blocks(a->n, ns), ns, m->nops, b.part_r, b.part_sr, b.part_s,
+    // the per-site partials come from the tensor-core estimators (est_tc_chunks) or the SIMT ones
+    site_means_kernel<<<ntraj, 256, 0, s>>>(a->n, est_tc_ok(a, fp32) ? est_tc_chunks(ns) : est_blocks(a->n, ns), ns,
+                                            m->nops,
+                                            b.part_r, b.part_sr, b.part_s,
                                             m->site_d, m->opidx_d, b.mean_r, b.mean_sr, b.mean_s, lpl);
     count_launch();
     return cudaGetLastError();
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(VRED_BLOCK) est2_kernel(
 // sqrt(kappa_j).  Products and runs of eight sites in FP32, the runs added in FP64.
 __global__ void __launch_bounds__(VRED_BLOCK) est2_mixed_kernel(
     int n, int W, int ns, int nops, double dt, const uint64_t* __restrict__ spins, const float2* __restrict__ r,
-    const double2* __restrict__ EH, const double* __restrict__ site, const int* __restrict__ opidx,
+    const double2* __restrict__ EH, int nq, const double* __restrict__ site, const int* __restrict__ opidx,
     const double* __restrict__ lpl, const double* __restrict__ dW, double2* __restrict__ Eeff_out,
     double2* __restrict__ v_out, double2* __restrict__ part_v, double* __restrict__ part_vmax) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -503,7 +507,13 @@ __global__ void __launch_bounds__(VRED_BLOCK) est2_mixed_kernel(
             Ds += ds;
         }
         const double br = c0s + Cs + Ar, bi = Ai;
-        double2 E = EH[(size_t)t * ns + s];
+        // E_H: the partials of the site blocks in order (one partial off the tensor-core path)
+        double2 E = EH[((size_t)t * ns + s) * nq];
+        for (int q = 1; q < nq; ++q) {
+            const double2 e = EH[((size_t)t * ns + s) * nq + q];
+            E.x += e.x;
+            E.y += e.y;
+        }
         E.x += 0.5 * bi;
         E.y -= 0.5 * br;
         v = make_double2(dt * E.y + Ds + Vr, -dt * E.x + Vi);
@@ -537,8 +547,8 @@ cudaError_t launch_est2(const otvmc_ansatz* a, const uint64_t* spins, int ntraj,
     dim3 grid(v_blocks(ns), ntraj);
     if (fp32)
         est2_mixed_kernel<<<grid, VRED_BLOCK, (size_t)4 * n * 4 + 16 + VRED_BLOCK * 24, s>>>(
-            n, W, ns, m->nops, dt, spins, reinterpret_cast<const float2*>(b.r), b.EH, m->site_d, m->opidx_d, lpl, dW,
-            Eeff, v, b.part_v, b.part_vmax);
+            n, W, ns, m->nops, dt, spins, reinterpret_cast<const float2*>(b.r), b.EH,
+            est_tc_ok(a, fp32) ? est_tc_nq(n) : 1, m->site_d, m->opidx_d, lpl, dW, Eeff, v, b.part_v, b.part_vmax);
     else
         est2_kernel<double2><<<grid, VRED_BLOCK, smem, s>>>(n, W, ns, m->nops, dt, spins, b.r, b.EH, m->site_d,
                                                             m->opidx_d, lpl, dW, Eeff, v, b.part_v, b.part_vmax);

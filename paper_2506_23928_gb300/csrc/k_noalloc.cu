@@ -84,7 +84,7 @@ extern "C" otvmc_status otvmc_local_estimators_noalloc(const otvmc_ansatz* a, co
     if (e != cudaSuccess) return cuda_status(e, "local_estimators_noalloc: prep launch");
     e = launch_est1_jastrow(a, spins_d, ntraj, ns, fp32, b, status_d, s);
     if (e != cudaSuccess) return cuda_status(e, "local_estimators_noalloc: est1 launch");
-    e = launch_site_means(a, ntraj, ns, b, lpl, s);
+    e = launch_site_means(a, ntraj, ns, fp32, b, lpl, s);
     if (e != cudaSuccess) return cuda_status(e, "local_estimators_noalloc: site means launch");
     e = launch_est2(a, spins_d, ntraj, ns, fp32, dW_d, dt, lpl, b, (double2*)Eeff_d, (double2*)v_d, s);
     if (e != cudaSuccess) return cuda_status(e, "local_estimators_noalloc: est2 launch");

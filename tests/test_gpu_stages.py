@@ -91,6 +91,23 @@ def test_local_estimators(precision, n, ns):
         assert rel_err(lpl[t, :c.nops], ev["lpl"]) < TOL[precision]
 
 
+@pytest.mark.parametrize("n,ns,scale", [(64, 1100, 0.1), (100, 300, 0.1), (128, 260, 0.05), (64, 700, 0.6),
+                                         (150, 200, 0.05)])
+def test_local_estimators_large_n(n, ns, scale):
+    """The mixed path's estimators at N = 64, 100 and 128 run on the tensor cores (one or two
+    64-site blocks of the contraction, ragged site blocks of 16 and sample tiles of 128); N = 150
+    on the SIMT kernel.  Scale 0.6 makes |Im f_j| several times pi, so that the fixed-point
+    reduction of the phase is exercised.  E_eff, v and <L + L^+> against the oracle."""
+    c = Case((n,), h=0.7, kappa=0.1, gamma=0.05)
+    T, dt = 2, 0.01
+    th, sig, dW, E, v, lpl = _estimators(c, MIXED, T, ns, dt, scale)
+    for t in range(T):
+        ev = tvmc.evaluate(c.omodel, c.oans, th[t], sig[t], tvmc.mc_weights(ns), dW[t], dt, with_S=False)
+        assert rel_err(E[t], ev["E"]) < TOL[MIXED]
+        assert rel_err(v[t], tvmc.local_v(ev, dW[t], dt)) < TOL[MIXED]
+        assert rel_err(lpl[t, :c.nops], ev["lpl"]) < TOL[MIXED]
+
+
 def _build(c, precision, T, ns, v, sp, want_S=True):
     v_d = to_dev_complex(v)
     P = c.P
