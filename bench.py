@@ -30,9 +30,10 @@ METRIC = "trajectory-steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of the Gram kernel per trajectory-evaluation, from an ncu capture
-# (None: not yet captured for the E4M3 operand)
-GRAM_DRAM_BYTES_PER_TRAJ = None
+# DRAM bytes (read + write) of the Gram kernel per trajectory-evaluation, from an ncu capture of
+# one launch of 32 trajectories (E4M3 O with its 33 extra rows: 279.5 MB read, 239.7 MB
+# written), chain64_jastrow shape
+GRAM_DRAM_BYTES_PER_TRAJ = (279.5e6 + 239.7e6) / 32
 # nominal dense FP8 / BF16 tensor rate (4.5 / 2.25 PFLOP/s): the FP8 peak is the measured BF16
 # peak times this
 FP8_PER_BF16 = 2.0
