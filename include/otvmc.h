@@ -202,8 +202,11 @@ OTVMC_API otvmc_status otvmc_sample(const otvmc_ansatz* ansatz, const double* th
  * c-number terms dropped: they cancel in F and N^n), and
  * v(x) = -i dt E_eff(x) + sum_n dW_n B^n(x), so that D = Cov(O^*, v).
  * Outputs (any may be NULL except v_d): Eeff_d [ntraj][ns] double2, v_d [ntraj][ns]
- * double2, lpl_d [ntraj][N_L] double.  precision selects FP64 or FP32 transcendentals
- * (fields are exact fixed-point sums in both). */
+ * double2, lpl_d [ntraj][N_L] double.  FP64: the fields are exact fixed-point sums and the
+ * transcendentals FP64.  MIXED: the imaginary field (the ratio's phase) stays exact in fixed
+ * point, the real and coupling fields carry FP32-level rounding (for the Jastrow ansatz with
+ * N <= 128 they come from a tensor-core product of sigma with FP16 pieces of the couplings
+ * and exact integer digits of the phase), the transcendentals are FP32. */
 OTVMC_API otvmc_status otvmc_local_estimators(const otvmc_ansatz* ansatz, const double* theta_d,
                                     const uint64_t* spins_d, int ntraj, int ns,
                                     const double* dW_d, double dt, int precision,
@@ -220,9 +223,11 @@ OTVMC_API otvmc_status otvmc_local_estimators(const otvmc_ansatz* ansatz, const 
  * that loads the library until the process exits.  Nothing is allocated by this call.
  *   - Batches whose scratch would exceed 32 MiB are rejected with OTVMC_ERR_WORKSPACE before
  *     anything is launched.  The scratch of a batch is about
- *     ntraj * (16 ns (N + 1) + 16 N^2 + 40 N ceil(ns / b)) bytes, b = 8 floor(256 / N32),
- *     N32 = N rounded up to a multiple of 32 (flip ratios, E_H, the fixed-point parameter
- *     tables and the per-block site sums): at N = 64 and 4096 samples, 7 trajectories fit.
+ *     ntraj * (16 ns (N + q) + 16 N^2 + 40 N ceil(ns / b) + 16384 q ceil(N / 64)) bytes,
+ *     b = 8 floor(256 / N32), N32 = N rounded up to a multiple of 32, q = ceil(N / 16) for
+ *     N <= 128, else q = 1 and no last term (flip ratios, E_H in q partials, the fixed-point
+ *     parameter tables, the per-block site sums, the operand images of the tensor-core
+ *     estimators): at N = 64 and 4096 samples, 6 trajectories fit.
  *   - status_d (optional, caller-cleared): device int[2].  Device-side errors are recorded
  *     there as in the workspace status word of the other entry points: word 0 the first error
  *     code (e.g. OTVMC_ERR_RANGE when a parameter field leaves the fixed-point range), word 1
