@@ -205,7 +205,7 @@ OTVMC_API otvmc_status otvmc_sample(const otvmc_ansatz* ansatz, const double* th
  * double2, lpl_d [ntraj][N_L] double.  FP64: the fields are exact fixed-point sums and the
  * transcendentals FP64.  MIXED: the imaginary field (the ratio's phase) stays exact in fixed
  * point, the real and coupling fields carry FP32-level rounding (for the Jastrow ansatz with
- * N <= 128 they come from a tensor-core product of sigma with FP16 pieces of the couplings
+ * 32 <= N <= 128 they come from a tensor-core product of sigma with FP16 pieces of the couplings
  * and exact integer digits of the phase), the transcendentals are FP32. */
 OTVMC_API otvmc_status otvmc_local_estimators(const otvmc_ansatz* ansatz, const double* theta_d,
                                     const uint64_t* spins_d, int ntraj, int ns,

@@ -90,10 +90,12 @@ inline int obs_blocks(int n, int ns) {
     const int sb = (256 / est_threads_per_sample(n)) * obs_samples_per_thread();
     return (ns + sb - 1) / sb;
 }
-// Tensor-core local estimators (Jastrow, mixed path, N <= ETC_MAX_N): CTAs of ETC_SITES sites
+// Tensor-core local estimators (Jastrow, mixed path, ETC_MIN_N <= N <= ETC_MAX_N): CTAs of ETC_SITES sites
 // by ETC_TILES tiles of 128 samples; E_H in one partial per site block, the per-site sums in
 // one partial per CTA along the samples.
-constexpr int ETC_SITES = 16, ETC_TILES = 4, ETC_MAX_N = 128;
+// Below ETC_MIN_N sites the SIMT kernel's N^2 work per sample is smaller than the tensor-core
+// kernel's fixed costs (operand preparation, TMEM allocation, one more launch).
+constexpr int ETC_SITES = 16, ETC_TILES = 4, ETC_MIN_N = 32, ETC_MAX_N = 128;
 inline int est_tc_chunks(int ns) { return (ns + 128 * ETC_TILES - 1) / (128 * ETC_TILES); }
 inline int est_tc_nq(int n) { return n <= ETC_MAX_N ? (n + ETC_SITES - 1) / ETC_SITES : 1; }
 constexpr int VRED_BLOCK = 256;  // samples per block of the v reduction
@@ -285,7 +287,7 @@ size_t est_tc_bytes(int ntraj, int n);
 cudaError_t launch_est_tc(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const EvalBufs& b,
                           int* status, cudaStream_t s);
 inline bool est_tc_ok(const otvmc_ansatz* a, bool fp32) {
-    return fp32 && a->kind == OTVMC_JASTROW && a->n <= ETC_MAX_N;
+    return fp32 && a->kind == OTVMC_JASTROW && a->n >= ETC_MIN_N && a->n <= ETC_MAX_N;
 }
 cudaError_t chol_set_wait_limit(unsigned long long ns);
 // number of trajectory groups of the mixed solver's launches issued by this host thread from now

@@ -1,4 +1,4 @@
-// Local-estimator fields of the Jastrow ansatz on the tensor cores (mixed path, N <= 128).
+// Local-estimator fields of the Jastrow ansatz on the tensor cores (mixed path, 32 <= N <= 128).
 //
 // The flip ratios r_j(x) = psi(x^j) / psi(x) = exp(-2 sigma_j f_j(x)) of the transverse-field
 // term and the diagonal Ising energy (E_H of the effective Hamiltonian, Eq. 5; the ansatz of
