@@ -266,7 +266,11 @@ cudaError_t launch_obuild_f8_jastrow(const otvmc_ansatz* a, const uint64_t* spin
     const int per_block = OB_THREADS * OB_SPT;
     const int gx = (pitch + per_block - 1) / per_block;
     // parameter ranges: about eight blocks per SM over the batch, each range >= 64 parameters
-    int kz = (8 * 152 + gx * ntraj - 1) / (gx * ntraj);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        sms = 152;
+    int kz = (8 * sms + gx * ntraj - 1) / (gx * ntraj);
     kz = max(1, min(kz, P / 64));
     dim3 grid(gx, ntraj, kz);
     const size_t smem = (size_t)n * OB_THREADS * sizeof(uint16_t);
