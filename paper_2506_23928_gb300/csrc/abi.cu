@@ -104,6 +104,7 @@ EvalBufs carve_eval_bufs(Carver& c, const otvmc_ansatz* a, int T, int ns) {
     b.dsum = c.take<long long>((size_t)T * a->P * 3);
     b.dx = a->kind == OTVMC_JASTROW ? c.take<float>((size_t)T * a->P * D_XROWS) : nullptr;
     b.etc = (a->kind == OTVMC_JASTROW && n <= ETC_MAX_N) ? c.take<char>(est_tc_bytes(T, n)) : nullptr;
+    b.otc = (a->kind == OTVMC_JASTROW && n >= OTC_MIN_N && n <= OTC_MAX_N) ? c.take<char>(obs_tc_bytes(T, n)) : nullptr;
     return b;
 }
 
@@ -199,6 +200,7 @@ otvmc_status otvmc_debug_set_wait_limit(uint64_t ns) {
     CK(gram_set_wait_limit(v), "set wait limit (Gram kernel)");
     CK(chol_set_wait_limit(v), "set wait limit (Cholesky kernels)");
     CK(est_tc_set_wait_limit(v), "set wait limit (estimator kernels)");
+    CK(obs_tc_set_wait_limit(v), "set wait limit (observables kernels)");
     return OTVMC_OK;
 }
 
@@ -778,7 +780,7 @@ otvmc_status otvmc_observables(const otvmc_ansatz* a, const double* theta_d, con
         return OTVMC_OK;
     }
     CK(launch_obs_prep(e, th, ntraj, fp32, b, s), "obs prep launch");
-    CK(launch_observables(e, spins_d, ntraj, ns, fp32, b, moments_d, s), "observables launch");
+    CK(launch_observables(e, spins_d, ntraj, ns, fp32, b, moments_d, (int*)work_d, s), "observables launch");
     return OTVMC_OK;
 }
 
@@ -1127,7 +1129,7 @@ static otvmc_status run_eval(const otvmc_ansatz* a, const otvmc_run_desc* d, con
     if (st) return st;
     if (moments_row) {
         CK(launch_obs_prep(e, th, T, fp32, r.eb, s), "obs prep launch");
-        CK(launch_observables(e, spins, T, ns, fp32, r.eb, moments_row, s), "observables launch");
+        CK(launch_observables(e, spins, T, ns, fp32, r.eb, moments_row, status, s), "observables launch");
     }
     if (a->kind == OTVMC_LJ) {
         CK(launch_vquant(T, ns, r.v, r.eb, s), "vquant launch");
@@ -1217,7 +1219,7 @@ static otvmc_status run_steps(const otvmc_ansatz* a, const otvmc_run_desc* d, do
             CK(launch_obs_final(a->n, d->ns, T, r.eb, mrow, s), "observables launch");
         } else {
             CK(launch_obs_prep(e, th, T, fp32, r.eb, s), "obs prep launch");
-            CK(launch_observables(e, spins_d, T, d->ns, fp32, r.eb, mrow, s), "observables launch");
+            CK(launch_observables(e, spins_d, T, d->ns, fp32, r.eb, mrow, status, s), "observables launch");
         }
     }
     return OTVMC_OK;

@@ -98,6 +98,10 @@ inline int obs_blocks(int n, int ns) {
 constexpr int ETC_SITES = 16, ETC_TILES = 4, ETC_MIN_N = 32, ETC_MAX_N = 128;
 inline int est_tc_chunks(int ns) { return (ns + 128 * ETC_TILES - 1) / (128 * ETC_TILES); }
 inline int est_tc_nq(int n) { return n <= ETC_MAX_N ? (n + ETC_SITES - 1) / ETC_SITES : 1; }
+// Tensor-core observables (Jastrow, mixed path, OTC_MIN_N <= N <= OTC_MAX_N): one partial of
+// the nine moments per 512 samples.
+constexpr int OTC_MIN_N = 32, OTC_MAX_N = 64;
+inline int obs_tc_chunks(int ns) { return (ns + 511) / 512; }
 constexpr int VRED_BLOCK = 256;  // samples per block of the v reduction
 inline int v_blocks(int ns) { return (ns + VRED_BLOCK - 1) / VRED_BLOCK; }
 
@@ -126,6 +130,7 @@ struct EvalBufs {
     float* dx;           // Jastrow only: [T][P][D_XROWS] sums of O_k against the extra rows of O
     float4* rtab;        // RBM only: the mixed kernels' FP32 tables (rbm_tab_bytes)
     char* etc;           // Jastrow, N <= ETC_MAX_N: operand images of the tensor-core estimators
+    char* otc;           // Jastrow, OTC_MIN_N <= N <= OTC_MAX_N: operand images of the tensor-core observables
 };
 // EH is [T][ns][est_tc_nq(n)] for the Jastrow ansatz (partials per site block on the
 // tensor-core path, the first entry alone otherwise), [T][ns] for the others.
@@ -201,6 +206,7 @@ cudaError_t launch_sample_rbm_mixed(const otvmc_ansatz* an, const double2* theta
 cudaError_t launch_est_rbm_mixed(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, int ntraj,
                                  int ns, const EvalBufs& b, cudaStream_t s);
 cudaError_t launch_obs_final(int n, int ns, int ntraj, const EvalBufs& b, double* moments, cudaStream_t s);
+cudaError_t launch_obs_final_n(int n, int ns, int ntraj, int nblk, const EvalBufs& b, double* moments, cudaStream_t s);
 size_t rbm_build_bytes(const otvmc_ansatz* a, int ntraj, int ns);
 size_t rbm_solve_bytes(int ntraj, int P);
 cudaError_t launch_rbm_build(const otvmc_ansatz* a, const double2* theta, const uint64_t* spins, const double2* v,
@@ -286,6 +292,15 @@ cudaError_t est_tc_set_wait_limit(unsigned long long ns);
 size_t est_tc_bytes(int ntraj, int n);
 cudaError_t launch_est_tc(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const EvalBufs& b,
                           int* status, cudaStream_t s);
+// Tensor-core observables (k_obs_tc.cu): bytes of b.otc, and the launch (operand preparation,
+// moments, final reduction) in place of observables_kernel + obs_final_kernel.
+size_t obs_tc_bytes(int ntraj, int n);
+cudaError_t obs_tc_set_wait_limit(unsigned long long ns);
+cudaError_t launch_obs_tc(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, const EvalBufs& b,
+                          double* moments, int* status, cudaStream_t s);
+inline bool obs_tc_ok(const otvmc_ansatz* a, bool fp32) {
+    return fp32 && a->kind == OTVMC_JASTROW && a->n >= OTC_MIN_N && a->n <= OTC_MAX_N;
+}
 inline bool est_tc_ok(const otvmc_ansatz* a, bool fp32) {
     return fp32 && a->kind == OTVMC_JASTROW && a->n >= ETC_MIN_N && a->n <= ETC_MAX_N;
 }
@@ -304,6 +319,6 @@ cudaError_t launch_sde(int ntraj, int64_t P, int scheme, int stage, const double
 cudaError_t launch_obs_prep(const otvmc_ansatz* a, const double2* theta, int ntraj, bool fp32,
                             const EvalBufs& b, cudaStream_t s);
 cudaError_t launch_observables(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
-                               const EvalBufs& b, double* moments, cudaStream_t s);
+                               const EvalBufs& b, double* moments, int* status, cudaStream_t s);
 
 }  // namespace otvmc

@@ -799,6 +799,12 @@ __global__ void obs_final_kernel(int n, int ns, int nblk, const double* __restri
     moments[(size_t)t * 9 + i] = out;
 }
 
+cudaError_t launch_obs_final_n(int n, int ns, int ntraj, int nblk, const EvalBufs& b, double* moments, cudaStream_t s) {
+    obs_final_kernel<<<ntraj, 32, 0, s>>>(n, ns, nblk, b.part_obs, moments);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_obs_final(int n, int ns, int ntraj, const EvalBufs& b, double* moments, cudaStream_t s) {
     obs_final_kernel<<<ntraj, 32, 0, s>>>(n, ns, obs_blocks(n, ns), b.part_obs, moments);
     count_launch();
@@ -806,7 +812,8 @@ cudaError_t launch_obs_final(int n, int ns, int ntraj, const EvalBufs& b, double
 }
 
 cudaError_t launch_observables(const otvmc_ansatz* a, const uint64_t* spins, int ntraj, int ns, bool fp32,
-                               const EvalBufs& b, double* moments, cudaStream_t s) {
+                               const EvalBufs& b, double* moments, int* status, cudaStream_t s) {
+    if (obs_tc_ok(a, fp32) && b.otc != nullptr) return launch_obs_tc(a, spins, ntraj, ns, b, moments, status, s);
     ProfScope prof_(OTVMC_K_OBS, s);
     const int n = a->n, W = (n + 63) / 64;
     const int NT = ((n + 31) / 32) * 32, SPP = 256 / NT;

@@ -298,8 +298,10 @@ def test_sde_combine(scheme):
 
 
 @pytest.mark.parametrize("precision", [FP64, MIXED])
-@pytest.mark.parametrize("n,ns", [(10, 400), (3, 33), (40, 64)])
+@pytest.mark.parametrize("n,ns", [(10, 400), (3, 33), (40, 64), (64, 1100), (33, 700)])
 def test_observables(precision, n, ns):
+    """Moments against the oracle; on the mixed path N = 33 ... 64 take the tensor-core kernel
+    (one ragged tile, several tiles and CTAs), the others the SIMT kernel."""
     c = Case((n,), kappa=0.1)
     T = 3
     th, th_d = c.theta(61, T, 0.2)
