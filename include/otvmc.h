@@ -333,7 +333,8 @@ OTVMC_API otvmc_status otvmc_sde_combine(int ntraj, int64_t P, int scheme, int s
  * Per-trajectory moments from the current samples (local estimators, LITF paragraph):
  * m_a = (1/N) sum_j <s^a_j>, q_ab = (1/N^2) sum_{jk} <(s^a_j s^b_k + s^b_k s^a_j)/2>.
  * moments_d: [ntraj][OTVMC_MOMENTS] double in the order m_x m_y m_z q_xx q_yy q_zz q_xy
- * q_xz q_yz. */
+ * q_xz q_yz.  MIXED: FP32 ratios and sums (for the Jastrow ansatz with 32 <= N <= 64 the pair
+ * sums as tensor-core products of FP16 pieces), agreeing with FP64 to about 1e-5 relative. */
 OTVMC_API otvmc_status otvmc_observables(const otvmc_ansatz* ansatz, const double* theta_d,
                                const uint64_t* spins_d, int ntraj, int ns, int precision,
                                double* moments_d, void* work_d, size_t work_bytes,
